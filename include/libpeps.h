@@ -1,0 +1,190 @@
+/*
+ * libpeps -- C ABI of the GB300 implicit-randomized-SVD PEPS contraction.
+ *
+ * The library implements the einsumsvd primitive of arXiv:2006.15234
+ * (Sec. II-C "einsumsvd"; Algorithm 4 "Randomized SVD" applied to an implicit
+ * operator, Sec. IV-A) and the boundary-MPS contraction that drives it
+ * (Algorithm 2 "Boundary MPS", Algorithm 3 zip-up "ApproxApply", two-layer
+ * form of Sec. III-B).
+ *
+ * Conventions shared by every entry point
+ *  - Tensor pointers are DEVICE pointers owned by the caller.  The library
+ *    never allocates, frees or retains device memory: all scratch lives in a
+ *    caller-provided workspace whose size a *_workspace / *_plan call reports.
+ *  - Work is enqueued on the caller's stream (a cudaStream_t passed as void*);
+ *    calls return once the work is enqueued unless stated otherwise.
+ *  - Every call returns a peps_status.  Shapes, dtypes and pointers are checked
+ *    on the host before anything is enqueued; on error nothing is enqueued and
+ *    peps_last_error() (thread-local) describes the failure.  No C++ exception
+ *    crosses the ABI.
+ *  - Layouts are row-major.  PEPS site tensors are [d][left][up][down][right]
+ *    (edge bonds have dimension 1).  Boundary-MPS sites are
+ *    [left][vert][right] with vert = (ket, bra) pair, ket-major.
+ *  - Complex data are interleaved (re, im) pairs of the real type.
+ */
+#ifndef LIBPEPS_H
+#define LIBPEPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t peps_status;
+#define PEPS_OK               0
+#define PEPS_ERR_ARG          1  /* NULL pointer, bad option value            */
+#define PEPS_ERR_SHAPE        2  /* inconsistent tensor shapes                */
+#define PEPS_ERR_UNSUPPORTED  3  /* valid request this build does not handle  */
+#define PEPS_ERR_CUDA         4  /* a CUDA runtime call failed                */
+#define PEPS_ERR_WORKSPACE    5  /* workspace missing, misaligned or too small */
+#define PEPS_ERR_NUMERIC      6  /* non-finite value met on the device        */
+#define PEPS_ERR_TIMEOUT      7  /* a bounded device wait expired             */
+#define PEPS_ERR_CAPTURE      8  /* call not allowed during stream capture    */
+
+/* Name of a status code (static string). */
+const char *peps_status_string(peps_status s);
+/* Detail of the last error raised on this host thread ("" if none). */
+const char *peps_last_error(void);
+/* Library version string. */
+const char *peps_version(void);
+
+/* Element type of every tensor handed to one call. */
+typedef enum {
+  PEPS_R32 = 0,   /* float                          */
+  PEPS_C64 = 1,   /* complex float  (float re, im)  */
+  PEPS_R64 = 2,   /* double                         */
+  PEPS_C128 = 3   /* complex double (double re, im) */
+} peps_dtype;
+
+/* Arithmetic of the implicit products (Algorithm 4's A Q and A^H P).
+ * PLAIN: CUDA-core arithmetic in the data type.
+ * MIXED: tensor-core (tcgen05) contraction GEMMs with FP32 accumulation for
+ *        single-precision data; falls back to PLAIN for double data. */
+typedef enum { PEPS_PREC_PLAIN = 0, PEPS_PREC_MIXED = 1 } peps_precision;
+
+/* Sketch distribution of Algorithm 4's first line: Gaussian (default) or the
+ * paper's uniform draw on [-1, 1]. */
+typedef enum { PEPS_SKETCH_GAUSS = 0, PEPS_SKETCH_UNIFORM = 1 } peps_sketch;
+
+/* Options of one randomized SVD (Algorithm 4) / boundary sweep (Algorithm 2).
+ *  m     truncation rank (boundary bond), >= 1
+ *  p     oversampling: the sketch has l = min(k + p, M, N) columns, >= 0
+ *  q     power iterations (Algorithm 4's loop count), >= 0
+ *  seed  Philox4x64-10 key of every sketch and gauge vector
+ *  sketch, prec  see the enums above
+ *  flags reserved, must be 0 */
+typedef struct {
+  int32_t m, p, q;
+  uint64_t seed;
+  int32_t sketch;
+  int32_t prec;
+  uint32_t flags;
+} peps_rsvd_opts;
+
+/* ------------------------------------------------------------------------
+ * Batched einsumsvd (Algorithm 3's einsumsvd line, Algorithm 4 inside).
+ *
+ * One instance factorises the implicit matrix
+ *   A[(k,t),(x,X,b,e,E)] = sum V[k,t,a,(l,L)] S[a,(u,U),b] K[s,l,u,x,e] conj(Kb[s,L,U,X,E])
+ * with operands
+ *   V   carry           [kL][t][a][Dl*DL]
+ *   S   boundary site   [a][Du*DU][b]
+ *   K   ket site        [d][Dl][Du][Dx][De]
+ *   Kb  bra site        [d][DL][DU][DX][DE]
+ * M = kL*t rows, N = Dx*DX*b*De*DE columns, k = min(m, M, N).  Outputs:
+ *   U      [kL][t][k]            left factor, orthonormal columns (new boundary site)
+ *   W      [k][Dx*DX][b][De*DE]  Sigma V^H divided by sigma_1 (new carry)
+ *   sigma  k doubles             singular values, descending (not divided)
+ *   log_scale  one double        log(sigma_1) (written, not accumulated)
+ * Directions with sigma_c <= 16 l eps64 sigma_1 are returned as zero columns
+ * of U / rows of W.  The phase of each U column is fixed so that <g, u_c> is
+ * real and >= 0 for a Philox vector g (stream tag 1), W compensating.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t kL, t, a, b;
+  int32_t d, Dl, Du, Dx, De;   /* ket site dims */
+  int32_t DL, DU, DX, DE;      /* bra site dims */
+} peps_einsumsvd_shape;
+
+typedef struct {
+  const void *V, *S, *ket, *bra;
+  void *U, *W;
+  double *sigma;
+  double *log_scale;
+} peps_einsumsvd_io;
+
+typedef struct peps_plan peps_plan;
+
+/* Plan `batch` independent instances.  shapes and instance_ids are HOST
+ * arrays of length batch; instance_ids (Philox stream id of each instance's
+ * sketch) may be NULL, meaning 0..batch-1.  *workspace_bytes receives the
+ * required workspace size (256-byte aligned base required). */
+peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch,
+                                const peps_einsumsvd_shape *shapes,
+                                const uint64_t *instance_ids,
+                                const peps_rsvd_opts *opts, size_t *workspace_bytes);
+
+/* Output rank k of instance i of a plan (host query). */
+peps_status peps_einsumsvd_rank(const peps_plan *plan, int32_t i, int32_t *k);
+
+/* Run the planned instances.  io is a HOST array of `batch` pointer sets.
+ * The first call for a given (io, workspace) pair uploads the launch
+ * descriptors into the workspace (stream-ordered copy); later calls with the
+ * same pointers enqueue kernels only and may be captured in a CUDA graph. */
+peps_status peps_einsumsvd_execute(peps_plan *plan, const peps_einsumsvd_io *io,
+                                   void *workspace, size_t workspace_bytes,
+                                   void *stream);
+
+peps_status peps_plan_destroy(peps_plan *plan);
+
+/* ------------------------------------------------------------------------
+ * Boundary-MPS contraction of a PEPS network (Algorithms 2 and 3).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t nrow, ncol, d;
+  int32_t dtype;                 /* peps_dtype */
+  const int32_t *bond_h;         /* HOST [nrow][ncol-1]: bond right of (p,q)  */
+  const int32_t *bond_v;         /* HOST [nrow-1][ncol]: bond below (p,q)     */
+  const void *const *site;       /* HOST array of nrow*ncol DEVICE pointers,
+                                    row-major, each [d][left][up][down][right] */
+} peps_network;
+
+/* Plan the contraction of <bra|ket> (bra != NULL: two-layer, the bra layer
+ * enters conjugated; pass the ket again for the norm) or of the one-layer
+ * network ket (bra == NULL, ket.d must be 1).  `direction` selects the sketch
+ * streams (stream id of the step at row r, column c is
+ * direction<<32 | r<<16 | c). */
+peps_status peps_contract_plan(peps_plan **out, const peps_network *ket,
+                               const peps_network *bra, const peps_rsvd_opts *opts,
+                               int32_t direction, size_t *workspace_bytes);
+
+/* Enqueue the planned sweep.  Results land in the workspace and are read by
+ * peps_contract_result(); same descriptor-upload rule as einsumsvd_execute. */
+peps_status peps_contract_execute(peps_plan *plan, void *workspace,
+                                  size_t workspace_bytes, void *stream);
+
+/* Synchronise `stream` and read the scalar as log|v| and arg v.  If sigma_out
+ * is non-NULL it receives, for every einsumsvd step in sweep order, the
+ * planned rank's singular values (peps_contract_sigma_count doubles). */
+peps_status peps_contract_result(peps_plan *plan, void *workspace, void *stream,
+                                 double *log_abs, double *phase, double *sigma_out);
+
+/* Number of doubles peps_contract_result writes to sigma_out. */
+peps_status peps_contract_sigma_count(const peps_plan *plan, int64_t *count);
+
+/* One-shot convenience: plan, execute, read the result and destroy. */
+peps_status peps_boundary_contract(const peps_network *ket, const peps_network *bra,
+                                   const peps_rsvd_opts *opts, void *workspace,
+                                   size_t workspace_bytes, void *stream,
+                                   double *log_abs, double *phase);
+
+/* Workspace size of peps_boundary_contract for these arguments. */
+peps_status peps_boundary_workspace(const peps_network *ket, const peps_network *bra,
+                                    const peps_rsvd_opts *opts, size_t *workspace_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBPEPS_H */

@@ -1,0 +1,150 @@
+// Launch descriptors and launcher declarations of the libpeps kernels.
+//
+// Every kernel is "grouped": it reads an array of per-problem descriptors
+// from device memory plus a prefix sum of the blocks each problem needs, so
+// one launch serves one problem (a step of a boundary sweep) or hundreds of
+// uneven ones (a batch of independent einsumsvd instances).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace peps {
+
+enum DType : int32_t { DT_R32 = 0, DT_C64 = 1, DT_R64 = 2, DT_C128 = 3 };
+
+inline int dtype_size(int dt) { return dt == DT_R32 ? 4 : (dt == DT_R64 || dt == DT_C64) ? 8 : 16; }
+inline bool dtype_complex(int dt) { return dt == DT_C64 || dt == DT_C128; }
+inline bool dtype_double(int dt) { return dt == DT_R64 || dt == DT_C128; }
+// size of the FP64 accumulation element (double or double2)
+inline int acc_size(int dt) { return dtype_complex(dt) ? 16 : 8; }
+
+// C[b](m,n) = alpha * sum_k opA(A[b](m,k)) * opB(B[b](k,n))  (+ C if accumulate)
+// with element (m,k) of A at A + b*sAb + m*sAm + k*sAk (likewise B, C).
+// In "atomic" launches C points to FP64 accumulators (double / double2) and
+// partial sums over K chunks are added atomically (split-K Gram matrices).
+struct GemmDesc {
+  const void *A, *B;
+  void *C;
+  int32_t M, N, K, batch;
+  int32_t ksplit, kchunk;          // K is cut into ksplit chunks of kchunk
+  int32_t tiles_m, tiles_n;
+  int64_t sAm, sAk, sAb, sBk, sBn, sBb, sCm, sCn, sCb;
+  double alpha;
+  const double *alpha_dev;         // optional device factor (e.g. 1/sigma_1)
+  int32_t conjA, conjB, conjC, accumulate;
+};
+
+// Two-layer site contraction of the implicit product (the two d*D^6 stages):
+//  forward (adjoint=0), per (j, b):
+//    out[j][(l,L)][(u,U,b)] = sum_s sum_{x,e,X,E} K[s,l,u,x,e] in[j][(x,X,b,e,E)] conj(Kb[s,L,U,X,E])
+//  adjoint (adjoint=1), per (j, b):
+//    out[j][(x,X,b,e,E)] = sum_s sum_{l,u,L,U} conj(K[s,l,u,x,e]) in[j][(l,L)][(u,U,b)] Kb[s,L,U,X,E]
+struct SandwichDesc {
+  const void *in;
+  void *out;
+  const void *K, *Kb;
+  int32_t d, Dl, Du, Dx, De, DL, DU, DX, DE, B, ell;
+  int32_t adjoint;
+  int64_t ld_in, ld_out;           // per-j strides (elements)
+  int32_t items_per_block;
+  int32_t nblocks;
+};
+
+// Philox4x64-10 draw of an N x ell block stored as X[j*ld + n].
+struct SketchDesc {
+  void *X;
+  int64_t N, ld;
+  int32_t ell;
+  int32_t tag, kind;               // kind 0 Gaussian, 1 uniform
+  uint64_t seed, instance;
+  int64_t nblocks;
+};
+
+// Cholesky of a Hermitian FP64 Gram (row-major n x n, destroyed) with pivot
+// skipping, upper factor R (optional, FP64) and T = R^+ (upper, working type).
+// If Rprev != nullptr the product R * Rprev is written to Rout (FP64).
+struct CholDesc {
+  void *G;
+  void *T;
+  void *R;
+  const void *Rprev;
+  void *Rout;
+  int32_t n;
+  double tol;
+};
+
+// One-sided Jacobi SVD of Mw = Rb^H (n x n, FP64, column-major, built from the
+// upper factor Rb by the kernel).  On return column c of Mw holds sigma_c u_c
+// and sig[c] = sigma_c (unsorted).
+struct JacobiDesc {
+  const void *Rb;
+  void *Mw;
+  double *sig;
+  int32_t n;
+  int32_t max_sweeps;
+  uint32_t *status;
+};
+
+// Sort, truncate, zero and gauge-fix the small SVD, then emit the ell x k
+// coefficient block Ut (working type, row-major [j][c]) used for U = P Ut and
+// W = conj(Ut^T Z) / sigma_1.
+struct FinalizeDesc {
+  const void *Mw;                  // FP64 n x n column-major, columns sigma_c u_c
+  const double *sig;               // n unsorted singular values
+  const void *P;                   // working type, [j][m], ld = M
+  const void *g;                   // gauge vector, M entries
+  void *Ut;                        // working type [j][c], n x k
+  double *sigma_out;               // k values
+  double *log_out;                 // log sigma_1
+  double *inv_s1;                  // 1 / sigma_1 (device scalar for the W GEMM)
+  int32_t n, k;
+  int64_t M;
+  double rtol;
+  uint32_t *status;
+};
+
+// Row one of the two-layer network (Algorithm 2, first line):
+// S[(l,L)][(x,X)][(e,E)] = sum_s K[s,l,0,x,e] conj(Kb[s,L,0,X,E]).
+// Zip-up start (Algorithm 3, first line), mode 1:
+// V[0][(x,X)][b][(e,E)] = sum_{s,u,U} S1[0][(u,U)][b] K[s,0,u,x,e] conj(Kb[s,0,U,X,E]).
+struct SiteDesc {
+  const void *K, *Kb, *S;
+  void *out;
+  int32_t mode;
+  int32_t d, Dl, Du, Dx, De, DL, DU, DX, DE, B;
+  int64_t total;
+};
+
+// Contract a boundary MPS with trivial vertical bonds to a scalar:
+// v = S_0[0,0,:] S_1[:,0,:] ... ; result log|v| + sum(logs), arg v.
+struct ScalarDesc {
+  const void *const *sites;        // device array of ncol site pointers
+  const int32_t *left, *right;     // device arrays of bond dims
+  int32_t ncol;
+  const double *logs;              // nlogs per-step log sigma_1 values
+  int32_t nlogs;
+  void *scratch;                   // 2 * maxbond working elements
+  double *out;                     // [log_abs, phase]
+};
+
+// ---- launchers (enqueue on stream; descriptor arrays live on the device) ----
+void launch_gemm(int dt, bool atomic, const GemmDesc *d, const int64_t *prefix, int nd,
+                 int64_t blocks, cudaStream_t s);
+void launch_sandwich(int dt, const SandwichDesc *d, const int64_t *prefix, int nd,
+                     int64_t blocks, int smem_bytes, cudaStream_t s);
+void launch_sketch(int dt, const SketchDesc *d, const int64_t *prefix, int nd,
+                   int64_t blocks, cudaStream_t s);
+void launch_chol(int dt, const CholDesc *d, int nd, cudaStream_t s);
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, cudaStream_t s);
+void launch_finalize(int dt, const FinalizeDesc *d, int nd, cudaStream_t s);
+void launch_site(int dt, const SiteDesc *d, const int64_t *prefix, int nd, int64_t blocks,
+                 cudaStream_t s);
+void launch_scalar(int dt, const ScalarDesc *d, cudaStream_t s);
+void launch_fill(int dt, void *p, int64_t n, double value, cudaStream_t s);
+
+int sandwich_smem_bytes(int dt, const SandwichDesc &d);
+constexpr int kGemmBM = 64, kGemmBN = 64;
+constexpr int kSketchPerBlock = 256 * 4;   // elements per sketch block
+constexpr int kSiteThreads = 256;
+
+}  // namespace peps

@@ -1,0 +1,250 @@
+// Sketch generation and the small per-row kernels of the boundary sweep.
+//
+//  * sketch: Philox4x64-10 (Salmon et al., SC'11) draw of Algorithm 4's start
+//    block, counter (block, instance, tag, 0), key (seed, 0); element
+//    e = j*N + n; Box-Muller on word pairs (real: 4 normals per block;
+//    complex: 2 values per block, scaled by 1/sqrt 2).  The uniform is
+//    ((x >> 11) + 1/2) 2^-53, rounded to the working precision.
+//  * site: the untruncated first row of the two-layer network (Algorithm 2,
+//    first line) and the zip-up start V1 = S1 O1 (Algorithm 3, first line).
+//  * scalar: the final contraction of a boundary with trivial vertical bonds
+//    (Algorithm 2, last line), returned as log|v| plus the carried logs.
+#include "common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace peps {
+
+namespace {
+
+__device__ __forceinline__ int find_desc(const int64_t *prefix, int nd, int64_t blk) {
+  int lo = 0, hi = nd - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr uint64_t PH_M0 = 0xD2E7470EE14C6C93ull, PH_M1 = 0xCA5A826395121157ull;
+constexpr uint64_t PH_W0 = 0x9E3779B97F4A7C15ull, PH_W1 = 0xBB67AE8584CAA73Bull;
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(PH_M0, c[0]), lo0 = PH_M0 * c[0];
+    const uint64_t hi1 = __umul64hi(PH_M1, c[2]), lo1 = PH_M1 * c[2];
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += PH_W0; k1 += PH_W1;
+  }
+}
+
+template <class R> struct Uni;
+template <> struct Uni<double> {
+  __device__ static double u(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1.0p-53; }
+  __device__ static void bm(double u0, double u1, double &a, double &b) {
+    const double r = sqrt(-2.0 * log(u0));
+    double sn, cs;
+    sincospi(2.0 * u1, &sn, &cs);
+    a = r * cs; b = r * sn;
+  }
+};
+template <> struct Uni<float> {
+  // same 53-bit uniform as the double path, rounded once to 24 bits, so the
+  // relative difference stays below 2^-24 even for the smallest draws
+  __device__ static float u(uint64_t x) {
+    return __fadd_rn(__ull2float_rn(x >> 11), 0.5f) * 0x1.0p-53f;
+  }
+  __device__ static void bm(float u0, float u1, float &a, float &b) {
+    const float r = sqrtf(-2.0f * logf(u0));
+    float sn, cs;
+    sincospif(2.0f * u1, &sn, &cs);
+    a = r * cs; b = r * sn;
+  }
+};
+
+template <class T>
+__global__ void sketch_kernel(const SketchDesc *__restrict__ descs, const int64_t *__restrict__ prefix,
+                              int nd) {
+  using R = typename Traits<T>::Real;
+  constexpr bool CPLX = Traits<T>::cplx;
+  constexpr int PER = CPLX ? 2 : 4;
+  const int di = find_desc(prefix, nd, blockIdx.x);
+  const SketchDesc &g = descs[di];
+  const int64_t total = g.N * g.ell;
+  const int64_t blk = (int64_t)(blockIdx.x - prefix[di]) * blockDim.x + threadIdx.x;
+  if (blk * PER >= total) return;
+  uint64_t c[4] = {(uint64_t)blk, g.instance, (uint64_t)g.tag, 0ull};
+  philox4x64_10(c, g.seed, 0ull);
+  R v[4];
+  if (g.kind == 0) {
+    Uni<R>::bm(Uni<R>::u(c[0]), Uni<R>::u(c[1]), v[0], v[1]);
+    Uni<R>::bm(Uni<R>::u(c[2]), Uni<R>::u(c[3]), v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = (R)2 * Uni<R>::u(c[i]) - (R)1;
+  }
+  T *X = (T *)g.X;
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int64_t e = blk * PER + r;
+    if (e >= total) break;
+    const int64_t j = e / g.N, n = e % g.N;
+    T val;
+    if constexpr (CPLX) {
+      const R sc = g.kind == 0 ? (R)0.70710678118654752440 : (R)1;
+      val = from_parts<T>((double)(v[2 * r] * sc), (double)(v[2 * r + 1] * sc));
+    } else {
+      val = from_parts<T>((double)v[r], 0.0);
+    }
+    X[j * g.ld + n] = val;
+  }
+}
+
+template <class T>
+__global__ void site_kernel(const SiteDesc *__restrict__ descs, const int64_t *__restrict__ prefix,
+                            int nd) {
+  const int di = find_desc(prefix, nd, blockIdx.x);
+  const SiteDesc &g = descs[di];
+  const int64_t idx = (int64_t)(blockIdx.x - prefix[di]) * blockDim.x + threadIdx.x;
+  if (idx >= g.total) return;
+  const T *K = (const T *)g.K, *Kb = (const T *)g.Kb;
+  // K strides for [d][Dl][Du][Dx][De]
+  const int64_t kE = 1, kX = g.De, kU = (int64_t)g.Dx * g.De, kL = kU * g.Du, kS = kL * g.Dl;
+  const int64_t bE = 1, bX = g.DE, bU = (int64_t)g.DX * g.DE, bL = bU * g.DU, bS = bL * g.DL;
+  T acc = zero<T>();
+  if (g.mode == 0) {
+    // out[(l,L)][(x,X)][(e,E)], u = U = 0
+    int64_t r = idx;
+    const int E = r % g.DE; r /= g.DE;
+    const int e = r % g.De; r /= g.De;
+    const int X_ = r % g.DX; r /= g.DX;
+    const int x = r % g.Dx; r /= g.Dx;
+    const int L = r % g.DL; r /= g.DL;
+    const int l = (int)r;
+    for (int s = 0; s < g.d; ++s)
+      acc = fma_(K[s * kS + l * kL + x * kX + e * kE],
+                 conj_(Kb[s * bS + L * bL + X_ * bX + E * bE]), acc);
+  } else {
+    // out[(x,X)][b][(e,E)] = sum S1[0][(u,U)][b] K[s,0,u,x,e] conj(Kb[s,0,U,X,E])
+    const T *S = (const T *)g.S;
+    int64_t r = idx;
+    const int E = r % g.DE; r /= g.DE;
+    const int e = r % g.De; r /= g.De;
+    const int b = r % g.B; r /= g.B;
+    const int X_ = r % g.DX; r /= g.DX;
+    const int x = (int)r;
+    for (int u = 0; u < g.Du; ++u)
+      for (int U = 0; U < g.DU; ++U) {
+        const T sv = S[((int64_t)u * g.DU + U) * g.B + b];
+        T t = zero<T>();
+        for (int s = 0; s < g.d; ++s)
+          t = fma_(K[s * kS + u * kU + x * kX + e * kE],
+                   conj_(Kb[s * bS + U * bU + X_ * bX + E * bE]), t);
+        acc = fma_(sv, t, acc);
+      }
+  }
+  ((T *)g.out)[idx] = acc;
+}
+
+__global__ void zero_kernel(const ZeroDesc *__restrict__ descs, const int64_t *__restrict__ prefix,
+                            int nd) {
+  const int di = find_desc(prefix, nd, blockIdx.x);
+  const ZeroDesc &g = descs[di];
+  const int64_t w0 = (int64_t)(blockIdx.x - prefix[di]) * kZeroWordsPerBlock;
+  uint64_t *p = (uint64_t *)g.p;
+  for (int64_t i = w0 + threadIdx.x; i < min(g.words, w0 + kZeroWordsPerBlock); i += blockDim.x) p[i] = 0ull;
+}
+
+template <class T> __global__ void fill_kernel(T *p, int64_t n, double value) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = from_parts<T>(value, 0.0);
+}
+
+// v_{q+1}[r] = sum_l v_q[l] S_q[l][0][r] in FP64; one block, sequential sites.
+template <class T> __global__ void scalar_kernel(ScalarDesc g) {
+  using Acc = typename Traits<T>::Acc;
+  Acc *v = (Acc *)g.scratch;
+  int maxb = 1;
+  for (int q = 0; q < g.ncol; ++q) maxb = max(maxb, max(g.left[q], g.right[q]));
+  Acc *w = v + maxb;
+  if (threadIdx.x == 0) v[0] = widen(from_parts<T>(1.0, 0.0));
+  __syncthreads();
+  for (int q = 0; q < g.ncol; ++q) {
+    const T *S = (const T *)g.sites[q];
+    const int L = g.left[q], R = g.right[q];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      Acc a = widen(zero<T>());
+      for (int l = 0; l < L; ++l) a = fma_(v[l], widen(S[(int64_t)l * R + r]), a);
+      w[r] = a;
+    }
+    __syncthreads();
+    Acc *t = v; v = w; w = t;
+  }
+  if (threadIdx.x == 0) {
+    double lg = 0.0;
+    for (int i = 0; i < g.nlogs; ++i) lg += g.logs[i];
+    const Acc x = v[0];
+    const double mag = sqrt(abs2(x));
+    g.out[0] = (mag > 0 ? log(mag) : -INFINITY) + lg;
+    g.out[1] = atan2((double)im(x), (double)re(x));
+  }
+}
+
+template <class T>
+void sketch_t(const SketchDesc *d, const int64_t *prefix, int nd, int64_t blocks, cudaStream_t s) {
+  if (blocks > 0) sketch_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, prefix, nd);
+}
+template <class T>
+void site_t(const SiteDesc *d, const int64_t *prefix, int nd, int64_t blocks, cudaStream_t s) {
+  if (blocks > 0) site_kernel<T><<<(unsigned)blocks, kSiteThreads, 0, s>>>(d, prefix, nd);
+}
+
+}  // namespace
+
+void launch_sketch(int dt, const SketchDesc *d, const int64_t *prefix, int nd, int64_t blocks,
+                   cudaStream_t s) {
+  switch (dt) {
+    case DT_R32: sketch_t<float>(d, prefix, nd, blocks, s); break;
+    case DT_C64: sketch_t<float2>(d, prefix, nd, blocks, s); break;
+    case DT_R64: sketch_t<double>(d, prefix, nd, blocks, s); break;
+    case DT_C128: sketch_t<double2>(d, prefix, nd, blocks, s); break;
+  }
+}
+
+void launch_site(int dt, const SiteDesc *d, const int64_t *prefix, int nd, int64_t blocks,
+                 cudaStream_t s) {
+  switch (dt) {
+    case DT_R32: site_t<float>(d, prefix, nd, blocks, s); break;
+    case DT_C64: site_t<float2>(d, prefix, nd, blocks, s); break;
+    case DT_R64: site_t<double>(d, prefix, nd, blocks, s); break;
+    case DT_C128: site_t<double2>(d, prefix, nd, blocks, s); break;
+  }
+}
+
+void launch_zero(const ZeroDesc *d, const int64_t *prefix, int nd, int64_t blocks, cudaStream_t s) {
+  if (blocks > 0) zero_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, prefix, nd);
+}
+
+void launch_fill(int dt, void *p, int64_t n, double value, cudaStream_t s) {
+  if (n <= 0) return;
+  const unsigned blocks = (unsigned)ceil_div(n, 256);
+  switch (dt) {
+    case DT_R32: fill_kernel<float><<<blocks, 256, 0, s>>>((float *)p, n, value); break;
+    case DT_C64: fill_kernel<float2><<<blocks, 256, 0, s>>>((float2 *)p, n, value); break;
+    case DT_R64: fill_kernel<double><<<blocks, 256, 0, s>>>((double *)p, n, value); break;
+    case DT_C128: fill_kernel<double2><<<blocks, 256, 0, s>>>((double2 *)p, n, value); break;
+  }
+}
+
+void launch_scalar(int dt, const ScalarDesc *d, cudaStream_t s) {
+  switch (dt) {
+    case DT_R32: scalar_kernel<float><<<1, 256, 0, s>>>(*d); break;
+    case DT_C64: scalar_kernel<float2><<<1, 256, 0, s>>>(*d); break;
+    case DT_R64: scalar_kernel<double><<<1, 256, 0, s>>>(*d); break;
+    case DT_C128: scalar_kernel<double2><<<1, 256, 0, s>>>(*d); break;
+  }
+}
+
+}  // namespace peps

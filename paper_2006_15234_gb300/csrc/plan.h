@@ -1,0 +1,104 @@
+// Host-side launch schedule of libpeps: a plan is a static list of grouped
+// kernel launches whose descriptors are built once per workspace address and
+// uploaded into the workspace, so an execute is a fixed kernel sequence that
+// can be replayed or captured in a CUDA graph.
+#pragma once
+#include <stdint.h>
+#include <string.h>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace peps {
+
+struct Op {
+  enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL } kind;
+  size_t desc_off = 0;    // byte offset of the descriptor array in the blob
+  size_t prefix_off = 0;  // byte offset of the int64 block prefix array in the blob
+  int nd = 0;
+  int64_t blocks = 0;
+  int smem = 0;
+  ScalarDesc scalar{};
+  size_t aux_off[3] = {0, 0, 0};  // blob offsets of the scalar's device arrays
+  void *fill_ptr = nullptr;
+  int64_t fill_n = 0;
+  double fill_value = 0.0;
+  std::string tag;        // stage name (profiling ledger)
+};
+
+struct ZeroDesc {
+  void *p;
+  int64_t words;          // 8-byte words
+};
+
+void launch_zero(const ZeroDesc *d, const int64_t *prefix, int nd, int64_t blocks, cudaStream_t s);
+constexpr int kZeroWordsPerBlock = 256 * 8;
+
+// Builds ops + descriptor blob for one workspace base address.
+struct Builder {
+  uintptr_t base = 0;
+  size_t top = 0;                 // bump allocator over buffer space
+  std::vector<uint8_t> blob;
+  std::vector<Op> ops;
+  int dt = 0;
+
+  size_t alloc(size_t bytes) {
+    size_t o = (top + 255) & ~(size_t)255;
+    top = o + bytes;
+    return o;
+  }
+  void *ptr(size_t off) const { return (void *)(base + off); }
+  void *buf(size_t bytes) { return ptr(alloc(bytes)); }
+
+  size_t put_bytes(const void *p, size_t n) {
+    size_t o = (blob.size() + 15) & ~(size_t)15;
+    blob.resize(o + n);
+    memcpy(blob.data() + o, p, n);
+    return o;
+  }
+  template <class D> size_t put(const std::vector<D> &v) { return put_bytes(v.data(), v.size() * sizeof(D)); }
+};
+
+}  // namespace peps
+
+namespace peps {
+
+// One einsumsvd instance (Algorithm 3's einsumsvd line, Algorithm 4 inside):
+// shape, operand / output pointers and the scratch buffers its stages use.
+struct Inst {
+  int kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE;
+  int h, v;
+  int64_t M, N;
+  int k, ell;
+  uint64_t instance;
+  const void *V, *S, *K, *Kb;
+  void *U, *W;
+  double *sigma, *logp;
+  // scratch (working type unless noted)
+  void *X, *Z, *T2, *T3, *Y, *P, *g, *Tm, *Ut;
+  void *G, *R1, *R2, *Rout, *Mw;   // FP64 (double or double2)
+  double *sig, *inv_s1;
+};
+
+struct RsvdOpts {
+  int m, p, q;
+  uint64_t seed;
+  int sketch;
+  int prec;
+};
+
+// Shape bookkeeping shared by every planner.
+void inst_derive(Inst &I, const RsvdOpts &o);
+// Bytes of per-instance scratch.
+size_t inst_scratch_bytes(const Inst &I, int dt);
+// Carve per-instance scratch out of the builder.
+void inst_alloc_scratch(Builder &B, Inst &I, int dt);
+// Point I's scratch at another instance's buffers (the sweep reuses one set).
+void inst_share_scratch(Inst &I, const Inst &owner);
+// Check the shape against the kernels' limits; returns "" when supported.
+std::string inst_check(const Inst &I, int dt);
+// Emit every stage of one einsumsvd over a group of instances.
+void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);
+
+}  // namespace peps

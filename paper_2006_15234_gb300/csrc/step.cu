@@ -1,0 +1,358 @@
+// Launch schedule of one einsumsvd (Algorithm 3's einsumsvd line with
+// Algorithm 4 applied to the implicit operator of Sec. IV-A), emitted as
+// grouped launches over any number of instances:
+//
+//   X <- Omega (Philox), g <- gauge vector
+//   Y <- A X;              P <- orth(Y)            (CholeskyQR2)
+//   repeat q:  Z <- A^H P; Q <- orth(Z);  Y <- A Q;  P <- orth(Y)
+//   Z <- A^H P  (= (P^H A)^H);  R_B <- R factor of Z (CholeskyQR2)
+//   U~, Sigma <- one-sided Jacobi SVD of R_B^H;  sort / truncate / gauge
+//   U <- P U~;   W <- U~^H P^H A / sigma_1
+//
+// A X runs as the two-layer site "sandwich" (ket and bra over their down and
+// right bonds) followed by the boundary-site and carry contractions; A^H Y
+// is the same chain reversed (Table 2's two-layer IBMPS contraction order).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace peps {
+
+namespace {
+
+constexpr int kSMs = 152;
+
+int64_t gemm_blocks(GemmDesc &g) {
+  g.tiles_m = (int)ceil_div(g.M, kGemmBM);
+  g.tiles_n = (int)ceil_div(g.N, kGemmBN);
+  return (int64_t)g.batch * g.ksplit * g.tiles_m * g.tiles_n;
+}
+
+GemmDesc mk_gemm(int M, int N, int K, int batch, const void *A, int64_t sAm, int64_t sAk, int64_t sAb,
+                 bool conjA, const void *B, int64_t sBk, int64_t sBn, int64_t sBb, bool conjB, void *C,
+                 int64_t sCm, int64_t sCn, int64_t sCb) {
+  GemmDesc g{};
+  g.A = A; g.B = B; g.C = C;
+  g.M = M; g.N = N; g.K = K; g.batch = batch;
+  g.ksplit = 1; g.kchunk = K;
+  g.sAm = sAm; g.sAk = sAk; g.sAb = sAb;
+  g.sBk = sBk; g.sBn = sBn; g.sBb = sBb;
+  g.sCm = sCm; g.sCn = sCn; g.sCb = sCb;
+  g.alpha = 1.0; g.alpha_dev = nullptr;
+  g.conjA = conjA; g.conjB = conjB; g.conjC = 0; g.accumulate = 0;
+  return g;
+}
+
+// split K of an atomic Gram so the launch fills the machine a few times over
+void set_ksplit(GemmDesc &g, int ndesc) {
+  const int64_t tiles = ceil_div(g.M, kGemmBM) * ceil_div(g.N, kGemmBN) * (int64_t)g.batch * ndesc;
+  int64_t ks = std::max<int64_t>(1, (4 * kSMs + tiles - 1) / tiles);
+  ks = std::min<int64_t>(ks, std::max<int64_t>(1, g.K / 256));
+  g.kchunk = (int)(ceil_div(ceil_div(g.K, ks), 16) * 16);
+  g.ksplit = (int)ceil_div(g.K, g.kchunk);
+}
+
+void push_grouped(Builder &B, Op::Kind kind, const void *descs, size_t desc_size, int nd,
+                  const std::vector<int64_t> &blocks, const char *tag, int smem = 0) {
+  std::vector<int64_t> prefix(nd);
+  int64_t tot = 0;
+  for (int i = 0; i < nd; ++i) { prefix[i] = tot; tot += blocks[i]; }
+  Op op;
+  op.kind = kind;
+  op.desc_off = B.put_bytes(descs, desc_size * nd);
+  op.prefix_off = B.put(prefix);
+  op.nd = nd;
+  op.blocks = tot;
+  op.smem = smem;
+  op.tag = tag;
+  if (nd > 0 && tot > 0) B.ops.push_back(op);
+}
+
+void push_gemm(Builder &B, std::vector<GemmDesc> &d, bool atomic, const char *tag) {
+  std::vector<int64_t> bl(d.size());
+  for (size_t i = 0; i < d.size(); ++i) bl[i] = gemm_blocks(d[i]);
+  push_grouped(B, atomic ? Op::GEMM_ATOMIC : Op::GEMM, d.data(), sizeof(GemmDesc), (int)d.size(), bl, tag);
+}
+
+void push_zero(Builder &B, const std::vector<std::pair<void *, int64_t>> &regions, const char *tag) {
+  std::vector<ZeroDesc> d;
+  std::vector<int64_t> bl;
+  for (auto &r : regions) {
+    d.push_back(ZeroDesc{r.first, r.second});
+    bl.push_back(ceil_div(r.second, kZeroWordsPerBlock));
+  }
+  push_grouped(B, Op::ZERO, d.data(), sizeof(ZeroDesc), (int)d.size(), bl, tag);
+}
+
+// ---- stages ---------------------------------------------------------------
+
+void emit_sketch(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
+  std::vector<SketchDesc> d;
+  std::vector<int64_t> bl;
+  const int per = dtype_complex(B.dt) ? 2 : 4;
+  for (Inst *p : I) {
+    SketchDesc s{};
+    s.X = p->X; s.N = p->N; s.ld = p->N; s.ell = p->ell; s.tag = 0; s.kind = o.sketch;
+    s.seed = o.seed; s.instance = p->instance;
+    s.nblocks = ceil_div(ceil_div(s.N * s.ell, per), 256);
+    d.push_back(s); bl.push_back(s.nblocks);
+    SketchDesc gg = s;
+    gg.X = p->g; gg.N = p->M; gg.ld = p->M; gg.ell = 1; gg.tag = 1; gg.kind = 0;
+    gg.nblocks = ceil_div(ceil_div(gg.N, per), 256);
+    d.push_back(gg); bl.push_back(gg.nblocks);
+  }
+  push_grouped(B, Op::SKETCH, d.data(), sizeof(SketchDesc), (int)d.size(), bl, "sketch");
+}
+
+SandwichDesc mk_sandwich(const Inst &I, const void *in, void *out, bool adjoint) {
+  SandwichDesc s{};
+  s.in = in; s.out = out; s.K = I.K; s.Kb = I.Kb;
+  s.d = I.d; s.Dl = I.Dl; s.Du = I.Du; s.Dx = I.Dx; s.De = I.De;
+  s.DL = I.DL; s.DU = I.DU; s.DX = I.DX; s.DE = I.DE;
+  s.B = I.b; s.ell = I.ell; s.adjoint = adjoint;
+  const int64_t ldT2 = (int64_t)I.h * I.v * I.b;
+  s.ld_in = adjoint ? ldT2 : I.N;
+  s.ld_out = adjoint ? I.N : ldT2;
+  return s;
+}
+
+void push_sandwich(Builder &B, std::vector<SandwichDesc> &d, const char *tag) {
+  int64_t items = 0;
+  int smem = 0;
+  for (auto &s : d) {
+    items += (int64_t)s.ell * s.B;
+    smem = std::max(smem, sandwich_smem_bytes(B.dt, s));
+  }
+  const int64_t per = std::max<int64_t>(1, std::min<int64_t>(32, items / (4 * kSMs)));
+  std::vector<int64_t> bl;
+  for (auto &s : d) {
+    s.items_per_block = (int)per;
+    s.nblocks = (int)ceil_div((int64_t)s.ell * s.B, per);
+    bl.push_back(s.nblocks);
+  }
+  push_grouped(B, Op::SANDWICH, d.data(), sizeof(SandwichDesc), (int)d.size(), bl, tag, smem);
+}
+
+// Y <- A X (src N-side [j][n] -> dst M-side [j][mrow])
+void emit_product(Builder &B, std::vector<Inst *> &I, bool from_x) {
+  std::vector<SandwichDesc> sw;
+  std::vector<GemmDesc> g3, g4;
+  for (Inst *p : I) {
+    const Inst &q = *p;
+    sw.push_back(mk_sandwich(q, from_x ? q.X : q.Z, q.T2, false));
+    const int64_t vb = (int64_t)q.v * q.b, hvb = (int64_t)q.h * vb, ah = (int64_t)q.a * q.h;
+    // T3_j[a][h] = sum_(v,b) S[a][(v,b)] T2_j[h][(v,b)]
+    g3.push_back(mk_gemm(q.a, q.h, (int)vb, q.ell, q.S, vb, 1, 0, false, q.T2, 1, vb, hvb, false, q.T3,
+                         q.h, 1, ah));
+    // Y[j][mrow] = sum_(a,h) T3[j][(a,h)] V[mrow][(a,h)]
+    g4.push_back(mk_gemm(q.ell, (int)q.M, (int)ah, 1, q.T3, ah, 1, 0, false, q.V, 1, ah, 0, false, q.Y,
+                         q.M, 1, 0));
+  }
+  push_sandwich(B, sw, "product_sites");
+  push_gemm(B, g3, false, "product_boundary");
+  push_gemm(B, g4, false, "product_carry");
+}
+
+// Z <- A^H Y (the chain reversed)
+void emit_adjoint(Builder &B, std::vector<Inst *> &I) {
+  std::vector<SandwichDesc> sw;
+  std::vector<GemmDesc> g4, g3;
+  for (Inst *p : I) {
+    const Inst &q = *p;
+    const int64_t vb = (int64_t)q.v * q.b, hvb = (int64_t)q.h * vb, ah = (int64_t)q.a * q.h;
+    // Z3[j][(a,h)] = sum_mrow P[j][mrow] conj(V[mrow][(a,h)])
+    g4.push_back(mk_gemm(q.ell, (int)ah, (int)q.M, 1, q.Y, q.M, 1, 0, false, q.V, ah, 1, 0, true, q.T3,
+                         ah, 1, 0));
+    // Z2_j[h][(v,b)] = sum_a Z3_j[a][h] conj(S[a][(v,b)])
+    g3.push_back(mk_gemm(q.h, (int)vb, q.a, q.ell, q.T3, 1, q.h, ah, false, q.S, vb, 1, 0, true, q.T2,
+                         vb, 1, hvb));
+    sw.push_back(mk_sandwich(q, q.T2, q.Z, true));
+  }
+  push_gemm(B, g4, false, "adjoint_carry");
+  push_gemm(B, g3, false, "adjoint_boundary");
+  push_sandwich(B, sw, "adjoint_sites");
+}
+
+double chol_tol(int dt, int ell) {
+  // Gram pivots below tol * max diag are numerically zero directions.  With
+  // FP64 data the Gram is accurate to ~eps64; with single-precision data only
+  // a breakdown (non-positive pivot) is treated as a zero direction.
+  return dtype_double(dt) ? 64.0 * ell * 2.220446049250313e-16 : 0.0;
+}
+
+// CholeskyQR pass: G <- src^H src; T <- R^+; dst <- src T
+void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*src, void *Inst::*dst,
+                   void *Inst::*Rdst, void *Inst::*Rprev, void *Inst::*Rout, bool apply, const char *tag) {
+  const int as = acc_size(B.dt);
+  std::vector<std::pair<void *, int64_t>> z;
+  std::vector<GemmDesc> gram, app;
+  std::vector<CholDesc> ch;
+  for (Inst *p : I) {
+    Inst &q = *p;
+    const int64_t L = mside ? q.M : q.N;
+    z.push_back({q.G, (int64_t)q.ell * q.ell * as / 8});
+    GemmDesc g = mk_gemm(q.ell, q.ell, (int)L, 1, q.*src, L, 1, 0, true, q.*src, 1, L, 0, false, q.G,
+                         q.ell, 1, 0);
+    gram.push_back(g);
+    CholDesc c{};
+    c.G = q.G; c.T = q.Tm; c.R = q.*Rdst; c.n = q.ell; c.tol = chol_tol(B.dt, q.ell);
+    c.Rprev = Rprev ? q.*Rprev : nullptr;
+    c.Rout = Rout ? q.*Rout : nullptr;
+    ch.push_back(c);
+    if (apply)
+      app.push_back(mk_gemm(q.ell, (int)L, q.ell, 1, q.Tm, 1, q.ell, 0, false, q.*src, L, 1, 0, false,
+                            q.*dst, L, 1, 0));
+  }
+  for (auto &g : gram) set_ksplit(g, (int)gram.size());
+  push_zero(B, z, tag);
+  push_gemm(B, gram, true, tag);
+  Op op;
+  op.kind = Op::CHOL;
+  op.desc_off = B.put(ch);
+  op.nd = (int)ch.size();
+  op.tag = tag;
+  B.ops.push_back(op);
+  if (apply) push_gemm(B, app, false, tag);
+}
+
+void emit_orth(Builder &B, std::vector<Inst *> &I, bool mside) {
+  void *Inst::*a = mside ? &Inst::Y : &Inst::Z;
+  void *Inst::*t = mside ? &Inst::P : &Inst::X;
+  const char *tag = mside ? "orth_m" : "orth_n";
+  emit_cqr_pass(B, I, mside, a, t, &Inst::R1, nullptr, nullptr, true, tag);
+  emit_cqr_pass(B, I, mside, t, a, &Inst::R1, nullptr, nullptr, true, tag);
+}
+
+void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
+  // R_B: CholeskyQR2 of Z = (P^H A)^H, R_B = R2 R1
+  emit_cqr_pass(B, I, false, &Inst::Z, &Inst::X, &Inst::R1, nullptr, nullptr, true, "svd_qr");
+  emit_cqr_pass(B, I, false, &Inst::X, nullptr, &Inst::R2, &Inst::R1, &Inst::Rout, false, "svd_qr");
+  std::vector<JacobiDesc> jd;
+  std::vector<FinalizeDesc> fd;
+  for (Inst *p : I) {
+    Inst &q = *p;
+    JacobiDesc j{};
+    j.Rb = q.Rout; j.Mw = q.Mw; j.sig = q.sig; j.n = q.ell; j.max_sweeps = 40; j.status = nullptr;
+    jd.push_back(j);
+    FinalizeDesc f{};
+    f.Mw = q.Mw; f.sig = q.sig; f.P = q.Y; f.g = q.g; f.Ut = q.Ut; f.sigma_out = q.sigma;
+    f.log_out = q.logp; f.inv_s1 = q.inv_s1; f.n = q.ell; f.k = q.k; f.M = q.M;
+    f.rtol = 16.0 * q.ell * 2.220446049250313e-16; f.status = nullptr;
+    fd.push_back(f);
+  }
+  Op oj;
+  oj.kind = Op::JACOBI; oj.desc_off = B.put(jd); oj.nd = (int)jd.size(); oj.tag = "svd_jacobi";
+  B.ops.push_back(oj);
+  Op of;
+  of.kind = Op::FINALIZE; of.desc_off = B.put(fd); of.nd = (int)fd.size(); of.tag = "svd_finalize";
+  B.ops.push_back(of);
+}
+
+void emit_epilogue(Builder &B, std::vector<Inst *> &I) {
+  std::vector<GemmDesc> gu, gw;
+  for (Inst *p : I) {
+    Inst &q = *p;
+    // U[mrow][c] = sum_j P[j][mrow] Ut[j][c]
+    gu.push_back(mk_gemm((int)q.M, q.k, q.ell, 1, q.Y, 1, q.M, 0, false, q.Ut, q.k, 1, 0, false, q.U, q.k,
+                         1, 0));
+    // W[c][n] = sum_j conj(Ut[j][c]) conj(Z[j][n]) / sigma_1
+    GemmDesc w = mk_gemm(q.k, (int)q.N, q.ell, 1, q.Ut, 1, q.k, 0, true, q.Z, q.N, 1, 0, true, q.W, q.N, 1, 0);
+    w.alpha_dev = q.inv_s1;
+    gw.push_back(w);
+  }
+  push_gemm(B, gu, false, "epilogue_u");
+  push_gemm(B, gw, false, "epilogue_w");
+}
+
+}  // namespace
+
+void inst_derive(Inst &I, const RsvdOpts &o) {
+  I.h = I.Dl * I.DL;
+  I.v = I.Du * I.DU;
+  I.M = (int64_t)I.kL * I.t;
+  I.N = (int64_t)I.Dx * I.DX * I.b * I.De * I.DE;
+  I.k = (int)std::min<int64_t>(o.m, std::min(I.M, I.N));
+  I.ell = (int)std::min<int64_t>((int64_t)I.k + o.p, std::min(I.M, I.N));
+}
+
+size_t inst_scratch_bytes(const Inst &I, int dt) {
+  const size_t es = dtype_size(dt), as = acc_size(dt);
+  const size_t l = I.ell;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t s = 0;
+  s += 2 * al(l * I.N * es);                              // X, Z
+  s += al(l * (size_t)I.h * I.v * I.b * es);              // T2
+  s += al(l * (size_t)I.a * I.h * es);                    // T3
+  s += 2 * al(l * I.M * es);                              // Y, P
+  s += al(I.M * es);                                      // g
+  s += al(l * l * es) + al(l * I.k * es);                 // Tm, Ut
+  s += 5 * al(l * l * as);                                // G, R1, R2, Rout, Mw
+  s += al(l * 8) + al(8);                                 // sig, inv_s1
+  return s;
+}
+
+void inst_alloc_scratch(Builder &B, Inst &I, int dt) {
+  const size_t es = dtype_size(dt), as = acc_size(dt);
+  const size_t l = I.ell;
+  I.X = B.buf(l * I.N * es);
+  I.Z = B.buf(l * I.N * es);
+  I.T2 = B.buf(l * (size_t)I.h * I.v * I.b * es);
+  I.T3 = B.buf(l * (size_t)I.a * I.h * es);
+  I.Y = B.buf(l * I.M * es);
+  I.P = B.buf(l * I.M * es);
+  I.g = B.buf(I.M * es);
+  I.Tm = B.buf(l * l * es);
+  I.Ut = B.buf(l * I.k * es);
+  I.G = B.buf(l * l * as);
+  I.R1 = B.buf(l * l * as);
+  I.R2 = B.buf(l * l * as);
+  I.Rout = B.buf(l * l * as);
+  I.Mw = B.buf(l * l * as);
+  I.sig = (double *)B.buf(l * 8);
+  I.inv_s1 = (double *)B.buf(8);
+}
+
+void inst_share_scratch(Inst &I, const Inst &o) {
+  I.X = o.X; I.Z = o.Z; I.T2 = o.T2; I.T3 = o.T3; I.Y = o.Y; I.P = o.P; I.g = o.g; I.Tm = o.Tm;
+  I.Ut = o.Ut; I.G = o.G; I.R1 = o.R1; I.R2 = o.R2; I.Rout = o.Rout; I.Mw = o.Mw; I.sig = o.sig;
+  I.inv_s1 = o.inv_s1;
+}
+
+std::string inst_check(const Inst &I, int dt) {
+  const int dims[] = {I.kL, I.t, I.a, I.b, I.d, I.Dl, I.Du, I.Dx, I.De, I.DL, I.DU, I.DX, I.DE};
+  for (int x : dims)
+    if (x < 1) return "every dimension must be >= 1";
+  auto p4 = [](int x) { return (x + 3) / 4; };
+  const int P1 = I.Dl * I.Du, Q1 = I.Dx * I.De, P2 = I.DL * I.DU, Q2 = I.DX * I.DE;
+  if (p4(P1) * p4(Q2) > 256 || p4(P1) * p4(P2) > 256 || p4(Q1) * p4(Q2) > 256)
+    return "site bond products (left*up, down*right) above 64 are not supported";
+  SandwichDesc s{};
+  s.d = I.d; s.Dl = I.Dl; s.Du = I.Du; s.Dx = I.Dx; s.De = I.De; s.DL = I.DL; s.DU = I.DU; s.DX = I.DX;
+  s.DE = I.DE;
+  for (int adj = 0; adj < 2; ++adj) {
+    s.adjoint = adj;
+    if (sandwich_smem_bytes(dt, s) > 227 * 1024) return "site tensors too large for shared memory";
+  }
+  if (I.ell > 1024) return "sketch width l = min(k+p, M, N) above 1024 is not supported";
+  if (I.M > (1ll << 31) || I.N > (1ll << 31)) return "matrix dimension above 2^31";
+  return "";
+}
+
+void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
+  emit_sketch(B, I, o);
+  emit_product(B, I, true);
+  emit_orth(B, I, true);
+  for (int it = 0; it < o.q; ++it) {
+    emit_adjoint(B, I);
+    emit_orth(B, I, false);
+    emit_product(B, I, false);
+    emit_orth(B, I, true);
+  }
+  emit_adjoint(B, I);
+  emit_small_svd(B, I);
+  emit_epilogue(B, I);
+}
+
+}  // namespace peps

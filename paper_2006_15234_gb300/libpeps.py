@@ -1,0 +1,274 @@
+"""ctypes binding of libpeps (argument marshalling only).
+
+Every function here forwards to an ``extern "C"`` entry point declared in
+``include/libpeps.h``; tensors are PyTorch CUDA tensors passed by pointer,
+streams are ``torch.cuda.Stream`` handles.  Importing this module does not
+need a GPU; calling into the library does.  There is no CPU fallback: if
+the shared library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+__all__ = [
+    "PepsError", "load", "lib_path", "RsvdOpts", "EinsumsvdShape", "EinsumsvdIO",
+    "Network", "ContractPlan", "EinsumsvdPlan", "boundary_contract", "dtype_code",
+    "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "SKETCH_GAUSS", "SKETCH_UNIFORM",
+]
+
+PREC_PLAIN, PREC_MIXED = 0, 1
+SKETCH_GAUSS, SKETCH_UNIFORM = 0, 1
+
+EXPORTED_SYMBOLS = [
+    "peps_status_string", "peps_last_error", "peps_version",
+    "peps_einsumsvd_plan", "peps_einsumsvd_rank", "peps_einsumsvd_execute", "peps_plan_destroy",
+    "peps_contract_plan", "peps_contract_execute", "peps_contract_result",
+    "peps_contract_sigma_count", "peps_boundary_contract", "peps_boundary_workspace",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def lib_path() -> str:
+    return os.environ.get("LIBPEPS_PATH", os.path.join(_HERE, "_build", "libpeps.so"))
+
+
+class PepsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class RsvdOpts(C.Structure):
+    _fields_ = [("m", C.c_int32), ("p", C.c_int32), ("q", C.c_int32), ("seed", C.c_uint64),
+                ("sketch", C.c_int32), ("prec", C.c_int32), ("flags", C.c_uint32)]
+
+
+class EinsumsvdShape(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in
+                ("kL", "t", "a", "b", "d", "Dl", "Du", "Dx", "De", "DL", "DU", "DX", "DE")]
+
+
+class EinsumsvdIO(C.Structure):
+    _fields_ = [("V", C.c_void_p), ("S", C.c_void_p), ("ket", C.c_void_p), ("bra", C.c_void_p),
+                ("U", C.c_void_p), ("W", C.c_void_p), ("sigma", C.c_void_p),
+                ("log_scale", C.c_void_p)]
+
+
+class Network(C.Structure):
+    _fields_ = [("nrow", C.c_int32), ("ncol", C.c_int32), ("d", C.c_int32), ("dtype", C.c_int32),
+                ("bond_h", C.POINTER(C.c_int32)), ("bond_v", C.POINTER(C.c_int32)),
+                ("site", C.POINTER(C.c_void_p))]
+
+
+_lib = None
+
+
+def load():
+    """Load libpeps.so (built in-tree by ``build.build_library``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise PepsError(-1, f"libpeps.so not found at {path}; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    st = C.c_int32
+    vp = C.c_void_p
+    lib.peps_status_string.restype = C.c_char_p
+    lib.peps_status_string.argtypes = [st]
+    lib.peps_last_error.restype = C.c_char_p
+    lib.peps_version.restype = C.c_char_p
+    lib.peps_einsumsvd_plan.restype = st
+    lib.peps_einsumsvd_plan.argtypes = [C.POINTER(vp), C.c_int32, C.c_int32, C.POINTER(EinsumsvdShape),
+                                        C.POINTER(C.c_uint64), C.POINTER(RsvdOpts), C.POINTER(C.c_size_t)]
+    lib.peps_einsumsvd_rank.restype = st
+    lib.peps_einsumsvd_rank.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+    lib.peps_einsumsvd_execute.restype = st
+    lib.peps_einsumsvd_execute.argtypes = [vp, C.POINTER(EinsumsvdIO), vp, C.c_size_t, vp]
+    lib.peps_plan_destroy.restype = st
+    lib.peps_plan_destroy.argtypes = [vp]
+    lib.peps_contract_plan.restype = st
+    lib.peps_contract_plan.argtypes = [C.POINTER(vp), C.POINTER(Network), C.POINTER(Network),
+                                       C.POINTER(RsvdOpts), C.c_int32, C.POINTER(C.c_size_t)]
+    lib.peps_contract_execute.restype = st
+    lib.peps_contract_execute.argtypes = [vp, vp, C.c_size_t, vp]
+    lib.peps_contract_result.restype = st
+    lib.peps_contract_result.argtypes = [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double)]
+    lib.peps_contract_sigma_count.restype = st
+    lib.peps_contract_sigma_count.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.peps_boundary_contract.restype = st
+    lib.peps_boundary_contract.argtypes = [C.POINTER(Network), C.POINTER(Network), C.POINTER(RsvdOpts),
+                                           vp, C.c_size_t, vp, C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double)]
+    lib.peps_boundary_workspace.restype = st
+    lib.peps_boundary_workspace.argtypes = [C.POINTER(Network), C.POINTER(Network), C.POINTER(RsvdOpts),
+                                            C.POINTER(C.c_size_t)]
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        lib = load()
+        raise PepsError(status, f"{lib.peps_status_string(status).decode()}: "
+                                f"{lib.peps_last_error().decode()}")
+
+
+def dtype_code(dtype) -> int:
+    import torch
+    return {torch.float32: 0, torch.complex64: 1, torch.float64: 2, torch.complex128: 3}[dtype]
+
+
+def make_opts(m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN) -> RsvdOpts:
+    return RsvdOpts(int(m), int(p), int(q), int(seed) & (2 ** 64 - 1), int(sketch), int(prec), 0)
+
+
+__all__.append("make_opts")
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _workspace(nbytes: int, device):
+    import torch
+    buf = torch.empty(max(int(nbytes), 1) + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf, buf.data_ptr() + off
+
+
+@dataclass
+class _NetHolder:
+    net: Network
+    keep: list
+
+
+def _network(sites, d=None) -> _NetHolder:
+    """sites: list of rows of CUDA tensors [d][left][up][down][right]."""
+    nrow, ncol = len(sites), len(sites[0])
+    t0 = sites[0][0]
+    dt = dtype_code(t0.dtype)
+    for row in sites:
+        for t in row:
+            if not t.is_cuda or not t.is_contiguous() or t.dim() != 5 or t.dtype != t0.dtype:
+                raise PepsError(1, "site tensors must be contiguous 5-d CUDA tensors of one dtype")
+    bh = (C.c_int32 * max(1, nrow * (ncol - 1)))()
+    bv = (C.c_int32 * max(1, (nrow - 1) * ncol))()
+    for p in range(nrow):
+        for q in range(ncol - 1):
+            bh[p * (ncol - 1) + q] = sites[p][q].shape[4]
+    for p in range(nrow - 1):
+        for q in range(ncol):
+            bv[p * ncol + q] = sites[p][q].shape[3]
+    ptrs = (C.c_void_p * (nrow * ncol))(*[sites[p][q].data_ptr() for p in range(nrow)
+                                          for q in range(ncol)])
+    net = Network(nrow, ncol, int(t0.shape[0] if d is None else d), dt,
+                  C.cast(bh, C.POINTER(C.c_int32)), C.cast(bv, C.POINTER(C.c_int32)),
+                  C.cast(ptrs, C.POINTER(C.c_void_p)))
+    return _NetHolder(net, [bh, bv, ptrs, sites])
+
+
+class ContractPlan:
+    """Boundary-MPS contraction plan (Algorithms 2 and 3) with its workspace."""
+
+    def __init__(self, ket, bra, opts: RsvdOpts, direction: int = 0):
+        import torch
+        self._lib = load()
+        self._ket = _network(ket)
+        self._bra = _network(bra) if bra is not None else None
+        self._opts = opts
+        plan = C.c_void_p()
+        ws = C.c_size_t()
+        _check(self._lib.peps_contract_plan(C.byref(plan), C.byref(self._ket.net),
+                                            C.byref(self._bra.net) if self._bra else None,
+                                            C.byref(opts), int(direction), C.byref(ws)))
+        self._plan = plan
+        self.workspace_bytes = ws.value
+        self._buf, self._ws = _workspace(ws.value, ket[0][0].device)
+        n = C.c_int64()
+        _check(self._lib.peps_contract_sigma_count(plan, C.byref(n)))
+        self.sigma_count = n.value
+
+    def execute(self, stream=None):
+        _check(self._lib.peps_contract_execute(self._plan, C.c_void_p(self._ws),
+                                               C.c_size_t(self.workspace_bytes),
+                                               _stream_handle(stream)))
+
+    def result(self, stream=None, with_sigma=False):
+        import numpy as np
+        la, ph = C.c_double(), C.c_double()
+        sig = np.zeros(max(1, self.sigma_count), dtype=np.float64) if with_sigma else None
+        _check(self._lib.peps_contract_result(
+            self._plan, C.c_void_p(self._ws), _stream_handle(stream), C.byref(la), C.byref(ph),
+            sig.ctypes.data_as(C.POINTER(C.c_double)) if with_sigma else None))
+        if with_sigma:
+            return la.value, ph.value, sig[: self.sigma_count]
+        return la.value, ph.value
+
+    def __del__(self):
+        try:
+            if getattr(self, "_plan", None):
+                self._lib.peps_plan_destroy(self._plan)
+                self._plan = None
+        except Exception:
+            pass
+
+
+class EinsumsvdPlan:
+    """Batched einsumsvd plan (one zip-up step per instance)."""
+
+    def __init__(self, dtype, shapes, opts: RsvdOpts, instance_ids=None, device="cuda"):
+        self._lib = load()
+        n = len(shapes)
+        arr = (EinsumsvdShape * n)(*[EinsumsvdShape(*s) for s in shapes])
+        ids = None
+        if instance_ids is not None:
+            ids = (C.c_uint64 * n)(*[int(x) for x in instance_ids])
+        plan = C.c_void_p()
+        ws = C.c_size_t()
+        _check(self._lib.peps_einsumsvd_plan(C.byref(plan), dtype_code(dtype), n, arr, ids,
+                                             C.byref(opts), C.byref(ws)))
+        self._plan = plan
+        self.batch = n
+        self.workspace_bytes = ws.value
+        self._buf, self._ws = _workspace(ws.value, device)
+        self.ranks = []
+        for i in range(n):
+            k = C.c_int32()
+            _check(self._lib.peps_einsumsvd_rank(plan, i, C.byref(k)))
+            self.ranks.append(k.value)
+
+    def execute(self, io_list, stream=None):
+        """io_list: per instance (V, S, ket, bra, U, W, sigma, log_scale) tensors."""
+        arr = (EinsumsvdIO * self.batch)()
+        for i, io in enumerate(io_list):
+            arr[i] = EinsumsvdIO(*[t.data_ptr() if t is not None else None for t in io])
+        self._keep = (arr, io_list)
+        _check(self._lib.peps_einsumsvd_execute(self._plan, arr, C.c_void_p(self._ws),
+                                                C.c_size_t(self.workspace_bytes),
+                                                _stream_handle(stream)))
+
+    def __del__(self):
+        try:
+            if getattr(self, "_plan", None):
+                self._lib.peps_plan_destroy(self._plan)
+                self._plan = None
+        except Exception:
+            pass
+
+
+def boundary_contract(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN,
+                      direction=0, with_sigma=False, stream=None):
+    """Contract <bra|ket> (or the one-layer ket when bra is None) on the GPU.
+
+    Returns (log|v|, arg v) [and the per-step singular values]."""
+    plan = ContractPlan(ket, bra, make_opts(m, p, q, seed, sketch, prec), direction)
+    plan.execute(stream)
+    return plan.result(stream, with_sigma)

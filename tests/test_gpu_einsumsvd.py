@@ -1,0 +1,124 @@
+"""GPU parity of batched einsumsvd (Algorithm 3's einsumsvd line with
+Algorithm 4 applied implicitly) against the oracle, instance by instance.
+
+Checked per instance: singular values (normwise 1e-5 against sigma_1 for
+single precision, 1e-10 for FP64), the factors U and W after the shared gauge
+rule, and log(sigma_1).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import rsvd
+from paper_2006_15234_gb300 import libpeps
+from tests.gpu_util import TORCH_DT, tensor
+
+pytestmark = pytest.mark.gpu
+
+
+def _operands(rng, kL, t, a, b, d, Dk, Db, dtype):
+    cplx = dtype.startswith("c")
+
+    def r(shape):
+        x = rng.standard_normal(shape)
+        if cplx:
+            x = x + 1j * rng.standard_normal(shape)
+        return synth.round_to(x, dtype)
+    Dl, Du, Dx, De = Dk
+    DL, DU, DX, DE = Db
+    return (r((kL, t, a, Dl * DL)), r((a, Du * DU, b)), r((d, Dl, Du, Dx, De)),
+            r((d, DL, DU, DX, DE)))
+
+
+def _run_batch(cases, dtype, m, p, q, seed, prec=libpeps.PREC_PLAIN):
+    shapes, ios, outs = [], [], []
+    for (V, S, K, Kb) in cases:
+        kL, t, a, h = V.shape
+        _, v, b = S.shape
+        d, Dl, Du, Dx, De = K.shape
+        _, DL, DU, DX, DE = Kb.shape
+        shapes.append((kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE))
+    plan = libpeps.EinsumsvdPlan(TORCH_DT[dtype], shapes, libpeps.make_opts(m, p, q, seed, prec=prec),
+                                 instance_ids=list(range(100, 100 + len(cases))))
+    for i, (V, S, K, Kb) in enumerate(cases):
+        k = plan.ranks[i]
+        kL, t = V.shape[:2]
+        d, Dl, Du, Dx, De = K.shape
+        _, DL, DU, DX, DE = Kb.shape
+        b = S.shape[2]
+        U = torch.zeros((kL, t, k), dtype=TORCH_DT[dtype], device="cuda")
+        W = torch.zeros((k, Dx * DX, b, De * DE), dtype=TORCH_DT[dtype], device="cuda")
+        sg = torch.zeros(k, dtype=torch.float64, device="cuda")
+        lg = torch.zeros(1, dtype=torch.float64, device="cuda")
+        io = (tensor(V, dtype), tensor(S, dtype), tensor(K, dtype), tensor(Kb, dtype), U, W, sg, lg)
+        ios.append(io)
+        outs.append((U, W, sg, lg))
+    plan.execute(ios)
+    torch.cuda.synchronize()
+    return [(o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy(), float(o[3].cpu()[0]))
+            for o in outs]
+
+
+def _check(case, out, m, p, q, seed, inst, dtype):
+    V, S, K, Kb = case
+    U, W, s, l1 = rsvd.einsumsvd(V, S, K, Kb, m, p, q, seed, inst)
+    gU, gW, gs, gl = out
+    tol = 1e-10 if dtype in ("f64", "c128") else 1e-5
+    assert np.max(np.abs(gs - s)) <= tol * s[0]
+    assert gl == pytest.approx(l1, abs=tol)
+    # factors: the product U W (gauge independent) and each factor (gauge fixed)
+    k = len(s)
+    UW = U.reshape(-1, k) @ W.reshape(k, -1)
+    gUW = gU.reshape(-1, k) @ gW.reshape(k, -1)
+    assert np.linalg.norm(gUW - UW) <= 10 * tol * np.linalg.norm(UW)
+    ftol = 1e-8 if dtype in ("f64", "c128") else 2e-3
+    assert np.max(np.abs(gU - U)) <= ftol
+    assert np.max(np.abs(gW - W)) <= ftol * np.max(np.abs(W))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "f32", "c128", "f64"])
+def test_single_instance_ragged_tiles(dtype):
+    rng = np.random.default_rng(3)
+    # M = 20*9 = 180, N = 9*17*9 = 1377: several 64-wide tiles plus ragged tails
+    case = _operands(rng, 20, 9, 20, 17, 2, (3, 3, 3, 3), (3, 3, 3, 3), dtype)
+    out = _run_batch([case], dtype, 16, 8, 2, 42)
+    _check(case, out[0], 16, 8, 2, 42, 100, dtype)
+
+
+def test_batched_uneven_instances():
+    rng = np.random.default_rng(4)
+    cases = [
+        _operands(rng, 4, 4, 6, 5, 2, (2, 2, 2, 2), (2, 2, 2, 2), "c64"),
+        _operands(rng, 1, 9, 9, 9, 2, (3, 1, 3, 3), (3, 1, 3, 3), "c64"),     # kL = 1 row start
+        _operands(rng, 16, 16, 16, 1, 2, (4, 4, 4, 1), (4, 4, 4, 1), "c64"),  # last column: b = e = 1
+        _operands(rng, 12, 4, 7, 3, 3, (2, 2, 2, 2), (2, 1, 2, 2), "c64"),    # uneven ket/bra bonds
+    ]
+    outs = _run_batch(cases, "c64", 8, 4, 2, 9)
+    for i, (c, o) in enumerate(zip(cases, outs)):
+        _check(c, o, 8, 4, 2, 9, 100 + i, "c64")
+
+
+def test_exact_regime_l_equals_m():
+    """l = min(k+p, M, N) = M: the sketch spans the whole row space."""
+    rng = np.random.default_rng(5)
+    case = _operands(rng, 2, 4, 3, 4, 2, (2, 2, 2, 2), (2, 2, 2, 2), "c128")
+    out = _run_batch([case], "c128", 50, 8, 1, 1)
+    _check(case, out[0], 50, 8, 1, 1, 100, "c128")
+
+
+def test_c3_sample_instances_full_size():
+    """A sample of the batched workload's instances at their full sizes."""
+    cfg = synth.config("c3")
+    dims = synth.batched_dims(cfg)
+    pick = [0, 1, int(np.argmax([m * D ** 4 for m, D in dims[:16]]))]
+    cases, ms = [], []
+    for i in pick:
+        mm, D = dims[i]
+        inst = synth.batched_instance(cfg, i, mm, D)
+        cases.append((inst["V"], inst["S"], inst["ket"], inst["bra"]))
+        ms.append(mm)
+    # one plan per rank (k = m per instance)
+    for c, mm, i in zip(cases, ms, pick):
+        out = _run_batch([c], "f32", mm, cfg.p, cfg.q, cfg.omega_seed)
+        _check(c, out[0], mm, cfg.p, cfg.q, cfg.omega_seed, 100, "f32")
