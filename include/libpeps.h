@@ -184,6 +184,35 @@ peps_status peps_boundary_contract(const peps_network *ket, const peps_network *
 peps_status peps_boundary_workspace(const peps_network *ket, const peps_network *bra,
                                     const peps_rsvd_opts *opts, size_t *workspace_bytes);
 
+/* ------------------------------------------------------------------------
+ * Launch ledger (profiling).  A plan's execute is a fixed list of grouped
+ * kernel launches, each tagged with the stage of Algorithm 4 it serves
+ * ("product_sites", "orth_m", "svd_jacobi", ...).
+ * ------------------------------------------------------------------------ */
+
+/* Number of kernel launches one execute of the plan enqueues. */
+peps_status peps_plan_launch_count(const peps_plan *plan, int64_t *count);
+
+/* Stage tag (static for the plan's lifetime), algorithmic flops and
+ * algorithmic DRAM bytes of launch i (0 <= i < count). */
+peps_status peps_plan_launch_info(const peps_plan *plan, int64_t i, const char **tag,
+                                  double *flops, double *bytes);
+
+/* Execute once more (same rules as the execute calls; the plan must have
+ * been executed before) with a CUDA event after every launch, synchronise,
+ * and write launch i's device time in milliseconds to ms[i]. */
+peps_status peps_plan_profile(peps_plan *plan, void *workspace, size_t workspace_bytes,
+                              void *stream, double *ms);
+
+/* Host-only check of a plan against concrete buffers: rebuilds the launch
+ * descriptors for `workspace` (and io, for einsumsvd plans; NULL otherwise)
+ * and verifies that every byte range any kernel may touch lies inside the
+ * workspace or a caller tensor of the planned shape.  Enqueues nothing and
+ * does not dereference any pointer, so it runs without a GPU; returns
+ * PEPS_ERR_ARG naming the first offending launch and field. */
+peps_status peps_plan_validate(peps_plan *plan, void *workspace, size_t workspace_bytes,
+                               const peps_einsumsvd_io *io);
+
 #ifdef __cplusplus
 }
 #endif

@@ -353,18 +353,155 @@ std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
   return "";
 }
 
+
+// ---- host-side access validator ---------------------------------------------
+// Recomputes, from every launch descriptor, the byte range each kernel may
+// read or write and checks it lies inside the workspace or a caller tensor.
+struct Extent { uintptr_t lo, hi; const char *what; };
+
+struct Checker {
+  std::vector<Extent> ext;
+  std::string err;
+  void need(const void *p, double nbytes, const char *op, const char *field) {
+    if (!err.empty() || nbytes <= 0) return;
+    if (!p) { err = std::string(op) + "." + field + " is NULL"; return; }
+    const uintptr_t lo = (uintptr_t)p, hi = lo + (uintptr_t)nbytes;
+    for (auto &e : ext)
+      if (lo >= e.lo && hi <= e.hi) return;
+    char b[256];
+    snprintf(b, sizeof b, "%s.%s: [%#lx, +%.0f bytes) outside every buffer", op, field,
+             (unsigned long)lo, nbytes);
+    err = b;
+  }
+};
+
+std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Checker &C) {
+  C.ext.push_back(Extent{ws, ws + ws_bytes, "workspace"});
+  const int dt = P->dt;
+  const double es = dtype_size(dt), as = acc_size(dt);
+  const uint8_t *blob = P->blob.data();
+  for (const Op &op : P->ops) {
+    const char *tag = op.tag.c_str();
+    const void *d = blob + op.desc_off;
+    switch (op.kind) {
+      case Op::GEMM:
+      case Op::GEMM_ATOMIC:
+        for (int i = 0; i < op.nd; ++i) {
+          const GemmDesc &g = ((const GemmDesc *)d)[i];
+          if (g.ksplit * (int64_t)g.kchunk < g.K) C.err = std::string(tag) + ": K chunks do not cover K";
+          C.need(g.A, es * ((g.batch - 1) * (double)g.sAb + (g.M - 1) * (double)g.sAm + (g.K - 1) * (double)g.sAk + 1), tag, "A");
+          C.need(g.B, es * ((g.batch - 1) * (double)g.sBb + (g.K - 1) * (double)g.sBk + (g.N - 1) * (double)g.sBn + 1), tag, "B");
+          C.need(g.C, (op.kind == Op::GEMM_ATOMIC ? as : es) *
+                          ((g.batch - 1) * (double)g.sCb + (g.M - 1) * (double)g.sCm + (g.N - 1) * (double)g.sCn + 1), tag, "C");
+          if (g.alpha_dev) C.need(g.alpha_dev, 8, tag, "alpha_dev");
+        }
+        break;
+      case Op::SANDWICH:
+        for (int i = 0; i < op.nd; ++i) {
+          const SandwichDesc &w = ((const SandwichDesc *)d)[i];
+          const double N = (double)w.Dx * w.DX * w.B * w.De * w.DE;
+          const double T2 = (double)w.Dl * w.DL * w.Du * w.DU * w.B;
+          const double nin = w.adjoint ? T2 : N, nout = w.adjoint ? N : T2;
+          if (w.ld_in < nin || w.ld_out < nout) C.err = std::string(tag) + ": leading dimension too small";
+          C.need(w.in, es * ((w.ell - 1) * (double)w.ld_in + nin), tag, "in");
+          C.need(w.out, es * ((w.ell - 1) * (double)w.ld_out + nout), tag, "out");
+          C.need(w.K, es * w.d * w.Dl * w.Du * w.Dx * w.De, tag, "K");
+          C.need(w.Kb, es * w.d * w.DL * w.DU * w.DX * w.DE, tag, "Kb");
+          if ((int64_t)w.nblocks * w.items_per_block < (int64_t)w.ell * w.B) C.err = std::string(tag) + ": items not covered";
+        }
+        break;
+      case Op::SKETCH:
+        for (int i = 0; i < op.nd; ++i) {
+          const SketchDesc &k = ((const SketchDesc *)d)[i];
+          C.need(k.X, es * ((k.ell - 1) * (double)k.ld + k.N), tag, "X");
+        }
+        break;
+      case Op::CHOL:
+        for (int i = 0; i < op.nd; ++i) {
+          const CholDesc &c = ((const CholDesc *)d)[i];
+          const double n2 = (double)c.n * c.n;
+          C.need(c.G, as * n2, tag, "G");
+          C.need(c.T, es * n2, tag, "T");
+          C.need(c.R, as * n2, tag, "R");
+          if (c.Rprev) { C.need(c.Rprev, as * n2, tag, "Rprev"); C.need(c.Rout, as * n2, tag, "Rout"); }
+          if (c.n > 4096) C.err = std::string(tag) + ": n above the pivot-flag buffer";
+        }
+        break;
+      case Op::JACOBI:
+        for (int i = 0; i < op.nd; ++i) {
+          const JacobiDesc &j = ((const JacobiDesc *)d)[i];
+          C.need(j.Rb, as * (double)j.n * j.n, tag, "Rb");
+          C.need(j.Mw, as * (double)j.n * j.n, tag, "Mw");
+          C.need(j.sig, 8.0 * j.n, tag, "sig");
+        }
+        break;
+      case Op::FINALIZE:
+        for (int i = 0; i < op.nd; ++i) {
+          const FinalizeDesc &f = ((const FinalizeDesc *)d)[i];
+          C.need(f.Mw, as * (double)f.n * f.n, tag, "Mw");
+          C.need(f.sig, 8.0 * f.n, tag, "sig");
+          C.need(f.P, es * (double)f.n * f.M, tag, "P");
+          C.need(f.g, es * (double)f.M, tag, "g");
+          C.need(f.Ut, es * (double)f.n * f.k, tag, "Ut");
+          C.need(f.sigma_out, 8.0 * f.k, tag, "sigma_out");
+          C.need(f.log_out, 8, tag, "log_out");
+          C.need(f.inv_s1, 8, tag, "inv_s1");
+          if (f.k > f.n || f.n > 1024) C.err = std::string(tag) + ": k > n or n > 1024";
+        }
+        break;
+      case Op::ZERO:
+        for (int i = 0; i < op.nd; ++i) {
+          const ZeroDesc &z = ((const ZeroDesc *)d)[i];
+          C.need(z.p, 8.0 * z.words, tag, "p");
+        }
+        break;
+      case Op::SITE:
+        for (int i = 0; i < op.nd; ++i) {
+          const SiteDesc &s = ((const SiteDesc *)d)[i];
+          C.need(s.K, es * s.d * s.Dl * s.Du * s.Dx * s.De, tag, "K");
+          C.need(s.Kb, es * s.d * s.DL * s.DU * s.DX * s.DE, tag, "Kb");
+          if (s.mode == 1) C.need(s.S, es * (double)s.Du * s.DU * s.B, tag, "S");
+          C.need(s.out, es * (double)s.total, tag, "out");
+        }
+        break;
+      case Op::SCALAR: {
+        const ScalarDesc &sd = op.scalar;
+        const void *const *sites = (const void *const *)(blob + op.aux_off[0]);
+        const int32_t *lb = (const int32_t *)(blob + op.aux_off[1]);
+        const int32_t *rb = (const int32_t *)(blob + op.aux_off[2]);
+        int maxb = 1;
+        for (int q = 0; q < sd.ncol; ++q) {
+          C.need(sites[q], es * (double)lb[q] * rb[q], tag, "site");
+          maxb = std::max(maxb, std::max(lb[q], rb[q]));
+        }
+        C.need(sd.scratch, 2.0 * maxb * as, tag, "scratch");
+        C.need(sd.out, 16, tag, "out");
+        C.need(sd.logs, 8.0 * sd.nlogs, tag, "logs");
+        break;
+      }
+      case Op::FILL:
+        C.need(op.fill_ptr, es * (double)op.fill_n, tag, "ptr");
+        break;
+    }
+    if (!C.err.empty()) return C.err;
+  }
+  if (P->blob_off + P->blob.size() > ws_bytes) return "descriptor blob beyond the workspace";
+  return "";
+}
+
 peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io) {
   Builder B;
   std::string e = P->kind == peps_plan::EINSUMSVD ? build_einsumsvd(P, (uintptr_t)ws, io, B)
                                                    : build_contract(P, (uintptr_t)ws, B);
   if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
+  P->ws_bytes = finish(B, &P->blob_off);   // needs the blob size: before the move
   P->ops = std::move(B.ops);
   P->blob = std::move(B.blob);
-  P->ws_bytes = finish(B, &P->blob_off);
   return PEPS_OK;
 }
 
-peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, bool upload) {
+peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, bool upload,
+                    cudaEvent_t *events = nullptr) {
   if (!ws) return fail(PEPS_ERR_WORKSPACE, "workspace is NULL");
   if ((uintptr_t)ws & 255) return fail(PEPS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   if (ws_bytes < P->ws_bytes)
@@ -376,6 +513,7 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
     CUDA_TRY(cudaMemcpyAsync(blob, P->blob.data(), P->blob.size(), cudaMemcpyHostToDevice, s));
   }
   const int dt = P->dt;
+  if (events) CUDA_TRY(cudaEventRecord(events[0], s));
   for (const Op &op : P->ops) {
     const void *d = blob + op.desc_off;
     const int64_t *pre = (const int64_t *)(blob + op.prefix_off);
@@ -401,6 +539,7 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
       }
       case Op::FILL: launch_fill(dt, op.fill_ptr, op.fill_n, op.fill_value, s); break;
     }
+    if (events) CUDA_TRY(cudaEventRecord(events[&op - P->ops.data() + 1], s));
   }
   CUDA_TRY(cudaGetLastError());
   return PEPS_OK;
@@ -582,6 +721,85 @@ peps_status peps_boundary_contract(const peps_network *ket, const peps_network *
   if (s == PEPS_OK) s = peps_contract_result(p, workspace, stream, log_abs, phase, nullptr);
   peps_plan_destroy(p);
   return s;
+}
+
+peps_status peps_plan_launch_count(const peps_plan *plan, int64_t *count) {
+  if (!plan || !count) return fail(PEPS_ERR_ARG, "NULL argument");
+  *count = (int64_t)plan->ops.size();
+  return PEPS_OK;
+}
+
+peps_status peps_plan_launch_info(const peps_plan *plan, int64_t i, const char **tag, double *flops,
+                                  double *bytes) {
+  if (!plan) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (i < 0 || i >= (int64_t)plan->ops.size()) return fail(PEPS_ERR_ARG, "launch index out of range");
+  const Op &op = plan->ops[i];
+  if (tag) *tag = op.tag.c_str();
+  if (flops) *flops = op.flops;
+  if (bytes) *bytes = op.bytes;
+  return PEPS_OK;
+}
+
+peps_status peps_plan_profile(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream,
+                              double *ms) {
+  g_last_error.clear();
+  if (!plan || !ms) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (!plan->built || plan->built_base != (uintptr_t)workspace)
+    return fail(PEPS_ERR_ARG, "execute the plan on this workspace before profiling it");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (in_capture(s)) return fail(PEPS_ERR_CAPTURE, "profiling during stream capture");
+  const size_t n = plan->ops.size();
+  std::vector<cudaEvent_t> ev(n + 1);
+  for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+  peps_status st = enqueue(plan, workspace, workspace_bytes, s, false, ev.data());
+  if (st == PEPS_OK) {
+    cudaError_t e = cudaEventSynchronize(ev[n]);
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      ms[i] = t;
+    }
+    if (e != cudaSuccess) st = fail(PEPS_ERR_CUDA, "profiling events: %s", cudaGetErrorString(e));
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  return st;
+}
+
+peps_status peps_plan_validate(peps_plan *plan, void *workspace, size_t workspace_bytes,
+                               const peps_einsumsvd_io *io) {
+  g_last_error.clear();
+  if (!plan || !workspace) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (plan->kind == peps_plan::EINSUMSVD && !io) return fail(PEPS_ERR_ARG, "einsumsvd plans need io");
+  if (peps_status s = rebuild(plan, workspace, plan->kind == peps_plan::EINSUMSVD ? io : nullptr)) return s;
+  plan->built = false;            // force an upload at the next execute
+  Checker C;
+  const double es = dtype_size(plan->dt);
+  if (plan->kind == peps_plan::EINSUMSVD) {
+    for (size_t i = 0; i < plan->insts.size(); ++i) {
+      const Inst &I = plan->insts[i];
+      auto add = [&](const void *p, double n) { C.ext.push_back(Extent{(uintptr_t)p, (uintptr_t)p + (uintptr_t)n, "io"}); };
+      add(io[i].V, es * I.kL * I.t * I.a * I.h);
+      add(io[i].S, es * I.a * I.v * I.b);
+      add(io[i].ket, es * I.d * I.Dl * I.Du * I.Dx * I.De);
+      add(io[i].bra, es * I.d * I.DL * I.DU * I.DX * I.DE);
+      add(io[i].U, es * (double)I.M * I.k);
+      add(io[i].W, es * (double)I.k * I.N);
+      add(io[i].sigma, 8.0 * I.k);
+      if (io[i].log_scale) add(io[i].log_scale, 8);
+    }
+  } else {
+    for (const Net *n : {&plan->ket, &plan->bra}) {
+      if (n == &plan->bra && plan->one_layer) continue;
+      for (size_t i = 0; i < n->site.size(); ++i) {
+        const SiteDims &d = n->dims[i];
+        C.ext.push_back(Extent{(uintptr_t)n->site[i],
+                               (uintptr_t)n->site[i] + (uintptr_t)(es * d.d * d.Dl * d.Du * d.Dx * d.De), "site"});
+      }
+    }
+  }
+  std::string e = validate_ops(plan, (uintptr_t)workspace, workspace_bytes, C);
+  if (!e.empty()) return fail(PEPS_ERR_ARG, "%s", e.c_str());
+  return PEPS_OK;
 }
 
 }  // extern "C"

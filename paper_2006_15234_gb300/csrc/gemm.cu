@@ -3,10 +3,13 @@
 // Serves every dense contraction of one einsumsvd step whose operands are
 // already laid out as matrices: the two m^2 stages of the implicit product
 // (boundary site S and carry V, Sec. IV-A / Table 2), their adjoints, the
-// Gram matrices of CholeskyQR (split over K, accumulated atomically in FP64),
+// Gram matrices of CholeskyQR (products of the single-precision inputs formed
+// exactly in FP64, summed in FP64, split over K and combined atomically),
 // the R^-1 applications and the U = P U~, W = U~^H B epilogue (Algorithm 4's
 // last lines).  Strides are arbitrary; each tile load picks the coalesced
 // direction from the unit stride.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -15,7 +18,6 @@ namespace peps {
 namespace {
 
 constexpr int BM = kGemmBM, BN = kGemmBN, BK = 16, NT = 256;
-constexpr int kFoldTiles = 8;   // K tiles per single-precision partial sum
 
 __device__ __forceinline__ int find_desc(const int64_t *prefix, int nd, int64_t blk) {
   int lo = 0, hi = nd - 1;
@@ -58,20 +60,15 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc *__restrict__ d
   const bool a_kc = (g.sAk == 1), a_mc = (g.sAm == 1);
   const bool b_nc = (g.sBn == 1), b_kc = (g.sBk == 1);
 
-  T acc[4][4];
-  Acc acc64[ATOMIC ? 4 : 1][ATOMIC ? 4 : 1];
+  // Store mode accumulates in the working type; Gram (atomic) mode forms each
+  // product of single-precision inputs exactly in FP64 and sums in FP64.
+  using AccT = typename std::conditional<ATOMIC, Acc, T>::type;
+  AccT acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = zero<T>();
-  if (ATOMIC) {
-#pragma unroll
-    for (int i = 0; i < (ATOMIC ? 4 : 1); ++i)
-#pragma unroll
-      for (int j = 0; j < (ATOMIC ? 4 : 1); ++j) acc64[i][j] = widen(zero<T>());
-  }
+    for (int j = 0; j < 4; ++j) acc[i][j] = AccT{};
 
-  int tile_count = 0;
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < (BM * BK) / NT; ++r) {
@@ -106,19 +103,12 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc *__restrict__ d
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma_(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-    // Gram accumulation: short single-precision partial sums folded into FP64
-    if (ATOMIC && ((++tile_count & (kFoldTiles - 1)) == 0 || k0 + BK >= kend)) {
-#pragma unroll
-      for (int i = 0; i < (ATOMIC ? 4 : 1); ++i)
-#pragma unroll
-        for (int j = 0; j < (ATOMIC ? 4 : 1); ++j) {
-          acc64[i][j] = add(acc64[i][j], widen(acc[i][j]));
-          acc[i][j] = zero<T>();
+        for (int j = 0; j < 4; ++j) {
+          if constexpr (ATOMIC) acc[i][j] = fma_(widen(a[i]), widen(b[j]), acc[i][j]);
+          else acc[i][j] = fma_(a[i], b[j], acc[i][j]);
         }
     }
+    __syncthreads();
   }
 
   double alpha = g.alpha;
@@ -132,8 +122,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc *__restrict__ d
       const int n = n0 + tx + 16 * j;
       if (n >= g.N) continue;
       const int64_t off = (int64_t)bi * g.sCb + (int64_t)m * g.sCm + (int64_t)n * g.sCn;
-      if (ATOMIC) {
-        Acc v = acc64[ATOMIC ? i : 0][ATOMIC ? j : 0];
+      if constexpr (ATOMIC) {
+        Acc v = acc[i][j];
         if (g.conjC) v = conj_(v);
         atomic_add_acc((Acc *)g.C + off, scale(v, alpha));
       } else {

@@ -25,6 +25,8 @@ struct Op {
   int64_t fill_n = 0;
   double fill_value = 0.0;
   std::string tag;        // stage name (profiling ledger)
+  double flops = 0.0;     // algorithmic flops of the launch
+  double bytes = 0.0;     // algorithmic DRAM bytes of the launch
 };
 
 struct ZeroDesc {

@@ -5,7 +5,7 @@
 //   X <- Omega (Philox), g <- gauge vector
 //   Y <- A X;              P <- orth(Y)            (CholeskyQR2)
 //   repeat q:  Z <- A^H P; Q <- orth(Z);  Y <- A Q;  P <- orth(Y)
-//   Z <- A^H P  (= (P^H A)^H);  R_B <- R factor of Z (CholeskyQR2)
+//   Z <- A^H P  (= (P^H A)^H);  R_B <- Cholesky factor of the FP64 Gram Z^H Z
 //   U~, Sigma <- one-sided Jacobi SVD of R_B^H;  sort / truncate / gauge
 //   U <- P U~;   W <- U~^H P^H A / sigma_1
 //
@@ -72,8 +72,18 @@ void push_grouped(Builder &B, Op::Kind kind, const void *descs, size_t desc_size
 
 void push_gemm(Builder &B, std::vector<GemmDesc> &d, bool atomic, const char *tag) {
   std::vector<int64_t> bl(d.size());
-  for (size_t i = 0; i < d.size(); ++i) bl[i] = gemm_blocks(d[i]);
+  double fl = 0, by = 0;
+  const double mult = dtype_complex(B.dt) ? 8.0 : 2.0, es = dtype_size(B.dt);
+  for (size_t i = 0; i < d.size(); ++i) {
+    bl[i] = gemm_blocks(d[i]);
+    const GemmDesc &g = d[i];
+    fl += mult * (double)g.M * g.N * g.K * g.batch;
+    by += es * ((double)g.M * g.K * (g.sAb ? g.batch : 1) + (double)g.K * g.N * (g.sBb ? g.batch : 1)) +
+          (atomic ? acc_size(B.dt) : es) * (double)g.M * g.N * g.batch;
+  }
+  const size_t before = B.ops.size();
   push_grouped(B, atomic ? Op::GEMM_ATOMIC : Op::GEMM, d.data(), sizeof(GemmDesc), (int)d.size(), bl, tag);
+  if (B.ops.size() > before) { B.ops.back().flops = fl; B.ops.back().bytes = by; }
 }
 
 void push_zero(Builder &B, const std::vector<std::pair<void *, int64_t>> &regions, const char *tag) {
@@ -104,6 +114,9 @@ void emit_sketch(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
     d.push_back(gg); bl.push_back(gg.nblocks);
   }
   push_grouped(B, Op::SKETCH, d.data(), sizeof(SketchDesc), (int)d.size(), bl, "sketch");
+  double by = 0;
+  for (auto &s : d) by += (double)dtype_size(B.dt) * s.N * s.ell;
+  B.ops.back().bytes = by;
 }
 
 SandwichDesc mk_sandwich(const Inst &I, const void *in, void *out, bool adjoint) {
@@ -132,7 +145,17 @@ void push_sandwich(Builder &B, std::vector<SandwichDesc> &d, const char *tag) {
     s.nblocks = (int)ceil_div((int64_t)s.ell * s.B, per);
     bl.push_back(s.nblocks);
   }
+  double fl = 0, by = 0;
+  const double mult = dtype_complex(B.dt) ? 8.0 : 2.0, es = dtype_size(B.dt);
+  for (auto &s : d) {
+    const double P1 = s.Dl * s.Du, Q1 = s.Dx * s.De, P2 = s.DL * s.DU, Q2 = s.DX * s.DE;
+    const double items_s = (double)s.ell * s.B;
+    fl += mult * items_s * s.d * (s.adjoint ? (P1 * P2 * Q2 + Q1 * P1 * Q2) : (P1 * Q1 * Q2 + P1 * Q2 * P2));
+    by += es * items_s * (P1 * P2 + Q1 * Q2);
+  }
+  const size_t before = B.ops.size();
   push_grouped(B, Op::SANDWICH, d.data(), sizeof(SandwichDesc), (int)d.size(), bl, tag, smem);
+  if (B.ops.size() > before) { B.ops.back().flops = fl; B.ops.back().bytes = by; }
 }
 
 // Y <- A X (src N-side [j][n] -> dst M-side [j][mrow])
@@ -226,9 +249,9 @@ void emit_orth(Builder &B, std::vector<Inst *> &I, bool mside) {
 }
 
 void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
-  // R_B: CholeskyQR2 of Z = (P^H A)^H, R_B = R2 R1
-  emit_cqr_pass(B, I, false, &Inst::Z, &Inst::X, &Inst::R1, nullptr, nullptr, true, "svd_qr");
-  emit_cqr_pass(B, I, false, &Inst::X, nullptr, &Inst::R2, &Inst::R1, &Inst::Rout, false, "svd_qr");
+  // R_B: Cholesky factor of the FP64 Gram of Z = (P^H A)^H, so that
+  // R_B^H R_B = B B^H with B = P^H A; its singular values are those of B.
+  emit_cqr_pass(B, I, false, &Inst::Z, nullptr, &Inst::Rout, nullptr, nullptr, false, "svd_qr");
   std::vector<JacobiDesc> jd;
   std::vector<FinalizeDesc> fd;
   for (Inst *p : I) {

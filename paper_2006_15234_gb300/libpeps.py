@@ -26,6 +26,7 @@ EXPORTED_SYMBOLS = [
     "peps_einsumsvd_plan", "peps_einsumsvd_rank", "peps_einsumsvd_execute", "peps_plan_destroy",
     "peps_contract_plan", "peps_contract_execute", "peps_contract_result",
     "peps_contract_sigma_count", "peps_boundary_contract", "peps_boundary_workspace",
+    "peps_plan_launch_count", "peps_plan_launch_info", "peps_plan_profile", "peps_plan_validate",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -107,6 +108,15 @@ def load():
     lib.peps_boundary_workspace.restype = st
     lib.peps_boundary_workspace.argtypes = [C.POINTER(Network), C.POINTER(Network), C.POINTER(RsvdOpts),
                                             C.POINTER(C.c_size_t)]
+    lib.peps_plan_launch_count.restype = st
+    lib.peps_plan_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.peps_plan_launch_info.restype = st
+    lib.peps_plan_launch_info.argtypes = [vp, C.c_int64, C.POINTER(C.c_char_p),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.peps_plan_profile.restype = st
+    lib.peps_plan_profile.argtypes = [vp, vp, C.c_size_t, vp, C.POINTER(C.c_double)]
+    lib.peps_plan_validate.restype = st
+    lib.peps_plan_validate.argtypes = [vp, vp, C.c_size_t, C.POINTER(EinsumsvdIO)]
     _lib = lib
     return lib
 
@@ -175,7 +185,34 @@ def _network(sites, d=None) -> _NetHolder:
     return _NetHolder(net, [bh, bv, ptrs, sites])
 
 
-class ContractPlan:
+class _Ledger:
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        _check(self._lib.peps_plan_launch_count(self._plan, C.byref(n)))
+        return n.value
+
+    def launches(self):
+        """[(stage tag, algorithmic flops, algorithmic bytes)] per kernel launch."""
+        out = []
+        for i in range(self.launch_count()):
+            tag, fl, by = C.c_char_p(), C.c_double(), C.c_double()
+            _check(self._lib.peps_plan_launch_info(self._plan, i, C.byref(tag), C.byref(fl),
+                                                   C.byref(by)))
+            out.append((tag.value.decode(), fl.value, by.value))
+        return out
+
+    def profile(self, stream=None):
+        """Device time (ms) of every launch of one more execute."""
+        import numpy as np
+        n = self.launch_count()
+        ms = np.zeros(max(n, 1), dtype=np.float64)
+        _check(self._lib.peps_plan_profile(self._plan, C.c_void_p(self._ws),
+                                           C.c_size_t(self.workspace_bytes), _stream_handle(stream),
+                                           ms.ctypes.data_as(C.POINTER(C.c_double))))
+        return ms[:n]
+
+
+class ContractPlan(_Ledger):
     """Boundary-MPS contraction plan (Algorithms 2 and 3) with its workspace."""
 
     def __init__(self, ket, bra, opts: RsvdOpts, direction: int = 0):
@@ -221,7 +258,7 @@ class ContractPlan:
             pass
 
 
-class EinsumsvdPlan:
+class EinsumsvdPlan(_Ledger):
     """Batched einsumsvd plan (one zip-up step per instance)."""
 
     def __init__(self, dtype, shapes, opts: RsvdOpts, instance_ids=None, device="cuda"):

@@ -1,0 +1,136 @@
+"""Host-side bounds check of every launch descriptor (no GPU needed).
+
+peps_plan_validate rebuilds a plan's launch schedule for concrete (fake)
+addresses and checks that each kernel's reachable byte range lies inside the
+workspace or a caller tensor of the planned shape.  Every shape the GPU tests
+and the benchmark use is checked here before it ever reaches a GPU.
+"""
+import ctypes as C
+
+import pytest
+
+import synth
+
+L = pytest.importorskip("paper_2006_15234_gb300.libpeps")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2006_15234_gb300 import build
+    build.build_library()
+    return L.load()
+
+
+class FakeHeap:
+    """Disjoint, page-aligned fake device addresses with guard gaps."""
+
+    def __init__(self):
+        self.top = 1 << 40
+
+    def __call__(self, nbytes):
+        p = self.top
+        self.top += ((int(nbytes) + 4095) // 4096 + 16) * 4096
+        return p
+
+
+ES = {0: 4, 1: 8, 2: 8, 3: 16}
+
+
+def _einsumsvd_ok(lib, dt, shapes, m, p, q):
+    heap = FakeHeap()
+    n = len(shapes)
+    arr = (L.EinsumsvdShape * n)(*[L.EinsumsvdShape(*s) for s in shapes])
+    plan, ws = C.c_void_p(), C.c_size_t()
+    opts = L.make_opts(m, p, q, 1)
+    assert lib.peps_einsumsvd_plan(C.byref(plan), dt, n, arr, None, C.byref(opts), C.byref(ws)) == 0
+    es = ES[dt]
+    io = (L.EinsumsvdIO * n)()
+    for i, s in enumerate(shapes):
+        kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE = s
+        k = C.c_int32()
+        lib.peps_einsumsvd_rank(plan, i, C.byref(k))
+        M, N = kL * t, Dx * DX * b * De * DE
+        io[i] = L.EinsumsvdIO(heap(es * kL * t * a * Dl * DL), heap(es * a * Du * DU * b),
+                              heap(es * d * Dl * Du * Dx * De), heap(es * d * DL * DU * DX * DE),
+                              heap(es * M * k.value), heap(es * k.value * N), heap(8 * k.value), heap(8))
+    wsp = heap(ws.value)
+    r = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, io)
+    msg = lib.peps_last_error().decode()
+    # one byte less of workspace must be refused
+    r2 = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value - 1, io)
+    lib.peps_plan_destroy(plan)
+    return r, msg, r2
+
+
+@pytest.mark.parametrize("dt", [0, 1, 2, 3])
+def test_einsumsvd_test_shapes(lib, dt):
+    shapes = [(20, 9, 20, 17, 2, 3, 3, 3, 3, 3, 3, 3, 3), (4, 4, 6, 5, 2, 2, 2, 2, 2, 2, 2, 2, 2),
+              (1, 9, 9, 9, 2, 3, 1, 3, 3, 3, 1, 3, 3), (16, 16, 16, 1, 2, 4, 4, 4, 1, 4, 4, 4, 1),
+              (12, 4, 7, 3, 3, 2, 2, 2, 2, 2, 1, 2, 2), (2, 4, 3, 4, 2, 2, 2, 2, 2, 2, 2, 2, 2)]
+    r, msg, r2 = _einsumsvd_ok(lib, dt, shapes, 8, 4, 2)
+    assert r == 0, msg
+    assert r2 != 0
+
+
+def test_batched_workload_sample(lib):
+    cfg = synth.config("c3")
+    dims = synth.batched_dims(cfg)[:64]
+    shapes = [(m, D * D, m, m, 2, D, D, D, D, D, D, D, D) for m, D in dims]
+    r, msg, _ = _einsumsvd_ok(lib, 0, shapes, 128, cfg.p, cfg.q)
+    assert r == 0, msg
+
+
+def _net(heap, sites_shape, dt):
+    nrow, ncol = len(sites_shape), len(sites_shape[0])
+    es = ES[dt]
+    bh = (C.c_int32 * max(1, nrow * (ncol - 1)))()
+    bv = (C.c_int32 * max(1, (nrow - 1) * ncol))()
+    for p in range(nrow):
+        for q in range(ncol - 1):
+            bh[p * (ncol - 1) + q] = sites_shape[p][q][4]
+    for p in range(nrow - 1):
+        for q in range(ncol):
+            bv[p * ncol + q] = sites_shape[p][q][3]
+    ptrs = (C.c_void_p * (nrow * ncol))()
+    for p in range(nrow):
+        for q in range(ncol):
+            s = sites_shape[p][q]
+            ptrs[p * ncol + q] = heap(es * s[0] * s[1] * s[2] * s[3] * s[4])
+    net = L.Network(nrow, ncol, sites_shape[0][0][0], dt, C.cast(bh, C.POINTER(C.c_int32)),
+                    C.cast(bv, C.POINTER(C.c_int32)), C.cast(ptrs, C.POINTER(C.c_void_p)))
+    return net, (bh, bv, ptrs)
+
+
+@pytest.mark.parametrize("key,dt,two", [("c1", 2, False), ("c2", 1, True), ("c4", 0, True),
+                                        ("c5", 1, True)])
+def test_contract_workloads(lib, key, dt, two):
+    cfg = synth.config(key)
+    shp = [[synth.site_shape(cfg.nrow, cfg.ncol, p, q, cfg.d, cfg.D) for q in range(cfg.ncol)]
+           for p in range(cfg.nrow)]
+    heap = FakeHeap()
+    net, keep = _net(heap, shp, dt)
+    plan, ws = C.c_void_p(), C.c_size_t()
+    opts = L.make_opts(cfg.m, cfg.p, cfg.q, 1)
+    assert lib.peps_contract_plan(C.byref(plan), C.byref(net), C.byref(net) if two else None,
+                                  C.byref(opts), 0, C.byref(ws)) == 0, lib.peps_last_error()
+    wsp = heap(ws.value)
+    r = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None)
+    assert r == 0, lib.peps_last_error().decode()
+    lib.peps_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("shape,D,m", [((3, 3), 2, 16), ((3, 5), 2, 64), ((1, 4), 2, 4),
+                                       ((4, 1), 2, 4), ((5, 3), 2, 5), ((3, 6), 3, 9)])
+def test_contract_test_shapes(lib, shape, D, m):
+    nr, nc = shape
+    shp = [[synth.site_shape(nr, nc, p, q, 2, D) for q in range(nc)] for p in range(nr)]
+    for dt in (1, 3):
+        heap = FakeHeap()
+        net, keep = _net(heap, shp, dt)
+        plan, ws = C.c_void_p(), C.c_size_t()
+        opts = L.make_opts(m, 8, 1, 1)
+        assert lib.peps_contract_plan(C.byref(plan), C.byref(net), C.byref(net), C.byref(opts), 0,
+                                      C.byref(ws)) == 0
+        wsp = heap(ws.value)
+        assert lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None) == 0, lib.peps_last_error()
+        lib.peps_plan_destroy(plan)
