@@ -1,0 +1,378 @@
+"""Benchmark: boundary-MPS contraction of a synthetic PEPS (implicit randomized
+SVD einsumsvd, two-layer zip-up) on one or more GB300s.
+
+One step = one full contraction <psi|psi> of the workload's PEPS (every row,
+every einsumsvd of Algorithms 2-4), inputs resident in HBM.  Prints one JSON
+line (rank 0).  ``--impl reference`` times the CPU oracle instead (the
+reference arm of this repository: a plain FP64 NumPy replay of the paper's
+algorithms) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "PEPS contraction s & einsumsvd TFLOP/s, mixed vs plain FP32 at 1e-5 rel err"
+L2_BYTES = 129 * 2 ** 20
+
+
+def algorithmic_flops(shapes, q, cplx):
+    """Algorithmic flops of one contraction from its einsumsvd step shapes.
+
+    Per step (complex MAC = 8 flops, real MAC = 2):
+      (2q+2) implicit products, each l*(b d D^6-type site stages + the two
+      m^2 stages) as counted by the plan (Table 2's two-layer terms);
+      q+1 orthogonalisations of the M x l block and q of the N x l block at
+      2 L l^2 (Householder-equivalent); the R factor of the N x l block of
+      P^H A (L l^2); U = P U~ (M l k) and W = U~^H B (k l N).
+    """
+    mult = 8.0 if cplx else 2.0
+    tot = 0.0
+    for s in shapes:
+        M, N, ell, k, prod = s["M"], s["N"], s["ell"], s["k"], s["prod_macs"]
+        macs = (2 * q + 2) * prod + (q + 1) * 2 * M * ell ** 2 + q * 2 * N * ell ** 2
+        macs += N * ell ** 2 + M * ell * k + k * ell * N
+        tot += mult * macs
+    return tot
+
+
+def step_shapes(cfg):
+    """Shapes of every einsumsvd step of the sweep (same rule as the library)."""
+    nrow, ncol, d, D, m, p = cfg.nrow, cfg.ncol, cfg.d, cfg.D, cfg.m, cfg.p
+    two = cfg.two_layer
+    dims = [[synth.site_shape(nrow, ncol, r, c, d, D) for c in range(ncol)] for r in range(nrow)]
+    bra = (lambda r, c: dims[r][c]) if two else (lambda r, c: (1, 1, 1, 1, 1))
+    bound = [(dims[0][c][1] * bra(0, c)[1], dims[0][c][3] * bra(0, c)[3], dims[0][c][4] * bra(0, c)[4])
+             for c in range(ncol)]
+    out = []
+    for r in range(1, nrow):
+        new = [None] * ncol
+        kprev = 1
+        for i in range(1, ncol):
+            kp, bp = dims[r][i - 1], bra(r, i - 1)
+            kc, bc = dims[r][i], bra(r, i)
+            a, v, b = bound[i]
+            t = kp[3] * bp[3]
+            M = kprev * t
+            N = kc[3] * bc[3] * b * kc[4] * bc[4]
+            k = min(m, M, N)
+            ell = min(k + p, M, N)
+            h = kc[1] * bc[1]
+            dd = kc[0]
+            P1, Q1, P2, Q2 = kc[1] * kc[2], kc[3] * kc[4], bc[1] * bc[2], bc[3] * bc[4]
+            prod = ell * (b * dd * (P1 * Q1 * Q2 + P1 * Q2 * P2) + a * h * v * b + M * a * h)
+            out.append(dict(M=M, N=N, ell=ell, k=k, prod_macs=prod, row=r, col=i))
+            new[i - 1] = (kprev, t, k)
+            kprev = k
+        kl, bl = dims[r][ncol - 1], bra(r, ncol - 1)
+        new[ncol - 1] = (kprev, kl[3] * bl[3], 1)
+        bound = new
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_ours(args, cfg):
+    import torch
+    import torch.distributed as dist
+    from paper_2006_15234_gb300 import libpeps
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tdt = {"c64": torch.complex64, "f32": torch.float32, "f64": torch.float64}[cfg.dtype]
+    # weak scaling: every rank contracts its own PEPS (replicas of the workload)
+    ket = synth.random_peps(cfg.nrow, cfg.ncol, cfg.d, cfg.D, cfg.dtype, cfg.dist, cfg.seed + 1000 * rank)
+    kt = [[torch.tensor(T, dtype=tdt, device=dev) for T in row] for row in ket]
+    prec = libpeps.PREC_MIXED if args.prec == "mixed" else libpeps.PREC_PLAIN
+    opts = libpeps.make_opts(cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=prec)
+    plan = libpeps.ContractPlan(kt, kt if cfg.two_layer else None, opts)
+    launches = plan.launches()
+    nlaunch = len(launches)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        plan.execute()
+    la, ph = plan.result()
+    if args.launch_list:
+        # one more contraction for an external launch-list capture, then stop
+        plan.execute()
+        torch.cuda.synchronize()
+        return
+    run = plan.execute
+    graph = None
+    if not args.no_graph:
+        # the whole sweep as one CUDA graph (descriptors are already resident)
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                plan.execute()
+        stream.wait_stream(side)
+        run = graph.replay
+        run()
+        la_g, _ = plan.result()
+        assert abs(la_g - la) <= 1e-6 * abs(la), (la_g, la)
+    barrier()
+    times = []
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.add_(1.0)                       # evict L2 between steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            times.append((e0, e1))
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    ms = [a.elapsed_time(b) for a, b in times]
+    ms_step = float(np.mean(ms))
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # end-to-end through the public API with host buffers: H2D of every site,
+    # the contraction, D2H of the result, every step inside the timed region
+    host = [[torch.tensor(T, dtype=tdt).pin_memory() for T in row] for row in ket]
+    h2d = sum(T.numel() * T.element_size() for row in host for T in row)
+    e2e = []
+    for _ in range(max(2, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r, row in enumerate(host):
+            for c, T in enumerate(row):
+                kt[r][c].copy_(T, non_blocking=True)
+        run()
+        la2, _ = plan.result()
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = float(np.median(e2e))
+
+    # per-launch device times of one more execute (CUDA events on the stream)
+    prof = plan.profile()
+    by_tag = {}
+    for (tag, fl, by), t in zip(launches, prof):
+        d = by_tag.setdefault(tag, [0.0, 0.0, 0.0, 0])
+        d[0] += t; d[1] += fl; d[2] += by; d[3] += 1
+    dom = max(by_tag.items(), key=lambda kv: kv[1][0])
+    shapes = step_shapes(cfg)
+    flops = algorithmic_flops(shapes, cfg.q, cfg.dtype == "c64")
+    value = world * flops / (ms_step * 1e-3) / 1e12
+    peaks, peak_src = measured_peaks()
+    tag, (dt_ms, dfl, dby, dn) = dom
+    if prec == libpeps.PREC_MIXED and dfl > 0 and "product" in tag:
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = dfl / (dt_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) / 2.0      # TF32 = half the bf16 rate
+        peak_note = f"TF32 = bf16 sustained/2 ({peak_src})"
+    elif dfl / max(dby, 1) > 12:
+        bound, unit = "alu", "TFLOP/s"
+        achieved = dfl / (dt_ms * 1e-3) / 1e12
+        clk_max = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * clk_max * 1e6 / 1e12                  # FP32 FMA lanes x 2 x clock
+        peak_note = "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock"
+    else:
+        bound, unit = "hbm", "GB/s"
+        achieved = dby / (dt_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        peak_note = f"HBM copy bandwidth ({peak_src})"
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": cfg.dtype,
+        "data": "synthetic (seeded Gaussian PEPS, shapes of the workload)",
+        "config": {"workload": cfg.name, "nrow": cfg.nrow, "ncol": cfg.ncol, "d": cfg.d,
+                   "bond": cfg.D, "m": cfg.m, "p": cfg.p, "q": cfg.q, "precision": args.prec,
+                   "contraction_s": round(ms_step / 1e3, 6), "einsumsvd_steps": len(shapes),
+                   "algorithmic_tflop_per_step": round(flops / 1e12, 6),
+                   "l2": "flushed between steps (2x L2 write outside the timed events)",
+                   "parallelism": f"replicas x{world}", "log_norm": la,
+                   "cuda_graph": graph is not None},
+        "gpu_launches": nlaunch * args.steps,
+        "e2e": {"value": round(world * flops / e2e_s / 1e12, 4), "unit": "TFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16},
+        "roofline": {"bound": bound, "kernel": tag, "achieved": round(achieved, 3),
+                     "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
+                     "traffic": None, "launches_per_step": dn,
+                     "avg_launch_ms": round(dt_ms / dn, 5), "peak_source": peak_note,
+                     "algorithmic_per_launch": round((dfl if unit == "TFLOP/s" else dby) / dn, 1)},
+        "stage_ms": {k: round(v[0], 4) for k, v in sorted(by_tag.items(), key=lambda kv: -kv[1][0])},
+    }
+    clk = clk.summary()
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(cfg, args):
+    """The oracle as it stands, on a bounded sample of the workload."""
+    from oracle import bmps, rsvd
+    cores = os.cpu_count()
+    ket = synth.peps_for(cfg)
+    shapes = step_shapes(cfg)
+    if cfg.nrow * cfg.ncol <= 64:
+        t0 = time.perf_counter()
+        bmps.contract(ket, ket if cfg.two_layer else None, cfg.m, cfg.p, cfg.q, cfg.omega_seed)
+        dt = time.perf_counter() - t0
+        fl = algorithmic_flops(shapes, cfg.q, cfg.dtype == "c64")
+        sample = "one full contraction"
+    else:
+        # the largest einsumsvd step of the sweep, on its own inputs
+        big = max(shapes, key=lambda s: s["prod_macs"])
+        rng = np.random.default_rng(0)
+        kL = big["M"] // (cfg.D ** 2)
+        a = b = cfg.m
+        R = cfg.D ** 2
+
+        def cg(shape):
+            z = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+            return synth.round_to(z / np.linalg.norm(z), cfg.dtype)
+        V, S = cg((kL, R, a, R)), cg((a, R, b))
+        K = cg((cfg.d, cfg.D, cfg.D, cfg.D, cfg.D))
+        t0 = time.perf_counter()
+        rsvd.einsumsvd(V, S, K, K, cfg.m, cfg.p, cfg.q, cfg.omega_seed, 0)
+        dt = time.perf_counter() - t0
+        fl = algorithmic_flops([big], cfg.q, True)
+        sample = f"one middle einsumsvd step (M={big['M']}, N={big['N']}, l={big['ell']})"
+    return {"value": round(fl / dt / 1e12, 6), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": sample, "seconds": round(dt, 3)}
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import bmps  # noqa: F401
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(cfg, args)
+    t_all = []
+    for _ in range(args.steps):
+        r = cpu_baseline(cfg, args)
+        vals.append(r["value"])
+        t_all.append(r["seconds"])
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "TFLOP/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.median(t_all)), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian PEPS, shapes of the workload)",
+            "config": {"workload": cfg.name, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": round(v, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": round(v, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c2", "c5", "c4"])
+    ap.add_argument("--prec", default="plain", choices=["plain", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--launch-list", action="store_true",
+                    help="warm up, run one more contraction and exit (for an ncu launch list)")
+    args = ap.parse_args()
+    cfg = synth.config(args.config)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()
