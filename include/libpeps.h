@@ -213,6 +213,19 @@ peps_status peps_plan_profile(peps_plan *plan, void *workspace, size_t workspace
 peps_status peps_plan_validate(peps_plan *plan, void *workspace, size_t workspace_bytes,
                                const peps_einsumsvd_io *io);
 
+/* Verification entry point of the tensor-core GEMM that carries the dense
+ * contraction stages (tcgen05 kind::tf32, operands fed by TMA):
+ *   C[m][n] = sum_k opA(A[m][k]) * opB(B[n][k]),  m < M, n < N, k < K
+ * A (M x K), B (N x K) and C (M x N) are row-major DEVICE arrays of float
+ * (cplx = 0) or interleaved complex float (cplx = 1); opA / opB conjugate
+ * when conjA / conjB.  split3 = 1 forms FP32-level products from TF32 head
+ * and tail parts (3xTF32), split3 = 0 plain TF32 products.  Rows must be
+ * 16-byte aligned (K even for complex, K % 4 == 0 for real).  Enqueued on
+ * `stream`; PEPS_ERR_UNSUPPORTED if TMA maps cannot be encoded. */
+peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t conjB, int32_t split3, int32_t M,
+                               int32_t N, int32_t K, const void *A, const void *B, void *C,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

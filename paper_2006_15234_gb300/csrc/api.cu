@@ -422,23 +422,25 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           const double n2 = (double)c.n * c.n;
           C.need(c.G, as * n2, tag, "G");
           C.need(c.T, es * n2, tag, "T");
-          C.need(c.R, as * n2, tag, "R");
-          if (c.Rprev) { C.need(c.Rprev, as * n2, tag, "Rprev"); C.need(c.Rout, as * n2, tag, "Rout"); }
-          if (c.n > 4096) C.err = std::string(tag) + ": n above the pivot-flag buffer";
+          C.need(c.R, es * n2, tag, "R");
+          if (c.Rprev) { C.need(c.Rprev, es * n2, tag, "Rprev"); C.need(c.Rout, es * n2, tag, "Rout"); }
+          if (c.n > 1024) C.err = std::string(tag) + ": n above the pivot-flag buffer";
+          if (op.smem < small_smem_bytes(dt, c.n)) C.err = std::string(tag) + ": shared memory too small";
         }
         break;
       case Op::JACOBI:
         for (int i = 0; i < op.nd; ++i) {
           const JacobiDesc &j = ((const JacobiDesc *)d)[i];
-          C.need(j.Rb, as * (double)j.n * j.n, tag, "Rb");
-          C.need(j.Mw, as * (double)j.n * j.n, tag, "Mw");
+          C.need(j.Rb, es * (double)j.n * j.n, tag, "Rb");
+          C.need(j.Mw, es * (double)j.n * j.n, tag, "Mw");
+          if (op.smem < small_smem_bytes(dt, j.n)) C.err = std::string(tag) + ": shared memory too small";
           C.need(j.sig, 8.0 * j.n, tag, "sig");
         }
         break;
       case Op::FINALIZE:
         for (int i = 0; i < op.nd; ++i) {
           const FinalizeDesc &f = ((const FinalizeDesc *)d)[i];
-          C.need(f.Mw, as * (double)f.n * f.n, tag, "Mw");
+          C.need(f.Mw, es * (double)f.n * f.n, tag, "Mw");
           C.need(f.sig, 8.0 * f.n, tag, "sig");
           C.need(f.P, es * (double)f.n * f.M, tag, "P");
           C.need(f.g, es * (double)f.M, tag, "g");
@@ -524,8 +526,8 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
       case Op::SANDWICH:
         launch_sandwich(dt, (const SandwichDesc *)d, pre, op.nd, op.blocks, op.smem, s);
         break;
-      case Op::CHOL: launch_chol(dt, (const CholDesc *)d, op.nd, s); break;
-      case Op::JACOBI: launch_jacobi(dt, (const JacobiDesc *)d, op.nd, s); break;
+      case Op::CHOL: launch_chol(dt, (const CholDesc *)d, op.nd, op.smem, s); break;
+      case Op::JACOBI: launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, s); break;
       case Op::FINALIZE: launch_finalize(dt, (const FinalizeDesc *)d, op.nd, s); break;
       case Op::ZERO: launch_zero((const ZeroDesc *)d, pre, op.nd, op.blocks, s); break;
       case Op::SITE: launch_site(dt, (const SiteDesc *)d, pre, op.nd, op.blocks, s); break;

@@ -3,8 +3,8 @@
 // Serves every dense contraction of one einsumsvd step whose operands are
 // already laid out as matrices: the two m^2 stages of the implicit product
 // (boundary site S and carry V, Sec. IV-A / Table 2), their adjoints, the
-// Gram matrices of CholeskyQR (products of the single-precision inputs formed
-// exactly in FP64, summed in FP64, split over K and combined atomically),
+// Gram matrices of CholeskyQR (64-term partial sums folded into FP64, split
+// over K and combined atomically in FP64),
 // the R^-1 applications and the U = P U~, W = U~^H B epilogue (Algorithm 4's
 // last lines).  Strides are arbitrary; each tile load picks the coalesced
 // direction from the unit stride.
@@ -18,6 +18,7 @@ namespace peps {
 namespace {
 
 constexpr int BM = kGemmBM, BN = kGemmBN, BK = 16, NT = 256;
+constexpr int kFoldTiles = 4;   // K tiles per single-precision partial sum of a Gram
 
 __device__ __forceinline__ int find_desc(const int64_t *prefix, int nd, int64_t blk) {
   int lo = 0, hi = nd - 1;
@@ -60,15 +61,21 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc *__restrict__ d
   const bool a_kc = (g.sAk == 1), a_mc = (g.sAm == 1);
   const bool b_nc = (g.sBn == 1), b_kc = (g.sBk == 1);
 
-  // Store mode accumulates in the working type; Gram (atomic) mode forms each
-  // product of single-precision inputs exactly in FP64 and sums in FP64.
-  using AccT = typename std::conditional<ATOMIC, Acc, T>::type;
-  AccT acc[4][4];
+  // Store mode accumulates in the working type.  Gram (atomic) mode keeps
+  // short partial sums (kFoldTiles K tiles) in the working type and folds
+  // them into FP64 accumulators, so rounding does not grow with K.
+  T acc[4][4];
+  Acc acc64[ATOMIC ? 4 : 1][ATOMIC ? 4 : 1];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = AccT{};
+    for (int j = 0; j < 4; ++j) acc[i][j] = zero<T>();
+#pragma unroll
+  for (int i = 0; i < (ATOMIC ? 4 : 1); ++i)
+#pragma unroll
+    for (int j = 0; j < (ATOMIC ? 4 : 1); ++j) acc64[i][j] = Acc{};
 
+  int tile_count = 0;
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < (BM * BK) / NT; ++r) {
@@ -103,12 +110,20 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc *__restrict__ d
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if constexpr (ATOMIC) acc[i][j] = fma_(widen(a[i]), widen(b[j]), acc[i][j]);
-          else acc[i][j] = fma_(a[i], b[j], acc[i][j]);
-        }
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma_(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
+    if constexpr (ATOMIC) {
+      if ((++tile_count % kFoldTiles) == 0 || k0 + BK >= kend) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc64[i][j] = add(acc64[i][j], widen(acc[i][j]));
+            acc[i][j] = zero<T>();
+          }
+      }
+    }
   }
 
   double alpha = g.alpha;
@@ -123,7 +138,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc *__restrict__ d
       if (n >= g.N) continue;
       const int64_t off = (int64_t)bi * g.sCb + (int64_t)m * g.sCm + (int64_t)n * g.sCn;
       if constexpr (ATOMIC) {
-        Acc v = acc[i][j];
+        Acc v = acc64[i][j];
         if (g.conjC) v = conj_(v);
         atomic_add_acc((Acc *)g.C + off, scale(v, alpha));
       } else {

@@ -60,9 +60,10 @@ struct SketchDesc {
   int64_t nblocks;
 };
 
-// Cholesky of a Hermitian FP64 Gram (row-major n x n, destroyed) with pivot
-// skipping, upper factor R (optional, FP64) and T = R^+ (upper, working type).
-// If Rprev != nullptr the product R * Rprev is written to Rout (FP64).
+// Cholesky of a Hermitian Gram (FP64 accumulators, row-major n x n) with
+// pivot skipping and an optional diagonal shift, in the working precision:
+// upper factor R and T = R^+ (working type, n x n).  If Rprev != nullptr the
+// product R * Rprev is written to Rout (working type).
 struct CholDesc {
   void *G;
   void *T;
@@ -70,12 +71,13 @@ struct CholDesc {
   const void *Rprev;
   void *Rout;
   int32_t n;
-  double tol;
+  double tol;       // pivot threshold relative to the largest diagonal entry
+  double shift;     // diagonal shift relative to the largest diagonal entry
 };
 
-// One-sided Jacobi SVD of Mw = Rb^H (n x n, FP64, column-major, built from the
-// upper factor Rb by the kernel).  On return column c of Mw holds sigma_c u_c
-// and sig[c] = sigma_c (unsorted).
+// One-sided Jacobi SVD of Mw = Rb^H (n x n, working type, column-major, built
+// from the upper factor Rb by the kernel).  On return column c of Mw holds
+// sigma_c u_c and sig[c] = sigma_c (unsorted, FP64).
 struct JacobiDesc {
   const void *Rb;
   void *Mw;
@@ -89,7 +91,7 @@ struct JacobiDesc {
 // coefficient block Ut (working type, row-major [j][c]) used for U = P Ut and
 // W = conj(Ut^T Z) / sigma_1.
 struct FinalizeDesc {
-  const void *Mw;                  // FP64 n x n column-major, columns sigma_c u_c
+  const void *Mw;                  // working type n x n column-major, columns sigma_c u_c
   const double *sig;               // n unsorted singular values
   const void *P;                   // working type, [j][m], ld = M
   const void *g;                   // gauge vector, M entries
@@ -134,8 +136,9 @@ void launch_sandwich(int dt, const SandwichDesc *d, const int64_t *prefix, int n
                      int64_t blocks, int smem_bytes, cudaStream_t s);
 void launch_sketch(int dt, const SketchDesc *d, const int64_t *prefix, int nd,
                    int64_t blocks, cudaStream_t s);
-void launch_chol(int dt, const CholDesc *d, int nd, cudaStream_t s);
-void launch_jacobi(int dt, const JacobiDesc *d, int nd, cudaStream_t s);
+void launch_chol(int dt, const CholDesc *d, int nd, int smem, cudaStream_t s);
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, cudaStream_t s);
+int small_smem_bytes(int dt, int n);   // shared memory of chol / jacobi for n x n (0: global)
 void launch_finalize(int dt, const FinalizeDesc *d, int nd, cudaStream_t s);
 void launch_site(int dt, const SiteDesc *d, const int64_t *prefix, int nd, int64_t blocks,
                  cudaStream_t s);

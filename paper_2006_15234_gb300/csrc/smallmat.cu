@@ -1,15 +1,22 @@
-// Small dense factorisations of one einsumsvd step, in FP64.
+// Small dense factorisations of one einsumsvd step (l x l, l = sketch width).
 //
-//  * chol: CholeskyQR's factor of a Gram matrix G = Y^H Y (the Gram-matrix
-//    orthogonalisation of Algorithm 5, with a Cholesky factor in place of
-//    its eigendecomposition).  A pivot <= tol * max diag means the column is
-//    numerically inside the span of the earlier ones: it is skipped (its row
-//    of R and column of R^+ are zero), which drops the direction exactly as
-//    Gram-Schmidt with deletion would.  Outputs R (FP64), T = R^+ in the
-//    working type, and optionally R * Rprev (the accumulated R of CholeskyQR2).
+// Arithmetic is the data's own precision: single-precision data factorise in
+// FP32, FP64 data in FP64 (GB300 runs FP64 at ~1/58 of the FP32 rate, and
+// the Gram matrices these kernels start from are already accumulated with
+// FP64 partial sums).  Matrices live in shared memory when they fit and in
+// the caller's global scratch otherwise.
+//
+//  * chol: the factor of CholeskyQR (Gram-matrix orthogonalisation, the role
+//    of Algorithm 5 with a Cholesky factor in place of its eigen route).
+//    A relative diagonal shift may be added first (shifted CholeskyQR, so a
+//    single-precision factorisation cannot break down on an ill-conditioned
+//    block; a second pass restores orthogonality).  A pivot <= tol * max diag
+//    marks the column as numerically inside the span of the earlier ones: its
+//    row of R and column of R^+ are zero, exactly Gram-Schmidt with deletion.
+//    Outputs R, T = R^+ and optionally R * Rprev (CholeskyQR2's R).
 //  * jacobi: one-sided (Hestenes) Jacobi SVD of Rb^H in round-robin order,
-//    one warp per column pair; the singular values of Algorithm 4's small
-//    matrix P^H A are those of Rb^H, where Rb is the R factor of (P^H A)^H.
+//    one warp per column pair.  The singular values of Algorithm 4's small
+//    matrix P^H A are those of Rb^H, Rb being the R factor of (P^H A)^H.
 //  * finalize: sort, truncate to k, zero directions below rtol * sigma_1 and
 //    fix the phase of each singular vector against a Philox vector g.
 #include "common.cuh"
@@ -19,14 +26,32 @@ namespace peps {
 
 namespace {
 
-constexpr int NT = 256;
+constexpr int NT = 512;
+constexpr int kSmemLimit = 200 * 1024;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class T> struct Eps;
+template <> struct Eps<float> { static constexpr double v = 5.9604644775390625e-08; };
+template <> struct Eps<float2> { static constexpr double v = 5.9604644775390625e-08; };
+template <> struct Eps<double> { static constexpr double v = 1.1102230246251565e-16; };
+template <> struct Eps<double2> { static constexpr double v = 1.1102230246251565e-16; };
+
+template <class T> __device__ __forceinline__ T warp_sum(T v);
+template <> __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double2 warp_sum(double2 v) {
+template <> __device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <> __device__ __forceinline__ float2 warp_sum(float2 v) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  return v;
+}
+template <> __device__ __forceinline__ double2 warp_sum(double2 v) {
   v.x = warp_sum(v.x);
   v.y = warp_sum(v.y);
   return v;
@@ -48,94 +73,117 @@ __device__ double block_max(double v, double *red) {
   return r;
 }
 
-// divide by a positive real
-PEPS_HD double divr(double a, double r) { return a / r; }
-PEPS_HD double2 divr(double2 a, double r) { return make_double2(a.x / r, a.y / r); }
-PEPS_HD double neg(double a) { return -a; }
-PEPS_HD double2 neg(double2 a) { return make_double2(-a.x, -a.y); }
+template <class T> __device__ __forceinline__ T real_scalar(double x) { return from_parts<T>(x, 0.0); }
 
+template <class T> __device__ __forceinline__ T div_real(T a, double r) {
+  return scale(a, (typename Traits<T>::Real)(1.0 / r));
+}
+
+// ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ descs) {
   using Acc = typename Traits<T>::Acc;
   __shared__ double red[32];
-  __shared__ double maxd_s;
+  __shared__ unsigned char dead[1024];
+  extern __shared__ __align__(16) unsigned char dyn[];
   const CholDesc &g = descs[blockIdx.x];
   const int n = g.n;
-  Acc *G = (Acc *)g.G;
-  Acc *R = (Acc *)g.R;
-  extern __shared__ unsigned char dyn[];
-  unsigned char *dead = dyn;   // n flags
+  const Acc *G = (const Acc *)g.G;
+  const bool in_smem = (int64_t)n * n * sizeof(T) <= kSmemLimit;
+  T *W = in_smem ? (T *)dyn : (T *)g.R;        // working matrix; its upper triangle becomes R
+  T *R = (T *)g.R;
 
   double md = 0.0;
   for (int i = threadIdx.x; i < n; i += NT) md = fmax(md, re(G[(int64_t)i * n + i]));
   md = block_max(md, red);
-  if (threadIdx.x == 0) maxd_s = md;
-  for (int i = threadIdx.x; i < n * n; i += NT) R[i] = widen(zero<T>());
+  const double shift = g.shift * md;
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+    const int i = (int)(t / n), k = (int)(t % n);
+    T v = zero<T>();
+    if (k >= i) {
+      v = narrow<T>(G[t]);
+      if (k == i) v = from_parts<T>(re(G[t]) + shift, 0.0);
+    }
+    W[t] = v;
+  }
   __syncthreads();
-  const double thr = g.tol * maxd_s;
+  const double thr = g.tol * md;
 
   for (int j = 0; j < n; ++j) {
-    const double dj = re(G[(int64_t)j * n + j]);
-    const bool isdead = !(dj > thr) || !(maxd_s > 0.0);
+    const double dj = (double)re(W[(int64_t)j * n + j]);
+    const bool isdead = !(dj > thr) || !(md > 0.0);
+    __syncthreads();   // everyone has read W[j][j] before row j is rewritten
     if (threadIdx.x == 0) dead[j] = isdead;
-    if (!isdead) {
-      const double r = sqrt(dj);
-      for (int k = j + threadIdx.x; k < n; k += NT)
-        R[(int64_t)j * n + k] = k == j ? widen(from_parts<T>(r, 0.0)) : divr(G[(int64_t)j * n + k], r);
+    if (isdead) {
+      for (int k = j + threadIdx.x; k < n; k += NT) W[(int64_t)j * n + k] = zero<T>();
+      __syncthreads();
+      continue;
     }
+    const double r = sqrt(dj);
+    for (int k = j + threadIdx.x; k < n; k += NT)
+      W[(int64_t)j * n + k] = k == j ? real_scalar<T>(r) : div_real(W[(int64_t)j * n + k], r);
     __syncthreads();
-    if (!isdead) {
-      // trailing update of the upper triangle: G[i][k] -= conj(R[j][i]) R[j][k], j < i <= k
-      const int m = n - j - 1;
-      const int64_t cnt = (int64_t)m * m;
-      for (int64_t t = threadIdx.x; t < cnt; t += NT) {
-        const int row = j + 1 + (int)(t / m), col = j + 1 + (int)(t % m);
-        if (row > col) continue;
-        const Acc a = conj_(R[(int64_t)j * n + row]);
-        const Acc b = R[(int64_t)j * n + col];
-        Acc &dst = G[(int64_t)row * n + col];
-        dst = sub(dst, mul(a, b));
-      }
+    // trailing update of the upper triangle: W[i][k] -= conj(R[j][i]) R[j][k], j < i <= k
+    const int m = n - j - 1;
+    for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += NT) {
+      const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
+      if (i > k) continue;
+      W[(int64_t)i * n + k] = sub(W[(int64_t)i * n + k], mul(conj_(W[(int64_t)j * n + i]), W[(int64_t)j * n + k]));
     }
     __syncthreads();
   }
-
-  // T = R^+ by back substitution (one thread per column), FP64 in G's storage
-  Acc *Ti = G;
-  for (int c = threadIdx.x; c < n; c += NT) {
-    for (int i = 0; i < n; ++i) Ti[(int64_t)i * n + c] = widen(zero<T>());
-    if (dead[c]) continue;
-    Ti[(int64_t)c * n + c] = widen(from_parts<T>(1.0 / re(R[(int64_t)c * n + c]), 0.0));
-    for (int i = c - 1; i >= 0; --i) {
-      if (dead[i]) continue;
-      Acc s = widen(zero<T>());
-      for (int k = i + 1; k <= c; ++k) s = fma_(R[(int64_t)i * n + k], Ti[(int64_t)k * n + c], s);
-      Ti[(int64_t)i * n + c] = divr(neg(s), re(R[(int64_t)i * n + i]));
+  // R (upper triangle of W, zero below) to global
+  if (in_smem)
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+      const int i = (int)(t / n), k = (int)(t % n);
+      R[t] = k >= i ? W[t] : zero<T>();
     }
-  }
+  else
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT)
+      if ((int)(t % n) < (int)(t / n)) R[t] = zero<T>();
   __syncthreads();
-  T *Tout = (T *)g.T;
-  for (int i = threadIdx.x; i < n * n; i += NT) Tout[i] = narrow<T>(Ti[i]);
+
+  // T = R^+ row by row from the bottom: T[i][c] = -(sum_{k=i+1..c} R[i][k] T[k][c]) / R[i][i]
+  T *Tm = (T *)g.T;
+  const int warps = NT / 32, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = n - 1; i >= 0; --i) {
+    if (dead[i]) {
+      for (int c = threadIdx.x; c < n; c += NT) Tm[(int64_t)i * n + c] = zero<T>();
+      __syncthreads();
+      continue;
+    }
+    const double rii = re(R[(int64_t)i * n + i]);
+    for (int c = threadIdx.x; c <= i; c += NT)
+      Tm[(int64_t)i * n + c] = c == i ? real_scalar<T>(1.0 / rii) : zero<T>();
+    for (int c = i + 1 + w; c < n; c += warps) {
+      T s = zero<T>();
+      for (int k = i + 1 + lane; k <= c; k += 32) s = fma_(R[(int64_t)i * n + k], Tm[(int64_t)k * n + c], s);
+      s = warp_sum(s);
+      if (lane == 0) Tm[(int64_t)i * n + c] = div_real(scale(s, (typename Traits<T>::Real)-1), rii);
+    }
+    __syncthreads();
+  }
   if (g.Rprev) {
-    const Acc *P = (const Acc *)g.Rprev;
-    Acc *O = (Acc *)g.Rout;
-    for (int t = threadIdx.x; t < n * n; t += NT) {
-      const int i = t / n, k = t % n;
-      Acc s = widen(zero<T>());
+    const T *P = (const T *)g.Rprev;
+    T *O = (T *)g.Rout;
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+      const int i = (int)(t / n), k = (int)(t % n);
+      T s = zero<T>();
       for (int l = i; l <= k; ++l) s = fma_(R[(int64_t)i * n + l], P[(int64_t)l * n + k], s);
       O[t] = s;
     }
   }
 }
 
-// Hestenes rotation of columns a, b (length n, FP64) in place.
-template <class Acc>
-__device__ bool jacobi_pair(Acc *a, Acc *b, int n, double tol) {
+// Hestenes rotation of columns a, b (length n) in place; returns whether it rotated.
+template <class T>
+__device__ bool jacobi_pair(T *a, T *b, int n, double tol) {
+  using R = typename Traits<T>::Real;
   const int lane = threadIdx.x & 31;
-  double al = 0.0, be = 0.0;
-  Acc ga = {};
+  R al = 0, be = 0;
+  T ga = zero<T>();
   for (int r = lane; r < n; r += 32) {
-    const Acc x = a[r], y = b[r];
+    const T x = a[r], y = b[r];
     al += abs2(x);
     be += abs2(y);
     ga = fma_(conj_(x), y, ga);
@@ -143,39 +191,42 @@ __device__ bool jacobi_pair(Acc *a, Acc *b, int n, double tol) {
   al = warp_sum(al);
   be = warp_sum(be);
   ga = warp_sum(ga);
-  const double g = sqrt(abs2(ga));
-  if (!(g > tol * sqrt(al * be)) || g == 0.0) return false;
-  const double zeta = (be - al) / (2.0 * g);
+  const double gm = sqrt((double)abs2(ga));
+  if (!(gm > tol * sqrt((double)al * (double)be)) || gm == 0.0) return false;
+  const double zeta = ((double)be - (double)al) / (2.0 * gm);
   const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
   const double c = 1.0 / sqrt(1.0 + t * t);
   const double s = c * t;
   // e^{-i phi} with gamma = |gamma| e^{i phi}
-  Acc ph;
-  if constexpr (sizeof(Acc) == 16) ph = make_double2(ga.x / g, -ga.y / g);
-  else ph = ga > 0 ? 1.0 : -1.0;
+  T ph;
+  if constexpr (Traits<T>::cplx) ph = from_parts<T>(re(ga) / gm, -im(ga) / gm);
+  else ph = re(ga) > 0 ? (R)1 : (R)-1;
+  const R cr = (R)c, sr = (R)s;
   for (int r = lane; r < n; r += 32) {
-    const Acc x = a[r];
-    const Acc y = mul(b[r], ph);
-    a[r] = sub(scale(x, c), scale(y, s));
-    b[r] = add(scale(x, s), scale(y, c));
+    const T x = a[r];
+    const T y = mul(b[r], ph);
+    a[r] = sub(scale(x, cr), scale(y, sr));
+    b[r] = add(scale(x, sr), scale(y, cr));
   }
   return true;
 }
 
 template <class T>
 __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict__ descs) {
-  using Acc = typename Traits<T>::Acc;
   __shared__ int rotated;
+  extern __shared__ __align__(16) unsigned char dyn[];
   const JacobiDesc &g = descs[blockIdx.x];
   const int n = g.n;
-  const Acc *Rb = (const Acc *)g.Rb;
-  Acc *M = (Acc *)g.Mw;
+  const bool in_smem = (int64_t)n * n * sizeof(T) <= kSmemLimit;
+  const T *Rb = (const T *)g.Rb;
+  T *Mg = (T *)g.Mw;
+  T *M = in_smem ? (T *)dyn : Mg;
   // column c of Rb^H = conj(row c of Rb)
-  for (int t = threadIdx.x; t < n * n; t += NT) M[t] = conj_(Rb[t]);
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) M[t] = conj_(Rb[t]);
   __syncthreads();
   const int n2 = n + (n & 1);
   const int warps = NT / 32, w = threadIdx.x >> 5;
-  const double tol = 4.0 * n * 1.1102230246251565e-16;
+  const double tol = 2.0 * sqrt((double)n) * Eps<T>::v;   // columns orthogonal to ~eps sqrt(n)
   int sweep = 0;
   for (; sweep < g.max_sweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
@@ -200,23 +251,24 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict
   if (sweep == g.max_sweeps && threadIdx.x == 0 && g.status) atomicOr(g.status, STATUS_JACOBI_NOCONV);
   for (int c = w; c < n; c += warps) {
     double s2 = 0.0;
-    for (int r = threadIdx.x & 31; r < n; r += 32) s2 += abs2(M[(int64_t)c * n + r]);
+    for (int r = threadIdx.x & 31; r < n; r += 32) s2 += (double)abs2(M[(int64_t)c * n + r]);
     s2 = warp_sum(s2);
     if ((threadIdx.x & 31) == 0) g.sig[c] = sqrt(s2);
   }
+  if (in_smem)
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) Mg[t] = M[t];
 }
 
 template <class T>
 __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__restrict__ descs) {
-  using Acc = typename Traits<T>::Acc;
   const FinalizeDesc &g = descs[blockIdx.x];
   const int n = g.n, k = g.k;
   extern __shared__ __align__(16) unsigned char dyn[];
   int *order = (int *)dyn;                                   // n
-  Acc *h = (Acc *)(dyn + ((n * sizeof(int) + 15) & ~15));    // n
-  Acc *rho = h + n;                                          // k
+  T *h = (T *)(dyn + ((n * sizeof(int) + 15) & ~15));        // n
+  T *rho = h + n;                                            // k
   const double *sig = g.sig;
-  const Acc *M = (const Acc *)g.Mw;
+  const T *M = (const T *)g.Mw;
   for (int c = threadIdx.x; c < n; c += NT) {
     int rank = 0;
     const double sc = sig[c];
@@ -231,38 +283,39 @@ __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__rest
   const T *gv = (const T *)g.g;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = w; j < n; j += NT / 32) {
-    Acc s = widen(zero<T>());
-    for (int64_t m = lane; m < g.M; m += 32)
-      s = fma_(widen(conj_(P[(int64_t)j * g.M + m])), widen(gv[m]), s);
+    T s = zero<T>();
+    for (int64_t m = lane; m < g.M; m += 32) s = fma_(conj_(P[(int64_t)j * g.M + m]), gv[m], s);
     s = warp_sum(s);
     if (lane == 0) h[j] = s;
   }
   __syncthreads();
   const double s1 = sig[order[0]];
-  // phi_i = sum_j conj(h_j) u_{j,i}, u_i = M[:, order[i]] / sigma
+  // phi_i = sum_j conj(h_j) u_{j,i}, u_i = M[:, order[i]] / sigma_i
   for (int i = w; i < k; i += NT / 32) {
     const int c = order[i];
     const double si = sig[c];
     const bool zero_dir = !(si > g.rtol * s1);
-    Acc s = widen(zero<T>());
+    T s = zero<T>();
     if (!zero_dir)
       for (int j = lane; j < n; j += 32) s = fma_(conj_(h[j]), M[(int64_t)c * n + j], s);
     s = warp_sum(s);
     if (lane == 0) {
-      Acc r;
-      const double mag = sqrt(abs2(s));
-      if constexpr (Traits<T>::cplx) r = mag > 0 ? make_double2(s.x / mag, s.y / mag) : make_double2(1.0, 0.0);
-      else r = re(s) < 0 ? -1.0 : 1.0;
+      T r;
+      const double mag = sqrt((double)abs2(s));
+      if constexpr (Traits<T>::cplx)
+        r = mag > 0 ? from_parts<T>(re(s) / mag, im(s) / mag) : from_parts<T>(1.0, 0.0);
+      else
+        r = re(s) < 0 ? from_parts<T>(-1.0, 0.0) : from_parts<T>(1.0, 0.0);
       // coefficient of u_i in Ut: conj(rho) / sigma_i (zero for dropped directions)
-      rho[i] = zero_dir ? widen(zero<T>()) : scale(conj_(r), 1.0 / si);
+      rho[i] = zero_dir ? zero<T>() : div_real(conj_(r), si);
       g.sigma_out[i] = zero_dir ? 0.0 : si;
     }
   }
   __syncthreads();
   T *Ut = (T *)g.Ut;
-  for (int t = threadIdx.x; t < n * k; t += NT) {
-    const int j = t / k, i = t % k;
-    Ut[t] = narrow<T>(mul(M[(int64_t)order[i] * n + j], rho[i]));
+  for (int64_t t = threadIdx.x; t < (int64_t)n * k; t += NT) {
+    const int j = (int)(t / k), i = (int)(t % k);
+    Ut[t] = mul(M[(int64_t)order[i] * n + j], rho[i]);
   }
   if (threadIdx.x == 0) {
     *g.log_out = s1 > 0 ? log(s1) : -INFINITY;
@@ -271,43 +324,52 @@ __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__rest
   }
 }
 
-template <class T> void chol_t(const CholDesc *d, int nd, cudaStream_t s) {
-  // dead flags: n bytes of dynamic shared memory (n <= 4096 enforced on the host)
-  chol_kernel<T><<<nd, NT, 4096, s>>>(d);
+template <class K> void set_smem(K kernel, int bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
-template <class T> void jacobi_t(const JacobiDesc *d, int nd, cudaStream_t s) {
-  jacobi_kernel<T><<<nd, NT, 0, s>>>(d);
+
+template <class T> void chol_t(const CholDesc *d, int nd, int smem, cudaStream_t s) {
+  static bool set = false;
+  if (!set) { set_smem(chol_kernel<T>, kSmemLimit); set = true; }
+  chol_kernel<T><<<nd, NT, smem, s>>>(d);
+}
+template <class T> void jacobi_t(const JacobiDesc *d, int nd, int smem, cudaStream_t s) {
+  static bool set = false;
+  if (!set) { set_smem(jacobi_kernel<T>, kSmemLimit); set = true; }
+  jacobi_kernel<T><<<nd, NT, smem, s>>>(d);
 }
 template <class T> void finalize_t(const FinalizeDesc *d, int nd, cudaStream_t s) {
-  // order (n ints) + h (n) + rho (k <= n) in FP64 complex at most: n <= 1024
-  const int smem = 4096 + 2 * 1024 * 16;
+  // order (n ints) + h (n) + rho (k <= n): n <= 1024
+  const int smem = 4096 + 16 + 2 * 1024 * (int)sizeof(T);
   static bool set = false;
-  if (!set) {
-    cudaFuncSetAttribute(finalize_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    set = true;
-  }
+  if (!set) { set_smem(finalize_kernel<T>, smem); set = true; }
   finalize_kernel<T><<<nd, NT, smem, s>>>(d);
 }
 
 }  // namespace
 
-void launch_chol(int dt, const CholDesc *d, int nd, cudaStream_t s) {
+int small_smem_bytes(int dt, int n) {
+  const int64_t b = (int64_t)n * n * dtype_size(dt);
+  return b <= kSmemLimit ? (int)b : 0;
+}
+
+void launch_chol(int dt, const CholDesc *d, int nd, int smem, cudaStream_t s) {
   if (nd <= 0) return;
   switch (dt) {
-    case DT_R32: chol_t<float>(d, nd, s); break;
-    case DT_C64: chol_t<float2>(d, nd, s); break;
-    case DT_R64: chol_t<double>(d, nd, s); break;
-    case DT_C128: chol_t<double2>(d, nd, s); break;
+    case DT_R32: chol_t<float>(d, nd, smem, s); break;
+    case DT_C64: chol_t<float2>(d, nd, smem, s); break;
+    case DT_R64: chol_t<double>(d, nd, smem, s); break;
+    case DT_C128: chol_t<double2>(d, nd, smem, s); break;
   }
 }
 
-void launch_jacobi(int dt, const JacobiDesc *d, int nd, cudaStream_t s) {
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, cudaStream_t s) {
   if (nd <= 0) return;
   switch (dt) {
-    case DT_R32: jacobi_t<float>(d, nd, s); break;
-    case DT_C64: jacobi_t<float2>(d, nd, s); break;
-    case DT_R64: jacobi_t<double>(d, nd, s); break;
-    case DT_C128: jacobi_t<double2>(d, nd, s); break;
+    case DT_R32: jacobi_t<float>(d, nd, smem, s); break;
+    case DT_C64: jacobi_t<float2>(d, nd, smem, s); break;
+    case DT_R64: jacobi_t<double>(d, nd, smem, s); break;
+    case DT_C128: jacobi_t<double2>(d, nd, smem, s); break;
   }
 }
 

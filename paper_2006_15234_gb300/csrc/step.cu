@@ -5,7 +5,7 @@
 //   X <- Omega (Philox), g <- gauge vector
 //   Y <- A X;              P <- orth(Y)            (CholeskyQR2)
 //   repeat q:  Z <- A^H P; Q <- orth(Z);  Y <- A Q;  P <- orth(Y)
-//   Z <- A^H P  (= (P^H A)^H);  R_B <- Cholesky factor of the FP64 Gram Z^H Z
+//   Z <- A^H P  (= (P^H A)^H);  R_B <- R factor of Z (CholeskyQR2)
 //   U~, Sigma <- one-sided Jacobi SVD of R_B^H;  sort / truncate / gauge
 //   U <- P U~;   W <- U~^H P^H A / sigma_1
 //
@@ -205,9 +205,18 @@ double chol_tol(int dt, int ell) {
   return dtype_double(dt) ? 64.0 * ell * 2.220446049250313e-16 : 0.0;
 }
 
+double chol_shift(int dt, int ell, bool first_pass) {
+  // Shifted CholeskyQR: a single-precision factorisation of an
+  // ill-conditioned block gets a diagonal shift of a few n*eps so it cannot
+  // break down; the next pass restores orthogonality.  FP64 data: no shift.
+  if (dtype_double(dt) || !first_pass) return 0.0;
+  return 4.0 * ell * 5.9604644775390625e-08;
+}
+
 // CholeskyQR pass: G <- src^H src; T <- R^+; dst <- src T
 void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*src, void *Inst::*dst,
-                   void *Inst::*Rdst, void *Inst::*Rprev, void *Inst::*Rout, bool apply, const char *tag) {
+                   void *Inst::*Rdst, void *Inst::*Rprev, void *Inst::*Rout, bool apply, const char *tag,
+                   bool first_pass) {
   const int as = acc_size(B.dt);
   std::vector<std::pair<void *, int64_t>> z;
   std::vector<GemmDesc> gram, app;
@@ -221,6 +230,7 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
     gram.push_back(g);
     CholDesc c{};
     c.G = q.G; c.T = q.Tm; c.R = q.*Rdst; c.n = q.ell; c.tol = chol_tol(B.dt, q.ell);
+    c.shift = chol_shift(B.dt, q.ell, first_pass);
     c.Rprev = Rprev ? q.*Rprev : nullptr;
     c.Rout = Rout ? q.*Rout : nullptr;
     ch.push_back(c);
@@ -236,6 +246,7 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
   op.desc_off = B.put(ch);
   op.nd = (int)ch.size();
   op.tag = tag;
+  for (auto &c : ch) op.smem = std::max(op.smem, small_smem_bytes(B.dt, c.n));
   B.ops.push_back(op);
   if (apply) push_gemm(B, app, false, tag);
 }
@@ -244,14 +255,20 @@ void emit_orth(Builder &B, std::vector<Inst *> &I, bool mside) {
   void *Inst::*a = mside ? &Inst::Y : &Inst::Z;
   void *Inst::*t = mside ? &Inst::P : &Inst::X;
   const char *tag = mside ? "orth_m" : "orth_n";
-  emit_cqr_pass(B, I, mside, a, t, &Inst::R1, nullptr, nullptr, true, tag);
-  emit_cqr_pass(B, I, mside, t, a, &Inst::R1, nullptr, nullptr, true, tag);
+  emit_cqr_pass(B, I, mside, a, t, &Inst::R1, nullptr, nullptr, true, tag, true);
+  emit_cqr_pass(B, I, mside, t, a, &Inst::R1, nullptr, nullptr, true, tag, false);
 }
 
 void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
-  // R_B: Cholesky factor of the FP64 Gram of Z = (P^H A)^H, so that
-  // R_B^H R_B = B B^H with B = P^H A; its singular values are those of B.
-  emit_cqr_pass(B, I, false, &Inst::Z, nullptr, &Inst::Rout, nullptr, nullptr, false, "svd_qr");
+  // R_B: CholeskyQR2 of Z = (P^H A)^H (R_B = R2 R1, R_B^H R_B = B B^H with
+  // B = P^H A, so its singular values are those of B).  FP64 data: one
+  // Cholesky of the FP64 Gram is already accurate.
+  if (dtype_double(B.dt)) {
+    emit_cqr_pass(B, I, false, &Inst::Z, nullptr, &Inst::Rout, nullptr, nullptr, false, "svd_qr", false);
+  } else {
+    emit_cqr_pass(B, I, false, &Inst::Z, &Inst::X, &Inst::R1, nullptr, nullptr, true, "svd_qr", true);
+    emit_cqr_pass(B, I, false, &Inst::X, nullptr, &Inst::R2, &Inst::R1, &Inst::Rout, false, "svd_qr", false);
+  }
   std::vector<JacobiDesc> jd;
   std::vector<FinalizeDesc> fd;
   for (Inst *p : I) {
@@ -267,6 +284,7 @@ void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
   }
   Op oj;
   oj.kind = Op::JACOBI; oj.desc_off = B.put(jd); oj.nd = (int)jd.size(); oj.tag = "svd_jacobi";
+  for (auto &j : jd) oj.smem = std::max(oj.smem, small_smem_bytes(B.dt, j.n));
   B.ops.push_back(oj);
   Op of;
   of.kind = Op::FINALIZE; of.desc_off = B.put(fd); of.nd = (int)fd.size(); of.tag = "svd_finalize";

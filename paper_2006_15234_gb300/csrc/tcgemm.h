@@ -1,0 +1,54 @@
+// Descriptor of the tensor-core GEMM (tcgemm.cu) and its host helpers.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+#include <cuda_runtime.h>
+
+namespace peps {
+
+// index -> sum_d digit_d * stride_d, digit 0 least significant (radix[d])
+struct DigitMap {
+  int32_t n;
+  int32_t radix[4];
+  int64_t stride[4];
+};
+
+// C(m, n) (+)= alpha * sum_k opA(A[m][k]) opB(B[n][k]); A, B row-major with K
+// contiguous, complex interleaved when cplx.  C's element (m, n) sits at
+// C + mm(m) + mn(n) (elements of the output type: float2 or float).
+struct TcDesc {
+  CUtensorMap ta;
+  CUtensorMap tb;
+  int32_t M, N, Kr;        // Kr = K extent in floats (2K for complex data)
+  int32_t cplx, conjA, conjB, split3;
+  int32_t tiles_m, tiles_n;
+  DigitMap mm, mn;
+  void *C;
+  double alpha;
+  const double *alpha_dev;
+  int32_t accumulate, conjC;
+  uint32_t *status;
+};
+
+// Block N (64 or 128 output columns, complex or real) for an N extent.
+int tc_block_n(int N);
+void launch_tc_gemm(const TcDesc &d, int bn, cudaStream_t s);
+
+// Encode a 2-D TMA map over rows x cols FP32 values (row pitch in bytes) with
+// a box of 32 floats x box_rows and the 128-byte swizzle.  Returns false when
+// the driver entry point is unavailable (no GPU driver) or encoding fails.
+bool tc_encode_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t pitch_bytes,
+                   int box_rows);
+// Whether a K-contiguous operand can be fed by TMA (alignment rules).
+bool tc_operand_ok(const void *base, int64_t pitch_bytes);
+
+inline DigitMap digits1(int64_t stride) {
+  DigitMap d{};
+  d.n = 1;
+  d.radix[0] = 0x7fffffff;
+  d.stride[0] = stride;
+  return d;
+}
+
+}  // namespace peps

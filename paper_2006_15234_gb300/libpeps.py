@@ -16,6 +16,7 @@ __all__ = [
     "PepsError", "load", "lib_path", "RsvdOpts", "EinsumsvdShape", "EinsumsvdIO",
     "Network", "ContractPlan", "EinsumsvdPlan", "boundary_contract", "dtype_code",
     "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "SKETCH_GAUSS", "SKETCH_UNIFORM",
+    "debug_tc_gemm",
 ]
 
 PREC_PLAIN, PREC_MIXED = 0, 1
@@ -27,6 +28,7 @@ EXPORTED_SYMBOLS = [
     "peps_contract_plan", "peps_contract_execute", "peps_contract_result",
     "peps_contract_sigma_count", "peps_boundary_contract", "peps_boundary_workspace",
     "peps_plan_launch_count", "peps_plan_launch_info", "peps_plan_profile", "peps_plan_validate",
+    "peps_debug_tc_gemm",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -115,6 +117,8 @@ def load():
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.peps_plan_profile.restype = st
     lib.peps_plan_profile.argtypes = [vp, vp, C.c_size_t, vp, C.POINTER(C.c_double)]
+    lib.peps_debug_tc_gemm.restype = st
+    lib.peps_debug_tc_gemm.argtypes = [C.c_int32] * 7 + [vp, vp, vp, vp]
     lib.peps_plan_validate.restype = st
     lib.peps_plan_validate.argtypes = [vp, vp, C.c_size_t, C.POINTER(EinsumsvdIO)]
     _lib = lib
@@ -309,3 +313,17 @@ def boundary_contract(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PL
     plan = ContractPlan(ket, bra, make_opts(m, p, q, seed, sketch, prec), direction)
     plan.execute(stream)
     return plan.result(stream, with_sigma)
+
+
+def debug_tc_gemm(A, B, conjA=False, conjB=False, split3=False, stream=None):
+    """C = opA(A) @ opB(B)^T on the tensor-core GEMM (A: M x K, B: N x K)."""
+    import torch
+    lib = load()
+    cplx = A.is_complex()
+    M, K = A.shape
+    N = B.shape[0]
+    C_ = torch.empty((M, N), dtype=A.dtype, device=A.device)
+    _check(lib.peps_debug_tc_gemm(int(cplx), int(conjA), int(conjB), int(split3), M, N, K,
+                                  C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                                  C.c_void_p(C_.data_ptr()), _stream_handle(stream)))
+    return C_

@@ -1,0 +1,54 @@
+"""The tensor-core GEMM (tcgen05 kind::tf32, TMA-fed) against an FP64 torch
+reference: complex and real, every conjugation mode, plain TF32 and 3xTF32
+products, shapes spanning several 128-row tiles with ragged M, N and K tails.
+
+Normwise bound |C - C_ref|_F <= tol |A|_F |B|_F: TF32 keeps 10+1 mantissa
+bits (relative rounding ~2^-11 per operand), 3xTF32 ~2^-21.
+"""
+import pytest
+import torch
+
+from paper_2006_15234_gb300 import libpeps
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(128, 64, 16), (300, 200, 90), (257, 129, 1000), (64, 70, 34)]
+
+
+def _ref(A, B, cA, cB):
+    A64, B64 = A.to(torch.complex128 if A.is_complex() else torch.float64), \
+        B.to(torch.complex128 if B.is_complex() else torch.float64)
+    if cA:
+        A64 = A64.conj()
+    if cB:
+        B64 = B64.conj()
+    return A64 @ B64.T
+
+
+@pytest.mark.parametrize("split3,tol", [(False, 2e-3), (True, 2e-6)])
+@pytest.mark.parametrize("cA,cB", [(False, False), (True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_complex(shape, cA, cB, split3, tol):
+    M, N, K = shape
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
+    A = torch.randn(M, K, dtype=torch.complex64, device="cuda", generator=g)
+    B = torch.randn(N, K, dtype=torch.complex64, device="cuda", generator=g)
+    C = libpeps.debug_tc_gemm(A, B, cA, cB, split3)
+    torch.cuda.synchronize()
+    R = _ref(A, B, cA, cB)
+    err = (C.to(torch.complex128) - R).norm() / (A.norm().double() * B.norm().double())
+    assert err <= tol, float(err)
+
+
+@pytest.mark.parametrize("split3,tol", [(False, 2e-3), (True, 2e-6)])
+@pytest.mark.parametrize("shape", [(128, 64, 32), (300, 200, 92), (257, 129, 1000)])
+def test_real(shape, split3, tol):
+    M, N, K = shape
+    g = torch.Generator(device="cuda").manual_seed(M + N)
+    A = torch.randn(M, K, dtype=torch.float32, device="cuda", generator=g)
+    B = torch.randn(N, K, dtype=torch.float32, device="cuda", generator=g)
+    C = libpeps.debug_tc_gemm(A, B, False, False, split3)
+    torch.cuda.synchronize()
+    R = _ref(A, B, False, False)
+    err = (C.double() - R).norm() / (A.norm().double() * B.norm().double())
+    assert err <= tol, float(err)
