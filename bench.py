@@ -159,7 +159,7 @@ def run_ours(args, cfg):
     # weak scaling: every rank contracts its own PEPS (replicas of the workload)
     ket = synth.random_peps(cfg.nrow, cfg.ncol, cfg.d, cfg.D, cfg.dtype, cfg.dist, cfg.seed + 1000 * rank)
     kt = [[torch.tensor(T, dtype=tdt, device=dev) for T in row] for row in ket]
-    prec = libpeps.PREC_MIXED if args.prec == "mixed" else libpeps.PREC_PLAIN
+    prec = {"plain": libpeps.PREC_PLAIN, "mixed": libpeps.PREC_MIXED, "fast": libpeps.PREC_FAST}[args.prec]
     opts = libpeps.make_opts(cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=prec)
     plan = libpeps.ContractPlan(kt, kt if cfg.two_layer else None, opts)
     launches = plan.launches()
@@ -244,7 +244,7 @@ def run_ours(args, cfg):
     value = world * flops / (ms_step * 1e-3) / 1e12
     peaks, peak_src = measured_peaks()
     tag, (dt_ms, dfl, dby, dn) = dom
-    if prec == libpeps.PREC_MIXED and dfl > 0 and "product" in tag:
+    if prec != libpeps.PREC_PLAIN and dfl > 0 and ("product" in tag or "adjoint" in tag):
         bound, unit = "tensor", "TFLOP/s"
         achieved = dfl / (dt_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0) / 2.0      # TF32 = half the bf16 rate
@@ -361,7 +361,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2", choices=["c2", "c5", "c4"])
-    ap.add_argument("--prec", default="plain", choices=["plain", "mixed"])
+    ap.add_argument("--prec", default="plain", choices=["plain", "mixed", "fast"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--launch-list", action="store_true",

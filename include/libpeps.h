@@ -60,9 +60,15 @@ typedef enum {
 
 /* Arithmetic of the implicit products (Algorithm 4's A Q and A^H P).
  * PLAIN: CUDA-core arithmetic in the data type.
- * MIXED: tensor-core (tcgen05) contraction GEMMs with FP32 accumulation for
- *        single-precision data; falls back to PLAIN for double data. */
-typedef enum { PEPS_PREC_PLAIN = 0, PEPS_PREC_MIXED = 1 } peps_precision;
+ * MIXED: tensor-core (tcgen05 kind::tf32) contraction GEMMs, every product
+ *        formed from TF32 head + tail splits (3xTF32: FP32-level products,
+ *        FP32 accumulation); single-precision data whose contracted extents
+ *        meet the TMA alignment rules, PLAIN otherwise.
+ * FAST:  as MIXED, but the products before the last A Q of the power
+ *        iteration use single TF32 products (faster; singular values move by
+ *        up to ~1e-4 relative on flat spectra, the contracted scalar by
+ *        ~1e-6 on the tested workloads). */
+typedef enum { PEPS_PREC_PLAIN = 0, PEPS_PREC_MIXED = 1, PEPS_PREC_FAST = 2 } peps_precision;
 
 /* Sketch distribution of Algorithm 4's first line: Gaussian (default) or the
  * paper's uniform draw on [-1, 1]. */
@@ -74,7 +80,9 @@ typedef enum { PEPS_SKETCH_GAUSS = 0, PEPS_SKETCH_UNIFORM = 1 } peps_sketch;
  *  q     power iterations (Algorithm 4's loop count), >= 0
  *  seed  Philox4x64-10 key of every sketch and gauge vector
  *  sketch, prec  see the enums above
- *  flags reserved, must be 0 */
+ *  flags PEPS_FLAG_ORTH_Q: in the MIXED / FAST paths, orthogonalise A^H P
+ *        explicitly (Algorithm 4 literally; the default feeds it to the next
+ *        product directly, which spans the same subspace) */
 typedef struct {
   int32_t m, p, q;
   uint64_t seed;
@@ -82,6 +90,7 @@ typedef struct {
   int32_t prec;
   uint32_t flags;
 } peps_rsvd_opts;
+#define PEPS_FLAG_ORTH_Q 1u
 
 /* ------------------------------------------------------------------------
  * Batched einsumsvd (Algorithm 3's einsumsvd line, Algorithm 4 inside).

@@ -15,6 +15,7 @@
 #include "../../include/libpeps.h"
 #include "common.cuh"
 #include "plan.h"
+#include "tcgemm.h"
 
 using namespace peps;
 
@@ -48,15 +49,16 @@ peps_status check_opts(const peps_rsvd_opts *o) {
   if (o->q < 0) return fail(PEPS_ERR_ARG, "q must be >= 0 (got %d)", o->q);
   if (o->sketch != PEPS_SKETCH_GAUSS && o->sketch != PEPS_SKETCH_UNIFORM)
     return fail(PEPS_ERR_ARG, "unknown sketch kind %d", o->sketch);
-  if (o->prec != PEPS_PREC_PLAIN && o->prec != PEPS_PREC_MIXED)
+  if (o->prec != PEPS_PREC_PLAIN && o->prec != PEPS_PREC_MIXED && o->prec != PEPS_PREC_FAST)
     return fail(PEPS_ERR_ARG, "unknown precision %d", o->prec);
-  if (o->flags != 0) return fail(PEPS_ERR_ARG, "flags must be 0");
+  if (o->flags & ~PEPS_FLAG_ORTH_Q) return fail(PEPS_ERR_ARG, "unknown flag bits %#x", o->flags);
   return PEPS_OK;
 }
 
 RsvdOpts to_opts(const peps_rsvd_opts *o) {
   RsvdOpts r;
   r.m = o->m; r.p = o->p; r.q = o->q; r.seed = o->seed; r.sketch = o->sketch; r.prec = o->prec;
+  r.orth_q = (o->flags & PEPS_FLAG_ORTH_Q) != 0;
   return r;
 }
 
@@ -206,6 +208,7 @@ std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
       std::string e = inst_check(I, dt);
       if (!e.empty()) return e;
       I.instance = ((uint64_t)P->direction << 32) | ((uint64_t)r << 16) | (uint64_t)i;
+      I.tc = P->opts.prec != PEPS_PREC_PLAIN && inst_tc_ok(I, dt);
       bound[r][i - 1] = Site{I.kL, I.t, I.k};
       max_carry = std::max(max_carry, (size_t)I.kL * I.t * I.a * I.h);
       max_carry = std::max(max_carry, (size_t)I.k * I.N);
@@ -242,6 +245,26 @@ std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
     owner.G = B.buf(ell * ell * as); owner.R1 = B.buf(ell * ell * as); owner.R2 = B.buf(ell * ell * as);
     owner.Rout = B.buf(ell * ell * as); owner.Mw = B.buf(ell * ell * as);
     owner.sig = (double *)B.buf(ell * 8); owner.inv_s1 = (double *)B.buf(8);
+    int64_t t1 = 0, vt = 0, st = 0, ut = 0, kt = 0, kb = 0;
+    for (auto &row : steps)
+      for (auto &I : row) {
+        if (!I.tc) continue;
+        const int64_t P1 = (int64_t)I.Dl * I.Du, Q1 = (int64_t)I.Dx * I.De, P2 = (int64_t)I.DL * I.DU,
+                      Q2 = (int64_t)I.DX * I.DE;
+        t1 = std::max<int64_t>(t1, (int64_t)I.ell * I.b * I.d * P1 * Q2);
+        vt = std::max<int64_t>(vt, I.M * I.a * I.h);
+        st = std::max<int64_t>(st, (int64_t)I.a * I.v * I.b);
+        ut = std::max<int64_t>(ut, (int64_t)I.k * I.M);
+        kt = std::max<int64_t>(kt, Q1 * I.d * P1);
+        kb = std::max<int64_t>(kb, (int64_t)I.d * P2 * Q2);
+      }
+    owner.T1 = t1 ? B.buf(t1 * es) : nullptr;
+    owner.VT = vt ? B.buf(vt * es) : nullptr;
+    owner.ST = st ? B.buf(st * es) : nullptr;
+    owner.UT = ut ? B.buf(ut * es) : nullptr;
+    owner.KT = kt ? B.buf(kt * es) : nullptr;
+    owner.KbP = kb ? B.buf(kb * es) : nullptr;
+    owner.KbT = kb ? B.buf(kb * es) : nullptr;
   }
   void *Sbuf[2][64];
   if (ncol > 64) return "ncol above 64 is not supported";
@@ -434,6 +457,7 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           C.need(j.Rb, es * (double)j.n * j.n, tag, "Rb");
           C.need(j.Mw, es * (double)j.n * j.n, tag, "Mw");
           if (op.smem < small_smem_bytes(dt, j.n)) C.err = std::string(tag) + ": shared memory too small";
+          if (op.smem2 < jacobi_cluster_smem_bytes(dt, j.n)) C.err = std::string(tag) + ": cluster shared memory too small";
           C.need(j.sig, 8.0 * j.n, tag, "sig");
         }
         break;
@@ -484,6 +508,35 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
       case Op::FILL:
         C.need(op.fill_ptr, es * (double)op.fill_n, tag, "ptr");
         break;
+      case Op::TC: {
+        const TcDesc &t = op.tc;
+        C.need(op.tcA, 4.0 * op.tcA_rows * op.tc_kr, tag, "A");
+        C.need(op.tcB, 4.0 * op.tcB_rows * op.tc_kr, tag, "B");
+        auto span = [](const DigitMap &m, int64_t extent) {
+          double mx = 0;
+          int64_t rest = extent - 1;
+          for (int d = 0; d < m.n; ++d) {
+            const int64_t dig = d == m.n - 1 ? rest : std::min<int64_t>(rest, (int64_t)m.radix[d] - 1);
+            mx += (double)dig * m.stride[d];
+            rest = d == m.n - 1 ? 0 : rest / m.radix[d];
+          }
+          return mx;
+        };
+        C.need(t.C, (t.atomic64 ? as : es) * (span(t.mm, t.M) + span(t.mn, t.N) + 1), tag, "C");
+        if (t.ksplit > 1 && (int64_t)t.ksplit * t.kb_per_split * 32 < t.Kr)
+          C.err = std::string(tag) + ": K chunks do not cover K";
+        if (t.alpha_dev) C.need(t.alpha_dev, 8, tag, "alpha_dev");
+        if (op.tc_kr % 4 || t.Kr != op.tc_kr) C.err = std::string(tag) + ": TMA rows not 16-byte aligned";
+        break;
+      }
+      case Op::PERMUTE:
+        for (int i = 0; i < op.nd; ++i) {
+          const PermuteDesc &q = ((const PermuteDesc *)d)[i];
+          const double n = (double)q.nb * q.R * q.Cc * q.Q;
+          C.need(q.in, es * n, tag, "in");
+          C.need(q.out, es * n, tag, "out");
+        }
+        break;
     }
     if (!C.err.empty()) return C.err;
   }
@@ -491,11 +544,13 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
   return "";
 }
 
-peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io) {
+peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool encode = false) {
   Builder B;
+  B.encode = encode;
   std::string e = P->kind == peps_plan::EINSUMSVD ? build_einsumsvd(P, (uintptr_t)ws, io, B)
                                                    : build_contract(P, (uintptr_t)ws, B);
   if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
+  if (!B.err.empty()) return fail(PEPS_ERR_UNSUPPORTED, "%s", B.err.c_str());
   P->ws_bytes = finish(B, &P->blob_off);   // needs the blob size: before the move
   P->ops = std::move(B.ops);
   P->blob = std::move(B.blob);
@@ -527,7 +582,7 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
         launch_sandwich(dt, (const SandwichDesc *)d, pre, op.nd, op.blocks, op.smem, s);
         break;
       case Op::CHOL: launch_chol(dt, (const CholDesc *)d, op.nd, op.smem, s); break;
-      case Op::JACOBI: launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, s); break;
+      case Op::JACOBI: launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, s); break;
       case Op::FINALIZE: launch_finalize(dt, (const FinalizeDesc *)d, op.nd, s); break;
       case Op::ZERO: launch_zero((const ZeroDesc *)d, pre, op.nd, op.blocks, s); break;
       case Op::SITE: launch_site(dt, (const SiteDesc *)d, pre, op.nd, op.blocks, s); break;
@@ -540,6 +595,8 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
         break;
       }
       case Op::FILL: launch_fill(dt, op.fill_ptr, op.fill_n, op.fill_value, s); break;
+      case Op::TC: launch_tc_gemm(op.tc, op.tc_bn, s); break;
+      case Op::PERMUTE: launch_permute(dt, (const PermuteDesc *)d, pre, op.nd, op.blocks, s); break;
     }
     if (events) CUDA_TRY(cudaEventRecord(events[&op - P->ops.data() + 1], s));
   }
@@ -592,6 +649,7 @@ peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch
     if (!e.empty()) return fail(PEPS_ERR_SHAPE, "instance %d: %s", i, e.c_str());
     inst_derive(I, P->opts);
     I.instance = instance_ids ? instance_ids[i] : (uint64_t)i;
+    I.tc = P->opts.prec != PEPS_PREC_PLAIN && inst_tc_ok(I, dtype);
     P->insts.push_back(I);
   }
   if (peps_status s = rebuild(P.get(), nullptr, nullptr)) return s;
@@ -621,7 +679,7 @@ peps_status peps_einsumsvd_execute(peps_plan *plan, const peps_einsumsvd_io *io,
   for (size_t i = 0; same && i < n; ++i)
     same = memcmp(&plan->io_cache[i], &io[i], sizeof(peps_einsumsvd_io)) == 0;
   if (!same) {
-    if (peps_status s = rebuild(plan, workspace, io)) return s;
+    if (peps_status s = rebuild(plan, workspace, io, true)) return s;
     plan->io_cache.assign(io, io + n);
     plan->built_base = (uintptr_t)workspace;
     plan->built = true;
@@ -670,7 +728,7 @@ peps_status peps_contract_execute(peps_plan *plan, void *workspace, size_t works
   if (plan->kind != peps_plan::CONTRACT) return fail(PEPS_ERR_ARG, "not a contraction plan");
   const bool same = plan->built && plan->built_base == (uintptr_t)workspace;
   if (!same) {
-    if (peps_status s = rebuild(plan, workspace, nullptr)) return s;
+    if (peps_status s = rebuild(plan, workspace, nullptr, true)) return s;
     plan->built_base = (uintptr_t)workspace;
     plan->built = true;
   }

@@ -50,7 +50,9 @@ struct SandwichDesc {
   int32_t nblocks;
 };
 
-// Philox4x64-10 draw of an N x ell block stored as X[j*ld + n].
+// Philox4x64-10 draw of an N x ell block stored as X[j*ld + map(n)]; map is
+// the identity when nd == 0, else n's mixed-radix digits (least significant
+// first) times their strides.
 struct SketchDesc {
   void *X;
   int64_t N, ld;
@@ -58,6 +60,18 @@ struct SketchDesc {
   int32_t tag, kind;               // kind 0 Gaussian, 1 uniform
   uint64_t seed, instance;
   int64_t nblocks;
+  int32_t nd;
+  int32_t radix[5];
+  int64_t stride[5];
+};
+
+// out[b][c][r][q] = op(in[b][r][c][q]) for b < nb, r < R, c < Cc, q < Q
+// (op = conjugate when conj): swaps two index groups of a tensor.
+struct PermuteDesc {
+  const void *in;
+  void *out;
+  int64_t nb, R, Cc, Q;
+  int32_t conj;
 };
 
 // Cholesky of a Hermitian Gram (FP64 accumulators, row-major n x n) with
@@ -137,13 +151,17 @@ void launch_sandwich(int dt, const SandwichDesc *d, const int64_t *prefix, int n
 void launch_sketch(int dt, const SketchDesc *d, const int64_t *prefix, int nd,
                    int64_t blocks, cudaStream_t s);
 void launch_chol(int dt, const CholDesc *d, int nd, int smem, cudaStream_t s);
-void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, cudaStream_t s);
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s);
+int jacobi_cluster_smem_bytes(int dt, int n);   // per-CTA shared memory of the cluster Jacobi (0: not used)
 int small_smem_bytes(int dt, int n);   // shared memory of chol / jacobi for n x n (0: global)
 void launch_finalize(int dt, const FinalizeDesc *d, int nd, cudaStream_t s);
 void launch_site(int dt, const SiteDesc *d, const int64_t *prefix, int nd, int64_t blocks,
                  cudaStream_t s);
 void launch_scalar(int dt, const ScalarDesc *d, cudaStream_t s);
 void launch_fill(int dt, void *p, int64_t n, double value, cudaStream_t s);
+void launch_permute(int dt, const PermuteDesc *d, const int64_t *prefix, int nd, int64_t blocks,
+                    cudaStream_t s);
+int64_t permute_blocks(const PermuteDesc &d);
 
 int sandwich_smem_bytes(int dt, const SandwichDesc &d);
 constexpr int kGemmBM = 64, kGemmBN = 64;

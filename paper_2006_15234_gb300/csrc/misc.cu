@@ -98,7 +98,48 @@ __global__ void sketch_kernel(const SketchDesc *__restrict__ descs, const int64_
     } else {
       val = from_parts<T>((double)v[r], 0.0);
     }
-    X[j * g.ld + n] = val;
+    int64_t off = n;
+    if (g.nd) {
+      off = 0;
+      int64_t r = n;
+      for (int d = 0; d < g.nd; ++d) {
+        off += (r % g.radix[d]) * g.stride[d];
+        r /= g.radix[d];
+      }
+    }
+    X[j * g.ld + off] = val;
+  }
+}
+
+// Tiled 32 x 32 transpose of the (r, c) index pair; the inner block q is
+// carried along (q == 1 for plain matrix transposes).
+template <class T>
+__global__ void permute_kernel(const PermuteDesc *__restrict__ descs, const int64_t *__restrict__ prefix,
+                               int nd) {
+  __shared__ T tile[32][33];
+  const int di = find_desc(prefix, nd, blockIdx.x);
+  const PermuteDesc &g = descs[di];
+  const int64_t tr = (g.R + 31) / 32, tc = (g.Cc + 31) / 32;
+  int64_t blk = blockIdx.x - prefix[di];
+  const int64_t q = blk % g.Q; blk /= g.Q;
+  const int64_t cb = blk % tc; blk /= tc;
+  const int64_t rb = blk % tr; blk /= tr;
+  const int64_t b = blk;
+  const T *in = (const T *)g.in + b * g.R * g.Cc * g.Q;
+  T *out = (T *)g.out + b * g.R * g.Cc * g.Q;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = rb * 32 + i, c = cb * 32 + tx;
+    if (r < g.R && c < g.Cc) tile[i][tx] = in[(r * g.Cc + c) * g.Q + q];
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t c = cb * 32 + i, r = rb * 32 + tx;
+    if (r < g.R && c < g.Cc) {
+      T v = tile[tx][i];
+      if (g.conj) v = conj_(v);
+      out[(c * g.R + r) * g.Q + q] = v;
+    }
   }
 }
 
@@ -220,6 +261,21 @@ void launch_site(int dt, const SiteDesc *d, const int64_t *prefix, int nd, int64
     case DT_C64: site_t<float2>(d, prefix, nd, blocks, s); break;
     case DT_R64: site_t<double>(d, prefix, nd, blocks, s); break;
     case DT_C128: site_t<double2>(d, prefix, nd, blocks, s); break;
+  }
+}
+
+int64_t permute_blocks(const PermuteDesc &d) {
+  return d.nb * ceil_div(d.R, 32) * ceil_div(d.Cc, 32) * d.Q;
+}
+
+void launch_permute(int dt, const PermuteDesc *d, const int64_t *prefix, int nd, int64_t blocks,
+                    cudaStream_t s) {
+  if (blocks <= 0) return;
+  switch (dt) {
+    case DT_R32: permute_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(d, prefix, nd); break;
+    case DT_C64: permute_kernel<float2><<<(unsigned)blocks, 256, 0, s>>>(d, prefix, nd); break;
+    case DT_R64: permute_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(d, prefix, nd); break;
+    case DT_C128: permute_kernel<double2><<<(unsigned)blocks, 256, 0, s>>>(d, prefix, nd); break;
   }
 }
 

@@ -9,16 +9,19 @@
 #include <vector>
 
 #include "kernels.h"
+#include "tcgemm.h"
 
 namespace peps {
 
 struct Op {
-  enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL } kind;
+  enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL, TC,
+              PERMUTE } kind;
   size_t desc_off = 0;    // byte offset of the descriptor array in the blob
   size_t prefix_off = 0;  // byte offset of the int64 block prefix array in the blob
   int nd = 0;
   int64_t blocks = 0;
   int smem = 0;
+  int smem2 = 0;          // second kernel of the launch (cluster Jacobi)
   ScalarDesc scalar{};
   size_t aux_off[3] = {0, 0, 0};  // blob offsets of the scalar's device arrays
   void *fill_ptr = nullptr;
@@ -27,6 +30,11 @@ struct Op {
   std::string tag;        // stage name (profiling ledger)
   double flops = 0.0;     // algorithmic flops of the launch
   double bytes = 0.0;     // algorithmic DRAM bytes of the launch
+  // tensor-core GEMM (kind TC): descriptor passed by value, operand spans
+  TcDesc tc{};
+  int tc_bn = 0;
+  const void *tcA = nullptr, *tcB = nullptr;
+  int64_t tcA_rows = 0, tcB_rows = 0, tc_kr = 0;
 };
 
 struct ZeroDesc {
@@ -44,6 +52,8 @@ struct Builder {
   std::vector<uint8_t> blob;
   std::vector<Op> ops;
   int dt = 0;
+  bool encode = false;            // encode TMA maps (real device pointers, driver present)
+  std::string err;                // first encoding failure
 
   size_t alloc(size_t bytes) {
     size_t o = (top + 255) & ~(size_t)255;
@@ -79,8 +89,11 @@ struct Inst {
   double *sigma, *logp;
   // scratch (working type unless noted)
   void *X, *Z, *T2, *T3, *Y, *P, *g, *Tm, *Ut;
-  void *G, *R1, *R2, *Rout, *Mw;   // FP64 (double or double2)
+  void *G, *R1, *R2, *Rout, *Mw;   // G: FP64 accumulators; the others working type
   double *sig, *inv_s1;
+  // tensor-core path scratch
+  void *T1, *VT, *ST, *UT, *KT, *KbP, *KbT;
+  bool tc;                          // this instance runs its products on tensor cores
 };
 
 struct RsvdOpts {
@@ -88,6 +101,7 @@ struct RsvdOpts {
   uint64_t seed;
   int sketch;
   int prec;
+  bool orth_q;
 };
 
 // Shape bookkeeping shared by every planner.
@@ -100,7 +114,10 @@ void inst_alloc_scratch(Builder &B, Inst &I, int dt);
 void inst_share_scratch(Inst &I, const Inst &owner);
 // Check the shape against the kernels' limits; returns "" when supported.
 std::string inst_check(const Inst &I, int dt);
+// Whether every stage GEMM of the instance meets the TMA alignment rules.
+bool inst_tc_ok(const Inst &I, int dt);
 // Emit every stage of one einsumsvd over a group of instances.
 void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);
+void emit_einsumsvd_simt(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);
 
 }  // namespace peps

@@ -19,6 +19,8 @@
 //    matrix P^H A are those of Rb^H, Rb being the R factor of (P^H A)^H.
 //  * finalize: sort, truncate to k, zero directions below rtol * sigma_1 and
 //    fix the phase of each singular vector against a Philox vector g.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -120,8 +122,9 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
       continue;
     }
     const double r = sqrt(dj);
+    const typename Traits<T>::Real rinv = (typename Traits<T>::Real)(1.0 / r);
     for (int k = j + threadIdx.x; k < n; k += NT)
-      W[(int64_t)j * n + k] = k == j ? real_scalar<T>(r) : div_real(W[(int64_t)j * n + k], r);
+      W[(int64_t)j * n + k] = k == j ? real_scalar<T>(r) : scale(W[(int64_t)j * n + k], rinv);
     __syncthreads();
     // trailing update of the upper triangle: W[i][k] -= conj(R[j][i]) R[j][k], j < i <= k
     const int m = n - j - 1;
@@ -153,13 +156,14 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
       continue;
     }
     const double rii = re(R[(int64_t)i * n + i]);
+    const typename Traits<T>::Real nrinv = (typename Traits<T>::Real)(-1.0 / rii);
     for (int c = threadIdx.x; c <= i; c += NT)
       Tm[(int64_t)i * n + c] = c == i ? real_scalar<T>(1.0 / rii) : zero<T>();
     for (int c = i + 1 + w; c < n; c += warps) {
       T s = zero<T>();
       for (int k = i + 1 + lane; k <= c; k += 32) s = fma_(R[(int64_t)i * n + k], Tm[(int64_t)k * n + c], s);
       s = warp_sum(s);
-      if (lane == 0) Tm[(int64_t)i * n + c] = div_real(scale(s, (typename Traits<T>::Real)-1), rii);
+      if (lane == 0) Tm[(int64_t)i * n + c] = scale(s, nrinv);
     }
     __syncthreads();
   }
@@ -175,9 +179,12 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
   }
 }
 
-// Hestenes rotation of columns a, b (length n) in place; returns whether it rotated.
+// Hestenes rotation of columns a, b (length n) in place.  Rotates when
+// |a^H b| > tol |a| |b|; returns that relative off-diagonal measure.  The
+// rotation scalars use the data's own precision (FP64 divide / square root
+// run at a small fraction of the FP32 rate on this GPU).
 template <class T>
-__device__ bool jacobi_pair(T *a, T *b, int n, double tol) {
+__device__ float jacobi_pair(T *a, T *b, int n, float tol) {
   using R = typename Traits<T>::Real;
   const int lane = threadIdx.x & 31;
   R al = 0, be = 0;
@@ -191,33 +198,35 @@ __device__ bool jacobi_pair(T *a, T *b, int n, double tol) {
   al = warp_sum(al);
   be = warp_sum(be);
   ga = warp_sum(ga);
-  const double gm = sqrt((double)abs2(ga));
-  if (!(gm > tol * sqrt((double)al * (double)be)) || gm == 0.0) return false;
-  const double zeta = ((double)be - (double)al) / (2.0 * gm);
-  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + t * t);
-  const double s = c * t;
+  const R gm = sqrt(abs2(ga));
+  const R nrm = sqrt(al * be);
+  const float rel = nrm > (R)0 ? (float)(gm / nrm) : 0.f;
+  if (!(gm > (R)tol * nrm) || gm == (R)0) return rel;
+  const R zeta = (be - al) / ((R)2 * gm);
+  const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+  const R c = (R)1 / sqrt((R)1 + t * t);
+  const R sn = c * t;
   // e^{-i phi} with gamma = |gamma| e^{i phi}
   T ph;
   if constexpr (Traits<T>::cplx) ph = from_parts<T>(re(ga) / gm, -im(ga) / gm);
-  else ph = re(ga) > 0 ? (R)1 : (R)-1;
-  const R cr = (R)c, sr = (R)s;
+  else ph = re(ga) > (R)0 ? (R)1 : (R)-1;
   for (int r = lane; r < n; r += 32) {
     const T x = a[r];
     const T y = mul(b[r], ph);
-    a[r] = sub(scale(x, cr), scale(y, sr));
-    b[r] = add(scale(x, sr), scale(y, cr));
+    a[r] = sub(scale(x, c), scale(y, sn));
+    b[r] = add(scale(x, sn), scale(y, c));
   }
-  return true;
+  return rel;
 }
 
 template <class T>
 __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict__ descs) {
-  __shared__ int rotated;
+  __shared__ float sweep_max;
   extern __shared__ __align__(16) unsigned char dyn[];
   const JacobiDesc &g = descs[blockIdx.x];
   const int n = g.n;
   const bool in_smem = (int64_t)n * n * sizeof(T) <= kSmemLimit;
+  if (!in_smem) return;                                      // cluster kernel
   const T *Rb = (const T *)g.Rb;
   T *Mg = (T *)g.Mw;
   T *M = in_smem ? (T *)dyn : Mg;
@@ -226,12 +235,15 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict
   __syncthreads();
   const int n2 = n + (n & 1);
   const int warps = NT / 32, w = threadIdx.x >> 5;
-  const double tol = 2.0 * sqrt((double)n) * Eps<T>::v;   // columns orthogonal to ~eps sqrt(n)
+  // rotate above the rounding level of the dot products; stop once a whole
+  // sweep found nothing above a few times that level
+  const double tol = 2.0 * sqrt((double)n) * Eps<T>::v;
+  const double stop_tol = 8.0 * tol;
   int sweep = 0;
   for (; sweep < g.max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
+    if (threadIdx.x == 0) sweep_max = 0.f;
     __syncthreads();
-    int mine = 0;
+    float mine = 0.f;
     for (int r = 0; r < n2 - 1; ++r) {
       for (int i = w; i < n2 / 2; i += warps) {
         int a, b;
@@ -239,14 +251,15 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict
         else { a = (r + i) % (n2 - 1); b = (r - i + (n2 - 1)) % (n2 - 1); }
         if (a > b) { const int t = a; a = b; b = t; }
         if (b >= n) continue;
-        if (jacobi_pair(M + (int64_t)a * n, M + (int64_t)b * n, n, tol)) mine = 1;
+        mine = fmaxf(mine, jacobi_pair(M + (int64_t)a * n, M + (int64_t)b * n, n, (float)tol));
       }
       __syncthreads();
     }
-    if (mine && (threadIdx.x & 31) == 0) rotated = 1;
+    if ((threadIdx.x & 31) == 0) atomicMax((int *)&sweep_max, __float_as_int(mine));
     __syncthreads();
-    if (!rotated) break;
+    const bool done = sweep_max <= (float)stop_tol;
     __syncthreads();
+    if (done) break;
   }
   if (sweep == g.max_sweeps && threadIdx.x == 0 && g.status) atomicOr(g.status, STATUS_JACOBI_NOCONV);
   for (int c = w; c < n; c += warps) {
@@ -257,6 +270,90 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict
   }
   if (in_smem)
     for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) Mg[t] = M[t];
+}
+
+
+// One-sided Jacobi on a thread-block cluster: for l x l matrices too large for
+// one SM's shared memory, eight CTAs hold the columns in distributed shared
+// memory and all column pairs of a round-robin round rotate in parallel (one
+// warp per pair, any CTA reaching any column through the cluster window),
+// with a cluster barrier between rounds.
+constexpr int kClusterCTAs = 8;
+
+template <class T>
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NT)
+    jacobi_cluster_kernel(const JacobiDesc *__restrict__ descs) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const JacobiDesc &g = descs[blockIdx.x / kClusterCTAs];
+  const int n = g.n;
+  if ((int64_t)n * n * sizeof(T) <= kSmemLimit) return;      // handled by the one-CTA kernel
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ float cta_max;
+  __shared__ float cluster_max;
+  T *local = (T *)dyn;
+  const int cpc = (n + kClusterCTAs - 1) / kClusterCTAs;     // columns per CTA
+  const T *Rb = (const T *)g.Rb;
+  for (int64_t t = threadIdx.x; t < (int64_t)cpc * n; t += NT) {
+    const int lc = (int)(t / n), r = (int)(t % n), c = rank * cpc + lc;
+    local[t] = c < n ? conj_(Rb[(int64_t)c * n + r]) : zero<T>();
+  }
+  if (threadIdx.x == 0) cluster_max = 0.f;
+  cluster.sync();
+  auto col = [&](int c) -> T * {
+    T *base = cluster.map_shared_rank(local, c / cpc);
+    return base + (int64_t)(c % cpc) * n;
+  };
+  const int n2 = n + (n & 1);
+  const int lane = threadIdx.x & 31;
+  const int gw = rank * (NT / 32) + (threadIdx.x >> 5), nwarps = kClusterCTAs * NT / 32;
+  const double tol = 2.0 * sqrt((double)n) * Eps<T>::v;
+  const double stop_tol = 8.0 * tol;
+  float *root_max = cluster.map_shared_rank(&cluster_max, 0);
+  int sweep = 0;
+  for (; sweep < g.max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) cta_max = 0.f;
+    __syncthreads();
+    float mine = 0.f;
+    for (int r = 0; r < n2 - 1; ++r) {
+      for (int i = gw; i < n2 / 2; i += nwarps) {
+        int a, b;
+        if (i == 0) { a = r; b = n2 - 1; }
+        else { a = (r + i) % (n2 - 1); b = (r - i + (n2 - 1)) % (n2 - 1); }
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (b >= n) continue;
+        mine = fmaxf(mine, jacobi_pair(col(a), col(b), n, (float)tol));
+      }
+      cluster.sync();
+    }
+    if (lane == 0) atomicMax((int *)&cta_max, __float_as_int(mine));
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax((int *)root_max, __float_as_int(cta_max));
+    cluster.sync();
+    const bool done = *root_max <= (float)stop_tol;
+    cluster.sync();                                          // all read before the reset
+    if (rank == 0 && threadIdx.x == 0) cluster_max = 0.f;
+    cluster.sync();
+    if (done) break;
+  }
+  if (sweep == g.max_sweeps && rank == 0 && threadIdx.x == 0 && g.status)
+    atomicOr(g.status, STATUS_JACOBI_NOCONV);
+  T *Mg = (T *)g.Mw;
+  const int w = threadIdx.x >> 5;
+  for (int lc = w; lc < cpc; lc += NT / 32) {
+    const int c = rank * cpc + lc;
+    if (c >= n) break;
+    double s2 = 0.0;
+    for (int r = lane; r < n; r += 32) {
+      const T v = local[(int64_t)lc * n + r];
+      Mg[(int64_t)c * n + r] = v;
+      s2 += (double)abs2(v);
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) g.sig[c] = sqrt(s2);
+  }
+  cluster.sync();   // keep this CTA's shared memory alive until every peer is done with it
 }
 
 template <class T>
@@ -333,10 +430,15 @@ template <class T> void chol_t(const CholDesc *d, int nd, int smem, cudaStream_t
   if (!set) { set_smem(chol_kernel<T>, kSmemLimit); set = true; }
   chol_kernel<T><<<nd, NT, smem, s>>>(d);
 }
-template <class T> void jacobi_t(const JacobiDesc *d, int nd, int smem, cudaStream_t s) {
+template <class T> void jacobi_t(const JacobiDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s) {
   static bool set = false;
-  if (!set) { set_smem(jacobi_kernel<T>, kSmemLimit); set = true; }
-  jacobi_kernel<T><<<nd, NT, smem, s>>>(d);
+  if (!set) {
+    set_smem(jacobi_kernel<T>, kSmemLimit);
+    set_smem(jacobi_cluster_kernel<T>, kSmemLimit);
+    set = true;
+  }
+  if (smem >= 0) jacobi_kernel<T><<<nd, NT, smem, s>>>(d);
+  if (cluster_smem > 0) jacobi_cluster_kernel<T><<<nd * kClusterCTAs, NT, cluster_smem, s>>>(d);
 }
 template <class T> void finalize_t(const FinalizeDesc *d, int nd, cudaStream_t s) {
   // order (n ints) + h (n) + rho (k <= n): n <= 1024
@@ -353,6 +455,12 @@ int small_smem_bytes(int dt, int n) {
   return b <= kSmemLimit ? (int)b : 0;
 }
 
+int jacobi_cluster_smem_bytes(int dt, int n) {
+  if ((int64_t)n * n * dtype_size(dt) <= kSmemLimit) return 0;
+  const int64_t cpc = (n + kClusterCTAs - 1) / kClusterCTAs;
+  return (int)(cpc * n * dtype_size(dt));
+}
+
 void launch_chol(int dt, const CholDesc *d, int nd, int smem, cudaStream_t s) {
   if (nd <= 0) return;
   switch (dt) {
@@ -363,13 +471,13 @@ void launch_chol(int dt, const CholDesc *d, int nd, int smem, cudaStream_t s) {
   }
 }
 
-void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, cudaStream_t s) {
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s) {
   if (nd <= 0) return;
   switch (dt) {
-    case DT_R32: jacobi_t<float>(d, nd, smem, s); break;
-    case DT_C64: jacobi_t<float2>(d, nd, smem, s); break;
-    case DT_R64: jacobi_t<double>(d, nd, smem, s); break;
-    case DT_C128: jacobi_t<double2>(d, nd, smem, s); break;
+    case DT_R32: jacobi_t<float>(d, nd, smem, cluster_smem, s); break;
+    case DT_C64: jacobi_t<float2>(d, nd, smem, cluster_smem, s); break;
+    case DT_R64: jacobi_t<double>(d, nd, smem, cluster_smem, s); break;
+    case DT_C128: jacobi_t<double2>(d, nd, smem, cluster_smem, s); break;
   }
 }
 

@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cstring>
+
 #include "common.cuh"
 #include "plan.h"
 
@@ -251,6 +253,8 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
   if (apply) push_gemm(B, app, false, tag);
 }
 
+void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I);
+
 void emit_orth(Builder &B, std::vector<Inst *> &I, bool mside) {
   void *Inst::*a = mside ? &Inst::Y : &Inst::Z;
   void *Inst::*t = mside ? &Inst::P : &Inst::X;
@@ -269,12 +273,16 @@ void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
     emit_cqr_pass(B, I, false, &Inst::Z, &Inst::X, &Inst::R1, nullptr, nullptr, true, "svd_qr", true);
     emit_cqr_pass(B, I, false, &Inst::X, nullptr, &Inst::R2, &Inst::R1, &Inst::Rout, false, "svd_qr", false);
   }
+  emit_jacobi_finalize(B, I);
+}
+
+void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I) {
   std::vector<JacobiDesc> jd;
   std::vector<FinalizeDesc> fd;
   for (Inst *p : I) {
     Inst &q = *p;
     JacobiDesc j{};
-    j.Rb = q.Rout; j.Mw = q.Mw; j.sig = q.sig; j.n = q.ell; j.max_sweeps = 40; j.status = nullptr;
+    j.Rb = q.Rout; j.Mw = q.Mw; j.sig = q.sig; j.n = q.ell; j.max_sweeps = 30; j.status = nullptr;
     jd.push_back(j);
     FinalizeDesc f{};
     f.Mw = q.Mw; f.sig = q.sig; f.P = q.Y; f.g = q.g; f.Ut = q.Ut; f.sigma_out = q.sigma;
@@ -284,7 +292,10 @@ void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
   }
   Op oj;
   oj.kind = Op::JACOBI; oj.desc_off = B.put(jd); oj.nd = (int)jd.size(); oj.tag = "svd_jacobi";
-  for (auto &j : jd) oj.smem = std::max(oj.smem, small_smem_bytes(B.dt, j.n));
+  for (auto &j : jd) {
+    oj.smem = std::max(oj.smem, small_smem_bytes(B.dt, j.n));
+    oj.smem2 = std::max(oj.smem2, jacobi_cluster_smem_bytes(B.dt, j.n));
+  }
   B.ops.push_back(oj);
   Op of;
   of.kind = Op::FINALIZE; of.desc_off = B.put(fd); of.nd = (int)fd.size(); of.tag = "svd_finalize";
@@ -305,6 +316,218 @@ void emit_epilogue(Builder &B, std::vector<Inst *> &I) {
   }
   push_gemm(B, gu, false, "epilogue_u");
   push_gemm(B, gw, false, "epilogue_w");
+}
+
+
+// ===========================================================================
+// Tensor-core path (PEPS_PREC_MIXED).  Every stage of A X and A^H Y is one
+// K-contiguous GEMM on tcgen05 through layout maps:
+//   N-side block layout XL: [j][b][(X,E)][(x,e)]
+//   A X :  S1  T1[(j,l,u,b)][(s,X,E)] = X (.) K          over (x,e)
+//          S2  T2[j][(l,L)][(u,U,b)]  = T1 (.) conj(Kb)  over (s,X,E)
+//          S3  T3[j][(a,h)]           = T2 (.) S         over (u,U,b)
+//          S4  Y[j][mrow]             = V (.) T3         over (a,h)
+//   A^H Y: S4' Z3[(j,h)][a]           = conj(V^T) (.) Y  over mrow
+//          S3' Z2[(j,b,l,u)][(U,L)]   = Z3 (.) conj(S^T) over a
+//          S2' T1[(j,b,X,E)][(s,l,u)] = Z2 (.) Kb^T      over (U,L)
+//          S1' Z[(j,b,X,E)][(x,e)]    = T1 (.) conj(K^T) over (s,l,u)
+// ===========================================================================
+
+constexpr int64_t BIG = 0x7fffffff;
+
+DigitMap mkmap(std::initializer_list<std::pair<int64_t, int64_t>> l) {
+  DigitMap m{};
+  m.n = 0;
+  for (auto &p : l) {
+    m.radix[m.n] = (int32_t)std::min<int64_t>(p.first, BIG);
+    m.stride[m.n] = p.second;
+    ++m.n;
+  }
+  return m;
+}
+
+void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const void *Bm, int64_t rowsB, int64_t K,
+             bool conjA, bool conjB, bool split3, void *C, DigitMap mm, DigitMap mn, bool conjC,
+             const double *alpha_dev) {
+  Op op;
+  op.kind = Op::TC;
+  op.tag = tag;
+  TcDesc &d = op.tc;
+  std::memset(&d, 0, sizeof d);
+  const bool cplx = dtype_complex(B.dt);
+  const int64_t kr = K * (cplx ? 2 : 1);
+  const int bn = tc_block_n((int)rowsB);
+  if (B.encode) {
+    const bool ok = tc_encode_map(&d.ta, A, rowsA, kr, kr * 4, 128) && tc_encode_map(&d.tb, Bm, rowsB, kr, kr * 4, bn);
+    if (!ok && B.err.empty()) B.err = std::string("TMA map encoding failed for ") + tag;
+  }
+  d.M = (int32_t)rowsA; d.N = (int32_t)rowsB; d.Kr = (int32_t)kr;
+  d.cplx = cplx; d.conjA = conjA; d.conjB = conjB; d.split3 = split3;
+  d.tiles_m = (int32_t)ceil_div(rowsA, 128);
+  d.tiles_n = (int32_t)ceil_div(rowsB, bn);
+  d.mm = mm; d.mn = mn;
+  d.C = C;
+  d.alpha = 1.0;
+  d.alpha_dev = alpha_dev;
+  d.conjC = conjC;
+  op.tc_bn = bn;
+  op.tcA = A; op.tcB = Bm; op.tcA_rows = rowsA; op.tcB_rows = rowsB; op.tc_kr = kr;
+  const double mult = cplx ? 8.0 : 2.0, es = dtype_size(B.dt);
+  op.flops = mult * (double)rowsA * rowsB * K;
+  op.bytes = es * ((double)rowsA * K + (double)rowsB * K + (double)rowsA * rowsB);
+  B.ops.push_back(op);
+}
+
+// G = src^H src for an l x L block stored [j][n] (any order of n), FP64
+// accumulators, split over K.
+void emit_gram_tc(Builder &B, Inst &q, const void *src, int64_t L, const char *tag) {
+  const int as = acc_size(B.dt);
+  std::vector<std::pair<void *, int64_t>> zr{{q.G, (int64_t)q.ell * q.ell * as / 8}};
+  push_zero(B, zr, tag);
+  emit_tc(B, tag, src, q.ell, src, q.ell, L, true, false, true, q.G, mkmap({{BIG, q.ell}}), mkmap({{BIG, 1}}),
+          false, nullptr);
+  Op &op = B.ops.back();
+  const int64_t kr = op.tc_kr;
+  const int64_t nkb = ceil_div(kr, 32);
+  const int64_t chunk_kb = dtype_complex(B.dt) ? 128 : 64;   // 2048 complex / 2048 real K values
+  op.tc.atomic64 = 1;
+  op.tc.kb_per_split = (int32_t)chunk_kb;
+  op.tc.ksplit = (int32_t)ceil_div(nkb, chunk_kb);
+  op.bytes = dtype_size(B.dt) * (double)q.ell * L + acc_size(B.dt) * (double)q.ell * q.ell;
+}
+
+void emit_permute(Builder &B, const char *tag, std::vector<PermuteDesc> d) {
+  std::vector<int64_t> bl;
+  double by = 0;
+  for (auto &p : d) {
+    bl.push_back(permute_blocks(p));
+    by += 2.0 * dtype_size(B.dt) * p.nb * p.R * p.Cc * p.Q;
+  }
+  const size_t before = B.ops.size();
+  push_grouped(B, Op::PERMUTE, d.data(), sizeof(PermuteDesc), (int)d.size(), bl, tag);
+  if (B.ops.size() > before) B.ops.back().bytes = by;
+}
+
+PermuteDesc mk_perm(const void *in, void *out, int64_t nb, int64_t R, int64_t C, int64_t Q, bool conj = false) {
+  PermuteDesc p{};
+  p.in = in; p.out = out; p.nb = nb; p.R = R; p.Cc = C; p.Q = Q; p.conj = conj;
+  return p;
+}
+
+struct Dims6 {
+  int64_t l, b, P1, Q1, P2, Q2, d, h, v, a, M, N;
+};
+Dims6 dims_of(const Inst &q, int64_t ncols) {
+  return Dims6{ncols, q.b, (int64_t)q.Dl * q.Du, (int64_t)q.Dx * q.De, (int64_t)q.DL * q.DU,
+               (int64_t)q.DX * q.DE, q.d, q.h, q.v, q.a, q.M, q.N};
+}
+
+// per-step operand preparation: K^T, Kb permutes, S^T, V^T
+void emit_tc_prep(Builder &B, Inst &q) {
+  const Dims6 z = dims_of(q, q.ell);
+  // Kb [s][L][U][(X,E)] -> KbT [s][(X,E)][U][L]: swap L and U, then move (X,E) ahead
+  emit_permute(B, "tc_prep", {mk_perm(q.K, q.KT, 1, z.d * z.P1, z.Q1, 1),
+                              mk_perm(q.Kb, q.KbP, z.d, q.DL, q.DU, z.Q2),
+                              mk_perm(q.S, q.ST, 1, z.a, z.v * z.b, 1),
+                              mk_perm(q.V, q.VT, 1, z.M, z.a * z.h, 1)});
+  emit_permute(B, "tc_prep", {mk_perm(q.KbP, q.KbT, z.d, z.P2, z.Q2, 1)});
+  // Kb [s][(L,U)][(X,E)] -> KbP [(L,U)][s][(X,E)] (forward stage S2)
+  emit_permute(B, "tc_prep", {mk_perm(q.Kb, q.KbP, 1, z.d, z.P2, z.Q2)});
+}
+
+void emit_product_tc(Builder &B, Inst &q, const void *src, void *dst, bool split3) {
+  const Dims6 z = dims_of(q, q.ell);
+  // T1 rows (j, l, u, b) with b fastest, columns (s, X, E)
+  emit_tc(B, "product_sites", src, z.l * z.b * z.Q2, q.K, z.d * z.P1, z.Q1, false, false, split3, q.T1,
+          mkmap({{z.Q2, 1}, {z.b, z.d * z.Q2}, {BIG, z.P1 * z.b * z.d * z.Q2}}),
+          mkmap({{z.P1, z.b * z.d * z.Q2}, {BIG, z.Q2}}), false, nullptr);
+  emit_tc(B, "product_sites", q.T1, z.l * z.b * z.P1, q.KbP, z.P2, z.d * z.Q2, false, true, split3, q.T2,
+          mkmap({{z.b, 1}, {q.Du, (int64_t)q.DU * z.b}, {q.Dl, (int64_t)q.DL * z.v * z.b}, {BIG, z.h * z.v * z.b}}),
+          mkmap({{q.DU, z.b}, {BIG, z.v * z.b}}), false, nullptr);
+  emit_tc(B, "product_boundary", q.T2, z.l * z.h, q.S, z.a, z.v * z.b, false, false, split3, q.T3,
+          mkmap({{z.h, 1}, {BIG, z.a * z.h}}), mkmap({{BIG, z.h}}), false, nullptr);
+  emit_tc(B, "product_carry", q.V, z.M, q.T3, z.l, z.a * z.h, false, false, split3, dst, mkmap({{BIG, 1}}),
+          mkmap({{BIG, z.M}}), false, nullptr);
+}
+
+// A^H P for ncols columns of P ([j][mrow]); result in the XL layout, or (W
+// mode) conjugated, scaled by 1/sigma_1 and written in the carry layout.
+void emit_adjoint_tc(Builder &B, Inst &q, const void *Pin, int64_t ncols, void *dst, bool wmode, bool split3) {
+  const Dims6 z = dims_of(q, ncols);
+  emit_tc(B, "adjoint_carry", q.VT, z.a * z.h, Pin, z.l, z.M, true, false, split3, q.T3,
+          mkmap({{z.h, z.a}, {BIG, 1}}), mkmap({{BIG, z.h * z.a}}), false, nullptr);
+  // Z2 rows (j, b, l, u) with u fastest, columns (U, L) with L fastest;
+  // computed as Z3 (.) conj(S^T) so that lanes write along L
+  emit_tc(B, "adjoint_boundary", q.T3, z.l * z.h, q.ST, z.v * z.b, z.a, false, true, split3, q.T2,
+          mkmap({{q.DL, 1}, {q.Dl, (int64_t)q.Du * z.P2}, {BIG, z.b * z.P1 * z.P2}}),
+          mkmap({{z.b, z.P1 * z.P2}, {q.DU, q.DL}, {BIG, z.P2}}), false, nullptr);
+  emit_tc(B, "adjoint_sites", q.T2, z.l * z.b * z.P1, q.KbT, z.d * z.Q2, z.P2, false, false, split3, q.T1,
+          mkmap({{q.Du, 1}, {q.Dl, q.Du}, {z.b, z.Q2 * z.d * z.P1}, {BIG, z.b * z.Q2 * z.d * z.P1}}),
+          mkmap({{z.Q2, z.d * z.P1}, {BIG, z.P1}}), false, nullptr);
+  if (!wmode)
+    emit_tc(B, "adjoint_sites", q.T1, z.l * z.b * z.Q2, q.KT, z.Q1, z.d * z.P1, false, true, split3, dst,
+            mkmap({{BIG, z.Q1}}), mkmap({{BIG, 1}}), false, nullptr);
+  else
+    emit_tc(B, "epilogue_w", q.T1, z.l * z.b * z.Q2, q.KT, z.Q1, z.d * z.P1, false, true, split3, dst,
+            mkmap({{q.DE, 1}, {q.DX, z.b * q.De * q.DE}, {z.b, (int64_t)q.De * q.DE}, {BIG, z.N}}),
+            mkmap({{q.De, q.DE}, {BIG, (int64_t)q.DX * z.b * q.De * q.DE}}), true, q.inv_s1);
+}
+
+// Sketch in the XL layout: logical n = (x, X, b, e, E), least significant E.
+void emit_sketch_xl(Builder &B, Inst &q, const RsvdOpts &o) {
+  std::vector<Inst *> one{&q};
+  const size_t before = B.ops.size();
+  emit_sketch(B, one, o);
+  if (B.ops.size() == before) return;
+  SketchDesc *d = (SketchDesc *)(B.blob.data() + B.ops.back().desc_off);
+  const int64_t Q1 = (int64_t)q.Dx * q.De;
+  d[0].nd = 5;
+  const int64_t rad[5] = {q.DE, q.De, q.b, q.DX, BIG};
+  const int64_t str[5] = {Q1, 1, (int64_t)q.DX * q.DE * Q1, (int64_t)q.DE * Q1, q.De};
+  for (int i = 0; i < 5; ++i) { d[0].radix[i] = (int32_t)rad[i]; d[0].stride[i] = str[i]; }
+}
+
+void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {
+  std::vector<Inst *> one{&q};
+  emit_tc_prep(B, q);
+  emit_sketch_xl(B, q, o);
+  // 3xTF32 (FP32-level) products throughout; the FAST precision runs the
+  // products before the last A Q of the power iteration on plain TF32
+  const bool fast = o.prec == 2;
+  emit_product_tc(B, q, q.X, q.Y, !fast || o.q == 0);
+  emit_orth(B, one, true);
+  for (int it = 0; it < o.q; ++it) {
+    const bool last = it == o.q - 1;
+    emit_adjoint_tc(B, q, q.Y, q.ell, q.Z, false, !fast);
+    if (o.orth_q) emit_orth(B, one, false);
+    emit_product_tc(B, q, q.Z, q.Y, !fast || last);
+    emit_orth(B, one, true);
+  }
+  emit_adjoint_tc(B, q, q.Y, q.ell, q.Z, false, true);      // Z = A^H P = B^H
+  // R_B: Cholesky factor of the Gram Z^H Z (= B B^H, B = P^H A).  3xTF32
+  // tensor-core products, FP32 partial sums over chunks of 2048 K values,
+  // chunks combined in FP64, so the factor carries Z's own error only (a Gram
+  // formed from P^H (A Z) would square the product error into the singular
+  // values).
+  emit_gram_tc(B, q, q.Z, q.N, "svd_gram");
+  {
+    std::vector<CholDesc> ch(1);
+    ch[0] = CholDesc{};
+    ch[0].G = q.G; ch[0].T = q.Tm; ch[0].R = q.Rout; ch[0].n = q.ell; ch[0].tol = chol_tol(B.dt, q.ell);
+    Op op;
+    op.kind = Op::CHOL; op.desc_off = B.put(ch); op.nd = 1; op.tag = "svd_gram";
+    op.smem = small_smem_bytes(B.dt, q.ell);
+    B.ops.push_back(op);
+  }
+  emit_jacobi_finalize(B, one);
+  // U = P U~ and its transpose (input of the W adjoint)
+  {
+    std::vector<GemmDesc> gu{mk_gemm((int)q.M, q.k, q.ell, 1, q.Y, 1, q.M, 0, false, q.Ut, q.k, 1, 0, false, q.U,
+                                     q.k, 1, 0)};
+    push_gemm(B, gu, false, "epilogue_u");
+    emit_permute(B, "epilogue_u", {mk_perm(q.U, q.UT, 1, q.M, q.k, 1)});
+  }
+  emit_adjoint_tc(B, q, q.UT, q.k, q.W, true, true);        // W = U^H A / sigma_1
 }
 
 }  // namespace
@@ -331,6 +554,12 @@ size_t inst_scratch_bytes(const Inst &I, int dt) {
   s += al(l * l * es) + al(l * I.k * es);                 // Tm, Ut
   s += 5 * al(l * l * as);                                // G, R1, R2, Rout, Mw
   s += al(l * 8) + al(8);                                 // sig, inv_s1
+  if (I.tc) {
+    const size_t P1 = (size_t)I.Dl * I.Du, Q1 = (size_t)I.Dx * I.De, P2 = (size_t)I.DL * I.DU,
+                 Q2 = (size_t)I.DX * I.DE;
+    s += al(l * I.b * I.d * P1 * Q2 * es) + al((size_t)I.M * I.a * I.h * es) + al((size_t)I.a * I.v * I.b * es);
+    s += al((size_t)I.k * I.M * es) + al(Q1 * I.d * P1 * es) + 2 * al((size_t)I.d * P2 * Q2 * es);
+  }
   return s;
 }
 
@@ -353,12 +582,37 @@ void inst_alloc_scratch(Builder &B, Inst &I, int dt) {
   I.Mw = B.buf(l * l * as);
   I.sig = (double *)B.buf(l * 8);
   I.inv_s1 = (double *)B.buf(8);
+  I.T1 = I.VT = I.ST = I.UT = I.KT = I.KbP = I.KbT = nullptr;
+  if (I.tc) {
+    const size_t P1 = (size_t)I.Dl * I.Du, Q1 = (size_t)I.Dx * I.De, P2 = (size_t)I.DL * I.DU,
+                 Q2 = (size_t)I.DX * I.DE;
+    I.T1 = B.buf(l * I.b * I.d * P1 * Q2 * es);
+    I.VT = B.buf((size_t)I.M * I.a * I.h * es);
+    I.ST = B.buf((size_t)I.a * I.v * I.b * es);
+    I.UT = B.buf((size_t)I.k * I.M * es);
+    I.KT = B.buf(Q1 * I.d * P1 * es);
+    I.KbP = B.buf((size_t)I.d * P2 * Q2 * es);
+    I.KbT = B.buf((size_t)I.d * P2 * Q2 * es);
+  }
 }
 
 void inst_share_scratch(Inst &I, const Inst &o) {
   I.X = o.X; I.Z = o.Z; I.T2 = o.T2; I.T3 = o.T3; I.Y = o.Y; I.P = o.P; I.g = o.g; I.Tm = o.Tm;
   I.Ut = o.Ut; I.G = o.G; I.R1 = o.R1; I.R2 = o.R2; I.Rout = o.Rout; I.Mw = o.Mw; I.sig = o.sig;
   I.inv_s1 = o.inv_s1;
+  I.T1 = o.T1; I.VT = o.VT; I.ST = o.ST; I.UT = o.UT; I.KT = o.KT; I.KbP = o.KbP; I.KbT = o.KbT;
+}
+
+bool inst_tc_ok(const Inst &I, int dt) {
+  if (dtype_double(dt)) return false;
+  const int64_t align = dtype_complex(dt) ? 2 : 4;    // K multiple: rows 16-byte aligned
+  const int64_t P1 = (int64_t)I.Dl * I.Du, Q1 = (int64_t)I.Dx * I.De, P2 = (int64_t)I.DL * I.DU,
+                Q2 = (int64_t)I.DX * I.DE;
+  const int64_t ks[] = {Q1, (int64_t)I.d * Q2, (int64_t)I.v * I.b, (int64_t)I.a * I.h, I.M, I.a, P2,
+                        (int64_t)I.d * P1};
+  for (int64_t k : ks)
+    if (k % align) return false;
+  return true;
 }
 
 std::string inst_check(const Inst &I, int dt) {
@@ -382,6 +636,17 @@ std::string inst_check(const Inst &I, int dt) {
 }
 
 void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
+  // tensor-core instances run one by one; the rest share grouped launches
+  std::vector<Inst *> simt;
+  for (Inst *p : I) {
+    if (p->tc) emit_einsumsvd_tc(B, *p, o);
+    else simt.push_back(p);
+  }
+  if (simt.empty()) return;
+  emit_einsumsvd_simt(B, simt, o);
+}
+
+void emit_einsumsvd_simt(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
   emit_sketch(B, I, o);
   emit_product(B, I, true);
   emit_orth(B, I, true);

@@ -15,7 +15,8 @@
 // worker warps apply them in shared memory between the TMA and the MMAs.
 // SPLIT3 ("3xTF32") splits each operand into a TF32 head and an FP32 tail
 // and accumulates head*head + tail*head + head*tail, recovering FP32-level
-// products on TF32 tensor cores.
+// products on TF32 tensor cores.  Plain TF32 products round both operands to
+// the nearest TF32 value first (unbiased, half the error of truncation).
 //
 // Roles: warp 0 issues TMA, warp 1 owns tensor memory and issues MMAs from
 // one thread, warps 2-5 rewrite operand tiles and run the epilogue (tensor
@@ -120,8 +121,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// nearest TF32 value (ties away from zero): exact input to the tensor core
 __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+__device__ __forceinline__ float4 round4(float4 v) {
+  return make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
 }
 
 __device__ __forceinline__ int64_t map_index(const DigitMap &m, int64_t i) {
@@ -154,13 +159,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   __shared__ __align__(8) uint64_t full_bar[STAGES], ready_bar[STAGES], empty_bar[STAGES], done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
+  __shared__ int64_t col_off[BN];
   extern __shared__ __align__(1024) unsigned char dyn[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tm = blockIdx.x % g.tiles_m, tn = blockIdx.x / g.tiles_m;
+  const int ntile = g.tiles_m * g.tiles_n;
+  const int tile = blockIdx.x % ntile, kc = blockIdx.x / ntile;
+  const int tm = tile % g.tiles_m, tn = tile / g.tiles_m;
   const int m0 = tm * BM, n0 = tn * BN;
-  const int nkb = (g.Kr + BKF - 1) / BKF;
+  const int nkb_all = (g.Kr + BKF - 1) / BKF;
+  const int kb0 = g.ksplit > 1 ? kc * g.kb_per_split : 0;
+  const int nkb = g.ksplit > 1 ? min(g.kb_per_split, nkb_all - kb0) : nkb_all;
 
   auto a_tile = [&](int s, int which) { return smem + s * L::STAGE + which * L::A_BYTES; };
   auto b_tile = [&](int s, int which) { return smem + s * L::STAGE + L::NA * L::A_BYTES + which * L::B_BYTES; };
@@ -194,8 +204,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         const int s = kb % STAGES;
         if (kb >= STAGES && !mbar_wait(&empty_bar[s], ((kb / STAGES) - 1) & 1, &abort_flag)) break;
         mbar_expect_tx(&full_bar[s], (uint32_t)(L::A_BYTES + L::B_BYTES));
-        tma_load_2d(a_tile(s, 0), &g.ta, kb * BKF, m0, &full_bar[s]);
-        tma_load_2d(b_tile(s, 0), &g.tb, kb * BKF, n0, &full_bar[s]);
+        tma_load_2d(a_tile(s, 0), &g.ta, (kb0 + kb) * BKF, m0, &full_bar[s]);
+        tma_load_2d(b_tile(s, 0), &g.tb, (kb0 + kb) * BKF, n0, &full_bar[s]);
         issued = kb + 1;
       }
     }
@@ -245,7 +255,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES;
       if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, &abort_flag)) break;
-      if (CPLX || SPLIT3) {
+      {
         float4 *A0 = (float4 *)a_tile(s, 0);
         float4 *A1 = (float4 *)a_tile(s, 1);
         for (int c = t; c < L::A_BYTES / 16; c += 128) {
@@ -253,6 +263,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
           if (CPLX) {
             float4 re = make_float4(v.x, sr * v.y, v.z, sr * v.w);
             float4 imv = make_float4(s1 * v.y, s2 * v.x, s1 * v.w, s2 * v.z);
+            if (!SPLIT3) {
+              re = round4(re);
+              imv = round4(imv);
+            }
             if (SPLIT3) {
               float4 *A2 = (float4 *)a_tile(s, 2);
               float4 *A3 = (float4 *)a_tile(s, 3);
@@ -265,12 +279,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             }
             A0[c] = re;
             A1[c] = imv;
-          } else {
+          } else if (SPLIT3) {
             // real SPLIT3: head in place, tail to tile 1
             const float4 h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
             A1[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
             A0[c] = h;
+          } else {
+            A0[c] = round4(v);
           }
+        }
+        if (!SPLIT3) {
+          // TF32 products: round B to nearest as well (the tensor core would truncate)
+          float4 *B0 = (float4 *)b_tile(s, 0);
+          for (int c = t; c < L::B_BYTES / 16; c += 128) B0[c] = round4(B0[c]);
         }
         if (SPLIT3) {
           float4 *B0 = (float4 *)b_tile(s, 0);
@@ -290,6 +311,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 
   // ---- epilogue (warps 2..5 own tensor-memory lane quarters 2, 3, 0, 1) ----
   if (warp >= 2) {
+    // output offsets of this tile's columns, once per tile
+    for (int c = threadIdx.x - 64; c < BN; c += 128) col_off[c] = n0 + c < g.N ? map_index(g.mn, n0 + c) : 0;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
     bool ok = !abort_flag && mbar_wait(&done_bar, 0, &abort_flag);
     ok = __all_sync(0xffffffffu, ok);      // tensor-memory loads are warp-collective
     if (ok) {
@@ -310,8 +334,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         for (int i = 0; i < 16; ++i) {
           const int n = n0 + c0 + i;
           if (n >= g.N) break;
-          const int64_t off = row_off + map_index(g.mn, n);
-          if (CPLX) {
+          const int64_t off = row_off + col_off[c0 + i];
+          if (g.atomic64) {
+            if (CPLX) {
+              double2 *C = (double2 *)g.C + off;
+              atomicAdd(&C->x, alpha * (double)re[i]);
+              atomicAdd(&C->y, (g.conjC ? -alpha : alpha) * (double)imv[i]);
+            } else {
+              atomicAdd((double *)g.C + off, alpha * (double)re[i]);
+            }
+          } else if (CPLX) {
             float2 v = make_float2((float)(alpha * re[i]), (float)(alpha * imv[i]));
             if (g.conjC) v.y = -v.y;
             float2 *C = (float2 *)g.C + off;
@@ -355,7 +387,7 @@ template <int BN, bool CPLX, bool SPLIT3> void launch_tc(const TcDesc &d, cudaSt
     cudaFuncSetAttribute(tc_gemm_kernel<BN, CPLX, SPLIT3>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
     set = true;
   }
-  const unsigned blocks = (unsigned)(d.tiles_m * d.tiles_n);
+  const unsigned blocks = (unsigned)(d.tiles_m * d.tiles_n * (d.ksplit > 1 ? d.ksplit : 1));
   if (blocks) tc_gemm_kernel<BN, CPLX, SPLIT3><<<blocks, NTHREADS, L::SMEM, s>>>(d);
 }
 

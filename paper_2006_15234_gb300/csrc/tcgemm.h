@@ -28,6 +28,8 @@ struct TcDesc {
   double alpha;
   const double *alpha_dev;
   int32_t accumulate, conjC;
+  int32_t atomic64;        // C holds FP64 accumulators (double / double2): atomicAdd
+  int32_t ksplit, kb_per_split;   // K cut into ksplit chunks of kb_per_split 32-float blocks
   uint32_t *status;
 };
 

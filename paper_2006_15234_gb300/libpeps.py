@@ -15,11 +15,11 @@ from dataclasses import dataclass
 __all__ = [
     "PepsError", "load", "lib_path", "RsvdOpts", "EinsumsvdShape", "EinsumsvdIO",
     "Network", "ContractPlan", "EinsumsvdPlan", "boundary_contract", "dtype_code",
-    "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "SKETCH_GAUSS", "SKETCH_UNIFORM",
-    "debug_tc_gemm",
+    "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "PREC_FAST", "SKETCH_GAUSS", "SKETCH_UNIFORM",
+    "debug_tc_gemm", "FLAG_ORTH_Q",
 ]
 
-PREC_PLAIN, PREC_MIXED = 0, 1
+PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
 SKETCH_GAUSS, SKETCH_UNIFORM = 0, 1
 
 EXPORTED_SYMBOLS = [
@@ -137,8 +137,11 @@ def dtype_code(dtype) -> int:
     return {torch.float32: 0, torch.complex64: 1, torch.float64: 2, torch.complex128: 3}[dtype]
 
 
-def make_opts(m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN) -> RsvdOpts:
-    return RsvdOpts(int(m), int(p), int(q), int(seed) & (2 ** 64 - 1), int(sketch), int(prec), 0)
+FLAG_ORTH_Q = 1
+
+
+def make_opts(m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN, flags=0) -> RsvdOpts:
+    return RsvdOpts(int(m), int(p), int(q), int(seed) & (2 ** 64 - 1), int(sketch), int(prec), int(flags))
 
 
 __all__.append("make_opts")
@@ -306,11 +309,11 @@ class EinsumsvdPlan(_Ledger):
 
 
 def boundary_contract(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN,
-                      direction=0, with_sigma=False, stream=None):
+                      direction=0, with_sigma=False, stream=None, flags=0):
     """Contract <bra|ket> (or the one-layer ket when bra is None) on the GPU.
 
     Returns (log|v|, arg v) [and the per-step singular values]."""
-    plan = ContractPlan(ket, bra, make_opts(m, p, q, seed, sketch, prec), direction)
+    plan = ContractPlan(ket, bra, make_opts(m, p, q, seed, sketch, prec, flags), direction)
     plan.execute(stream)
     return plan.result(stream, with_sigma)
 

@@ -110,3 +110,28 @@ def test_single_row_and_single_column():
         la, _, _ = _run(ket, ket, "c128", 4, 2, 1, 3)
         ex = bruteforce.exact_scalar(ket, ket)
         assert la == pytest.approx(np.log(abs(ex)), abs=1e-9)
+
+
+def test_c2_mixed_precision():
+    """Tensor-core products: the log-norm stays within 1e-5 of the FP64
+    oracle and the first row's einsumsvd steps (identical inputs) keep their
+    singular values within 1e-5 normwise."""
+    cfg = synth.config("c2")
+    ket = synth.peps_for(cfg)
+    rec = []
+    la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=libpeps.PREC_MIXED)
+    ra, rp = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec)
+    assert abs(la - ra) <= 1e-5 * abs(ra)
+    errs = sigma_errors(sig, rec)
+    row1 = [i for i, r in enumerate(rec) if r["row"] == 1]
+    assert errs[row1].max() <= 1e-5
+
+
+def test_c2_fast_precision_log_norm():
+    """PEPS_PREC_FAST (plain TF32 for the early power-iteration products): the
+    contracted scalar stays within 1e-5 of the FP64 oracle."""
+    cfg = synth.config("c2")
+    ket = synth.peps_for(cfg)
+    la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=libpeps.PREC_FAST)
+    ra, rp = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed)
+    assert abs(la - ra) <= 1e-5 * abs(ra)

@@ -122,3 +122,25 @@ def test_c3_sample_instances_full_size():
     for c, mm, i in zip(cases, ms, pick):
         out = _run_batch([c], "f32", mm, cfg.p, cfg.q, cfg.omega_seed)
         _check(c, out[0], mm, cfg.p, cfg.q, cfg.omega_seed, 100, "f32")
+
+
+@pytest.mark.parametrize("dtype", ["c64", "f32"])
+def test_mixed_precision_tensor_core_step(dtype):
+    """PEPS_PREC_MIXED: tensor-core products (TF32 for the early power-iteration
+    products, 3xTF32 from the last A Q on).  Singular values stay within 1e-5
+    of the FP64 oracle (normwise); the factors within the looser bound that
+    single-precision singular vectors allow."""
+    rng = np.random.default_rng(8)
+    # every contracted extent even (complex) / a multiple of 4 (real): TMA rows
+    D = 4 if dtype == "c64" else 4
+    case = _operands(rng, 20, D * D, 20, 17 if dtype == "c64" else 16, 2, (D,) * 4, (D,) * 4, dtype)
+    out = _run_batch([case], dtype, 16, 8, 2, 42, prec=libpeps.PREC_MIXED)
+    V, S, K, Kb = case
+    U, W, s, l1 = rsvd.einsumsvd(V, S, K, Kb, 16, 8, 2, 42, 100)
+    gU, gW, gs, gl = out[0]
+    assert np.max(np.abs(gs - s)) <= 1e-5 * s[0]
+    assert gl == pytest.approx(l1, abs=1e-5)
+    k = len(s)
+    UW = U.reshape(-1, k) @ W.reshape(k, -1)
+    gUW = gU.reshape(-1, k) @ gW.reshape(k, -1)
+    assert np.linalg.norm(gUW - UW) <= 1e-4 * np.linalg.norm(UW)

@@ -36,12 +36,12 @@ class FakeHeap:
 ES = {0: 4, 1: 8, 2: 8, 3: 16}
 
 
-def _einsumsvd_ok(lib, dt, shapes, m, p, q):
+def _einsumsvd_ok(lib, dt, shapes, m, p, q, prec=0):
     heap = FakeHeap()
     n = len(shapes)
     arr = (L.EinsumsvdShape * n)(*[L.EinsumsvdShape(*s) for s in shapes])
     plan, ws = C.c_void_p(), C.c_size_t()
-    opts = L.make_opts(m, p, q, 1)
+    opts = L.make_opts(m, p, q, 1, prec=prec)
     assert lib.peps_einsumsvd_plan(C.byref(plan), dt, n, arr, None, C.byref(opts), C.byref(ws)) == 0
     es = ES[dt]
     io = (L.EinsumsvdIO * n)()
@@ -62,21 +62,23 @@ def _einsumsvd_ok(lib, dt, shapes, m, p, q):
     return r, msg, r2
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dt", [0, 1, 2, 3])
-def test_einsumsvd_test_shapes(lib, dt):
+def test_einsumsvd_test_shapes(lib, dt, prec):
     shapes = [(20, 9, 20, 17, 2, 3, 3, 3, 3, 3, 3, 3, 3), (4, 4, 6, 5, 2, 2, 2, 2, 2, 2, 2, 2, 2),
               (1, 9, 9, 9, 2, 3, 1, 3, 3, 3, 1, 3, 3), (16, 16, 16, 1, 2, 4, 4, 4, 1, 4, 4, 4, 1),
               (12, 4, 7, 3, 3, 2, 2, 2, 2, 2, 1, 2, 2), (2, 4, 3, 4, 2, 2, 2, 2, 2, 2, 2, 2, 2)]
-    r, msg, r2 = _einsumsvd_ok(lib, dt, shapes, 8, 4, 2)
+    r, msg, r2 = _einsumsvd_ok(lib, dt, shapes, 8, 4, 2, prec)
     assert r == 0, msg
     assert r2 != 0
 
 
-def test_batched_workload_sample(lib):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_workload_sample(lib, prec):
     cfg = synth.config("c3")
     dims = synth.batched_dims(cfg)[:64]
     shapes = [(m, D * D, m, m, 2, D, D, D, D, D, D, D, D) for m, D in dims]
-    r, msg, _ = _einsumsvd_ok(lib, 0, shapes, 128, cfg.p, cfg.q)
+    r, msg, _ = _einsumsvd_ok(lib, 0, shapes, 128, cfg.p, cfg.q, prec)
     assert r == 0, msg
 
 
@@ -101,16 +103,17 @@ def _net(heap, sites_shape, dt):
     return net, (bh, bv, ptrs)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("key,dt,two", [("c1", 2, False), ("c2", 1, True), ("c4", 0, True),
                                         ("c5", 1, True)])
-def test_contract_workloads(lib, key, dt, two):
+def test_contract_workloads(lib, key, dt, two, prec):
     cfg = synth.config(key)
     shp = [[synth.site_shape(cfg.nrow, cfg.ncol, p, q, cfg.d, cfg.D) for q in range(cfg.ncol)]
            for p in range(cfg.nrow)]
     heap = FakeHeap()
     net, keep = _net(heap, shp, dt)
     plan, ws = C.c_void_p(), C.c_size_t()
-    opts = L.make_opts(cfg.m, cfg.p, cfg.q, 1)
+    opts = L.make_opts(cfg.m, cfg.p, cfg.q, 1, prec=prec)
     assert lib.peps_contract_plan(C.byref(plan), C.byref(net), C.byref(net) if two else None,
                                   C.byref(opts), 0, C.byref(ws)) == 0, lib.peps_last_error()
     wsp = heap(ws.value)
@@ -128,7 +131,7 @@ def test_contract_test_shapes(lib, shape, D, m):
         heap = FakeHeap()
         net, keep = _net(heap, shp, dt)
         plan, ws = C.c_void_p(), C.c_size_t()
-        opts = L.make_opts(m, 8, 1, 1)
+        opts = L.make_opts(m, 8, 1, 1, prec=1 if dt == 1 else 0)
         assert lib.peps_contract_plan(C.byref(plan), C.byref(net), C.byref(net), C.byref(opts), 0,
                                       C.byref(ws)) == 0
         wsp = heap(ws.value)
