@@ -235,6 +235,44 @@ peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t conjB, int32
                                int32_t N, int32_t K, const void *A, const void *B, void *C,
                                void *stream);
 
+/* ------------------------------------------------------------------------
+ * Contraction without any allocation.  The paper has no counterpart: this
+ * is a service of this library for callers that cannot obtain device
+ * memory themselves.  Examples: a plugin whose host application hands it
+ * only the input and output buffers and keeps every allocator to itself;
+ * a process whose device memory is already reserved by another framework's
+ * caching allocator, so that a cudaMalloc would fail; a latency-bound loop
+ * that cannot afford cudaMalloc/cudaFree, which synchronise the device.
+ * ------------------------------------------------------------------------ */
+
+/* Size of the library's fixed device scratch array (32 MiB).  Every GPU
+ * on which the library is loaded holds one such array until the process
+ * exits. */
+#define PEPS_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* Same contraction and result as peps_boundary_contract (Algorithms 2 and 3
+ * with the einsumsvd of Algorithm 4), but the workspace is the library's
+ * static device array instead of caller memory, and the call allocates no
+ * device memory (no cudaMalloc, cudaFree or allocating library routine).
+ * The site tensors in ket / bra are device arrays as for
+ * peps_contract_plan; log_abs and phase are host pointers (either may be
+ * NULL).  The call synchronises `stream` before it returns.
+ *  - PEPS_ERR_WORKSPACE, before anything is enqueued, when the contraction
+ *    needs more than PEPS_STATIC_SCRATCH_BYTES of workspace (the need is
+ *    what peps_boundary_workspace reports; the message states both sizes).
+ *    Such contractions must use peps_boundary_contract with caller memory.
+ *  - Set-up: the first call on a device looks up the array's device
+ *    address, with that device current, and keeps it for later calls.
+ *    Make that first call before any stream capture is begun.
+ *  - Sharing: every call on a device uses the same array, which keeps what
+ *    the previous call left in it.  Each call clears the bytes it uses
+ *    before its kernels run.  Calls whose work can overlap on the GPU
+ *    (different streams, or host threads with no ordering between their
+ *    calls) race on the array and give wrong results: serialise them. */
+peps_status peps_boundary_contract_static(const peps_network *ket, const peps_network *bra,
+                                          const peps_rsvd_opts *opts, void *stream,
+                                          double *log_abs, double *phase);
+
 #ifdef __cplusplus
 }
 #endif

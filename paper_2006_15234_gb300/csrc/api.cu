@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -863,3 +864,63 @@ peps_status peps_plan_validate(peps_plan *plan, void *workspace, size_t workspac
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Contraction into the library's own device array (no allocation anywhere).
+// Some callers cannot allocate device memory: a plugin given only its input
+// and output buffers by a host application that owns every allocator, a
+// process whose memory another framework's caching allocator already holds,
+// or a latency-bound loop that cannot pay for cudaMalloc's device-wide
+// synchronisation.  They get the same sweep with this fixed scratch instead.
+// ---------------------------------------------------------------------------
+// One copy per device that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[PEPS_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+peps_status static_scratch(void **addr) {
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(PEPS_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+    if (!p || ((uintptr_t)p & 255)) return fail(PEPS_ERR_CUDA, "static scratch address %p unusable", p);
+    g_static_addr[dev] = p;
+  }
+  *addr = g_static_addr[dev];
+  return PEPS_OK;
+}
+
+}  // namespace
+
+extern "C" peps_status peps_boundary_contract_static(const peps_network *ket, const peps_network *bra,
+                                                     const peps_rsvd_opts *opts, void *stream,
+                                                     double *log_abs, double *phase) {
+  g_last_error.clear();
+  peps_plan *raw = nullptr;
+  size_t need = 0;
+  if (peps_status s = peps_contract_plan(&raw, ket, bra, opts, 0, &need)) return s;
+  std::unique_ptr<peps_plan> plan(raw);
+  if (need > PEPS_STATIC_SCRATCH_BYTES)
+    return fail(PEPS_ERR_WORKSPACE,
+                "contraction needs %zu bytes of workspace, more than the %zu-byte static scratch; "
+                "call peps_boundary_contract with caller memory instead",
+                need, (size_t)PEPS_STATIC_SCRATCH_BYTES);
+  void *ws = nullptr;
+  if (peps_status s = static_scratch(&ws)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array holds the previous call's values: start this one from zeros
+  CUDA_TRY(cudaMemsetAsync(ws, 0, need, st));
+  if (peps_status s = peps_contract_execute(plan.get(), ws, PEPS_STATIC_SCRATCH_BYTES, stream)) return s;
+  return peps_contract_result(plan.get(), ws, stream, log_abs, phase, nullptr);
+}

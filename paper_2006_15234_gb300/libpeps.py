@@ -16,7 +16,7 @@ __all__ = [
     "PepsError", "load", "lib_path", "RsvdOpts", "EinsumsvdShape", "EinsumsvdIO",
     "Network", "ContractPlan", "EinsumsvdPlan", "boundary_contract", "dtype_code",
     "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "PREC_FAST", "SKETCH_GAUSS", "SKETCH_UNIFORM",
-    "debug_tc_gemm", "FLAG_ORTH_Q",
+    "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -28,8 +28,11 @@ EXPORTED_SYMBOLS = [
     "peps_contract_plan", "peps_contract_execute", "peps_contract_result",
     "peps_contract_sigma_count", "peps_boundary_contract", "peps_boundary_workspace",
     "peps_plan_launch_count", "peps_plan_launch_info", "peps_plan_profile", "peps_plan_validate",
-    "peps_debug_tc_gemm",
+    "peps_debug_tc_gemm", "peps_boundary_contract_static",
 ]
+
+# Size of the library's fixed device scratch used by boundary_contract_static.
+STATIC_SCRATCH_BYTES = 32 << 20
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -121,6 +124,10 @@ def load():
     lib.peps_debug_tc_gemm.argtypes = [C.c_int32] * 7 + [vp, vp, vp, vp]
     lib.peps_plan_validate.restype = st
     lib.peps_plan_validate.argtypes = [vp, vp, C.c_size_t, C.POINTER(EinsumsvdIO)]
+    lib.peps_boundary_contract_static.restype = st
+    lib.peps_boundary_contract_static.argtypes = [C.POINTER(Network), C.POINTER(Network),
+                                                  C.POINTER(RsvdOpts), vp, C.POINTER(C.c_double),
+                                                  C.POINTER(C.c_double)]
     _lib = lib
     return lib
 
@@ -316,6 +323,23 @@ def boundary_contract(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PL
     plan = ContractPlan(ket, bra, make_opts(m, p, q, seed, sketch, prec, flags), direction)
     plan.execute(stream)
     return plan.result(stream, with_sigma)
+
+
+def boundary_contract_static(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN,
+                             stream=None, flags=0):
+    """boundary_contract without any device allocation: the workspace is the
+    library's own fixed scratch array (STATIC_SCRATCH_BYTES per device), for
+    callers that cannot allocate device memory.  Contractions needing more
+    raise.  Calls on one device share the array, so calls that may overlap on
+    the GPU must be serialised.  Returns (log|v|, arg v)."""
+    lib = load()
+    k = _network(ket)
+    b = _network(bra) if bra is not None else None
+    opts = make_opts(m, p, q, seed, sketch, prec, flags)
+    la, ph = C.c_double(), C.c_double()
+    _check(lib.peps_boundary_contract_static(C.byref(k.net), C.byref(b.net) if b else None, C.byref(opts),
+                                             _stream_handle(stream), C.byref(la), C.byref(ph)))
+    return la.value, ph.value
 
 
 def debug_tc_gemm(A, B, conjA=False, conjB=False, split3=False, stream=None):
