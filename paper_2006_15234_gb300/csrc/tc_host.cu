@@ -65,7 +65,7 @@ extern "C" peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t c
   const int64_t pitch = kr * 4;
   TcDesc d;
   std::memset(&d, 0, sizeof d);
-  const int bn = tc_block_n(N);
+  const int bn = tc_block_n(N, cplx != 0, split3 != 0);
   if (!tc_encode_map(&d.ta, A, M, kr, pitch, 128) || !tc_encode_map(&d.tb, B, N, kr, pitch, bn))
     return PEPS_ERR_UNSUPPORTED;
   d.M = M; d.N = N; d.Kr = (int32_t)kr;

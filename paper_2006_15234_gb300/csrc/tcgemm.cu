@@ -17,6 +17,12 @@
 // and accumulates head*head + tail*head + head*tail, recovering FP32-level
 // products on TF32 tensor cores.  Plain TF32 products round both operands to
 // the nearest TF32 value first (unbiased, half the error of truncation).
+// The tensor core's FP32 accumulator drops the bits of each addend below the
+// running sum's last place (measured: a relative bias of about 1e-8 per
+// accumulated K value, growing linearly with K).  SPLIT3 products therefore
+// accumulate only CK k blocks at a time in tensor memory (two buffers, so the
+// MMAs of one chunk overlap the read-back of the previous one) and the worker
+// warps add each chunk into FP32 registers with round-to-nearest.
 //
 // Roles: warp 0 issues TMA, warp 1 owns tensor memory and issues MMAs from
 // one thread, warps 2-5 rewrite operand tiles and run the epilogue (tensor
@@ -38,6 +44,7 @@ constexpr int BM = 128;
 constexpr int BKF = 32;              // floats of K per stage (one 128-byte swizzle row)
 constexpr int NTHREADS = 192;
 constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a wait gives up (~1 s)
+constexpr int CK = 2;                // k blocks per tensor-memory accumulation chunk (SPLIT3)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -149,14 +156,19 @@ template <int BN, bool CPLX, bool SPLIT3> struct Layout {
   static constexpr int STAGE = NA * A_BYTES + NB * B_BYTES;
   static constexpr int STAGES = (200 * 1024) / STAGE >= 4 ? 4 : ((200 * 1024) / STAGE >= 2 ? (200 * 1024) / STAGE : 1);
   static constexpr int SMEM = STAGES * STAGE + 1024;
-  static constexpr int TMEM_COLS = CPLX ? 2 * BN : (BN < 32 ? 32 : BN);
+  static constexpr int ACC_COLS = CPLX ? 2 * BN : (BN < 32 ? 32 : BN);   // one accumulator set
+  static constexpr bool FOLD = SPLIT3;                                     // chunked accumulation
+  static constexpr int TMEM_COLS = FOLD ? 2 * ACC_COLS : ACC_COLS;
+  static_assert(!FOLD || ACC_COLS <= 128, "register accumulators hold at most 128 columns");
 };
 
 template <int BN, bool CPLX, bool SPLIT3>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ TcDesc g) {
   using L = Layout<BN, CPLX, SPLIT3>;
   constexpr int STAGES = L::STAGES;
+  constexpr bool FOLD = L::FOLD;
   __shared__ __align__(8) uint64_t full_bar[STAGES], ready_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ int64_t col_off[BN];
@@ -183,6 +195,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -198,6 +214,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   int issued = 0;          // producer: k blocks whose TMA was issued
   bool mma_any = false;    // MMA thread: at least one MMA issued
 
+  // SPLIT3 workers: per-row FP32 sums of the chunks read back from tensor memory
+  const int q = warp & 3;  // tensor-memory lane quarter a worker warp may access
+  const int nchunks = (nkb + CK - 1) / CK;
+  int folded = 0;
+  float facc[FOLD ? L::ACC_COLS : 1];
+#pragma unroll
+  for (int i = 0; i < (FOLD ? L::ACC_COLS : 1); ++i) facc[i] = 0.f;
+  auto fold = [&]() -> bool {       // add chunk `folded` into facc (warp-collective)
+    const int b = folded & 1;
+    bool ok = !abort_flag && mbar_wait(&acc_full[b], (folded >> 1) & 1, &abort_flag);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * L::ACC_COLS);
+#pragma unroll
+    for (int c0 = 0; c0 < (FOLD ? L::ACC_COLS : 0); c0 += 16) {
+      float v[16];
+      tmem_ld16(base + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) facc[c0 + i] += v[i];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(&acc_empty[b]);
+    ++folded;
+    return true;
+  };
+
   if (warp == 0) {
     if (lane == 0) {
       for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
@@ -212,16 +255,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tf32_idesc(BN);
-      const uint32_t t_re = tmem, t_im = tmem + BN;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES;
+        const int chunk = kb / CK, buf = FOLD ? (chunk & 1) : 0;
+        const bool first = FOLD ? (kb % CK == 0) : (kb == 0);
+        // a buffer is reused once the workers have read back the chunk two before
+        if (FOLD && first && chunk >= 2 && !mbar_wait(&acc_empty[buf], ((chunk >> 1) - 1) & 1, &abort_flag)) break;
         if (!mbar_wait(&ready_bar[s], (kb / STAGES) & 1, &abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t t_re = tmem + (uint32_t)(buf * L::ACC_COLS), t_im = t_re + BN;
         const uint32_t a0 = smem_u32(a_tile(s, 0)), a1 = smem_u32(a_tile(s, 1));
         const uint32_t b0 = smem_u32(b_tile(s, 0));
 #pragma unroll
         for (int kk = 0; kk < BKF / 8; ++kk) {
-          const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+          const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
           const uint32_t off = kk * 32;
           mma_tf32(t_re, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc);
           if (CPLX) mma_tf32(t_im, sw128_desc(a1 + off), sw128_desc(b0 + off), idesc, acc);
@@ -239,6 +286,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         }
         mma_any = true;
         mma_commit(&empty_bar[s]);
+        if (FOLD && (kb % CK == CK - 1 || kb == nkb - 1)) mma_commit(&acc_full[buf]);
       }
       if (mma_any) mma_commit(&done_bar);
     }
@@ -254,7 +302,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     }
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES;
-      if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, &abort_flag)) break;
+      // warp-uniform exit: the read-backs below are warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[s], (kb / STAGES) & 1, &abort_flag))) break;
       {
         float4 *A0 = (float4 *)a_tile(s, 0);
         float4 *A1 = (float4 *)a_tile(s, 1);
@@ -306,6 +355,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
       mbar_arrive(&ready_bar[s]);
+      // with the next chunk's operands ready, read back the chunk before it
+      if (FOLD && kb % CK == CK - 1 && kb >= 2 * CK - 1 && !fold()) break;
     }
   }
 
@@ -314,47 +365,57 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     // output offsets of this tile's columns, once per tile
     for (int c = threadIdx.x - 64; c < BN; c += 128) col_off[c] = n0 + c < g.N ? map_index(g.mn, n0 + c) : 0;
     asm volatile("bar.sync 1, 128;" ::: "memory");
-    bool ok = !abort_flag && mbar_wait(&done_bar, 0, &abort_flag);
+    bool ok = __all_sync(0xffffffffu, !abort_flag);
+    if (FOLD)
+      while (ok && folded < nchunks) ok = fold();
+    // done_bar also tracks the last MMAs' completion signal, which must land before exit
+    ok = ok && mbar_wait(&done_bar, 0, &abort_flag);
     ok = __all_sync(0xffffffffu, ok);      // tensor-memory loads are warp-collective
     if (ok) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int q = warp & 3;
       const int m = m0 + q * 32 + lane;
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
       double alpha = g.alpha;
       if (g.alpha_dev) alpha *= *g.alpha_dev;
       const int64_t row_off = m < g.M ? map_index(g.mm, m) : 0;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float re[16], imv[16];
-        tmem_ld16(lane_base + c0, re);
-        if (CPLX) tmem_ld16(lane_base + BN + c0, imv);
-        if (m >= g.M) continue;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int n = n0 + c0 + i;
-          if (n >= g.N) break;
-          const int64_t off = row_off + col_off[c0 + i];
-          if (g.atomic64) {
-            if (CPLX) {
-              double2 *C = (double2 *)g.C + off;
-              atomicAdd(&C->x, alpha * (double)re[i]);
-              atomicAdd(&C->y, (g.conjC ? -alpha : alpha) * (double)imv[i]);
-            } else {
-              atomicAdd((double *)g.C + off, alpha * (double)re[i]);
-            }
-          } else if (CPLX) {
-            float2 v = make_float2((float)(alpha * re[i]), (float)(alpha * imv[i]));
-            if (g.conjC) v.y = -v.y;
-            float2 *C = (float2 *)g.C + off;
-            if (g.accumulate) { const float2 o = *C; v.x += o.x; v.y += o.y; }
-            *C = v;
+      auto store = [&](int cl, float re, float im) {
+        if (n0 + cl >= g.N) return;
+        const int64_t off = row_off + col_off[cl];
+        if (g.atomic64) {
+          if (CPLX) {
+            double2 *C = (double2 *)g.C + off;
+            atomicAdd(&C->x, alpha * (double)re);
+            atomicAdd(&C->y, (g.conjC ? -alpha : alpha) * (double)im);
           } else {
-            float v = (float)(alpha * re[i]);
-            float *C = (float *)g.C + off;
-            if (g.accumulate) v += *C;
-            *C = v;
+            atomicAdd((double *)g.C + off, alpha * (double)re);
           }
+        } else if (CPLX) {
+          float2 v = make_float2((float)(alpha * re), (float)(alpha * im));
+          if (g.conjC) v.y = -v.y;
+          float2 *C = (float2 *)g.C + off;
+          if (g.accumulate) { const float2 o = *C; v.x += o.x; v.y += o.y; }
+          *C = v;
+        } else {
+          float v = (float)(alpha * re);
+          float *C = (float *)g.C + off;
+          if (g.accumulate) v += *C;
+          *C = v;
+        }
+      };
+      if (FOLD) {
+        if (m < g.M) {
+#pragma unroll
+          for (int c = 0; c < BN; ++c) store(c, facc[c], CPLX ? facc[(BN + c) % L::ACC_COLS] : 0.f);
+        }
+      } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float re[16], imv[16];
+          tmem_ld16(lane_base + c0, re);
+          if (CPLX) tmem_ld16(lane_base + BN + c0, imv);
+          if (m >= g.M) continue;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) store(c0 + i, re[i], CPLX ? imv[i] : 0.f);
         }
       }
     }
@@ -393,14 +454,15 @@ template <int BN, bool CPLX, bool SPLIT3> void launch_tc(const TcDesc &d, cudaSt
 
 }  // namespace
 
-int tc_block_n(int N) { return N <= 64 ? 64 : 128; }
+int tc_block_n(int N, bool cplx, bool split3) { return N <= 64 || (cplx && split3) ? 64 : 128; }
 
 void launch_tc_gemm(const TcDesc &d, int bn, cudaStream_t s) {
   if (bn == 64) {
     if (d.cplx) { if (d.split3) launch_tc<64, true, true>(d, s); else launch_tc<64, true, false>(d, s); }
     else { if (d.split3) launch_tc<64, false, true>(d, s); else launch_tc<64, false, false>(d, s); }
   } else {
-    if (d.cplx) { if (d.split3) launch_tc<128, true, true>(d, s); else launch_tc<128, true, false>(d, s); }
+    // (tc_block_n never gives 128 for complex SPLIT3)
+    if (d.cplx) { if (!d.split3) launch_tc<128, true, false>(d, s); }
     else { if (d.split3) launch_tc<128, false, true>(d, s); else launch_tc<128, false, false>(d, s); }
   }
 }

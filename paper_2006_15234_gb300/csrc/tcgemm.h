@@ -33,8 +33,9 @@ struct TcDesc {
   uint32_t *status;
 };
 
-// Block N (64 or 128 output columns, complex or real) for an N extent.
-int tc_block_n(int N);
+// Block N (64 or 128 output columns) for an N extent; complex SPLIT3 products
+// use 64 (their register accumulators hold 2 x 64 columns).
+int tc_block_n(int N, bool cplx, bool split3);
 void launch_tc_gemm(const TcDesc &d, int bn, cudaStream_t s);
 
 // Encode a 2-D TMA map over rows x cols FP32 values (row pitch in bytes) with
