@@ -444,12 +444,16 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         for (int i = 0; i < op.nd; ++i) {
           const CholDesc &c = ((const CholDesc *)d)[i];
           const double n2 = (double)c.n * c.n;
+          const double ws_ = op.wide ? as : es;        // working-type size
           C.need(c.G, as * n2, tag, "G");
-          C.need(c.T, es * n2, tag, "T");
-          C.need(c.R, es * n2, tag, "R");
-          if (c.Rprev) { C.need(c.Rprev, es * n2, tag, "Rprev"); C.need(c.Rout, es * n2, tag, "Rout"); }
+          if (c.T) C.need(c.T, ws_ * n2, tag, "T");
+          C.need(c.R, ws_ * n2, tag, "R");
+          if (c.Rprev) { C.need(c.Rprev, ws_ * n2, tag, "Rprev"); C.need(c.Rout, ws_ * n2, tag, "Rout"); }
+          if (c.Rlow) C.need(c.Rlow, es * n2, tag, "Rlow");
+          if (c.Rlow && !op.wide) C.err = std::string(tag) + ": Rlow needs an FP64 factorisation";
           if (c.n > 1024) C.err = std::string(tag) + ": n above the pivot-flag buffer";
-          if (op.smem < small_smem_bytes(dt, c.n)) C.err = std::string(tag) + ": shared memory too small";
+          if (op.smem < small_smem_bytes(op.wide ? (dt | 2) : dt, c.n))
+            C.err = std::string(tag) + ": shared memory too small";
         }
         break;
       case Op::JACOBI:
@@ -582,7 +586,7 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
       case Op::SANDWICH:
         launch_sandwich(dt, (const SandwichDesc *)d, pre, op.nd, op.blocks, op.smem, s);
         break;
-      case Op::CHOL: launch_chol(dt, (const CholDesc *)d, op.nd, op.smem, s); break;
+      case Op::CHOL: launch_chol(op.wide ? (dt | 2) : dt, (const CholDesc *)d, op.nd, op.smem, s); break;
       case Op::JACOBI: launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, s); break;
       case Op::FINALIZE: launch_finalize(dt, (const FinalizeDesc *)d, op.nd, s); break;
       case Op::ZERO: launch_zero((const ZeroDesc *)d, pre, op.nd, op.blocks, s); break;

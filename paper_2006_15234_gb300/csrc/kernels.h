@@ -87,6 +87,7 @@ struct CholDesc {
   int32_t n;
   double tol;       // pivot threshold relative to the largest diagonal entry
   double shift;     // diagonal shift relative to the largest diagonal entry
+  void *Rlow;       // optional: R rounded to single precision (FP64 kernels only)
 };
 
 // One-sided Jacobi SVD of Mw = Rb^H (n x n, working type, column-major, built

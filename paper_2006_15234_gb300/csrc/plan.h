@@ -22,6 +22,7 @@ struct Op {
   int64_t blocks = 0;
   int smem = 0;
   int smem2 = 0;          // second kernel of the launch (cluster Jacobi)
+  bool wide = false;      // CHOL: run in FP64 on single-precision data
   ScalarDesc scalar{};
   size_t aux_off[3] = {0, 0, 0};  // blob offsets of the scalar's device arrays
   void *fill_ptr = nullptr;

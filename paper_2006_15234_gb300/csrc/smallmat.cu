@@ -146,6 +146,16 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
       if ((int)(t % n) < (int)(t / n)) R[t] = zero<T>();
   __syncthreads();
 
+  if constexpr (sizeof(typename Traits<T>::Real) == 8) {
+    if (g.Rlow) {
+      for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+        if constexpr (sizeof(T) == 16) ((float2 *)g.Rlow)[t] = narrow<float2>(widen(R[t]));
+        else ((float *)g.Rlow)[t] = narrow<float>(widen(R[t]));
+      }
+    }
+  }
+  if (!g.T) return;
+
   // T = R^+ row by row from the bottom: T[i][c] = -(sum_{k=i+1..c} R[i][k] T[k][c]) / R[i][i]
   T *Tm = (T *)g.T;
   const int warps = NT / 32, w = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -511,12 +511,20 @@ void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {
   // values).
   emit_gram_tc(B, q, q.Z, q.N, "svd_gram");
   {
+    // FP64 Cholesky of the FP64 Gram (its backward error then stays far
+    // below the Gram's own, so sigma_i carries only O(u sigma_1^2 / sigma_i)
+    // from Z; an FP32 factorisation would add O(sqrt(l) u sigma_1^2 / sigma_i)),
+    // R_B rounded once to the working precision for the Jacobi SVD.
+    const int wdt = B.dt | 2;   // R32 -> R64, C64 -> C128
     std::vector<CholDesc> ch(1);
     ch[0] = CholDesc{};
-    ch[0].G = q.G; ch[0].T = q.Tm; ch[0].R = q.Rout; ch[0].n = q.ell; ch[0].tol = chol_tol(B.dt, q.ell);
+    ch[0].G = q.G; ch[0].T = nullptr; ch[0].R = q.R2; ch[0].n = q.ell; ch[0].tol = chol_tol(B.dt, q.ell);
+    ch[0].Rlow = wdt != B.dt ? q.Rout : nullptr;
+    if (wdt == B.dt) ch[0].R = q.Rout;
     Op op;
     op.kind = Op::CHOL; op.desc_off = B.put(ch); op.nd = 1; op.tag = "svd_gram";
-    op.smem = small_smem_bytes(B.dt, q.ell);
+    op.wide = wdt != B.dt;
+    op.smem = small_smem_bytes(wdt, q.ell);
     B.ops.push_back(op);
   }
   emit_jacobi_finalize(B, one);
