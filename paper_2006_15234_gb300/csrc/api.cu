@@ -454,6 +454,8 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           if (c.n > 1024) C.err = std::string(tag) + ": n above the pivot-flag buffer";
           if (op.smem < small_smem_bytes(op.wide ? (dt | 2) : dt, c.n))
             C.err = std::string(tag) + ": shared memory too small";
+          if (op.smem2 < chol_cluster_smem_bytes(op.wide ? (dt | 2) : dt, c.n, c.T != nullptr))
+            C.err = std::string(tag) + ": cluster shared memory too small";
         }
         break;
       case Op::JACOBI:
@@ -463,6 +465,7 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           C.need(j.Mw, es * (double)j.n * j.n, tag, "Mw");
           if (op.smem < small_smem_bytes(dt, j.n)) C.err = std::string(tag) + ": shared memory too small";
           if (op.smem2 < jacobi_cluster_smem_bytes(dt, j.n)) C.err = std::string(tag) + ": cluster shared memory too small";
+          if (op.blocks < j.n) C.err = std::string(tag) + ": sigma refinement grid too small";
           C.need(j.sig, 8.0 * j.n, tag, "sig");
         }
         break;
@@ -586,8 +589,8 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
       case Op::SANDWICH:
         launch_sandwich(dt, (const SandwichDesc *)d, pre, op.nd, op.blocks, op.smem, s);
         break;
-      case Op::CHOL: launch_chol(op.wide ? (dt | 2) : dt, (const CholDesc *)d, op.nd, op.smem, s); break;
-      case Op::JACOBI: launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, s); break;
+      case Op::CHOL: launch_chol(op.wide ? (dt | 2) : dt, (const CholDesc *)d, op.nd, op.smem, op.smem2, s); break;
+      case Op::JACOBI: launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, (int)op.blocks, s); break;
       case Op::FINALIZE: launch_finalize(dt, (const FinalizeDesc *)d, op.nd, s); break;
       case Op::ZERO: launch_zero((const ZeroDesc *)d, pre, op.nd, op.blocks, s); break;
       case Op::SITE: launch_site(dt, (const SiteDesc *)d, pre, op.nd, op.blocks, s); break;

@@ -151,8 +151,10 @@ void launch_sandwich(int dt, const SandwichDesc *d, const int64_t *prefix, int n
                      int64_t blocks, int smem_bytes, cudaStream_t s);
 void launch_sketch(int dt, const SketchDesc *d, const int64_t *prefix, int nd,
                    int64_t blocks, cudaStream_t s);
-void launch_chol(int dt, const CholDesc *d, int nd, int smem, cudaStream_t s);
-void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s);
+void launch_chol(int dt, const CholDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s);
+// per-CTA shared memory of the cluster Cholesky for n x n (0: not routed there)
+int chol_cluster_smem_bytes(int dt, int n, bool needT);
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int cluster_smem, int nmax, cudaStream_t s);
 int jacobi_cluster_smem_bytes(int dt, int n);   // per-CTA shared memory of the cluster Jacobi (0: not used)
 int small_smem_bytes(int dt, int n);   // shared memory of chol / jacobi for n x n (0: global)
 void launch_finalize(int dt, const FinalizeDesc *d, int nd, cudaStream_t s);

@@ -154,7 +154,8 @@ __global__ void site_kernel(const SiteDesc *__restrict__ descs, const int64_t *_
   // K strides for [d][Dl][Du][Dx][De]
   const int64_t kE = 1, kX = g.De, kU = (int64_t)g.Dx * g.De, kL = kU * g.Du, kS = kL * g.Dl;
   const int64_t bE = 1, bX = g.DE, bU = (int64_t)g.DX * g.DE, bL = bU * g.DU, bS = bL * g.DL;
-  T acc = zero<T>();
+  using Acc = typename Traits<T>::Acc;      // FP64 sums: these sites start every row's sweep
+  Acc acc = zero<Acc>();
   if (g.mode == 0) {
     // out[(l,L)][(x,X)][(e,E)], u = U = 0
     int64_t r = idx;
@@ -165,8 +166,8 @@ __global__ void site_kernel(const SiteDesc *__restrict__ descs, const int64_t *_
     const int L = r % g.DL; r /= g.DL;
     const int l = (int)r;
     for (int s = 0; s < g.d; ++s)
-      acc = fma_(K[s * kS + l * kL + x * kX + e * kE],
-                 conj_(Kb[s * bS + L * bL + X_ * bX + E * bE]), acc);
+      acc = fma_(widen(K[s * kS + l * kL + x * kX + e * kE]),
+                 conj_(widen(Kb[s * bS + L * bL + X_ * bX + E * bE])), acc);
   } else {
     // out[(x,X)][b][(e,E)] = sum S1[0][(u,U)][b] K[s,0,u,x,e] conj(Kb[s,0,U,X,E])
     const T *S = (const T *)g.S;
@@ -178,15 +179,15 @@ __global__ void site_kernel(const SiteDesc *__restrict__ descs, const int64_t *_
     const int x = (int)r;
     for (int u = 0; u < g.Du; ++u)
       for (int U = 0; U < g.DU; ++U) {
-        const T sv = S[((int64_t)u * g.DU + U) * g.B + b];
-        T t = zero<T>();
+        const Acc sv = widen(S[((int64_t)u * g.DU + U) * g.B + b]);
+        Acc t = zero<Acc>();
         for (int s = 0; s < g.d; ++s)
-          t = fma_(K[s * kS + u * kU + x * kX + e * kE],
-                   conj_(Kb[s * bS + U * bU + X_ * bX + E * bE]), t);
+          t = fma_(widen(K[s * kS + u * kU + x * kX + e * kE]),
+                   conj_(widen(Kb[s * bS + U * bU + X_ * bX + E * bE])), t);
         acc = fma_(sv, t, acc);
       }
   }
-  ((T *)g.out)[idx] = acc;
+  ((T *)g.out)[idx] = narrow<T>(acc);
 }
 
 __global__ void zero_kernel(const ZeroDesc *__restrict__ descs, const int64_t *__restrict__ prefix,

@@ -30,6 +30,20 @@ namespace {
 
 constexpr int NT = 512;
 constexpr int kSmemLimit = 200 * 1024;
+constexpr int kCholCTAs = 8;     // CTAs of the cluster Cholesky
+
+// Where a Cholesky of size n runs: one CTA with the matrix in shared memory,
+// a cluster holding the rows in distributed shared memory, or one CTA on the
+// caller's global scratch (too large for either).
+enum CholRoute { kCholSmem = 0, kCholCluster = 1, kCholGlobal = 2 };
+__host__ __device__ inline int64_t chol_cluster_bytes(int n, int es, bool needT) {
+  const int64_t cap = (n + kCholCTAs - 1) / kCholCTAs;
+  return (needT ? 2 : 1) * cap * n * es + (int64_t)n * es;
+}
+__host__ __device__ inline int chol_route(int n, int es, bool needT) {
+  if ((int64_t)n * n * es <= kSmemLimit) return kCholSmem;
+  return chol_cluster_bytes(n, es, needT) <= kSmemLimit ? kCholCluster : kCholGlobal;
+}
 
 template <class T> struct Eps;
 template <> struct Eps<float> { static constexpr double v = 5.9604644775390625e-08; };
@@ -90,6 +104,7 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
   extern __shared__ __align__(16) unsigned char dyn[];
   const CholDesc &g = descs[blockIdx.x];
   const int n = g.n;
+  if (chol_route(n, (int)sizeof(T), g.T != nullptr) == kCholCluster) return;
   const Acc *G = (const Acc *)g.G;
   const bool in_smem = (int64_t)n * n * sizeof(T) <= kSmemLimit;
   T *W = in_smem ? (T *)dyn : (T *)g.R;        // working matrix; its upper triangle becomes R
@@ -187,6 +202,135 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
       O[t] = s;
     }
   }
+}
+
+// Cluster Cholesky for l beyond one CTA's shared memory: the rows of W (then
+// R) and of T = R^+ are dealt round-robin to kCholCTAs CTAs (row i on CTA
+// i mod kCholCTAs), each in its own shared memory.  Right-looking over the
+// pivots: the owner of row j takes the square root and scales the row, one
+// cluster barrier publishes it, every CTA copies it through distributed
+// shared memory and updates its own rows below.  R^+ is formed the same way
+// from the last row up (row k of T is final once every later row has been
+// added into it).  Same outputs and pivot rule as chol_kernel.
+template <class T>
+__global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
+    chol_cluster_kernel(const CholDesc *__restrict__ descs) {
+  namespace cg = cooperative_groups;
+  using Acc = typename Traits<T>::Acc;
+  using Real = typename Traits<T>::Real;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const CholDesc &g = descs[blockIdx.x / kCholCTAs];
+  const int n = g.n;
+  const bool needT = g.T != nullptr;
+  if (chol_route(n, (int)sizeof(T), needT) != kCholCluster) return;   // uniform over the cluster
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ double red[32];
+  const int cap = (n + kCholCTAs - 1) / kCholCTAs;
+  const int nloc = rank < n ? (n - rank + kCholCTAs - 1) / kCholCTAs : 0;   // rows rank + kCholCTAs * li
+  T *Wl = (T *)dyn;
+  T *Tl = Wl + (int64_t)cap * n;
+  T *buf = Tl + (needT ? (int64_t)cap * n : 0);
+  const Acc *G = (const Acc *)g.G;
+
+  double md = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) md = fmax(md, re(G[(int64_t)i * n + i]));
+  md = block_max(md, red);
+  const double shift = g.shift * md, thr = g.tol * md;
+  for (int64_t t = threadIdx.x; t < (int64_t)nloc * n; t += NT) {
+    const int li = (int)(t / n), k = (int)(t % n), i = rank + kCholCTAs * li;
+    T v = zero<T>();
+    if (k >= i) {
+      const Acc a = G[(int64_t)i * n + k];
+      v = k == i ? from_parts<T>(re(a) + shift, 0.0) : narrow<T>(a);
+    }
+    Wl[t] = v;
+    if (needT) Tl[t] = zero<T>();
+  }
+  __syncthreads();
+
+  for (int j = 0; j < n; ++j) {
+    const int owner = j % kCholCTAs;
+    if (rank == owner) {
+      T *row = Wl + (int64_t)(j / kCholCTAs) * n;
+      const double dj = re(row[j]);
+      const bool dead = !(dj > thr) || !(md > 0.0);
+      __syncthreads();                 // every thread has read the pivot before the row changes
+      if (dead) {
+        for (int k = j + threadIdx.x; k < n; k += NT) row[k] = zero<T>();
+      } else {
+        const double r = sqrt(dj);
+        const Real rinv = (Real)(1.0 / r);
+        for (int k = j + threadIdx.x; k < n; k += NT) row[k] = k == j ? real_scalar<T>(r) : scale(row[k], rinv);
+      }
+    }
+    cluster.sync();                    // row j of R is final and visible
+    const T *src = cluster.map_shared_rank(Wl, owner) + (int64_t)(j / kCholCTAs) * n;
+    for (int k = j + threadIdx.x; k < n; k += NT) buf[k] = src[k];
+    __syncthreads();
+    // W[i][k] -= conj(R[j][i]) R[j][k] for this CTA's rows i > j, k >= i
+    const int li0 = j + 1 - rank <= 0 ? 0 : (j + 1 - rank + kCholCTAs - 1) / kCholCTAs;
+    for (int64_t t = threadIdx.x; t < (int64_t)(nloc - li0) * n; t += NT) {
+      const int li = li0 + (int)(t / n), k = (int)(t % n), i = rank + kCholCTAs * li;
+      if (k < i) continue;
+      T *w = Wl + (int64_t)li * n + k;
+      *w = sub(*w, mul(conj_(buf[i]), buf[k]));
+    }
+    __syncthreads();
+  }
+
+  if (needT) {
+    // right-looking R^+: Tl rows hold sum_{l > i, l done} R[i][l] T[l][c] until row i is finalised
+    for (int k = n - 1; k >= 0; --k) {
+      const int owner = k % kCholCTAs, lk = k / kCholCTAs;
+      if (rank == owner) {
+        const double rkk = re(Wl[(int64_t)lk * n + k]);
+        T *trow = Tl + (int64_t)lk * n;
+        if (rkk == 0.0) {
+          for (int c = k + threadIdx.x; c < n; c += NT) trow[c] = zero<T>();
+        } else {
+          const Real ninv = (Real)(-1.0 / rkk);
+          for (int c = k + threadIdx.x; c < n; c += NT)
+            trow[c] = c == k ? real_scalar<T>(1.0 / rkk) : scale(trow[c], ninv);
+        }
+      }
+      cluster.sync();                  // row k of T is final and visible
+      const T *src = cluster.map_shared_rank(Tl, owner) + (int64_t)lk * n;
+      for (int c = k + threadIdx.x; c < n; c += NT) buf[c] = src[c];
+      __syncthreads();
+      const int li1 = k - rank <= 0 ? 0 : (k - rank + kCholCTAs - 1) / kCholCTAs;   // rows i < k
+      const int m = n - k;
+      for (int64_t t = threadIdx.x; t < (int64_t)li1 * m; t += NT) {
+        const int li = (int)(t / m), c = k + (int)(t % m);
+        T *acc = Tl + (int64_t)li * n + c;
+        *acc = fma_(Wl[(int64_t)li * n + k], buf[c], *acc);
+      }
+      __syncthreads();
+    }
+  }
+
+  // outputs: R (upper, zero below), T, R * Rprev, R in single precision
+  T *R = (T *)g.R;
+  T *Tg = (T *)g.T;
+  for (int64_t t = threadIdx.x; t < (int64_t)nloc * n; t += NT) {
+    const int li = (int)(t / n), k = (int)(t % n), i = rank + kCholCTAs * li;
+    const int64_t o = (int64_t)i * n + k;
+    R[o] = Wl[t];
+    if (needT) Tg[o] = Tl[t];
+    if constexpr (sizeof(Real) == 8) {
+      if (g.Rlow) {
+        if constexpr (sizeof(T) == 16) ((float2 *)g.Rlow)[o] = narrow<float2>(widen(Wl[t]));
+        else ((float *)g.Rlow)[o] = narrow<float>(widen(Wl[t]));
+      }
+    }
+    if (g.Rprev) {
+      const T *P = (const T *)g.Rprev;
+      T sacc = zero<T>();
+      for (int l = i; l <= k; ++l) sacc = fma_(Wl[(int64_t)li * n + l], P[(int64_t)l * n + k], sacc);
+      ((T *)g.Rout)[o] = sacc;
+    }
+  }
+  cluster.sync();   // peers may still read this CTA's shared memory until here
 }
 
 // Hestenes rotation of columns a, b (length n) in place.  Rotates when
@@ -366,6 +510,39 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NT)
   cluster.sync();   // keep this CTA's shared memory alive until every peer is done with it
 }
 
+// Singular values recomputed from the converged directions.  With Mw = Rb^H
+// rotated to Mw J = [sigma_c u_c] (J unitary), Rb u_c = sigma_c j_c, so
+// sigma_c = |Rb u_c| for the unit column u_c.  Each rotation's rounding
+// (cosine and sine not exactly on the unit circle, a phase of modulus
+// 1 + O(eps)) scales the columns it touches, and over the ~n rotations per
+// sweep per column that drift reaches ~n eps relative; the product with the
+// unrotated upper-triangular Rb, summed in FP64, carries Rb's rounding only.
+// One warp per column.
+template <class T>
+__global__ void __launch_bounds__(NT) sigma_refine_kernel(const JacobiDesc *__restrict__ descs, int cols_blocks) {
+  using Acc = typename Traits<T>::Acc;
+  const JacobiDesc &g = descs[blockIdx.x / cols_blocks];
+  const int n = g.n;
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x % cols_blocks) * (NT / 32) + (threadIdx.x >> 5);
+  if (c >= n) return;
+  const T *m = (const T *)g.Mw + (int64_t)c * n;
+  const T *Rb = (const T *)g.Rb;
+  double s2 = 0.0;
+  for (int k = lane; k < n; k += 32) s2 += (double)abs2(m[k]);
+  s2 = warp_sum(s2);
+  double v2 = 0.0;
+  if (s2 > 0.0) {
+    for (int i = 0; i < n; ++i) {
+      Acc d = zero<Acc>();
+      for (int k = i + lane; k < n; k += 32) d = fma_(widen(Rb[(int64_t)i * n + k]), widen(m[k]), d);
+      d = warp_sum(d);
+      v2 += abs2(d);
+    }
+  }
+  if (lane == 0) g.sig[c] = s2 > 0.0 ? sqrt(v2 / s2) : 0.0;
+}
+
 template <class T>
 __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__restrict__ descs) {
   const FinalizeDesc &g = descs[blockIdx.x];
@@ -435,12 +612,18 @@ template <class K> void set_smem(K kernel, int bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <class T> void chol_t(const CholDesc *d, int nd, int smem, cudaStream_t s) {
+template <class T> void chol_t(const CholDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s) {
   static bool set = false;
-  if (!set) { set_smem(chol_kernel<T>, kSmemLimit); set = true; }
+  if (!set) {
+    set_smem(chol_kernel<T>, kSmemLimit);
+    set_smem(chol_cluster_kernel<T>, kSmemLimit);
+    set = true;
+  }
   chol_kernel<T><<<nd, NT, smem, s>>>(d);
+  if (cluster_smem > 0) chol_cluster_kernel<T><<<nd * kCholCTAs, NT, cluster_smem, s>>>(d);
 }
-template <class T> void jacobi_t(const JacobiDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s) {
+template <class T>
+void jacobi_t(const JacobiDesc *d, int nd, int smem, int cluster_smem, int nmax, cudaStream_t s) {
   static bool set = false;
   if (!set) {
     set_smem(jacobi_kernel<T>, kSmemLimit);
@@ -449,6 +632,8 @@ template <class T> void jacobi_t(const JacobiDesc *d, int nd, int smem, int clus
   }
   if (smem >= 0) jacobi_kernel<T><<<nd, NT, smem, s>>>(d);
   if (cluster_smem > 0) jacobi_cluster_kernel<T><<<nd * kClusterCTAs, NT, cluster_smem, s>>>(d);
+  const int cb = (nmax + NT / 32 - 1) / (NT / 32);
+  if (cb > 0) sigma_refine_kernel<T><<<nd * cb, NT, 0, s>>>(d, cb);
 }
 template <class T> void finalize_t(const FinalizeDesc *d, int nd, cudaStream_t s) {
   // order (n ints) + h (n) + rho (k <= n): n <= 1024
@@ -471,23 +656,28 @@ int jacobi_cluster_smem_bytes(int dt, int n) {
   return (int)(cpc * n * dtype_size(dt));
 }
 
-void launch_chol(int dt, const CholDesc *d, int nd, int smem, cudaStream_t s) {
+int chol_cluster_smem_bytes(int dt, int n, bool needT) {
+  return chol_route(n, dtype_size(dt), needT) == kCholCluster ? (int)chol_cluster_bytes(n, dtype_size(dt), needT)
+                                                              : 0;
+}
+
+void launch_chol(int dt, const CholDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s) {
   if (nd <= 0) return;
   switch (dt) {
-    case DT_R32: chol_t<float>(d, nd, smem, s); break;
-    case DT_C64: chol_t<float2>(d, nd, smem, s); break;
-    case DT_R64: chol_t<double>(d, nd, smem, s); break;
-    case DT_C128: chol_t<double2>(d, nd, smem, s); break;
+    case DT_R32: chol_t<float>(d, nd, smem, cluster_smem, s); break;
+    case DT_C64: chol_t<float2>(d, nd, smem, cluster_smem, s); break;
+    case DT_R64: chol_t<double>(d, nd, smem, cluster_smem, s); break;
+    case DT_C128: chol_t<double2>(d, nd, smem, cluster_smem, s); break;
   }
 }
 
-void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s) {
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int cluster_smem, int nmax, cudaStream_t s) {
   if (nd <= 0) return;
   switch (dt) {
-    case DT_R32: jacobi_t<float>(d, nd, smem, cluster_smem, s); break;
-    case DT_C64: jacobi_t<float2>(d, nd, smem, cluster_smem, s); break;
-    case DT_R64: jacobi_t<double>(d, nd, smem, cluster_smem, s); break;
-    case DT_C128: jacobi_t<double2>(d, nd, smem, cluster_smem, s); break;
+    case DT_R32: jacobi_t<float>(d, nd, smem, cluster_smem, nmax, s); break;
+    case DT_C64: jacobi_t<float2>(d, nd, smem, cluster_smem, nmax, s); break;
+    case DT_R64: jacobi_t<double>(d, nd, smem, cluster_smem, nmax, s); break;
+    case DT_C128: jacobi_t<double2>(d, nd, smem, cluster_smem, nmax, s); break;
   }
 }
 

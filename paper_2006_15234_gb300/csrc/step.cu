@@ -248,7 +248,10 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
   op.desc_off = B.put(ch);
   op.nd = (int)ch.size();
   op.tag = tag;
-  for (auto &c : ch) op.smem = std::max(op.smem, small_smem_bytes(B.dt, c.n));
+  for (auto &c : ch) {
+    op.smem = std::max(op.smem, small_smem_bytes(B.dt, c.n));
+    op.smem2 = std::max(op.smem2, chol_cluster_smem_bytes(B.dt, c.n, c.T != nullptr));
+  }
   B.ops.push_back(op);
   if (apply) push_gemm(B, app, false, tag);
 }
@@ -295,6 +298,7 @@ void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I) {
   for (auto &j : jd) {
     oj.smem = std::max(oj.smem, small_smem_bytes(B.dt, j.n));
     oj.smem2 = std::max(oj.smem2, jacobi_cluster_smem_bytes(B.dt, j.n));
+    oj.blocks = std::max<int64_t>(oj.blocks, j.n);       // largest n: column blocks of the sigma refinement
   }
   B.ops.push_back(oj);
   Op of;
@@ -525,6 +529,7 @@ void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {
     op.kind = Op::CHOL; op.desc_off = B.put(ch); op.nd = 1; op.tag = "svd_gram";
     op.wide = wdt != B.dt;
     op.smem = small_smem_bytes(wdt, q.ell);
+    op.smem2 = chol_cluster_smem_bytes(wdt, q.ell, false);
     B.ops.push_back(op);
   }
   emit_jacobi_finalize(B, one);

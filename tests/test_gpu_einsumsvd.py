@@ -144,3 +144,17 @@ def test_mixed_precision_tensor_core_step(dtype):
     UW = U.reshape(-1, k) @ W.reshape(k, -1)
     gUW = gU.reshape(-1, k) @ gW.reshape(k, -1)
     assert np.linalg.norm(gUW - UW) <= 1e-4 * np.linalg.norm(UW)
+
+
+@pytest.mark.parametrize("dtype,prec", [("c64", libpeps.PREC_PLAIN), ("c64", libpeps.PREC_MIXED),
+                                        ("f32", libpeps.PREC_PLAIN), ("c128", libpeps.PREC_PLAIN)])
+def test_wide_sketch_cluster_factorisations(dtype, prec):
+    """l = 264: the l x l Cholesky and Jacobi no longer fit one CTA's shared
+    memory and run as 8-CTA clusters (rows / columns in distributed shared
+    memory); FP64 data take the global-memory Cholesky.  Same parity bar."""
+    rng = np.random.default_rng(21)
+    D = 4
+    # a * D^2 = 320 >= l: A has full rank 288 (no directions below rounding level)
+    case = _operands(rng, 18, D * D, 20, 18, 2, (D,) * 4, (D,) * 4, dtype)
+    out = _run_batch([case], dtype, 256, 8, 2, 77, prec=prec)
+    _check(case, out[0], 256, 8, 2, 77, 100, dtype)
