@@ -360,7 +360,9 @@ void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const vo
   std::memset(&d, 0, sizeof d);
   const bool cplx = dtype_complex(B.dt);
   const int64_t kr = K * (cplx ? 2 : 1);
-  const int bn = tc_block_n((int)rowsB, cplx, split3);
+  const int nmma = tc_pick_nmma((int)rowsB, cplx);
+  const int bn = tc_tile_cols(nmma, cplx);
+  (void)split3;
   if (B.encode) {
     const bool ok = tc_encode_map(&d.ta, A, rowsA, kr, kr * 4, 128) && tc_encode_map(&d.tb, Bm, rowsB, kr, kr * 4, bn);
     if (!ok && B.err.empty()) B.err = std::string("TMA map encoding failed for ") + tag;
@@ -374,7 +376,7 @@ void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const vo
   d.alpha = 1.0;
   d.alpha_dev = alpha_dev;
   d.conjC = conjC;
-  op.tc_bn = bn;
+  op.tc_bn = nmma;
   op.tcA = A; op.tcB = Bm; op.tcA_rows = rowsA; op.tcB_rows = rowsB; op.tc_kr = kr;
   const double mult = cplx ? 8.0 : 2.0, es = dtype_size(B.dt);
   op.flops = mult * (double)rowsA * rowsB * K;

@@ -65,7 +65,8 @@ extern "C" peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t c
   const int64_t pitch = kr * 4;
   TcDesc d;
   std::memset(&d, 0, sizeof d);
-  const int bn = tc_block_n(N, cplx != 0, split3 != 0);
+  const int nmma = tc_pick_nmma(N, cplx != 0);
+  const int bn = tc_tile_cols(nmma, cplx != 0);
   if (!tc_encode_map(&d.ta, A, M, kr, pitch, 128) || !tc_encode_map(&d.tb, B, N, kr, pitch, bn))
     return PEPS_ERR_UNSUPPORTED;
   d.M = M; d.N = N; d.Kr = (int32_t)kr;
@@ -76,6 +77,6 @@ extern "C" peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t c
   d.mn = digits1(1);
   d.C = C;
   d.alpha = 1.0;
-  launch_tc_gemm(d, bn, (cudaStream_t)stream);
+  launch_tc_gemm(d, nmma, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? PEPS_OK : PEPS_ERR_CUDA;
 }

@@ -7,16 +7,19 @@
 //
 // A and B are row-major with K contiguous (real, or complex interleaved
 // re/im).  Tiles arrive by TMA with the 128-byte swizzle; the accumulators
-// live in tensor memory.  Complex products run as real MMAs on a rewritten A
-// tile: with b = (br, bi) interleaved along K,
-//   Re C = sum [ar, sr*ai] . [br, bi],   Im C = sum [s1*ai, s2*ar] . [br, bi]
-// where the signs encode the conjugation of A and/or B; both rewrites act
-// inside each 16-byte chunk, so they commute with the TMA swizzle and four
-// worker warps apply them in shared memory between the TMA and the MMAs.
-// SPLIT3 ("3xTF32") splits each operand into a TF32 head and an FP32 tail
-// and accumulates head*head + tail*head + head*tail, recovering FP32-level
-// products on TF32 tensor cores.  Plain TF32 products round both operands to
-// the nearest TF32 value first (unbiased, half the error of truncation).
+// live in tensor memory.  A complex product runs as ONE real MMA chain: A's
+// interleaved rows (ar, ai) are used as they are, and each complex row b of
+// the B tile is expanded in shared memory into two real rows,
+//   (br, sr*bi) -> Re C,     (s1*bi, s2*br) -> Im C,
+// the signs encoding the conjugation of A and/or B.  The accumulator then
+// holds (Re, Im) column pairs, i.e. C's interleaved layout, and A is read
+// once per k step for both parts.  The expansion acts per 16-byte chunk (two
+// complex values), so it commutes with the swizzle up to the row-dependent
+// chunk permutation, which the rewrite applies.
+// SPLIT3 ("3xTF32") splits each operand into a TF32 head (round to nearest)
+// and an FP32 tail and accumulates head*head + tail*head + head*tail,
+// recovering FP32-level products on TF32 tensor cores.  Plain TF32 products
+// round both operands to the nearest TF32 value first (unbiased).
 // The tensor core's FP32 accumulator drops the bits of each addend below the
 // running sum's last place (measured: a relative bias of about 1e-8 per
 // accumulated K value, growing linearly with K).  SPLIT3 products therefore
@@ -25,11 +28,14 @@
 // warps add each chunk into FP32 registers with round-to-nearest.
 //
 // Roles: warp 0 issues TMA, warp 1 owns tensor memory and issues MMAs from
-// one thread, warps 2-5 rewrite operand tiles and run the epilogue (tensor
-// memory -> registers -> global through an arbitrary mixed-radix index map).
-// Every mbarrier wait is bounded: on expiry the kernel raises a status bit,
-// lets its own TMA copies and MMAs drain (again bounded), frees its tensor
-// memory and returns.
+// one thread, warps 2-9 rewrite operand tiles, fold accumulator chunks and
+// run the epilogue (tensor memory or registers -> global through an arbitrary
+// mixed-radix index map; warp w owns lane quarter w % 4 and column half
+// (w - 2) / 4).  Every mbarrier wait is bounded: on expiry the kernel raises a
+// status bit, lets its own TMA copies and MMAs drain (again bounded), frees
+// its tensor memory and returns.  Decisions to leave a loop are taken by all
+// worker threads together (a barrier reduction), so no worker is left at a
+// named barrier.
 #include <cuda.h>
 
 #include "common.cuh"
@@ -42,7 +48,8 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BKF = 32;              // floats of K per stage (one 128-byte swizzle row)
-constexpr int NTHREADS = 192;
+constexpr int NWORK = 256;           // worker threads (warps 2..9)
+constexpr int NTHREADS = 64 + NWORK;
 constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a wait gives up (~1 s)
 constexpr int CK = 2;                // k blocks per tensor-memory accumulation chunk (SPLIT3)
 
@@ -132,9 +139,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
-__device__ __forceinline__ float4 round4(float4 v) {
-  return make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
-}
 
 __device__ __forceinline__ int64_t map_index(const DigitMap &m, int64_t i) {
   int64_t off = 0;
@@ -148,30 +152,61 @@ __device__ __forceinline__ int64_t map_index(const DigitMap &m, int64_t i) {
   return off;
 }
 
-template <int BN, bool CPLX, bool SPLIT3> struct Layout {
+// AND over the worker threads (barrier 3); every worker must call it.
+__device__ __forceinline__ bool workers_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.and.pred q, 3, 256, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void workers_sync(int id) {
+  asm volatile("barrier.cta.sync %0, 256;" ::"r"(id) : "memory");
+}
+
+__device__ __forceinline__ float4 head4(float4 v) {
+  return make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) {
+  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+
+template <int NMMA, bool CPLX, bool SPLIT3> struct Layout {
+  static constexpr int BNR = CPLX ? NMMA / 2 : NMMA;   // output columns (complex or real) per tile
   static constexpr int A_BYTES = BM * 128;
-  static constexpr int B_BYTES = BN * 128;
-  static constexpr int NA = (CPLX ? 2 : 1) * (SPLIT3 ? 2 : 1);   // A_re, A_im, A_re_s, A_im_s
-  static constexpr int NB = SPLIT3 ? 2 : 1;                      // B (head), B tail
-  static constexpr int STAGE = NA * A_BYTES + NB * B_BYTES;
-  static constexpr int STAGES = (200 * 1024) / STAGE >= 4 ? 4 : ((200 * 1024) / STAGE >= 2 ? (200 * 1024) / STAGE : 1);
+  static constexpr int B_BYTES = NMMA * 128;           // MMA-ready B tile
+  static constexpr int RAW_BYTES = BNR * 128;          // B tile as TMA lands it
+  static constexpr int NA = SPLIT3 ? 2 : 1;            // A head (in place), A tail
+  static constexpr int NB = SPLIT3 ? 2 : 1;            // B head, B tail
+  // complex: the raw B tile lands in the tail tile (read out before the tail
+  // is written) or, without SPLIT3, in a buffer of its own
+  static constexpr bool RAW_SEP = CPLX && !SPLIT3;
+  static constexpr int STAGE = NA * A_BYTES + NB * B_BYTES + (RAW_SEP ? RAW_BYTES : 0);
+  static constexpr int STAGES = (200 * 1024) / STAGE >= 4 ? 4 : (200 * 1024) / STAGE;
   static constexpr int SMEM = STAGES * STAGE + 1024;
-  static constexpr int ACC_COLS = CPLX ? 2 * BN : (BN < 32 ? 32 : BN);   // one accumulator set
-  static constexpr bool FOLD = SPLIT3;                                     // chunked accumulation
-  static constexpr int TMEM_COLS = FOLD ? 2 * ACC_COLS : ACC_COLS;
-  static_assert(!FOLD || ACC_COLS <= 128, "register accumulators hold at most 128 columns");
+  static constexpr bool FOLD = SPLIT3;
+  static constexpr int ACC_COLS = NMMA;                // one accumulator set
+  static constexpr int HALF = NMMA / 2;                // columns per epilogue thread
+  static constexpr int TMEM_NEED = (FOLD ? 2 : 1) * NMMA;
+  static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
+  static_assert(STAGES >= 2, "two pipeline stages at least");
+  static_assert(NMMA % 16 == 0 && NMMA >= 16 && NMMA <= 256, "tcgen05 N for M = 128");
 };
 
-template <int BN, bool CPLX, bool SPLIT3>
+template <int NMMA, bool CPLX, bool SPLIT3>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ TcDesc g) {
-  using L = Layout<BN, CPLX, SPLIT3>;
+  using L = Layout<NMMA, CPLX, SPLIT3>;
   constexpr int STAGES = L::STAGES;
   constexpr bool FOLD = L::FOLD;
+  constexpr int HALF = L::HALF;
   __shared__ __align__(8) uint64_t full_bar[STAGES], ready_bar[STAGES], empty_bar[STAGES], done_bar;
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
-  __shared__ int64_t col_off[BN];
+  __shared__ int64_t col_off[L::BNR];
   extern __shared__ __align__(1024) unsigned char dyn[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
 
@@ -179,25 +214,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   const int ntile = g.tiles_m * g.tiles_n;
   const int tile = blockIdx.x % ntile, kc = blockIdx.x / ntile;
   const int tm = tile % g.tiles_m, tn = tile / g.tiles_m;
-  const int m0 = tm * BM, n0 = tn * BN;
+  const int m0 = tm * BM, n0 = tn * L::BNR;
   const int nkb_all = (g.Kr + BKF - 1) / BKF;
   const int kb0 = g.ksplit > 1 ? kc * g.kb_per_split : 0;
   const int nkb = g.ksplit > 1 ? min(g.kb_per_split, nkb_all - kb0) : nkb_all;
 
   auto a_tile = [&](int s, int which) { return smem + s * L::STAGE + which * L::A_BYTES; };
   auto b_tile = [&](int s, int which) { return smem + s * L::STAGE + L::NA * L::A_BYTES + which * L::B_BYTES; };
+  auto raw_tile = [&](int s) {
+    if constexpr (!CPLX) return b_tile(s, 0);
+    else if constexpr (L::RAW_SEP) return smem + s * L::STAGE + L::NA * L::A_BYTES + L::NB * L::B_BYTES;
+    else return b_tile(s, 1);
+  };
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&ready_bar[s], 128);
+      mbar_init(&ready_bar[s], NWORK);
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&done_bar, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);
+      mbar_init(&acc_empty[b], NWORK);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -214,22 +254,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   int issued = 0;          // producer: k blocks whose TMA was issued
   bool mma_any = false;    // MMA thread: at least one MMA issued
 
-  // SPLIT3 workers: per-row FP32 sums of the chunks read back from tensor memory
-  const int q = warp & 3;  // tensor-memory lane quarter a worker warp may access
+  // workers: lane quarter q (tensor-memory lanes 32q..32q+31), column half h
+  const int q = warp & 3, h = warp >= 2 ? (warp - 2) >> 2 : 0;
   const int nchunks = (nkb + CK - 1) / CK;
   int folded = 0;
-  float facc[FOLD ? L::ACC_COLS : 1];
+  float facc[FOLD ? HALF : 1];
 #pragma unroll
-  for (int i = 0; i < (FOLD ? L::ACC_COLS : 1); ++i) facc[i] = 0.f;
-  auto fold = [&]() -> bool {       // add chunk `folded` into facc (warp-collective)
+  for (int i = 0; i < (FOLD ? HALF : 1); ++i) facc[i] = 0.f;
+  // add chunk `folded` (whose completion was awaited) into facc
+  auto fold_body = [&]() {
     const int b = folded & 1;
-    bool ok = !abort_flag && mbar_wait(&acc_full[b], (folded >> 1) & 1, &abort_flag);
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * L::ACC_COLS);
+    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * L::ACC_COLS + h * HALF);
 #pragma unroll
-    for (int c0 = 0; c0 < (FOLD ? L::ACC_COLS : 0); c0 += 16) {
+    for (int c0 = 0; c0 < (FOLD ? HALF : 0); c0 += 16) {
       float v[16];
       tmem_ld16(base + c0, v);
 #pragma unroll
@@ -238,7 +276,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     mbar_arrive(&acc_empty[b]);
     ++folded;
-    return true;
+  };
+  auto fold_wait = [&]() -> bool {
+    return !abort_flag && mbar_wait(&acc_full[folded & 1], (folded >> 1) & 1, &abort_flag);
   };
 
   if (warp == 0) {
@@ -246,15 +286,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
         const int s = kb % STAGES;
         if (kb >= STAGES && !mbar_wait(&empty_bar[s], ((kb / STAGES) - 1) & 1, &abort_flag)) break;
-        mbar_expect_tx(&full_bar[s], (uint32_t)(L::A_BYTES + L::B_BYTES));
+        mbar_expect_tx(&full_bar[s], (uint32_t)(L::A_BYTES + L::RAW_BYTES));
         tma_load_2d(a_tile(s, 0), &g.ta, (kb0 + kb) * BKF, m0, &full_bar[s]);
-        tma_load_2d(b_tile(s, 0), &g.tb, (kb0 + kb) * BKF, n0, &full_bar[s]);
+        tma_load_2d(raw_tile(s), &g.tb, (kb0 + kb) * BKF, n0, &full_bar[s]);
         issued = kb + 1;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tf32_idesc(BN);
+      constexpr uint32_t idesc = tf32_idesc(NMMA);
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES;
         const int chunk = kb / CK, buf = FOLD ? (chunk & 1) : 0;
@@ -263,25 +303,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         if (FOLD && first && chunk >= 2 && !mbar_wait(&acc_empty[buf], ((chunk >> 1) - 1) & 1, &abort_flag)) break;
         if (!mbar_wait(&ready_bar[s], (kb / STAGES) & 1, &abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t t_re = tmem + (uint32_t)(buf * L::ACC_COLS), t_im = t_re + BN;
-        const uint32_t a0 = smem_u32(a_tile(s, 0)), a1 = smem_u32(a_tile(s, 1));
-        const uint32_t b0 = smem_u32(b_tile(s, 0));
+        const uint32_t tacc = tmem + (uint32_t)(buf * L::ACC_COLS);
+        const uint32_t a0 = smem_u32(a_tile(s, 0)), b0 = smem_u32(b_tile(s, 0));
 #pragma unroll
         for (int kk = 0; kk < BKF / 8; ++kk) {
           const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
           const uint32_t off = kk * 32;
-          mma_tf32(t_re, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc);
-          if (CPLX) mma_tf32(t_im, sw128_desc(a1 + off), sw128_desc(b0 + off), idesc, acc);
+          mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc);
           if (SPLIT3) {
-            const uint32_t as = smem_u32(a_tile(s, CPLX ? 2 : 1));
-            const uint32_t bs = smem_u32(b_tile(s, 1));
-            mma_tf32(t_re, sw128_desc(as + off), sw128_desc(b0 + off), idesc, 1u);
-            mma_tf32(t_re, sw128_desc(a0 + off), sw128_desc(bs + off), idesc, 1u);
-            if (CPLX) {
-              const uint32_t ais = smem_u32(a_tile(s, 3));
-              mma_tf32(t_im, sw128_desc(ais + off), sw128_desc(b0 + off), idesc, 1u);
-              mma_tf32(t_im, sw128_desc(a1 + off), sw128_desc(bs + off), idesc, 1u);
-            }
+            const uint32_t at = smem_u32(a_tile(s, 1)), bt = smem_u32(b_tile(s, 1));
+            mma_tf32(tacc, sw128_desc(at + off), sw128_desc(b0 + off), idesc, 1u);
+            mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(bt + off), idesc, 1u);
           }
         }
         mma_any = true;
@@ -291,131 +323,145 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       if (mma_any) mma_commit(&done_bar);
     }
   } else {
-    // rewrite workers: 128 threads over the A tile (and the B tile for SPLIT3)
+    // workers: operand rewrites
     const int t = threadIdx.x - 64;
     float sr = 1.f, s1 = 1.f, s2 = 1.f;
     if (CPLX) {
       if (!g.conjA && !g.conjB) { sr = -1.f; s1 = 1.f; s2 = 1.f; }
-      else if (g.conjA && !g.conjB) { sr = 1.f; s1 = -1.f; s2 = 1.f; }
-      else if (!g.conjA && g.conjB) { sr = 1.f; s1 = 1.f; s2 = -1.f; }
+      else if (g.conjA && !g.conjB) { sr = 1.f; s1 = 1.f; s2 = -1.f; }
+      else if (!g.conjA && g.conjB) { sr = 1.f; s1 = -1.f; s2 = 1.f; }
       else { sr = -1.f; s1 = -1.f; s2 = -1.f; }
     }
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES;
-      // warp-uniform exit: the read-backs below are warp-collective
-      if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[s], (kb / STAGES) & 1, &abort_flag))) break;
+      bool ok = mbar_wait(&full_bar[s], (kb / STAGES) & 1, &abort_flag);
+      // with this k block's operands in, read back the chunk before the last one
+      const bool fold_now = FOLD && kb % CK == 0 && kb >= 2 * CK;
+      if (fold_now) ok = ok && fold_wait();
+      if (!workers_all(ok)) break;
+      if (fold_now) fold_body();
       {
+        // A: head in place (+ tail tile), or nearest TF32 in place
         float4 *A0 = (float4 *)a_tile(s, 0);
         float4 *A1 = (float4 *)a_tile(s, 1);
-        for (int c = t; c < L::A_BYTES / 16; c += 128) {
+#pragma unroll
+        for (int c = t; c < L::A_BYTES / 16; c += NWORK) {
           const float4 v = A0[c];
-          if (CPLX) {
-            float4 re = make_float4(v.x, sr * v.y, v.z, sr * v.w);
-            float4 imv = make_float4(s1 * v.y, s2 * v.x, s1 * v.w, s2 * v.z);
-            if (!SPLIT3) {
-              re = round4(re);
-              imv = round4(imv);
-            }
-            if (SPLIT3) {
-              float4 *A2 = (float4 *)a_tile(s, 2);
-              float4 *A3 = (float4 *)a_tile(s, 3);
-              const float4 rh = make_float4(tf32_head(re.x), tf32_head(re.y), tf32_head(re.z), tf32_head(re.w));
-              const float4 ih = make_float4(tf32_head(imv.x), tf32_head(imv.y), tf32_head(imv.z), tf32_head(imv.w));
-              A2[c] = make_float4(re.x - rh.x, re.y - rh.y, re.z - rh.z, re.w - rh.w);
-              A3[c] = make_float4(imv.x - ih.x, imv.y - ih.y, imv.z - ih.z, imv.w - ih.w);
-              re = rh;
-              imv = ih;
-            }
-            A0[c] = re;
-            A1[c] = imv;
-          } else if (SPLIT3) {
-            // real SPLIT3: head in place, tail to tile 1
-            const float4 h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
-            A1[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-            A0[c] = h;
-          } else {
-            A0[c] = round4(v);
+          const float4 hd = head4(v);
+          if (SPLIT3) A1[c] = sub4(v, hd);
+          A0[c] = hd;
+        }
+        if constexpr (CPLX) {
+          // B: complex row n -> real rows 2n (Re) and 2n+1 (Im), chunk by chunk
+          constexpr int RAWC = L::RAW_BYTES / 16;
+          constexpr int PER = (RAWC + NWORK - 1) / NWORK;
+          const unsigned char *raw = raw_tile(s);
+          unsigned char *BH = b_tile(s, 0);
+          unsigned char *BT = b_tile(s, 1);
+          float4 v[PER];
+#pragma unroll
+          for (int u = 0; u < PER; ++u) {
+            const int i = t + u * NWORK;
+            if (i < RAWC) v[u] = ((const float4 *)raw)[i];
           }
-        }
-        if (!SPLIT3) {
-          // TF32 products: round B to nearest as well (the tensor core would truncate)
-          float4 *B0 = (float4 *)b_tile(s, 0);
-          for (int c = t; c < L::B_BYTES / 16; c += 128) B0[c] = round4(B0[c]);
-        }
-        if (SPLIT3) {
+          if (!L::RAW_SEP) workers_sync(2);    // raw tile is the tail tile: read out before writing
+#pragma unroll
+          for (int u = 0; u < PER; ++u) {
+            const int i = t + u * NWORK;
+            if (i >= RAWC) continue;
+            const int n = i >> 3, c = (i & 7) ^ (n & 7);           // logical chunk of row n
+            const float4 x = v[u];
+            const float4 re = make_float4(x.x, sr * x.y, x.z, sr * x.w);
+            const float4 im = make_float4(s1 * x.y, s2 * x.x, s1 * x.w, s2 * x.z);
+            const int r0 = 2 * n, r1 = 2 * n + 1;
+            float4 *p0h = (float4 *)(BH + r0 * 128 + ((c ^ (r0 & 7)) << 4));
+            float4 *p1h = (float4 *)(BH + r1 * 128 + ((c ^ (r1 & 7)) << 4));
+            const float4 reh = head4(re), imh = head4(im);
+            *p0h = reh;
+            *p1h = imh;
+            if (SPLIT3) {
+              *(float4 *)(BT + r0 * 128 + ((c ^ (r0 & 7)) << 4)) = sub4(re, reh);
+              *(float4 *)(BT + r1 * 128 + ((c ^ (r1 & 7)) << 4)) = sub4(im, imh);
+            }
+          }
+        } else {
           float4 *B0 = (float4 *)b_tile(s, 0);
           float4 *B1 = (float4 *)b_tile(s, 1);
-          for (int c = t; c < L::B_BYTES / 16; c += 128) {
+#pragma unroll
+          for (int c = t; c < L::B_BYTES / 16; c += NWORK) {
             const float4 v = B0[c];
-            const float4 h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
-            B1[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-            B0[c] = h;
+            const float4 hd = head4(v);
+            if (SPLIT3) B1[c] = sub4(v, hd);
+            B0[c] = hd;
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
       mbar_arrive(&ready_bar[s]);
-      // with the next chunk's operands ready, read back the chunk before it
-      if (FOLD && kb % CK == CK - 1 && kb >= 2 * CK - 1 && !fold()) break;
     }
   }
 
-  // ---- epilogue (warps 2..5 own tensor-memory lane quarters 2, 3, 0, 1) ----
+  // ---- epilogue (workers) ----
   if (warp >= 2) {
-    // output offsets of this tile's columns, once per tile
-    for (int c = threadIdx.x - 64; c < BN; c += 128) col_off[c] = n0 + c < g.N ? map_index(g.mn, n0 + c) : 0;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    bool ok = __all_sync(0xffffffffu, !abort_flag);
-    if (FOLD)
-      while (ok && folded < nchunks) ok = fold();
+    for (int c = threadIdx.x - 64; c < L::BNR; c += NWORK) col_off[c] = n0 + c < g.N ? map_index(g.mn, n0 + c) : 0;
+    workers_sync(1);
+    bool ok = workers_all(!abort_flag);
+    if (FOLD) {
+      while (ok && folded < nchunks) {
+        ok = workers_all(fold_wait());
+        if (ok) fold_body();
+      }
+    }
     // done_bar also tracks the last MMAs' completion signal, which must land before exit
     ok = ok && mbar_wait(&done_bar, 0, &abort_flag);
     ok = __all_sync(0xffffffffu, ok);      // tensor-memory loads are warp-collective
     if (ok) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int m = m0 + q * 32 + lane;
-      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * HALF);
       double alpha = g.alpha;
       if (g.alpha_dev) alpha *= *g.alpha_dev;
       const int64_t row_off = m < g.M ? map_index(g.mm, m) : 0;
-      auto store = [&](int cl, float re, float im) {
+      // local accumulator column j of this half -> output column
+      auto store = [&](int j, float v0, float v1) {
+        const int cl = CPLX ? (h * HALF + j) >> 1 : h * HALF + j;
         if (n0 + cl >= g.N) return;
         const int64_t off = row_off + col_off[cl];
         if (g.atomic64) {
           if (CPLX) {
             double2 *C = (double2 *)g.C + off;
-            atomicAdd(&C->x, alpha * (double)re);
-            atomicAdd(&C->y, (g.conjC ? -alpha : alpha) * (double)im);
+            atomicAdd(&C->x, alpha * (double)v0);
+            atomicAdd(&C->y, (g.conjC ? -alpha : alpha) * (double)v1);
           } else {
-            atomicAdd((double *)g.C + off, alpha * (double)re);
+            atomicAdd((double *)g.C + off, alpha * (double)v0);
           }
         } else if (CPLX) {
-          float2 v = make_float2((float)(alpha * re), (float)(alpha * im));
+          float2 v = make_float2((float)(alpha * v0), (float)(alpha * v1));
           if (g.conjC) v.y = -v.y;
           float2 *C = (float2 *)g.C + off;
           if (g.accumulate) { const float2 o = *C; v.x += o.x; v.y += o.y; }
           *C = v;
         } else {
-          float v = (float)(alpha * re);
+          float v = (float)(alpha * v0);
           float *C = (float *)g.C + off;
           if (g.accumulate) v += *C;
           *C = v;
         }
       };
+      constexpr int STEP = CPLX ? 2 : 1;
       if (FOLD) {
         if (m < g.M) {
 #pragma unroll
-          for (int c = 0; c < BN; ++c) store(c, facc[c], CPLX ? facc[(BN + c) % L::ACC_COLS] : 0.f);
+          for (int j = 0; j < HALF; j += STEP) store(j, facc[j], CPLX ? facc[(j + 1) % HALF] : 0.f);
         }
       } else {
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          float re[16], imv[16];
-          tmem_ld16(lane_base + c0, re);
-          if (CPLX) tmem_ld16(lane_base + BN + c0, imv);
+        for (int c0 = 0; c0 < HALF; c0 += 16) {
+          float v[16];
+          tmem_ld16(lane_base + c0, v);
           if (m >= g.M) continue;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) store(c0 + i, re[i], CPLX ? imv[i] : 0.f);
+          for (int i = 0; i < 16; i += STEP) store(c0 + i, v[i], CPLX ? v[(i + 1) & 15] : 0.f);
         }
       }
     }
@@ -441,29 +487,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   }
 }
 
-template <int BN, bool CPLX, bool SPLIT3> void launch_tc(const TcDesc &d, cudaStream_t s) {
-  using L = Layout<BN, CPLX, SPLIT3>;
+template <int NMMA, bool CPLX, bool SPLIT3> void launch_tc(const TcDesc &d, cudaStream_t s) {
+  using L = Layout<NMMA, CPLX, SPLIT3>;
   static bool set = false;
   if (!set) {
-    cudaFuncSetAttribute(tc_gemm_kernel<BN, CPLX, SPLIT3>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    cudaFuncSetAttribute(tc_gemm_kernel<NMMA, CPLX, SPLIT3>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
     set = true;
   }
   const unsigned blocks = (unsigned)(d.tiles_m * d.tiles_n * (d.ksplit > 1 ? d.ksplit : 1));
-  if (blocks) tc_gemm_kernel<BN, CPLX, SPLIT3><<<blocks, NTHREADS, L::SMEM, s>>>(d);
+  if (blocks) tc_gemm_kernel<NMMA, CPLX, SPLIT3><<<blocks, NTHREADS, L::SMEM, s>>>(d);
+}
+
+template <int NMMA> void launch_n(const TcDesc &d, cudaStream_t s) {
+  if (d.cplx) { if (d.split3) launch_tc<NMMA, true, true>(d, s); else launch_tc<NMMA, true, false>(d, s); }
+  else { if (d.split3) launch_tc<NMMA, false, true>(d, s); else launch_tc<NMMA, false, false>(d, s); }
 }
 
 }  // namespace
 
-int tc_block_n(int N, bool cplx, bool split3) { return N <= 64 || (cplx && split3) ? 64 : 128; }
+int tc_pick_nmma(int N, bool cplx) {
+  // fewest padded columns, a tile's fixed cost (its A rewrite) counted as 32 columns
+  static const int cand[4] = {64, 128, 192, 256};
+  int best = 256;
+  int64_t best_cost = -1;
+  for (int nm : cand) {
+    const int64_t bnr = cplx ? nm / 2 : nm;
+    const int64_t tiles = (N + bnr - 1) / bnr;
+    const int64_t cost = tiles * (bnr + 32);
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = nm; }
+  }
+  return best;
+}
 
-void launch_tc_gemm(const TcDesc &d, int bn, cudaStream_t s) {
-  if (bn == 64) {
-    if (d.cplx) { if (d.split3) launch_tc<64, true, true>(d, s); else launch_tc<64, true, false>(d, s); }
-    else { if (d.split3) launch_tc<64, false, true>(d, s); else launch_tc<64, false, false>(d, s); }
-  } else {
-    // (tc_block_n never gives 128 for complex SPLIT3)
-    if (d.cplx) { if (!d.split3) launch_tc<128, true, false>(d, s); }
-    else { if (d.split3) launch_tc<128, false, true>(d, s); else launch_tc<128, false, false>(d, s); }
+void launch_tc_gemm(const TcDesc &d, int nmma, cudaStream_t s) {
+  switch (nmma) {
+    case 64: launch_n<64>(d, s); break;
+    case 128: launch_n<128>(d, s); break;
+    case 192: launch_n<192>(d, s); break;
+    default: launch_n<256>(d, s); break;
   }
 }
 

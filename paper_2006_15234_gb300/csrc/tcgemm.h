@@ -33,10 +33,11 @@ struct TcDesc {
   uint32_t *status;
 };
 
-// Block N (64 or 128 output columns) for an N extent; complex SPLIT3 products
-// use 64 (their register accumulators hold 2 x 64 columns).
-int tc_block_n(int N, bool cplx, bool split3);
-void launch_tc_gemm(const TcDesc &d, int bn, cudaStream_t s);
+// MMA width (64, 128, 192 or 256 accumulator columns) for an N extent: a
+// tile covers nmma output columns (real) or nmma / 2 (complex, Re/Im pairs).
+int tc_pick_nmma(int N, bool cplx);
+inline int tc_tile_cols(int nmma, bool cplx) { return cplx ? nmma / 2 : nmma; }
+void launch_tc_gemm(const TcDesc &d, int nmma, cudaStream_t s);
 
 // Encode a 2-D TMA map over rows x cols FP32 values (row pitch in bytes) with
 // a box of 32 floats x box_rows and the 128-byte swizzle.  Returns false when

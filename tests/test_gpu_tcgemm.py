@@ -12,7 +12,8 @@ from paper_2006_15234_gb300 import libpeps
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(128, 64, 16), (300, 200, 90), (257, 129, 1000), (64, 70, 34)]
+# N chosen to reach every MMA width: complex tiles of 32 / 64 / 96 / 128 columns
+SHAPES = [(128, 64, 16), (300, 200, 90), (257, 129, 1000), (64, 70, 34), (130, 272, 48), (64, 20, 34)]
 
 
 def _ref(A, B, cA, cB):
@@ -41,7 +42,8 @@ def test_complex(shape, cA, cB, split3, tol):
 
 
 @pytest.mark.parametrize("split3,tol", [(False, 2e-3), (True, 2e-6)])
-@pytest.mark.parametrize("shape", [(128, 64, 32), (300, 200, 92), (257, 129, 1000)])
+@pytest.mark.parametrize("shape", [(128, 64, 32), (300, 200, 92), (257, 129, 1000), (150, 190, 64),
+                                   (100, 40, 36)])
 def test_real(shape, split3, tol):
     M, N, K = shape
     g = torch.Generator(device="cuda").manual_seed(M + N)
