@@ -360,9 +360,8 @@ void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const vo
   std::memset(&d, 0, sizeof d);
   const bool cplx = dtype_complex(B.dt);
   const int64_t kr = K * (cplx ? 2 : 1);
-  const int nmma = tc_pick_nmma((int)rowsB, cplx);
+  const int nmma = tc_pick_nmma((int)rowsB, cplx, tc_folds(split3, kr, 0));
   const int bn = tc_tile_cols(nmma, cplx);
-  (void)split3;
   if (B.encode) {
     const bool ok = tc_encode_map(&d.ta, A, rowsA, kr, kr * 4, 128) && tc_encode_map(&d.tb, Bm, rowsB, kr, kr * 4, bn);
     if (!ok && B.err.empty()) B.err = std::string("TMA map encoding failed for ") + tag;

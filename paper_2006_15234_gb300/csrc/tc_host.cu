@@ -65,7 +65,7 @@ extern "C" peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t c
   const int64_t pitch = kr * 4;
   TcDesc d;
   std::memset(&d, 0, sizeof d);
-  const int nmma = tc_pick_nmma(N, cplx != 0);
+  const int nmma = tc_pick_nmma(N, cplx != 0, tc_folds(split3 != 0, kr, 0));
   const int bn = tc_tile_cols(nmma, cplx != 0);
   if (!tc_encode_map(&d.ta, A, M, kr, pitch, 128) || !tc_encode_map(&d.tb, B, N, kr, pitch, bn))
     return PEPS_ERR_UNSUPPORTED;

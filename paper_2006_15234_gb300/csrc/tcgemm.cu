@@ -38,6 +38,8 @@
 // named barrier.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tcgemm.h"
@@ -174,7 +176,7 @@ __device__ __forceinline__ float4 sub4(float4 a, float4 b) {
   return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
 
-template <int NMMA, bool CPLX, bool SPLIT3> struct Layout {
+template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD_> struct Layout {
   static constexpr int BNR = CPLX ? NMMA / 2 : NMMA;   // output columns (complex or real) per tile
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = NMMA * 128;           // MMA-ready B tile
@@ -187,18 +189,20 @@ template <int NMMA, bool CPLX, bool SPLIT3> struct Layout {
   static constexpr int STAGE = NA * A_BYTES + NB * B_BYTES + (RAW_SEP ? RAW_BYTES : 0);
   static constexpr int STAGES = (200 * 1024) / STAGE >= 4 ? 4 : (200 * 1024) / STAGE;
   static constexpr int SMEM = STAGES * STAGE + 1024;
-  static constexpr bool FOLD = SPLIT3;
+  static constexpr bool FOLD = SPLIT3 && FOLD_;          // chunked accumulation (long K)
   static constexpr int ACC_COLS = NMMA;                // one accumulator set
   static constexpr int HALF = NMMA / 2;                // columns per epilogue thread
-  static constexpr int TMEM_NEED = (FOLD ? 2 : 1) * NMMA;
+  static constexpr int TMEM_NEED = 2 * NMMA;           // two accumulator buffers
   static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   static_assert(STAGES >= 2, "two pipeline stages at least");
   static_assert(NMMA % 16 == 0 && NMMA >= 16 && NMMA <= 256, "tcgen05 N for M = 128");
 };
 
-template <int NMMA, bool CPLX, bool SPLIT3>
+// 10 warps: each SM sub-partition (16K registers) holds 3 of them, so at most
+// 168 registers per thread
+template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD_>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ TcDesc g) {
-  using L = Layout<NMMA, CPLX, SPLIT3>;
+  using L = Layout<NMMA, CPLX, SPLIT3, FOLD_>;
   constexpr int STAGES = L::STAGES;
   constexpr bool FOLD = L::FOLD;
   constexpr int HALF = L::HALF;
@@ -211,13 +215,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   unsigned char *smem = (unsigned char *)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // persistent: this CTA takes work items blockIdx.x, + gridDim.x, ...; an
+  // item is one output tile (and one K chunk when K is split)
   const int ntile = g.tiles_m * g.tiles_n;
-  const int tile = blockIdx.x % ntile, kc = blockIdx.x / ntile;
-  const int tm = tile % g.tiles_m, tn = tile / g.tiles_m;
-  const int m0 = tm * BM, n0 = tn * L::BNR;
+  const int total = ntile * (g.ksplit > 1 ? g.ksplit : 1);
   const int nkb_all = (g.Kr + BKF - 1) / BKF;
-  const int kb0 = g.ksplit > 1 ? kc * g.kb_per_split : 0;
-  const int nkb = g.ksplit > 1 ? min(g.kb_per_split, nkb_all - kb0) : nkb_all;
+  struct Item { int m0, n0, kb0, nkb; };
+  auto item = [&](int w) {
+    const int tile = w % ntile, kc = w / ntile;
+    Item it;
+    // N tiles of one M tile are neighbours: the CTAs sharing an A tile run together (L2 reuse)
+    it.m0 = (tile / g.tiles_n) * BM;
+    it.n0 = (tile % g.tiles_n) * L::BNR;
+    it.kb0 = g.ksplit > 1 ? kc * g.kb_per_split : 0;
+    it.nkb = g.ksplit > 1 ? min(g.kb_per_split, nkb_all - it.kb0) : nkb_all;
+    return it;
+  };
+  // accumulation chunks of an item: CK k blocks (SPLIT3) or the whole item
+  auto nchunks_of = [&](int nkb) { return FOLD ? (nkb + CK - 1) / CK : 1; };
 
   auto a_tile = [&](int s, int which) { return smem + s * L::STAGE + which * L::A_BYTES; };
   auto b_tile = [&](int s, int which) { return smem + s * L::STAGE + L::NA * L::A_BYTES + which * L::B_BYTES; };
@@ -251,16 +266,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  int issued = 0;          // producer: k blocks whose TMA was issued
+  int issued = 0;          // producer: k blocks whose TMA was issued (over all items)
   bool mma_any = false;    // MMA thread: at least one MMA issued
 
   // workers: lane quarter q (tensor-memory lanes 32q..32q+31), column half h
   const int q = warp & 3, h = warp >= 2 ? (warp - 2) >> 2 : 0;
-  const int nchunks = (nkb + CK - 1) / CK;
-  int folded = 0;
+  int folded = 0;          // workers: chunks read back so far (over all items)
   float facc[FOLD ? HALF : 1];
-#pragma unroll
-  for (int i = 0; i < (FOLD ? HALF : 1); ++i) facc[i] = 0.f;
   // add chunk `folded` (whose completion was awaited) into facc
   auto fold_body = [&]() {
     const int b = folded & 1;
@@ -277,53 +289,63 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     mbar_arrive(&acc_empty[b]);
     ++folded;
   };
-  auto fold_wait = [&]() -> bool {
+  auto acc_wait = [&]() -> bool {
     return !abort_flag && mbar_wait(&acc_full[folded & 1], (folded >> 1) & 1, &abort_flag);
   };
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
-        const int s = kb % STAGES;
-        if (kb >= STAGES && !mbar_wait(&empty_bar[s], ((kb / STAGES) - 1) & 1, &abort_flag)) break;
-        mbar_expect_tx(&full_bar[s], (uint32_t)(L::A_BYTES + L::RAW_BYTES));
-        tma_load_2d(a_tile(s, 0), &g.ta, (kb0 + kb) * BKF, m0, &full_bar[s]);
-        tma_load_2d(raw_tile(s), &g.tb, (kb0 + kb) * BKF, n0, &full_bar[s]);
-        issued = kb + 1;
+      int gk = 0;
+      for (int w = blockIdx.x; w < total && !abort_flag; w += gridDim.x) {
+        const Item it = item(w);
+        for (int kb = 0; kb < it.nkb && !abort_flag; ++kb, ++gk) {
+          const int s = gk % STAGES;
+          if (gk >= STAGES && !mbar_wait(&empty_bar[s], ((gk / STAGES) - 1) & 1, &abort_flag)) break;
+          mbar_expect_tx(&full_bar[s], (uint32_t)(L::A_BYTES + L::RAW_BYTES));
+          tma_load_2d(a_tile(s, 0), &g.ta, (it.kb0 + kb) * BKF, it.m0, &full_bar[s]);
+          tma_load_2d(raw_tile(s), &g.tb, (it.kb0 + kb) * BKF, it.n0, &full_bar[s]);
+          issued = gk + 1;
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tf32_idesc(NMMA);
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES;
-        const int chunk = kb / CK, buf = FOLD ? (chunk & 1) : 0;
-        const bool first = FOLD ? (kb % CK == 0) : (kb == 0);
-        // a buffer is reused once the workers have read back the chunk two before
-        if (FOLD && first && chunk >= 2 && !mbar_wait(&acc_empty[buf], ((chunk >> 1) - 1) & 1, &abort_flag)) break;
-        if (!mbar_wait(&ready_bar[s], (kb / STAGES) & 1, &abort_flag)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t tacc = tmem + (uint32_t)(buf * L::ACC_COLS);
-        const uint32_t a0 = smem_u32(a_tile(s, 0)), b0 = smem_u32(b_tile(s, 0));
+      int gk = 0, gch = 0;
+      bool alive = true;
+      for (int w = blockIdx.x; w < total && alive; w += gridDim.x) {
+        const Item it = item(w);
+        for (int kb = 0; kb < it.nkb; ++kb, ++gk) {
+          const int s = gk % STAGES;
+          const bool first = FOLD ? (kb % CK == 0) : (kb == 0);
+          const bool last = FOLD ? (kb % CK == CK - 1 || kb == it.nkb - 1) : (kb == it.nkb - 1);
+          const int buf = gch & 1;
+          // a buffer is reused once the workers have read back the chunk two before
+          if (first && gch >= 2 && !mbar_wait(&acc_empty[buf], ((gch >> 1) - 1) & 1, &abort_flag)) { alive = false; break; }
+          if (!mbar_wait(&ready_bar[s], (gk / STAGES) & 1, &abort_flag)) { alive = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t tacc = tmem + (uint32_t)(buf * L::ACC_COLS);
+          const uint32_t a0 = smem_u32(a_tile(s, 0)), b0 = smem_u32(b_tile(s, 0));
 #pragma unroll
-        for (int kk = 0; kk < BKF / 8; ++kk) {
-          const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
-          const uint32_t off = kk * 32;
-          mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc);
-          if (SPLIT3) {
-            const uint32_t at = smem_u32(a_tile(s, 1)), bt = smem_u32(b_tile(s, 1));
-            mma_tf32(tacc, sw128_desc(at + off), sw128_desc(b0 + off), idesc, 1u);
-            mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(bt + off), idesc, 1u);
+          for (int kk = 0; kk < BKF / 8; ++kk) {
+            const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+            const uint32_t off = kk * 32;
+            mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc);
+            if (SPLIT3) {
+              const uint32_t at = smem_u32(a_tile(s, 1)), bt = smem_u32(b_tile(s, 1));
+              mma_tf32(tacc, sw128_desc(at + off), sw128_desc(b0 + off), idesc, 1u);
+              mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(bt + off), idesc, 1u);
+            }
           }
+          mma_any = true;
+          mma_commit(&empty_bar[s]);
+          if (last) { mma_commit(&acc_full[buf]); ++gch; }
         }
-        mma_any = true;
-        mma_commit(&empty_bar[s]);
-        if (FOLD && (kb % CK == CK - 1 || kb == nkb - 1)) mma_commit(&acc_full[buf]);
       }
       if (mma_any) mma_commit(&done_bar);
     }
   } else {
-    // workers: operand rewrites
+    // ---- workers: operand rewrites, chunk read-back, epilogue ----
     const int t = threadIdx.x - 64;
     float sr = 1.f, s1 = 1.f, s2 = 1.f;
     if (CPLX) {
@@ -332,100 +354,104 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       else if (!g.conjA && g.conjB) { sr = 1.f; s1 = -1.f; s2 = 1.f; }
       else { sr = -1.f; s1 = -1.f; s2 = -1.f; }
     }
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      bool ok = mbar_wait(&full_bar[s], (kb / STAGES) & 1, &abort_flag);
-      // with this k block's operands in, read back the chunk before the last one
-      const bool fold_now = FOLD && kb % CK == 0 && kb >= 2 * CK;
-      if (fold_now) ok = ok && fold_wait();
-      if (!workers_all(ok)) break;
-      if (fold_now) fold_body();
-      {
-        // A: head in place (+ tail tile), or nearest TF32 in place
-        float4 *A0 = (float4 *)a_tile(s, 0);
-        float4 *A1 = (float4 *)a_tile(s, 1);
+    double alpha = g.alpha;
+    if (g.alpha_dev) alpha *= *g.alpha_dev;
+    const float alpha_f = (float)alpha;       // single-precision outputs: no FP64 multiplies per element
+    bool alive = workers_all(!abort_flag);
+    int gk = 0, items = 0;
+    for (int w = blockIdx.x; w < total && alive; w += gridDim.x, ++items) {
+      const Item it = item(w);
+      const int chunk0 = folded;              // first chunk of this item
 #pragma unroll
-        for (int c = t; c < L::A_BYTES / 16; c += NWORK) {
-          const float4 v = A0[c];
-          const float4 hd = head4(v);
-          if (SPLIT3) A1[c] = sub4(v, hd);
-          A0[c] = hd;
-        }
-        if constexpr (CPLX) {
-          // B: complex row n -> real rows 2n (Re) and 2n+1 (Im), chunk by chunk
-          constexpr int RAWC = L::RAW_BYTES / 16;
-          constexpr int PER = (RAWC + NWORK - 1) / NWORK;
-          const unsigned char *raw = raw_tile(s);
-          unsigned char *BH = b_tile(s, 0);
-          unsigned char *BT = b_tile(s, 1);
-          float4 v[PER];
+      for (int i = 0; i < (FOLD ? HALF : 1); ++i) facc[i] = 0.f;
+      for (int kb = 0; kb < it.nkb; ++kb, ++gk) {
+        const int s = gk % STAGES;
+        bool ok = mbar_wait(&full_bar[s], (gk / STAGES) & 1, &abort_flag);
+        // with this k block's operands in, read back the chunk before the last one
+        const bool fold_now = FOLD && kb % CK == 0 && kb >= 2 * CK;
+        if (fold_now) ok = ok && acc_wait();
+        if (!workers_all(ok)) { alive = false; break; }
+        if (fold_now) fold_body();
+        {
+          // A: head in place (+ tail tile), or nearest TF32 in place
+          float4 *A0 = (float4 *)a_tile(s, 0);
+          float4 *A1 = (float4 *)a_tile(s, 1);
 #pragma unroll
-          for (int u = 0; u < PER; ++u) {
-            const int i = t + u * NWORK;
-            if (i < RAWC) v[u] = ((const float4 *)raw)[i];
+          for (int c = t; c < L::A_BYTES / 16; c += NWORK) {
+            const float4 v = A0[c];
+            const float4 hd = head4(v);
+            if (SPLIT3) A1[c] = sub4(v, hd);
+            A0[c] = hd;
           }
-          if (!L::RAW_SEP) workers_sync(2);    // raw tile is the tail tile: read out before writing
+          if constexpr (CPLX) {
+            // B: complex row n -> real rows 2n (Re) and 2n+1 (Im), chunk by chunk
+            constexpr int RAWC = L::RAW_BYTES / 16;
+            constexpr int PER = (RAWC + NWORK - 1) / NWORK;
+            const unsigned char *raw = raw_tile(s);
+            unsigned char *BH = b_tile(s, 0);
+            unsigned char *BT = b_tile(s, 1);
+            float4 v[PER];
 #pragma unroll
-          for (int u = 0; u < PER; ++u) {
-            const int i = t + u * NWORK;
-            if (i >= RAWC) continue;
-            const int n = i >> 3, c = (i & 7) ^ (n & 7);           // logical chunk of row n
-            const float4 x = v[u];
-            const float4 re = make_float4(x.x, sr * x.y, x.z, sr * x.w);
-            const float4 im = make_float4(s1 * x.y, s2 * x.x, s1 * x.w, s2 * x.z);
-            const int r0 = 2 * n, r1 = 2 * n + 1;
-            float4 *p0h = (float4 *)(BH + r0 * 128 + ((c ^ (r0 & 7)) << 4));
-            float4 *p1h = (float4 *)(BH + r1 * 128 + ((c ^ (r1 & 7)) << 4));
-            const float4 reh = head4(re), imh = head4(im);
-            *p0h = reh;
-            *p1h = imh;
-            if (SPLIT3) {
-              *(float4 *)(BT + r0 * 128 + ((c ^ (r0 & 7)) << 4)) = sub4(re, reh);
-              *(float4 *)(BT + r1 * 128 + ((c ^ (r1 & 7)) << 4)) = sub4(im, imh);
+            for (int u = 0; u < PER; ++u) {
+              const int i = t + u * NWORK;
+              if (i < RAWC) v[u] = ((const float4 *)raw)[i];
+            }
+            if (!L::RAW_SEP) workers_sync(2);    // raw tile is the tail tile: read out before writing
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+              const int i = t + u * NWORK;
+              if (i >= RAWC) continue;
+              const int n = i >> 3, c = (i & 7) ^ (n & 7);           // logical chunk of row n
+              const float4 x = v[u];
+              const float4 re = make_float4(x.x, sr * x.y, x.z, sr * x.w);
+              const float4 im = make_float4(s1 * x.y, s2 * x.x, s1 * x.w, s2 * x.z);
+              const int r0 = 2 * n, r1 = 2 * n + 1;
+              const float4 reh = head4(re), imh = head4(im);
+              *(float4 *)(BH + r0 * 128 + ((c ^ (r0 & 7)) << 4)) = reh;
+              *(float4 *)(BH + r1 * 128 + ((c ^ (r1 & 7)) << 4)) = imh;
+              if (SPLIT3) {
+                *(float4 *)(BT + r0 * 128 + ((c ^ (r0 & 7)) << 4)) = sub4(re, reh);
+                *(float4 *)(BT + r1 * 128 + ((c ^ (r1 & 7)) << 4)) = sub4(im, imh);
+              }
+            }
+          } else {
+            float4 *B0 = (float4 *)b_tile(s, 0);
+            float4 *B1 = (float4 *)b_tile(s, 1);
+#pragma unroll
+            for (int c = t; c < L::B_BYTES / 16; c += NWORK) {
+              const float4 v = B0[c];
+              const float4 hd = head4(v);
+              if (SPLIT3) B1[c] = sub4(v, hd);
+              B0[c] = hd;
             }
           }
-        } else {
-          float4 *B0 = (float4 *)b_tile(s, 0);
-          float4 *B1 = (float4 *)b_tile(s, 1);
-#pragma unroll
-          for (int c = t; c < L::B_BYTES / 16; c += NWORK) {
-            const float4 v = B0[c];
-            const float4 hd = head4(v);
-            if (SPLIT3) B1[c] = sub4(v, hd);
-            B0[c] = hd;
-          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&ready_bar[s]);
       }
-      mbar_arrive(&ready_bar[s]);
-    }
-  }
+      if (!alive) break;
+      // the item's last chunks (FOLD), or its whole accumulator
+      const int chunk_end = chunk0 + nchunks_of(it.nkb);
+      if (FOLD) {
+        while (alive && folded < chunk_end) {
+          alive = workers_all(acc_wait());
+          if (alive) fold_body();
+        }
+      } else {
+        alive = workers_all(acc_wait());
+      }
+      if (!alive) break;
 
-  // ---- epilogue (workers) ----
-  if (warp >= 2) {
-    for (int c = threadIdx.x - 64; c < L::BNR; c += NWORK) col_off[c] = n0 + c < g.N ? map_index(g.mn, n0 + c) : 0;
-    workers_sync(1);
-    bool ok = workers_all(!abort_flag);
-    if (FOLD) {
-      while (ok && folded < nchunks) {
-        ok = workers_all(fold_wait());
-        if (ok) fold_body();
-      }
-    }
-    // done_bar also tracks the last MMAs' completion signal, which must land before exit
-    ok = ok && mbar_wait(&done_bar, 0, &abort_flag);
-    ok = __all_sync(0xffffffffu, ok);      // tensor-memory loads are warp-collective
-    if (ok) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int m = m0 + q * 32 + lane;
-      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * HALF);
-      double alpha = g.alpha;
-      if (g.alpha_dev) alpha *= *g.alpha_dev;
+      // ---- epilogue of this item ----
+      workers_sync(1);                        // previous item's column offsets no longer read
+      for (int c = t; c < L::BNR; c += NWORK) col_off[c] = it.n0 + c < g.N ? map_index(g.mn, it.n0 + c) : 0;
+      workers_sync(1);
+      const int m = it.m0 + q * 32 + lane;
       const int64_t row_off = m < g.M ? map_index(g.mm, m) : 0;
       // local accumulator column j of this half -> output column
       auto store = [&](int j, float v0, float v1) {
         const int cl = CPLX ? (h * HALF + j) >> 1 : h * HALF + j;
-        if (n0 + cl >= g.N) return;
+        if (it.n0 + cl >= g.N) return;
         const int64_t off = row_off + col_off[cl];
         if (g.atomic64) {
           if (CPLX) {
@@ -436,13 +462,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             atomicAdd((double *)g.C + off, alpha * (double)v0);
           }
         } else if (CPLX) {
-          float2 v = make_float2((float)(alpha * v0), (float)(alpha * v1));
+          float2 v = make_float2(alpha_f * v0, alpha_f * v1);
           if (g.conjC) v.y = -v.y;
           float2 *C = (float2 *)g.C + off;
           if (g.accumulate) { const float2 o = *C; v.x += o.x; v.y += o.y; }
           *C = v;
         } else {
-          float v = (float)(alpha * v0);
+          float v = alpha_f * v0;
           float *C = (float *)g.C + off;
           if (g.accumulate) v += *C;
           *C = v;
@@ -455,16 +481,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
           for (int j = 0; j < HALF; j += STEP) store(j, facc[j], CPLX ? facc[(j + 1) % HALF] : 0.f);
         }
       } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((folded & 1) * L::ACC_COLS + h * HALF);
 #pragma unroll 1
         for (int c0 = 0; c0 < HALF; c0 += 16) {
           float v[16];
-          tmem_ld16(lane_base + c0, v);
+          tmem_ld16(base + c0, v);
           if (m >= g.M) continue;
 #pragma unroll
           for (int i = 0; i < 16; i += STEP) store(c0 + i, v[i], CPLX ? v[(i + 1) & 15] : 0.f);
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&acc_empty[folded & 1]);
+        ++folded;
       }
     }
+    // the MMA thread's final completion signal lands before the CTA may exit
+    if (alive && items > 0) mbar_wait(&done_bar, 0, &abort_flag);
   }
 
   // ---- teardown: drain own copies and MMAs if a wait gave up ----
@@ -472,8 +505,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   if (abort_flag) {
     if (threadIdx.x == 0 && g.status) atomicOr(g.status, STATUS_TIMEOUT);
     if (warp == 0 && lane == 0)
-      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-        for (uint32_t i = 0; i < kWaitLimit && !mbar_test(&full_bar[kb % STAGES], (kb / STAGES) & 1); ++i) {
+      for (int k = issued > STAGES ? issued - STAGES : 0; k < issued; ++k)
+        for (uint32_t i = 0; i < kWaitLimit && !mbar_test(&full_bar[k % STAGES], (k / STAGES) & 1); ++i) {
         }
     if (warp == 1 && lane == 0 && mma_any)
       for (uint32_t i = 0; i < kWaitLimit && !mbar_test(&done_bar, 0); ++i) {
@@ -487,30 +520,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   }
 }
 
-template <int NMMA, bool CPLX, bool SPLIT3> void launch_tc(const TcDesc &d, cudaStream_t s) {
-  using L = Layout<NMMA, CPLX, SPLIT3>;
-  static bool set = false;
-  if (!set) {
-    cudaFuncSetAttribute(tc_gemm_kernel<NMMA, CPLX, SPLIT3>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-    set = true;
+template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD> void launch_tc(const TcDesc &d, cudaStream_t s) {
+  using L = Layout<NMMA, CPLX, SPLIT3, FOLD>;
+  static int resident = 0;     // CTAs of this instantiation that fit the whole GPU at once
+  if (!resident) {
+    cudaFuncSetAttribute(tc_gemm_kernel<NMMA, CPLX, SPLIT3, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         L::SMEM);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tc_gemm_kernel<NMMA, CPLX, SPLIT3, FOLD>, NTHREADS, L::SMEM);
+    resident = std::max(1, sms) * std::max(1, per);
   }
-  const unsigned blocks = (unsigned)(d.tiles_m * d.tiles_n * (d.ksplit > 1 ? d.ksplit : 1));
-  if (blocks) tc_gemm_kernel<NMMA, CPLX, SPLIT3><<<blocks, NTHREADS, L::SMEM, s>>>(d);
+  const int64_t items = (int64_t)d.tiles_m * d.tiles_n * (d.ksplit > 1 ? d.ksplit : 1);
+  const unsigned blocks = (unsigned)std::min<int64_t>(items, resident);
+  if (blocks) tc_gemm_kernel<NMMA, CPLX, SPLIT3, FOLD><<<blocks, NTHREADS, L::SMEM, s>>>(d);
 }
 
 template <int NMMA> void launch_n(const TcDesc &d, cudaStream_t s) {
-  if (d.cplx) { if (d.split3) launch_tc<NMMA, true, true>(d, s); else launch_tc<NMMA, true, false>(d, s); }
-  else { if (d.split3) launch_tc<NMMA, false, true>(d, s); else launch_tc<NMMA, false, false>(d, s); }
+  // SPLIT3 items longer than two chunks fold; shorter ones keep one tensor-memory accumulation
+  const bool fold = tc_folds(d.split3 != 0, d.Kr, d.ksplit > 1 ? d.kb_per_split : 0);
+  if (d.cplx) {
+    if (!d.split3) launch_tc<NMMA, true, false, false>(d, s);
+    else if (fold) launch_tc<NMMA, true, true, true>(d, s);
+    else launch_tc<NMMA, true, true, false>(d, s);
+  } else {
+    if (!d.split3) launch_tc<NMMA, false, false, false>(d, s);
+    else if (fold) launch_tc<NMMA, false, true, true>(d, s);
+    else launch_tc<NMMA, false, true, false>(d, s);
+  }
 }
 
 }  // namespace
 
-int tc_pick_nmma(int N, bool cplx) {
-  // fewest padded columns, a tile's fixed cost (its A rewrite) counted as 32 columns
+bool tc_folds(bool split3, int64_t kr, int kb_per_split) {
+  const int64_t nkb = kb_per_split > 0 ? kb_per_split : (kr + BKF - 1) / BKF;
+  return split3 && nkb > 2 * CK;
+}
+
+int tc_pick_nmma(int N, bool cplx, bool fold) {
+  // fewest padded columns, a tile's fixed cost (its A rewrite) counted as 32
+  // columns; folding kernels keep half a tile row in registers: at most 192
   static const int cand[4] = {64, 128, 192, 256};
-  int best = 256;
+  int best = 64;
   int64_t best_cost = -1;
   for (int nm : cand) {
+    if (fold && nm > 192) continue;
     const int64_t bnr = cplx ? nm / 2 : nm;
     const int64_t tiles = (N + bnr - 1) / bnr;
     const int64_t cost = tiles * (bnr + 32);
@@ -524,7 +579,10 @@ void launch_tc_gemm(const TcDesc &d, int nmma, cudaStream_t s) {
     case 64: launch_n<64>(d, s); break;
     case 128: launch_n<128>(d, s); break;
     case 192: launch_n<192>(d, s); break;
-    default: launch_n<256>(d, s); break;
+    default:
+      if (tc_folds(d.split3 != 0, d.Kr, d.ksplit > 1 ? d.kb_per_split : 0)) return;   // never planned
+      launch_n<256>(d, s);
+      break;
   }
 }
 

@@ -35,7 +35,10 @@ struct TcDesc {
 
 // MMA width (64, 128, 192 or 256 accumulator columns) for an N extent: a
 // tile covers nmma output columns (real) or nmma / 2 (complex, Re/Im pairs).
-int tc_pick_nmma(int N, bool cplx);
+// Whether a SPLIT3 product folds its accumulation chunks (K longer than two
+// chunks); kb_per_split > 0 when K is split across CTAs.
+bool tc_folds(bool split3, int64_t kr, int kb_per_split);
+int tc_pick_nmma(int N, bool cplx, bool fold);
 inline int tc_tile_cols(int nmma, bool cplx) { return cplx ? nmma / 2 : nmma; }
 void launch_tc_gemm(const TcDesc &d, int nmma, cudaStream_t s);
 
