@@ -47,8 +47,11 @@ def strip_value(upper, ket_row, bra_row, lower, ops):
         c, _, f = lower[q].shape
         T = upper[q].reshape(a, Du, DU, b)
         Bt = lower[q].reshape(c, Dx, DX, f)
-        L = np.einsum("alLc,auUb,sluxe,sLUXE,cxXf->beEf", L, T, K, np.conj(Kb),
-                      Bt, optimize="greedy")
+        # the five-tensor product of this column as four pairwise sums
+        A1 = np.einsum("alLc,auUb->lLcuUb", L, T)
+        A2 = np.einsum("lLcuUb,sluxe->LcUbsxe", A1, K)
+        A3 = np.einsum("LcUbsxe,sLUXE->cbexXE", A2, np.conj(Kb))
+        L = np.einsum("cbexXE,cxXf->beEf", A3, Bt)
     return L.reshape(-1)[0]
 
 
