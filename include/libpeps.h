@@ -194,6 +194,65 @@ peps_status peps_boundary_workspace(const peps_network *ket, const peps_network 
                                     const peps_rsvd_opts *opts, size_t *workspace_bytes);
 
 /* ------------------------------------------------------------------------
+ * Expectation values <psi|H|psi> / <psi|psi> with cached environments
+ * (Eq. 6; Sec. IV-B).  Two boundary sweeps (top-down, and bottom-up on the
+ * row-reversed lattice) keep the boundary MPS above and below every row;
+ * every local term is then one exact strip contraction (environment above,
+ * the term's row with the operator applied to the ket, environment below),
+ * normalised by the same strip without operator:
+ *     E = sum_t coeff_t * Re( strip_t(O_t) / strip_t(1) ).
+ * Terms on vertical bonds use the same procedure on the transposed lattice
+ * (sketch streams 2 and 3; the direct lattice uses 0 and 1).  The bra is
+ * the ket conjugated.
+ * ------------------------------------------------------------------------ */
+
+/* One term coeff * O of H.  nsite = 1: O acts on site[0]; nsite = 2: a
+ * nearest-neighbour bond, either horizontal (site[1] = site[0] + 1, same
+ * row) or vertical (site[1] = site[0] + ncol).  Sites are numbered
+ * p * ncol + q.  op is a HOST array of (d^nsite) x (d^nsite) values,
+ * row-major [out][in], site[0]'s index most significant; doubles for real
+ * networks, interleaved (re, im) doubles for complex ones.  It is copied
+ * when the plan is made. */
+typedef struct {
+  int32_t nsite;
+  int32_t site[2];
+  const double *op;
+  double coeff;
+} peps_term;
+
+/* Plan the expectation value of H = sum_t terms[t] on the network ket
+ * (d <= 4, at most 32 rows and columns).  use_cache = 1 keeps the two
+ * sweeps' boundaries for every row (the caching of Sec. IV-B); use_cache = 0
+ * recomputes the environments of each row that holds a term with fresh
+ * sweeps (same sketches, hence the same values, at O(rows) times the cost).
+ * PEPS_ERR_UNSUPPORTED for terms that are not on nearest-neighbour bonds. */
+peps_status peps_expectation_plan(peps_plan **out, const peps_network *ket, const peps_term *terms,
+                                  int32_t nterms, const peps_rsvd_opts *opts, int32_t use_cache,
+                                  size_t *workspace_bytes);
+
+/* Enqueue the planned sweeps and strips (same descriptor-upload rule as
+ * peps_einsumsvd_execute). */
+peps_status peps_expectation_execute(peps_plan *plan, void *workspace, size_t workspace_bytes,
+                                     void *stream);
+
+/* Synchronise `stream` and read the results: energy = sum of the terms'
+ * contributions, log_norm = log <psi|psi> (row 0's strip and the scales of
+ * the boundary below it), term_values[t] (nterms doubles, optional) =
+ * coeff_t * <O_t>.  Any output pointer may be NULL. */
+peps_status peps_expectation_result(peps_plan *plan, void *workspace, void *stream, double *energy,
+                                    double *log_norm, double *term_values);
+
+/* Workspace size of peps_expectation for these arguments. */
+peps_status peps_expectation_workspace(const peps_network *ket, const peps_term *terms, int32_t nterms,
+                                       const peps_rsvd_opts *opts, int32_t use_cache,
+                                       size_t *workspace_bytes);
+
+/* One-shot convenience: plan, execute, read energy and log-norm, destroy. */
+peps_status peps_expectation(const peps_network *ket, const peps_term *terms, int32_t nterms,
+                             const peps_rsvd_opts *opts, int32_t use_cache, void *workspace,
+                             size_t workspace_bytes, void *stream, double *energy, double *log_norm);
+
+/* ------------------------------------------------------------------------
  * Launch ledger (profiling).  A plan's execute is a fixed list of grouped
  * kernel launches, each tagged with the stage of Algorithm 4 it serves
  * ("product_sites", "orth_m", "svd_jacobi", ...).

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -114,7 +115,7 @@ peps_status read_net(const peps_network *n, Net &out, const char *which) {
 // ---- plans ------------------------------------------------------------------
 
 struct peps_plan {
-  enum Kind { EINSUMSVD, CONTRACT } kind;
+  enum Kind { EINSUMSVD, CONTRACT, EXPECT } kind;
   int dt = 0;
   RsvdOpts opts{};
   // einsumsvd
@@ -126,6 +127,16 @@ struct peps_plan {
   int direction = 0;
   int64_t nsigma = 0;
   size_t result_off = 0, sigma_off = 0;
+  // expectation value
+  struct Term { int nsite; int site[2]; std::vector<double> op; double coeff; };
+  std::vector<Term> terms;
+  bool use_cache = true;
+  int64_t nstrips = 0;
+  size_t strip_off = 0;                     // strip values (accumulation type)
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> term_strips;   // per term: (component strip, norm strip)
+  int64_t lognorm_strip = 0;                // row 0 norm strip of the original lattice
+  size_t lognorm_logs_off = 0;              // logs of the sweep below row 0
+  int64_t lognorm_nlogs = 0;
   // built schedule
   uintptr_t built_base = 0;
   bool built = false;
@@ -162,73 +173,86 @@ std::string build_einsumsvd(peps_plan *P, uintptr_t base, const peps_einsumsvd_i
   return "";
 }
 
-// Boundary sweep of Algorithms 2 and 3 over the whole network.
-std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
-  B.base = base;
-  B.dt = P->dt;
-  const Net &K = P->ket;
-  const int nrow = K.nrow, ncol = K.ncol, dt = P->dt;
-  const size_t es = dtype_size(dt);
-  auto bra_dims = [&](int p, int q) -> SiteDims {
-    if (P->one_layer) return SiteDims{1, 1, 1, 1, 1};
-    return P->bra.at(p, q);
-  };
-  // --- shapes of every boundary site and einsumsvd step
-  struct Site { int left, vert, right; };
-  std::vector<std::vector<Site>> bound(nrow);
-  std::vector<std::vector<Inst>> steps(nrow);
-  for (int q = 0; q < ncol; ++q) {
-    const SiteDims k = K.at(0, q), b = bra_dims(0, q);
-    bound[0].push_back(Site{k.Dl * b.Dl, k.Dx * b.Dx, k.De * b.De});
-  }
+// ---- boundary sweeps (Algorithms 2 and 3) -----------------------------------
+// A sweep contracts rows 0..last of a lattice into a boundary MPS, keeping the
+// boundary after each row in caller-chosen buffers (ping-pong for a plain
+// contraction, one set per row for cached environments).
+
+struct BSite { int left, vert, right; };
+
+struct Sweep {
+  const Net *ket = nullptr, *bra = nullptr;   // bra NULL: one-layer
+  int last = 0;                               // last row contracted into the boundary
+  int direction = 0;
+  std::vector<std::vector<BSite>> bound;      // [r][q] boundary after row r
+  std::vector<std::vector<Inst>> steps;       // [r] einsumsvd steps of row r (r >= 1)
   size_t max_site = 0, max_carry = 0;
-  for (auto &s : bound[0]) max_site = std::max(max_site, (size_t)s.left * s.vert * s.right);
   int64_t nsteps = 0, nsigma = 0;
-  for (int r = 1; r < nrow; ++r) {
-    bound[r].resize(ncol);
-    // V1 = [1][t0][b0][h0]
-    const SiteDims k0 = K.at(r, 0), b0 = bra_dims(r, 0);
+};
+
+SiteDims sweep_bra_dims(const Sweep &S, int p, int q) {
+  if (!S.bra) return SiteDims{1, 1, 1, 1, 1};
+  return S.bra->at(p, q);
+}
+
+// Shapes of every boundary site and einsumsvd step of rows 0..S.last.
+std::string sweep_shapes(Sweep &S, const RsvdOpts &opts, int dt) {
+  const Net &K = *S.ket;
+  const int ncol = K.ncol;
+  S.bound.assign(S.last + 1, {});
+  S.steps.assign(S.last + 1, {});
+  for (int q = 0; q < ncol; ++q) {
+    const SiteDims k = K.at(0, q), b = sweep_bra_dims(S, 0, q);
+    S.bound[0].push_back(BSite{k.Dl * b.Dl, k.Dx * b.Dx, k.De * b.De});
+  }
+  for (auto &x : S.bound[0]) S.max_site = std::max(S.max_site, (size_t)x.left * x.vert * x.right);
+  for (int r = 1; r <= S.last; ++r) {
+    S.bound[r].resize(ncol);
+    const SiteDims k0 = K.at(r, 0), b0 = sweep_bra_dims(S, r, 0);
     {
-      const Site &s0 = bound[r - 1][0];
+      const BSite &s0 = S.bound[r - 1][0];
       if (s0.vert != k0.Du * b0.Du) return "vertical bond mismatch between rows";
-      max_carry = std::max(max_carry, (size_t)k0.Dx * b0.Dx * s0.right * k0.De * b0.De);
+      S.max_carry = std::max(S.max_carry, (size_t)k0.Dx * b0.Dx * s0.right * k0.De * b0.De);
     }
     int kprev = 1;
     for (int i = 1; i < ncol; ++i) {
-      const SiteDims kp = K.at(r, i - 1), bp = bra_dims(r, i - 1);
-      const SiteDims kc = K.at(r, i), bc = bra_dims(r, i);
-      const Site &S = bound[r - 1][i];
+      const SiteDims kp = K.at(r, i - 1), bp = sweep_bra_dims(S, r, i - 1);
+      const SiteDims kc = K.at(r, i), bc = sweep_bra_dims(S, r, i);
+      const BSite &B0 = S.bound[r - 1][i];
       Inst I{};
-      I.kL = kprev; I.t = kp.Dx * bp.Dx; I.a = S.left; I.b = S.right;
+      I.kL = kprev; I.t = kp.Dx * bp.Dx; I.a = B0.left; I.b = B0.right;
       I.d = kc.d; I.Dl = kc.Dl; I.Du = kc.Du; I.Dx = kc.Dx; I.De = kc.De;
       I.DL = bc.Dl; I.DU = bc.Du; I.DX = bc.Dx; I.DE = bc.De;
       if (kp.De != kc.Dl || bp.De != bc.Dl) return "horizontal bond mismatch";
-      if (S.vert != kc.Du * bc.Du) return "vertical bond mismatch between rows";
-      if (!P->one_layer && kc.d != bc.d) return "ket and bra physical dimensions differ";
-      inst_derive(I, P->opts);
+      if (B0.vert != kc.Du * bc.Du) return "vertical bond mismatch between rows";
+      if (S.bra && kc.d != bc.d) return "ket and bra physical dimensions differ";
+      inst_derive(I, opts);
       std::string e = inst_check(I, dt);
       if (!e.empty()) return e;
-      I.instance = ((uint64_t)P->direction << 32) | ((uint64_t)r << 16) | (uint64_t)i;
-      I.tc = P->opts.prec != PEPS_PREC_PLAIN && inst_tc_ok(I, dt);
-      bound[r][i - 1] = Site{I.kL, I.t, I.k};
-      max_carry = std::max(max_carry, (size_t)I.kL * I.t * I.a * I.h);
-      max_carry = std::max(max_carry, (size_t)I.k * I.N);
-      steps[r].push_back(I);
+      I.instance = ((uint64_t)S.direction << 32) | ((uint64_t)r << 16) | (uint64_t)i;
+      I.tc = opts.prec != PEPS_PREC_PLAIN && inst_tc_ok(I, dt);
+      S.bound[r][i - 1] = BSite{I.kL, I.t, I.k};
+      S.max_carry = std::max(S.max_carry, (size_t)I.kL * I.t * I.a * I.h);
+      S.max_carry = std::max(S.max_carry, (size_t)I.k * I.N);
+      S.steps[r].push_back(I);
       kprev = I.k;
-      ++nsteps;
-      nsigma += I.k;
+      ++S.nsteps;
+      S.nsigma += I.k;
     }
-    const SiteDims kl = K.at(r, ncol - 1), bl = bra_dims(r, ncol - 1);
-    bound[r][ncol - 1] = Site{kprev, kl.Dx * bl.Dx, 1};
-    for (auto &s : bound[r]) max_site = std::max(max_site, (size_t)s.left * s.vert * s.right);
+    const SiteDims kl = K.at(r, ncol - 1), bl = sweep_bra_dims(S, r, ncol - 1);
+    S.bound[r][ncol - 1] = BSite{kprev, kl.Dx * bl.Dx, 1};
+    for (auto &x : S.bound[r]) S.max_site = std::max(S.max_site, (size_t)x.left * x.vert * x.right);
   }
-  P->nsigma = nsigma;
-  // --- buffers
-  Inst owner{};
-  {
-    // scratch sized by the largest step in each dimension
-    int64_t xN = 0, t2 = 0, t3 = 0, yM = 0, ell = 1, kk = 1;
-    for (auto &row : steps)
+  return "";
+}
+
+// One set of einsumsvd scratch, sized by the largest step of all sweeps.
+void sweep_owner_scratch(Builder &B, const std::vector<Sweep *> &sw, int dt, Inst &owner) {
+  const size_t es = dtype_size(dt), as = acc_size(dt);
+  int64_t xN = 0, t2 = 0, t3 = 0, yM = 0, ell = 1, kk = 1;
+  int64_t t1 = 0, vt = 0, st = 0, ut = 0, kt = 0, kb = 0;
+  for (Sweep *S : sw)
+    for (auto &row : S->steps)
       for (auto &I : row) {
         xN = std::max<int64_t>(xN, (int64_t)I.ell * I.N);
         t2 = std::max<int64_t>(t2, (int64_t)I.ell * I.h * I.v * I.b);
@@ -236,19 +260,6 @@ std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
         yM = std::max<int64_t>(yM, (int64_t)I.ell * I.M);
         ell = std::max<int64_t>(ell, I.ell);
         kk = std::max<int64_t>(kk, I.k);
-      }
-    const size_t as = acc_size(dt);
-    owner.X = B.buf(xN * es); owner.Z = B.buf(xN * es);
-    owner.T2 = B.buf(t2 * es); owner.T3 = B.buf(t3 * es);
-    owner.Y = B.buf(yM * es); owner.P = B.buf(yM * es);
-    owner.g = B.buf(std::max<int64_t>(yM, 1) * es);
-    owner.Tm = B.buf(ell * ell * es); owner.Ut = B.buf(ell * kk * es);
-    owner.G = B.buf(ell * ell * as); owner.R1 = B.buf(ell * ell * as); owner.R2 = B.buf(ell * ell * as);
-    owner.Rout = B.buf(ell * ell * as); owner.Mw = B.buf(ell * ell * as);
-    owner.sig = (double *)B.buf(ell * 8); owner.inv_s1 = (double *)B.buf(8);
-    int64_t t1 = 0, vt = 0, st = 0, ut = 0, kt = 0, kb = 0;
-    for (auto &row : steps)
-      for (auto &I : row) {
         if (!I.tc) continue;
         const int64_t P1 = (int64_t)I.Dl * I.Du, Q1 = (int64_t)I.Dx * I.De, P2 = (int64_t)I.DL * I.DU,
                       Q2 = (int64_t)I.DX * I.DE;
@@ -259,108 +270,142 @@ std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
         kt = std::max<int64_t>(kt, Q1 * I.d * P1);
         kb = std::max<int64_t>(kb, (int64_t)I.d * P2 * Q2);
       }
-    owner.T1 = t1 ? B.buf(t1 * es) : nullptr;
-    owner.VT = vt ? B.buf(vt * es) : nullptr;
-    owner.ST = st ? B.buf(st * es) : nullptr;
-    owner.UT = ut ? B.buf(ut * es) : nullptr;
-    owner.KT = kt ? B.buf(kt * es) : nullptr;
-    owner.KbP = kb ? B.buf(kb * es) : nullptr;
-    owner.KbT = kb ? B.buf(kb * es) : nullptr;
-  }
-  void *Sbuf[2][64];
-  if (ncol > 64) return "ncol above 64 is not supported";
-  for (int c = 0; c < 2; ++c)
-    for (int q = 0; q < ncol; ++q) Sbuf[c][q] = B.buf(max_site * es);
-  void *Vbuf[2] = {B.buf(std::max<size_t>(max_carry, 1) * es), B.buf(std::max<size_t>(max_carry, 1) * es)};
-  double *logs = (double *)B.buf(std::max<int64_t>(nsteps, 1) * 8);
-  P->sigma_off = B.alloc(std::max<int64_t>(nsigma, 1) * 8);
-  double *sigma = (double *)B.ptr(P->sigma_off);
-  P->result_off = B.alloc(16);
-  double *result = (double *)B.ptr(P->result_off);
-  int maxbond = 1;
-  for (int q = 0; q < ncol; ++q)
-    maxbond = std::max(maxbond, std::max(bound[nrow - 1][q].left, bound[nrow - 1][q].right));
-  void *sc_scratch = B.buf((size_t)2 * maxbond * acc_size(dt));
-  void *ones = B.buf(es);
+  owner.X = B.buf(xN * es); owner.Z = B.buf(xN * es);
+  owner.T2 = B.buf(t2 * es); owner.T3 = B.buf(t3 * es);
+  owner.Y = B.buf(yM * es); owner.P = B.buf(yM * es);
+  owner.g = B.buf(std::max<int64_t>(yM, 1) * es);
+  owner.Tm = B.buf(ell * ell * es); owner.Ut = B.buf(ell * kk * es);
+  owner.G = B.buf(ell * ell * as); owner.R1 = B.buf(ell * ell * as); owner.R2 = B.buf(ell * ell * as);
+  owner.Rout = B.buf(ell * ell * as); owner.Mw = B.buf(ell * ell * as);
+  owner.sig = (double *)B.buf(ell * 8); owner.inv_s1 = (double *)B.buf(8);
+  owner.T1 = t1 ? B.buf(t1 * es) : nullptr;
+  owner.VT = vt ? B.buf(vt * es) : nullptr;
+  owner.ST = st ? B.buf(st * es) : nullptr;
+  owner.UT = ut ? B.buf(ut * es) : nullptr;
+  owner.KT = kt ? B.buf(kt * es) : nullptr;
+  owner.KbP = kb ? B.buf(kb * es) : nullptr;
+  owner.KbT = kb ? B.buf(kb * es) : nullptr;
+}
 
-  // --- ops
-  auto bra_ptr = [&](int p, int q) -> const void * { return P->one_layer ? ones : P->bra.ptr(p, q); };
-  if (P->one_layer) {
-    Op f;
-    f.kind = Op::FILL; f.fill_ptr = ones; f.fill_n = 1; f.fill_value = 1.0; f.tag = "init";
-    B.ops.push_back(f);
+void push_site(Builder &B, std::vector<SiteDesc> &d, const char *tag) {
+  std::vector<int64_t> prefix;
+  int64_t tot = 0;
+  for (auto &x : d) {
+    prefix.push_back(tot);
+    tot += ceil_div(x.total, kSiteThreads);
   }
-  auto push_site = [&](std::vector<SiteDesc> &d, const char *tag) {
-    std::vector<int64_t> bl;
-    std::vector<int64_t> prefix;
-    int64_t tot = 0;
-    for (auto &s : d) {
-      prefix.push_back(tot);
-      bl.push_back(ceil_div(s.total, kSiteThreads));
-      tot += bl.back();
-    }
-    Op op;
-    op.kind = Op::SITE; op.desc_off = B.put(d); op.prefix_off = B.put(prefix);
-    op.nd = (int)d.size(); op.blocks = tot; op.tag = tag;
-    B.ops.push_back(op);
-  };
+  Op op;
+  op.kind = Op::SITE; op.desc_off = B.put(d); op.prefix_off = B.put(prefix);
+  op.nd = (int)d.size(); op.blocks = tot; op.tag = tag;
+  B.ops.push_back(op);
+}
+
+// Ops of a sweep: row[r][q] receives the boundary after row r; logs (one per
+// step, sweep order) and sigma (the planned ranks' values) are written too.
+void emit_sweep(Builder &B, const Sweep &S, const RsvdOpts &opts, const void *ones,
+                const std::vector<std::vector<void *>> &row, void *const Vbuf[2], double *logs, double *sigma,
+                Inst &owner) {
+  const Net &K = *S.ket;
+  const int ncol = K.ncol;
+  auto bra_ptr = [&](int p, int q) -> const void * { return S.bra ? S.bra->ptr(p, q) : ones; };
   {
     std::vector<SiteDesc> d;
     for (int q = 0; q < ncol; ++q) {
-      const SiteDims k = K.at(0, q), b = bra_dims(0, q);
-      SiteDesc s{};
-      s.K = K.ptr(0, q); s.Kb = bra_ptr(0, q); s.S = nullptr; s.out = Sbuf[0][q]; s.mode = 0;
-      s.d = k.d; s.Dl = k.Dl; s.Du = k.Du; s.Dx = k.Dx; s.De = k.De;
-      s.DL = b.Dl; s.DU = b.Du; s.DX = b.Dx; s.DE = b.De; s.B = 1;
-      s.total = (int64_t)k.Dl * b.Dl * k.Dx * b.Dx * k.De * b.De;
-      d.push_back(s);
+      const SiteDims k = K.at(0, q), b = sweep_bra_dims(S, 0, q);
+      SiteDesc x{};
+      x.K = K.ptr(0, q); x.Kb = bra_ptr(0, q); x.S = nullptr; x.out = row[0][q]; x.mode = 0;
+      x.d = k.d; x.Dl = k.Dl; x.Du = k.Du; x.Dx = k.Dx; x.De = k.De;
+      x.DL = b.Dl; x.DU = b.Du; x.DX = b.Dx; x.DE = b.De; x.B = 1;
+      x.total = (int64_t)k.Dl * b.Dl * k.Dx * b.Dx * k.De * b.De;
+      d.push_back(x);
     }
-    push_site(d, "first_row");
+    push_site(B, d, "first_row");
   }
-  int cur = 0;
   int64_t step_idx = 0, sig_pos = 0;
-  for (int r = 1; r < nrow; ++r) {
-    const int nxt = 1 - cur;
+  for (int r = 1; r <= S.last; ++r) {
     {
-      const SiteDims k = K.at(r, 0), b = bra_dims(r, 0);
-      SiteDesc s{};
-      s.K = K.ptr(r, 0); s.Kb = bra_ptr(r, 0); s.S = Sbuf[cur][0];
-      s.out = ncol == 1 ? Sbuf[nxt][0] : Vbuf[0];
-      s.mode = 1;
-      s.d = k.d; s.Dl = k.Dl; s.Du = k.Du; s.Dx = k.Dx; s.De = k.De;
-      s.DL = b.Dl; s.DU = b.Du; s.DX = b.Dx; s.DE = b.De; s.B = bound[r - 1][0].right;
-      s.total = (int64_t)k.Dx * b.Dx * s.B * k.De * b.De;
-      std::vector<SiteDesc> d{s};
-      push_site(d, "zipup_start");
+      const SiteDims k = K.at(r, 0), b = sweep_bra_dims(S, r, 0);
+      SiteDesc x{};
+      x.K = K.ptr(r, 0); x.Kb = bra_ptr(r, 0); x.S = row[r - 1][0];
+      x.out = ncol == 1 ? row[r][0] : Vbuf[0];
+      x.mode = 1;
+      x.d = k.d; x.Dl = k.Dl; x.Du = k.Du; x.Dx = k.Dx; x.De = k.De;
+      x.DL = b.Dl; x.DU = b.Du; x.DX = b.Dx; x.DE = b.De; x.B = S.bound[r - 1][0].right;
+      x.total = (int64_t)k.Dx * b.Dx * x.B * k.De * b.De;
+      std::vector<SiteDesc> d{x};
+      push_site(B, d, "zipup_start");
     }
     int cv = 0;
     for (int i = 1; i < ncol; ++i) {
-      Inst &I = steps[r][i - 1];
+      Inst I = S.steps[r][i - 1];
       inst_share_scratch(I, owner);
       I.V = Vbuf[cv];
-      I.S = Sbuf[cur][i];
+      I.S = row[r - 1][i];
       I.K = K.ptr(r, i);
       I.Kb = bra_ptr(r, i);
-      I.U = Sbuf[nxt][i - 1];
-      I.W = (i == ncol - 1) ? Sbuf[nxt][ncol - 1] : Vbuf[1 - cv];
+      I.U = row[r][i - 1];
+      I.W = (i == ncol - 1) ? row[r][ncol - 1] : Vbuf[1 - cv];
       I.sigma = sigma + sig_pos;
       I.logp = logs + step_idx;
       sig_pos += I.k;
       ++step_idx;
       std::vector<Inst *> one{&I};
-      emit_einsumsvd(B, one, P->opts);
+      emit_einsumsvd(B, one, opts);
       cv = 1 - cv;
     }
-    cur = nxt;
   }
+}
+
+// Boundary sweep of Algorithms 2 and 3 over the whole network.
+std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
+  B.base = base;
+  B.dt = P->dt;
+  const Net &K = P->ket;
+  const int nrow = K.nrow, ncol = K.ncol, dt = P->dt;
+  const size_t es = dtype_size(dt);
+  if (ncol > 64) return "ncol above 64 is not supported";
+  Sweep S;
+  S.ket = &K;
+  S.bra = P->one_layer ? nullptr : &P->bra;
+  S.last = nrow - 1;
+  S.direction = P->direction;
+  std::string e = sweep_shapes(S, P->opts, dt);
+  if (!e.empty()) return e;
+  P->nsigma = S.nsigma;
+  Inst owner{};
+  sweep_owner_scratch(B, {&S}, dt, owner);
+  std::vector<void *> Sbuf[2];
+  for (int c = 0; c < 2; ++c)
+    for (int q = 0; q < ncol; ++q) Sbuf[c].push_back(B.buf(S.max_site * es));
+  std::vector<std::vector<void *>> row(nrow);
+  for (int r = 0; r < nrow; ++r) row[r] = Sbuf[r & 1];
+  void *Vbuf[2] = {B.buf(std::max<size_t>(S.max_carry, 1) * es), B.buf(std::max<size_t>(S.max_carry, 1) * es)};
+  double *logs = (double *)B.buf(std::max<int64_t>(S.nsteps, 1) * 8);
+  P->sigma_off = B.alloc(std::max<int64_t>(S.nsigma, 1) * 8);
+  double *sigma = (double *)B.ptr(P->sigma_off);
+  P->result_off = B.alloc(16);
+  double *result = (double *)B.ptr(P->result_off);
+  int maxbond = 1;
+  for (int q = 0; q < ncol; ++q)
+    maxbond = std::max(maxbond, std::max(S.bound[nrow - 1][q].left, S.bound[nrow - 1][q].right));
+  void *sc_scratch = B.buf((size_t)2 * maxbond * acc_size(dt));
+  void *ones = B.buf(es);
+
+  if (P->one_layer) {
+    Op f;
+    f.kind = Op::FILL; f.fill_ptr = ones; f.fill_n = 1; f.fill_value = 1.0; f.tag = "init";
+    B.ops.push_back(f);
+  }
+  emit_sweep(B, S, P->opts, ones, row, Vbuf, logs, sigma, owner);
   // --- final scalar
+  const std::vector<void *> &last = row[nrow - 1];
   std::vector<const void *> sp(ncol);
   std::vector<int32_t> lb(ncol), rb(ncol);
   for (int q = 0; q < ncol; ++q) {
-    sp[q] = Sbuf[cur][q];
-    lb[q] = bound[nrow - 1][q].left;
-    rb[q] = bound[nrow - 1][q].right;
-    if (bound[nrow - 1][q].vert != 1) return "last row has open vertical bonds";
+    sp[q] = last[q];
+    lb[q] = S.bound[nrow - 1][q].left;
+    rb[q] = S.bound[nrow - 1][q].right;
+    if (S.bound[nrow - 1][q].vert != 1) return "last row has open vertical bonds";
   }
   Op sc;
   sc.kind = Op::SCALAR;
@@ -369,7 +414,7 @@ std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
   sc.aux_off[2] = B.put(rb);
   sc.scalar.ncol = ncol;
   sc.scalar.logs = logs;
-  sc.scalar.nlogs = (int)nsteps;
+  sc.scalar.nlogs = (int)S.nsteps;
   sc.scalar.scratch = sc_scratch;
   sc.scalar.out = result;
   sc.tag = "scalar";
@@ -377,6 +422,338 @@ std::string build_contract(peps_plan *P, uintptr_t base, Builder &B) {
   return "";
 }
 
+
+// ---- expectation values (Eq. 6 with cached environments, Sec. IV-B) --------
+
+// A lattice the sweeps read: the caller's network, or a permuted copy of it
+// (rows read bottom-up, rows and columns exchanged) in the workspace.
+struct LatticeCopy {
+  Net net;                                   // site pointers into the workspace
+  std::vector<PermuteDesc> perm;             // how the copy is made
+};
+
+void push_permute(Builder &B, std::vector<PermuteDesc> &d, const char *tag) {
+  if (d.empty()) return;
+  std::vector<int64_t> prefix;
+  int64_t tot = 0;
+  for (auto &x : d) {
+    prefix.push_back(tot);
+    tot += permute_blocks(x);
+  }
+  Op op;
+  op.kind = Op::PERMUTE; op.desc_off = B.put(d); op.prefix_off = B.put(prefix);
+  op.nd = (int)d.size(); op.blocks = tot; op.tag = tag;
+  B.ops.push_back(op);
+}
+
+PermuteDesc mk_permute(const void *in, void *out, int64_t nb, int64_t R, int64_t C, int64_t Q) {
+  PermuteDesc p{};
+  p.in = in; p.out = out; p.nb = nb; p.R = R; p.Cc = C; p.Q = Q; p.conj = 0;
+  return p;
+}
+
+int64_t site_elems(const SiteDims &x) { return (int64_t)x.d * x.Dl * x.Du * x.Dx * x.De; }
+
+// Rows reversed, up and down bonds exchanged: [d][l][u][x][e] -> [d][l][x][u][e].
+LatticeCopy flip_copy(Builder &B, const Net &src, size_t es) {
+  LatticeCopy L;
+  L.net.nrow = src.nrow; L.net.ncol = src.ncol; L.net.d = src.d; L.net.dt = src.dt;
+  L.net.dims.resize(src.dims.size());
+  L.net.site.resize(src.site.size());
+  for (int p = 0; p < src.nrow; ++p)
+    for (int q = 0; q < src.ncol; ++q) {
+      const SiteDims x = src.at(src.nrow - 1 - p, q);
+      void *out = B.buf(site_elems(x) * es);
+      L.perm.push_back(mk_permute(src.ptr(src.nrow - 1 - p, q), out, (int64_t)x.d * x.Dl, x.Du, x.Dx, x.De));
+      L.net.dims[(size_t)p * src.ncol + q] = SiteDims{x.d, x.Dl, x.Dx, x.Du, x.De};
+      L.net.site[(size_t)p * src.ncol + q] = out;
+    }
+  return L;
+}
+
+// Rows and columns exchanged: [d][l][u][x][e] -> [d][u][l][e][x] (two passes).
+LatticeCopy transpose_copy(Builder &B, const Net &src, size_t es, std::vector<PermuteDesc> &first_pass) {
+  LatticeCopy L;
+  L.net.nrow = src.ncol; L.net.ncol = src.nrow; L.net.d = src.d; L.net.dt = src.dt;
+  L.net.dims.resize(src.dims.size());
+  L.net.site.resize(src.site.size());
+  for (int p = 0; p < src.nrow; ++p)
+    for (int q = 0; q < src.ncol; ++q) {
+      const SiteDims x = src.at(p, q);
+      void *tmp = B.buf(site_elems(x) * es);
+      void *out = B.buf(site_elems(x) * es);
+      first_pass.push_back(mk_permute(src.ptr(p, q), tmp, x.d, x.Dl, x.Du, (int64_t)x.Dx * x.De));
+      L.perm.push_back(mk_permute(tmp, out, (int64_t)x.d * x.Du * x.Dl, x.Dx, x.De, 1));
+      L.net.dims[(size_t)q * src.nrow + p] = SiteDims{x.d, x.Du, x.Dl, x.De, x.Dx};
+      L.net.site[(size_t)q * src.nrow + p] = out;
+    }
+  return L;
+}
+
+// Cached environments of one lattice: boundaries above every row (top-down
+// sweep) and below every row (sweep of the row-reversed copy).
+struct EnvSet {
+  Sweep top, bot;
+  bool has_top = false, has_bot = false;
+  std::vector<std::vector<void *>> top_rows, bot_rows;
+  double *top_logs = nullptr, *bot_logs = nullptr;
+  double *top_sigma = nullptr, *bot_sigma = nullptr;
+};
+
+std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
+  B.base = base;
+  B.dt = P->dt;
+  const int dt = P->dt;
+  const size_t es = dtype_size(dt), as = acc_size(dt);
+  const bool cplx = dtype_complex(dt);
+  const Net &H = P->ket;
+  const int d = H.d;
+  if (d > 4) return "physical dimension above 4 is not supported by the strip kernel";
+  if (H.ncol > kStripMaxCols || H.nrow > kStripMaxCols) return "lattice side above 32 is not supported";
+
+  // --- terms -> strips: (lattice 0 = as given, 1 = transposed; row; column -> operator)
+  struct Comp { int lat, row; std::vector<std::pair<int, int>> ops; };   // (column, op table index)
+  std::vector<std::vector<double>> optab;     // d x d matrices (re, im interleaved when complex)
+  auto add_op = [&](const std::vector<double> &m) { optab.push_back(m); return (int)optab.size() - 1; };
+  const int vals = cplx ? 2 : 1;
+  std::vector<std::vector<Comp>> comps(P->terms.size());
+  bool need_v = false;
+  for (size_t t = 0; t < P->terms.size(); ++t) {
+    const auto &T = P->terms[t];
+    const int r0 = T.site[0] / H.ncol, c0 = T.site[0] % H.ncol;
+    if (T.nsite == 1) {
+      std::vector<double> m(T.op.begin(), T.op.end());
+      comps[t].push_back(Comp{0, r0, {{c0, add_op(m)}}});
+      continue;
+    }
+    const int r1 = T.site[1] / H.ncol, c1 = T.site[1] % H.ncol;
+    const bool horiz = r1 == r0 && c1 == c0 + 1;
+    if (!horiz) need_v = true;
+    // O[(a,s'),(b,s)] = sum_{a,b} E_ab (x) O^(a,b): one component per nonzero block
+    const int dd = d * d;
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        std::vector<double> blk((size_t)dd * vals);
+        bool nz = false;
+        for (int s2 = 0; s2 < d; ++s2)
+          for (int t2 = 0; t2 < d; ++t2)
+            for (int v = 0; v < vals; ++v) {
+              const double x = T.op[((size_t)(a * d + s2) * dd + (b * d + t2)) * vals + v];
+              blk[((size_t)s2 * d + t2) * vals + v] = x;
+              nz = nz || x != 0.0;
+            }
+        if (!nz) continue;
+        std::vector<double> e((size_t)dd * vals, 0.0);
+        e[((size_t)a * d + b) * vals] = 1.0;
+        const int ia = add_op(e), ib = add_op(blk);
+        if (horiz) comps[t].push_back(Comp{0, r0, {{c0, ia}, {c1, ib}}});
+        else comps[t].push_back(Comp{1, c0, {{r0, ia}, {r1, ib}}});
+      }
+  }
+
+  // --- lattices
+  const Net *lat[2] = {&H, nullptr};
+  LatticeCopy Vt, Hf, Vf;
+  std::vector<PermuteDesc> tpass;
+  Hf = flip_copy(B, H, es);
+  if (need_v) {
+    Vt = transpose_copy(B, H, es, tpass);
+    lat[1] = &Vt.net;
+    Vf = flip_copy(B, Vt.net, es);
+  }
+  const Net *flat[2] = {&Hf.net, need_v ? &Vf.net : nullptr};
+
+  // --- sweeps: cached (one top and one bottom sweep per lattice) or one
+  // pair per row that holds strips (uncached: the environments are
+  // recomputed for every row, with the same sketches)
+  std::vector<bool> rows_used[2];
+  for (int l = 0; l < 2; ++l) rows_used[l].assign(lat[l] ? lat[l]->nrow : 0, false);
+  rows_used[0][0] = true;                  // log-norm strip
+  for (auto &cv : comps)
+    for (auto &c : cv) rows_used[c.lat][c.row] = true;
+  // env[l][r]: environment set used by row r of lattice l (index into envs)
+  std::vector<std::unique_ptr<EnvSet>> envs;
+  std::vector<int> env_of[2];
+  for (int l = 0; l < 2; ++l) {
+    if (!lat[l]) continue;
+    const int nrow = lat[l]->nrow;
+    env_of[l].assign(nrow, -1);
+    auto make = [&](int top_last, int bot_last) {
+      auto E = std::make_unique<EnvSet>();
+      if (top_last >= 0) {
+        E->has_top = true;
+        E->top.ket = lat[l]; E->top.bra = lat[l]; E->top.last = top_last; E->top.direction = 2 * l;
+      }
+      if (bot_last >= 0) {
+        E->has_bot = true;
+        E->bot.ket = flat[l]; E->bot.bra = flat[l]; E->bot.last = bot_last; E->bot.direction = 2 * l + 1;
+      }
+      envs.push_back(std::move(E));
+      return (int)envs.size() - 1;
+    };
+    if (P->use_cache) {
+      const int e = make(nrow - 2, nrow - 2);
+      for (int r = 0; r < nrow; ++r) env_of[l][r] = e;
+    } else {
+      for (int r = 0; r < nrow; ++r)
+        if (rows_used[l][r]) env_of[l][r] = make(r - 1, nrow - 2 - r);
+    }
+  }
+  std::vector<Sweep *> all;
+  for (auto &E : envs) {
+    if (E->has_top) {
+      std::string e = sweep_shapes(E->top, P->opts, dt);
+      if (!e.empty()) return e;
+      all.push_back(&E->top);
+    }
+    if (E->has_bot) {
+      std::string e = sweep_shapes(E->bot, P->opts, dt);
+      if (!e.empty()) return e;
+      all.push_back(&E->bot);
+    }
+  }
+  Inst owner{};
+  sweep_owner_scratch(B, all, dt, owner);
+  size_t max_carry = 1;
+  for (Sweep *S : all) max_carry = std::max(max_carry, S->max_carry);
+  void *Vbuf[2] = {B.buf(max_carry * es), B.buf(max_carry * es)};
+  void *ones = B.buf(es);
+  auto rows_for = [&](const Sweep &S) {
+    std::vector<std::vector<void *>> rows(S.last + 1);
+    for (int r = 0; r <= S.last; ++r)
+      for (auto &x : S.bound[r]) rows[r].push_back(B.buf((size_t)x.left * x.vert * x.right * es));
+    return rows;
+  };
+  for (auto &E : envs) {
+    if (E->has_top) {
+      E->top_rows = rows_for(E->top);
+      E->top_logs = (double *)B.buf(std::max<int64_t>(E->top.nsteps, 1) * 8);
+      E->top_sigma = (double *)B.buf(std::max<int64_t>(E->top.nsigma, 1) * 8);
+    }
+    if (E->has_bot) {
+      E->bot_rows = rows_for(E->bot);
+      E->bot_logs = (double *)B.buf(std::max<int64_t>(E->bot.nsteps, 1) * 8);
+      E->bot_sigma = (double *)B.buf(std::max<int64_t>(E->bot.nsigma, 1) * 8);
+    }
+  }
+
+  // --- strips
+  std::vector<StripCol> cols;
+  std::vector<StripDesc> sd;
+  int64_t l_cap = 1, a1_cap = 1, a2_cap = 1, a3_cap = 1;
+  // column table of row r of lattice l (shared by all strips of that row)
+  std::map<std::pair<int, int>, int> row_cols;
+  auto columns = [&](int l, int r) -> std::string {
+    if (row_cols.count({l, r})) return "";
+    const Net &L = *lat[l];
+    const EnvSet &E = *envs[env_of[l][r]];
+    const int nrow = L.nrow;
+    row_cols[{l, r}] = (int)cols.size();
+    for (int q = 0; q < L.ncol; ++q) {
+      const SiteDims x = L.at(r, q);
+      StripCol c{};
+      c.ket = L.ptr(r, q);
+      c.d = x.d; c.Dl = x.Dl; c.Du = x.Du; c.Dx = x.Dx; c.De = x.De;
+      if (r > 0) {
+        const BSite &u = E.top.bound[r - 1][q];
+        if (u.vert != x.Du * x.Du) return "environment above does not match the row";
+        c.up = E.top_rows[r - 1][q]; c.a = u.left; c.b = u.right;
+      } else {
+        c.up = ones; c.a = 1; c.b = 1;
+      }
+      if (r < nrow - 1) {
+        const BSite &w = E.bot.bound[nrow - 2 - r][q];
+        if (w.vert != x.Dx * x.Dx) return "environment below does not match the row";
+        c.lo = E.bot_rows[nrow - 2 - r][q]; c.c = w.left; c.f = w.right;
+      } else {
+        c.lo = ones; c.c = 1; c.f = 1;
+      }
+      const int64_t vu = (int64_t)x.Du * x.Du;
+      l_cap = std::max<int64_t>(l_cap, (int64_t)c.a * x.Dl * x.Dl * c.c);
+      l_cap = std::max<int64_t>(l_cap, (int64_t)c.b * x.De * x.De * c.f);
+      a1_cap = std::max<int64_t>(a1_cap, (int64_t)x.Dl * x.Dl * c.c * vu * c.b);
+      a2_cap = std::max<int64_t>(a2_cap, (int64_t)x.Dl * c.c * x.Du * c.b * x.d * x.Dx * x.De);
+      a3_cap = std::max<int64_t>(a3_cap, (int64_t)c.c * c.b * x.De * x.Dx * x.Dx * x.De);
+      cols.push_back(c);
+    }
+    return "";
+  };
+  std::map<std::pair<int, int>, int64_t> norm_strip;
+  auto add_strip = [&](int l, int r, const std::vector<std::pair<int, int>> &ops) -> int64_t {
+    StripDesc x{};
+    x.col0 = row_cols[{l, r}];
+    x.ncol = lat[l]->ncol;
+    for (int q = 0; q < kStripMaxCols; ++q) x.op[q] = -1;
+    for (auto &o : ops) x.op[o.first] = o.second;
+    sd.push_back(x);
+    return (int64_t)sd.size() - 1;
+  };
+  auto norm_of = [&](int l, int r) -> std::string {
+    if (norm_strip.count({l, r})) return "";
+    std::string e = columns(l, r);
+    if (!e.empty()) return e;
+    norm_strip[{l, r}] = add_strip(l, r, {});
+    return "";
+  };
+  {
+    std::string e = norm_of(0, 0);
+    if (!e.empty()) return e;
+  }
+  P->term_strips.assign(P->terms.size(), {});
+  for (size_t t = 0; t < comps.size(); ++t)
+    for (auto &c : comps[t]) {
+      std::string e = norm_of(c.lat, c.row);
+      if (!e.empty()) return e;
+      const int64_t k = add_strip(c.lat, c.row, c.ops);
+      P->term_strips[t].push_back({k, norm_strip[{c.lat, c.row}]});
+    }
+  P->nstrips = (int64_t)sd.size();
+  P->lognorm_strip = norm_strip[{0, 0}];
+  const int64_t per = l_cap + a1_cap + a2_cap + a3_cap;
+  void *scr = B.buf((size_t)P->nstrips * per * as);
+  P->strip_off = B.alloc((size_t)P->nstrips * as);
+  for (int64_t i = 0; i < P->nstrips; ++i) {
+    sd[i].scratch = (uint8_t *)scr + (size_t)i * per * as;
+    sd[i].l_cap = l_cap; sd[i].a1_cap = a1_cap; sd[i].a2_cap = a2_cap; sd[i].a3_cap = a3_cap;
+    sd[i].out = (uint8_t *)B.ptr(P->strip_off) + (size_t)i * as;
+  }
+  // log |<psi|psi>| from row 0: its strip and the scales of the sweep below it
+  {
+    const EnvSet &E = *envs[env_of[0][0]];
+    P->lognorm_nlogs = E.has_bot ? E.bot.nsteps : 0;
+    P->lognorm_logs_off = E.has_bot ? (size_t)((uintptr_t)E.bot_logs - base) : 0;
+  }
+
+  // --- ops: lattice copies, sweeps, strips
+  {
+    Op f;
+    f.kind = Op::FILL; f.fill_ptr = ones; f.fill_n = 1; f.fill_value = 1.0; f.tag = "init";
+    B.ops.push_back(f);
+  }
+  push_permute(B, Hf.perm, "lattice_copy");
+  if (need_v) {
+    push_permute(B, tpass, "lattice_copy");
+    push_permute(B, Vt.perm, "lattice_copy");
+    push_permute(B, Vf.perm, "lattice_copy");
+  }
+  for (auto &E : envs) {
+    if (E->has_top) emit_sweep(B, E->top, P->opts, ones, E->top_rows, Vbuf, E->top_logs, E->top_sigma, owner);
+    if (E->has_bot) emit_sweep(B, E->bot, P->opts, ones, E->bot_rows, Vbuf, E->bot_logs, E->bot_sigma, owner);
+  }
+  // operator table in the accumulation type
+  std::vector<double> opflat;
+  for (auto &m : optab) opflat.insert(opflat.end(), m.begin(), m.end());
+  if (opflat.empty()) opflat.push_back(0.0);
+  Op st;
+  st.kind = Op::STRIP;
+  st.desc_off = B.put(sd);
+  st.aux_off[0] = B.put(cols);
+  st.aux_off[1] = B.put(opflat);
+  st.nd = (int)P->nstrips;
+  st.tag = "strips";
+  B.ops.push_back(st);
+  return "";
+}
 
 // ---- host-side access validator ---------------------------------------------
 // Recomputes, from every launch descriptor, the byte range each kernel may
@@ -537,6 +914,28 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         if (op.tc_kr % 4 || t.Kr != op.tc_kr) C.err = std::string(tag) + ": TMA rows not 16-byte aligned";
         break;
       }
+      case Op::STRIP: {
+        const StripCol *cl = (const StripCol *)(blob + op.aux_off[0]);
+        for (int i = 0; i < op.nd; ++i) {
+          const StripDesc &x = ((const StripDesc *)d)[i];
+          if (x.ncol > kStripMaxCols) C.err = std::string(tag) + ": too many columns";
+          for (int q = 0; q < x.ncol && q < kStripMaxCols; ++q) {
+            const StripCol &c = cl[x.col0 + q];
+            C.need(c.up, es * (double)c.a * c.Du * c.Du * c.b, tag, "up");
+            C.need(c.lo, es * (double)c.c * c.Dx * c.Dx * c.f, tag, "lo");
+            C.need(c.ket, es * (double)c.d * c.Dl * c.Du * c.Dx * c.De, tag, "ket");
+            const double vu = (double)c.Du * c.Du;
+            if ((double)c.a * c.Dl * c.Dl * c.c > x.l_cap || (double)c.b * c.De * c.De * c.f > x.l_cap ||
+                (double)c.Dl * c.Dl * c.c * vu * c.b > x.a1_cap ||
+                (double)c.Dl * c.c * c.Du * c.b * c.d * c.Dx * c.De > x.a2_cap ||
+                (double)c.c * c.b * c.De * c.Dx * c.Dx * c.De > x.a3_cap)
+              C.err = std::string(tag) + ": strip scratch too small";
+          }
+          C.need(x.scratch, as * ((double)x.l_cap + x.a1_cap + x.a2_cap + x.a3_cap), tag, "scratch");
+          C.need(x.out, as, tag, "out");
+        }
+        break;
+      }
       case Op::PERMUTE:
         for (int i = 0; i < op.nd; ++i) {
           const PermuteDesc &q = ((const PermuteDesc *)d)[i];
@@ -556,7 +955,8 @@ peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool en
   Builder B;
   B.encode = encode;
   std::string e = P->kind == peps_plan::EINSUMSVD ? build_einsumsvd(P, (uintptr_t)ws, io, B)
-                                                   : build_contract(P, (uintptr_t)ws, B);
+                  : P->kind == peps_plan::CONTRACT ? build_contract(P, (uintptr_t)ws, B)
+                                                   : build_expect(P, (uintptr_t)ws, B);
   if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
   if (!B.err.empty()) return fail(PEPS_ERR_UNSUPPORTED, "%s", B.err.c_str());
   P->ws_bytes = finish(B, &P->blob_off);   // needs the blob size: before the move
@@ -605,6 +1005,10 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
       case Op::FILL: launch_fill(dt, op.fill_ptr, op.fill_n, op.fill_value, s); break;
       case Op::TC: launch_tc_gemm(op.tc, op.tc_bn, s); break;
       case Op::PERMUTE: launch_permute(dt, (const PermuteDesc *)d, pre, op.nd, op.blocks, s); break;
+      case Op::STRIP:
+        launch_strip(dt, (const StripDesc *)d, (const StripCol *)(blob + op.aux_off[0]), blob + op.aux_off[1], op.nd,
+                     s);
+        break;
     }
     if (events) CUDA_TRY(cudaEventRecord(events[&op - P->ops.data() + 1], s));
   }
@@ -787,6 +1191,133 @@ peps_status peps_boundary_contract(const peps_network *ket, const peps_network *
   if (s != PEPS_OK) return s;
   s = peps_contract_execute(p, workspace, workspace_bytes, stream);
   if (s == PEPS_OK) s = peps_contract_result(p, workspace, stream, log_abs, phase, nullptr);
+  peps_plan_destroy(p);
+  return s;
+}
+
+peps_status peps_expectation_plan(peps_plan **out, const peps_network *ket, const peps_term *terms,
+                                  int32_t nterms, const peps_rsvd_opts *opts, int32_t use_cache,
+                                  size_t *workspace_bytes) {
+  g_last_error.clear();
+  if (!out || !workspace_bytes) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (nterms < 0 || (nterms > 0 && !terms)) return fail(PEPS_ERR_ARG, "terms missing");
+  if (peps_status s = check_opts(opts)) return s;
+  std::unique_ptr<peps_plan> P(new (std::nothrow) peps_plan());
+  if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
+  P->kind = peps_plan::EXPECT;
+  P->opts = to_opts(opts);
+  P->use_cache = use_cache != 0;
+  if (peps_status s = read_net(ket, P->ket, "ket")) return s;
+  P->dt = P->ket.dt;
+  const Net &H = P->ket;
+  const int d = H.d, vals = dtype_complex(P->dt) ? 2 : 1;
+  for (int t = 0; t < nterms; ++t) {
+    const peps_term &T = terms[t];
+    if (T.nsite != 1 && T.nsite != 2) return fail(PEPS_ERR_ARG, "term %d: nsite must be 1 or 2", t);
+    if (!T.op) return fail(PEPS_ERR_ARG, "term %d: operator is NULL", t);
+    const int nsites = H.nrow * H.ncol;
+    for (int k = 0; k < T.nsite; ++k)
+      if (T.site[k] < 0 || T.site[k] >= nsites) return fail(PEPS_ERR_ARG, "term %d: site out of range", t);
+    if (T.nsite == 2) {
+      const int r0 = T.site[0] / H.ncol, c0 = T.site[0] % H.ncol;
+      const int r1 = T.site[1] / H.ncol, c1 = T.site[1] % H.ncol;
+      if (!((r1 == r0 && c1 == c0 + 1) || (c1 == c0 && r1 == r0 + 1)))
+        return fail(PEPS_ERR_UNSUPPORTED, "term %d: only nearest-neighbour bonds, left-to-right or top-down", t);
+    }
+    peps_plan::Term X;
+    X.nsite = T.nsite;
+    X.site[0] = T.site[0];
+    X.site[1] = T.nsite == 2 ? T.site[1] : -1;
+    const int64_t n = T.nsite == 1 ? d : (int64_t)d * d;
+    X.op.assign(T.op, T.op + n * n * vals);
+    X.coeff = T.coeff;
+    P->terms.push_back(X);
+  }
+  if (peps_status s = rebuild(P.get(), nullptr, nullptr)) return s;
+  *workspace_bytes = P->ws_bytes;
+  *out = P.release();
+  return PEPS_OK;
+}
+
+peps_status peps_expectation_execute(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream) {
+  g_last_error.clear();
+  if (!plan) return fail(PEPS_ERR_ARG, "plan is NULL");
+  if (plan->kind != peps_plan::EXPECT) return fail(PEPS_ERR_ARG, "not an expectation plan");
+  const bool same = plan->built && plan->built_base == (uintptr_t)workspace;
+  if (!same) {
+    if (peps_status s = rebuild(plan, workspace, nullptr, true)) return s;
+    plan->built_base = (uintptr_t)workspace;
+    plan->built = true;
+  }
+  return enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, !same);
+}
+
+peps_status peps_expectation_result(peps_plan *plan, void *workspace, void *stream, double *energy,
+                                    double *log_norm, double *term_values) {
+  g_last_error.clear();
+  if (!plan || !workspace) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (plan->kind != peps_plan::EXPECT) return fail(PEPS_ERR_ARG, "not an expectation plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (in_capture(s)) return fail(PEPS_ERR_CAPTURE, "result read during stream capture");
+  const bool cplx = dtype_complex(plan->dt);
+  const int vals = cplx ? 2 : 1;
+  std::vector<double> sv((size_t)plan->nstrips * vals);
+  std::vector<double> lg((size_t)std::max<int64_t>(plan->lognorm_nlogs, 1));
+  CUDA_TRY(cudaMemcpyAsync(sv.data(), (uint8_t *)workspace + plan->strip_off, sv.size() * 8, cudaMemcpyDeviceToHost,
+                           s));
+  if (plan->lognorm_nlogs > 0)
+    CUDA_TRY(cudaMemcpyAsync(lg.data(), (uint8_t *)workspace + plan->lognorm_logs_off,
+                             (size_t)plan->lognorm_nlogs * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  auto re_ = [&](int64_t i) { return sv[(size_t)i * vals]; };
+  auto im_ = [&](int64_t i) { return cplx ? sv[(size_t)i * vals + 1] : 0.0; };
+  double e = 0.0;
+  for (size_t t = 0; t < plan->terms.size(); ++t) {
+    double num_re = 0.0, num_im = 0.0;
+    int64_t nrm = -1;
+    for (auto &pr : plan->term_strips[t]) {
+      num_re += re_(pr.first);
+      num_im += im_(pr.first);
+      nrm = pr.second;
+    }
+    double v = 0.0;
+    if (nrm >= 0) {
+      const double dr = re_(nrm), di = im_(nrm), den = dr * dr + di * di;
+      if (!(den > 0.0)) return fail(PEPS_ERR_NUMERIC, "term %zu: vanishing strip norm", t);
+      v = (num_re * dr + num_im * di) / den;       // Re(num / norm)
+    }
+    v *= plan->terms[t].coeff;
+    if (term_values) term_values[t] = v;
+    e += v;
+  }
+  if (energy) *energy = e;
+  if (log_norm) {
+    const double dr = re_(plan->lognorm_strip), di = im_(plan->lognorm_strip);
+    double l = 0.5 * std::log(dr * dr + di * di);
+    for (int64_t i = 0; i < plan->lognorm_nlogs; ++i) l += lg[(size_t)i];
+    *log_norm = l;
+  }
+  if (!std::isfinite(e)) return fail(PEPS_ERR_NUMERIC, "non-finite expectation value");
+  return PEPS_OK;
+}
+
+peps_status peps_expectation_workspace(const peps_network *ket, const peps_term *terms, int32_t nterms,
+                                       const peps_rsvd_opts *opts, int32_t use_cache, size_t *workspace_bytes) {
+  peps_plan *p = nullptr;
+  peps_status s = peps_expectation_plan(&p, ket, terms, nterms, opts, use_cache, workspace_bytes);
+  if (s == PEPS_OK) peps_plan_destroy(p);
+  return s;
+}
+
+peps_status peps_expectation(const peps_network *ket, const peps_term *terms, int32_t nterms,
+                             const peps_rsvd_opts *opts, int32_t use_cache, void *workspace, size_t workspace_bytes,
+                             void *stream, double *energy, double *log_norm) {
+  peps_plan *p = nullptr;
+  size_t need = 0;
+  peps_status s = peps_expectation_plan(&p, ket, terms, nterms, opts, use_cache, &need);
+  if (s != PEPS_OK) return s;
+  s = peps_expectation_execute(p, workspace, workspace_bytes, stream);
+  if (s == PEPS_OK) s = peps_expectation_result(p, workspace, stream, energy, log_norm, nullptr);
   peps_plan_destroy(p);
   return s;
 }

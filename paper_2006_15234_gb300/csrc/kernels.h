@@ -170,5 +170,26 @@ int sandwich_smem_bytes(int dt, const SandwichDesc &d);
 constexpr int kGemmBM = 64, kGemmBN = 64;
 constexpr int kSketchPerBlock = 256 * 4;   // elements per sketch block
 constexpr int kSiteThreads = 256;
+// One column of an expectation strip: boundary site above ([a][(u,U)][b]),
+// the row's ket site (the bra is the same tensor, conjugated) and boundary
+// site below ([c][(x,X)][f]).
+struct StripCol {
+  const void *up, *lo, *ket;
+  int32_t a, b, c, f;
+  int32_t d, Dl, Du, Dx, De;
+};
+constexpr int kStripMaxCols = 32;
+// One strip: columns col0..col0+ncol-1 of the column table, a one-site
+// operator index per column (-1: identity; d x d entries of the operator
+// table, accumulation type), FP64 scratch blocks, the scalar result.
+struct StripDesc {
+  int32_t col0, ncol;
+  int32_t op[kStripMaxCols];
+  void *scratch;
+  int64_t l_cap, a1_cap, a2_cap, a3_cap;
+  void *out;
+};
+void launch_strip(int dt, const StripDesc *d, const StripCol *cols, const void *ops, int nd, cudaStream_t s);
+
 
 }  // namespace peps

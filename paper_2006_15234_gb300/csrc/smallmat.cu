@@ -338,11 +338,67 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
 // rotation scalars use the data's own precision (FP64 divide / square root
 // run at a small fraction of the FP32 rate on this GPU).
 template <class T>
+__device__ __forceinline__ float jacobi_rotate_params(typename Traits<T>::Real al, typename Traits<T>::Real be, T ga,
+                                                      float tol, typename Traits<T>::Real &c,
+                                                      typename Traits<T>::Real &sn, T &ph, bool &rot) {
+  using R = typename Traits<T>::Real;
+  const R gm = sqrt(abs2(ga));
+  const R nrm = sqrt(al * be);
+  const float rel = nrm > (R)0 ? (float)(gm / nrm) : 0.f;
+  rot = gm > (R)tol * nrm && gm != (R)0;
+  if (!rot) return rel;
+  const R zeta = (be - al) / ((R)2 * gm);
+  const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+  c = (R)1 / sqrt((R)1 + t * t);
+  sn = c * t;
+  // e^{-i phi} with gamma = |gamma| e^{i phi}
+  if constexpr (Traits<T>::cplx) ph = from_parts<T>(re(ga) / gm, -im(ga) / gm);
+  else ph = re(ga) > (R)0 ? (R)1 : (R)-1;
+  return rel;
+}
+
+template <class T>
 __device__ float jacobi_pair(T *a, T *b, int n, float tol) {
   using R = typename Traits<T>::Real;
   const int lane = threadIdx.x & 31;
+  constexpr int kRegs = sizeof(T) <= 8 ? 16 : 8;   // columns up to 32 * kRegs rows stay in registers
   R al = 0, be = 0;
   T ga = zero<T>();
+  R c = 0, sn = 0;
+  T ph = zero<T>();
+  bool rot = false;
+  float rel;
+  if (n <= 32 * kRegs) {
+    // both columns read once (all loads issued back to back), rotated in registers
+    T x[kRegs], y[kRegs];
+#pragma unroll
+    for (int i = 0; i < kRegs; ++i) {
+      const int r = lane + 32 * i;
+      x[i] = r < n ? a[r] : zero<T>();
+      y[i] = r < n ? b[r] : zero<T>();
+    }
+#pragma unroll
+    for (int i = 0; i < kRegs; ++i) {
+      al += abs2(x[i]);
+      be += abs2(y[i]);
+      ga = fma_(conj_(x[i]), y[i], ga);
+    }
+    al = warp_sum(al);
+    be = warp_sum(be);
+    ga = warp_sum(ga);
+    rel = jacobi_rotate_params<T>(al, be, ga, tol, c, sn, ph, rot);
+    if (!rot) return rel;
+#pragma unroll
+    for (int i = 0; i < kRegs; ++i) {
+      const int r = lane + 32 * i;
+      if (r < n) {
+        const T yy = mul(y[i], ph);
+        a[r] = sub(scale(x[i], c), scale(yy, sn));
+        b[r] = add(scale(x[i], sn), scale(yy, c));
+      }
+    }
+    return rel;
+  }
   for (int r = lane; r < n; r += 32) {
     const T x = a[r], y = b[r];
     al += abs2(x);
@@ -352,18 +408,8 @@ __device__ float jacobi_pair(T *a, T *b, int n, float tol) {
   al = warp_sum(al);
   be = warp_sum(be);
   ga = warp_sum(ga);
-  const R gm = sqrt(abs2(ga));
-  const R nrm = sqrt(al * be);
-  const float rel = nrm > (R)0 ? (float)(gm / nrm) : 0.f;
-  if (!(gm > (R)tol * nrm) || gm == (R)0) return rel;
-  const R zeta = (be - al) / ((R)2 * gm);
-  const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
-  const R c = (R)1 / sqrt((R)1 + t * t);
-  const R sn = c * t;
-  // e^{-i phi} with gamma = |gamma| e^{i phi}
-  T ph;
-  if constexpr (Traits<T>::cplx) ph = from_parts<T>(re(ga) / gm, -im(ga) / gm);
-  else ph = re(ga) > (R)0 ? (R)1 : (R)-1;
+  rel = jacobi_rotate_params<T>(al, be, ga, tol, c, sn, ph, rot);
+  if (!rot) return rel;
   for (int r = lane; r < n; r += 32) {
     const T x = a[r];
     const T y = mul(b[r], ph);

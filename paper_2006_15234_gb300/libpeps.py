@@ -17,6 +17,7 @@ __all__ = [
     "Network", "ContractPlan", "EinsumsvdPlan", "boundary_contract", "dtype_code",
     "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "PREC_FAST", "SKETCH_GAUSS", "SKETCH_UNIFORM",
     "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
+    "Term", "ExpectationPlan", "expectation",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -29,6 +30,8 @@ EXPORTED_SYMBOLS = [
     "peps_contract_sigma_count", "peps_boundary_contract", "peps_boundary_workspace",
     "peps_plan_launch_count", "peps_plan_launch_info", "peps_plan_profile", "peps_plan_validate",
     "peps_debug_tc_gemm", "peps_boundary_contract_static",
+    "peps_expectation_plan", "peps_expectation_execute", "peps_expectation_result",
+    "peps_expectation_workspace", "peps_expectation",
 ]
 
 # Size of the library's fixed device scratch used by boundary_contract_static.
@@ -67,6 +70,11 @@ class Network(C.Structure):
     _fields_ = [("nrow", C.c_int32), ("ncol", C.c_int32), ("d", C.c_int32), ("dtype", C.c_int32),
                 ("bond_h", C.POINTER(C.c_int32)), ("bond_v", C.POINTER(C.c_int32)),
                 ("site", C.POINTER(C.c_void_p))]
+
+
+class Term(C.Structure):
+    _fields_ = [("nsite", C.c_int32), ("site", C.c_int32 * 2), ("op", C.POINTER(C.c_double)),
+                ("coeff", C.c_double)]
 
 
 _lib = None
@@ -124,6 +132,21 @@ def load():
     lib.peps_debug_tc_gemm.argtypes = [C.c_int32] * 7 + [vp, vp, vp, vp]
     lib.peps_plan_validate.restype = st
     lib.peps_plan_validate.argtypes = [vp, vp, C.c_size_t, C.POINTER(EinsumsvdIO)]
+    lib.peps_expectation_plan.restype = st
+    lib.peps_expectation_plan.argtypes = [C.POINTER(vp), C.POINTER(Network), C.POINTER(Term), C.c_int32,
+                                          C.POINTER(RsvdOpts), C.c_int32, C.POINTER(C.c_size_t)]
+    lib.peps_expectation_execute.restype = st
+    lib.peps_expectation_execute.argtypes = [vp, vp, C.c_size_t, vp]
+    lib.peps_expectation_result.restype = st
+    lib.peps_expectation_result.argtypes = [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]
+    lib.peps_expectation_workspace.restype = st
+    lib.peps_expectation_workspace.argtypes = [C.POINTER(Network), C.POINTER(Term), C.c_int32,
+                                               C.POINTER(RsvdOpts), C.c_int32, C.POINTER(C.c_size_t)]
+    lib.peps_expectation.restype = st
+    lib.peps_expectation.argtypes = [C.POINTER(Network), C.POINTER(Term), C.c_int32, C.POINTER(RsvdOpts),
+                                     C.c_int32, vp, C.c_size_t, vp, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]
     lib.peps_boundary_contract_static.restype = st
     lib.peps_boundary_contract_static.argtypes = [C.POINTER(Network), C.POINTER(Network),
                                                   C.POINTER(RsvdOpts), vp, C.POINTER(C.c_double),
@@ -323,6 +346,73 @@ def boundary_contract(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PL
     plan = ContractPlan(ket, bra, make_opts(m, p, q, seed, sketch, prec, flags), direction)
     plan.execute(stream)
     return plan.result(stream, with_sigma)
+
+
+class ExpectationPlan(_Ledger):
+    """<psi|H|psi>/<psi|psi> with cached environments (Eq. 6, Sec. IV-B).
+
+    terms: [(sites, op, coeff)]; sites = ((p, q),) or ((p0, q0), (p1, q1)) on a
+    nearest-neighbour bond; op a (d^n x d^n) array (host)."""
+
+    def __init__(self, ket, terms, opts: RsvdOpts, use_cache=True):
+        import numpy as np
+        self._lib = load()
+        self._ket = _network(ket)
+        ncol = len(ket[0])
+        cplx = ket[0][0].is_complex()
+        n = len(terms)
+        self._tarr = (Term * max(1, n))()
+        self._keep = []
+        for i, (st, op, coeff) in enumerate(terms):
+            a = np.ascontiguousarray(np.asarray(op, dtype=np.complex128 if cplx else np.float64))
+            if cplx:
+                a = np.ascontiguousarray(a.view(np.float64))
+            self._keep.append(a)
+            t = self._tarr[i]
+            t.nsite = len(st)
+            for k, (p, q) in enumerate(st):
+                t.site[k] = p * ncol + q
+            t.op = a.ctypes.data_as(C.POINTER(C.c_double))
+            t.coeff = float(coeff)
+        self.nterms = n
+        plan = C.c_void_p()
+        ws = C.c_size_t()
+        _check(self._lib.peps_expectation_plan(C.byref(plan), C.byref(self._ket.net), self._tarr, n,
+                                               C.byref(opts), int(bool(use_cache)), C.byref(ws)))
+        self._plan = plan
+        self.workspace_bytes = ws.value
+        self._buf, self._ws = _workspace(ws.value, ket[0][0].device)
+
+    def execute(self, stream=None):
+        _check(self._lib.peps_expectation_execute(self._plan, C.c_void_p(self._ws),
+                                                  C.c_size_t(self.workspace_bytes), _stream_handle(stream)))
+
+    def result(self, stream=None):
+        """(energy, log <psi|psi>, per-term coeff_t <O_t>)."""
+        import numpy as np
+        e, ln = C.c_double(), C.c_double()
+        tv = np.zeros(max(1, self.nterms), dtype=np.float64)
+        _check(self._lib.peps_expectation_result(self._plan, C.c_void_p(self._ws), _stream_handle(stream),
+                                                 C.byref(e), C.byref(ln),
+                                                 tv.ctypes.data_as(C.POINTER(C.c_double))))
+        return e.value, ln.value, tv[: self.nterms]
+
+    def __del__(self):
+        try:
+            if getattr(self, "_plan", None):
+                self._lib.peps_plan_destroy(self._plan)
+                self._plan = None
+        except Exception:
+            pass
+
+
+def expectation(ket, terms, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN, use_cache=True,
+                stream=None, flags=0):
+    """Energy <psi|H|psi>/<psi|psi> of H = sum coeff * op on the GPU; returns
+    (energy, log <psi|psi>, per-term values)."""
+    plan = ExpectationPlan(ket, terms, make_opts(m, p, q, seed, sketch, prec, flags), use_cache)
+    plan.execute(stream)
+    return plan.result(stream)
 
 
 def boundary_contract_static(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN,

@@ -137,3 +137,56 @@ def test_contract_test_shapes(lib, shape, D, m):
         wsp = heap(ws.value)
         assert lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None) == 0, lib.peps_last_error()
         lib.peps_plan_destroy(plan)
+
+
+def _term_array(terms, ncol, cplx):
+    import numpy as np
+    arr = (L.Term * len(terms))()
+    keep = []
+    for i, (st, op, coeff) in enumerate(terms):
+        a = np.ascontiguousarray(np.asarray(op, dtype=np.complex128 if cplx else np.float64))
+        if cplx:
+            a = np.ascontiguousarray(a.view(np.float64))
+        keep.append(a)
+        arr[i].nsite = len(st)
+        for k, (p, q) in enumerate(st):
+            arr[i].site[k] = p * ncol + q
+        arr[i].op = a.ctypes.data_as(C.POINTER(C.c_double))
+        arr[i].coeff = coeff
+    return arr, keep
+
+
+@pytest.mark.parametrize("use_cache", [1, 0])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("key,dt,shape", [("c4", 0, None), ("c4", 2, (3, 4)), ("c2", 1, (3, 3))])
+def test_expectation_plans(lib, key, dt, shape, prec, use_cache):
+    """Cached and uncached expectation plans (lattice copies, four sweeps,
+    strips) stay inside the workspace and the network."""
+    cfg = synth.config(key)
+    nr, nc = shape if shape else (cfg.nrow, cfg.ncol)
+    D = cfg.D if key == "c4" else 2
+    shp = [[synth.site_shape(nr, nc, p, q, cfg.d, D) for q in range(nc)] for p in range(nr)]
+    heap = FakeHeap()
+    net, keep = _net(heap, shp, dt)
+    terms = synth.tfi_terms(nr, nc, 1.0, 3.0)
+    arr, tkeep = _term_array(terms, nc, dt in (1, 3))
+    plan, ws = C.c_void_p(), C.c_size_t()
+    opts = L.make_opts(cfg.m if key == "c4" else 8, 8, 2, 1, prec=prec)
+    assert lib.peps_expectation_plan(C.byref(plan), C.byref(net), arr, len(terms), C.byref(opts), use_cache,
+                                     C.byref(ws)) == 0, lib.peps_last_error()
+    wsp = heap(ws.value)
+    r = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None)
+    assert r == 0, lib.peps_last_error().decode()
+    lib.peps_plan_destroy(plan)
+
+
+def test_expectation_rejects_long_range_terms(lib):
+    import numpy as np
+    shp = [[synth.site_shape(3, 3, p, q, 2, 2) for q in range(3)] for p in range(3)]
+    net, keep = _net(FakeHeap(), shp, 0)
+    zz = np.kron(np.diag([1.0, -1.0]), np.diag([1.0, -1.0]))
+    arr, tkeep = _term_array([(((0, 0), (0, 2)), zz, 1.0)], 3, False)
+    plan, ws = C.c_void_p(), C.c_size_t()
+    opts = L.make_opts(4, 2, 1, 1)
+    assert lib.peps_expectation_plan(C.byref(plan), C.byref(net), arr, 1, C.byref(opts), 1, C.byref(ws)) == 3
+    assert b"nearest-neighbour" in lib.peps_last_error()
