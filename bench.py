@@ -2,10 +2,12 @@
 SVD einsumsvd, two-layer zip-up) on one or more GB300s.
 
 One step = one full contraction <psi|psi> of the workload's PEPS (every row,
-every einsumsvd of Algorithms 2-4), inputs resident in HBM.  Prints one JSON
-line (rank 0).  ``--impl reference`` times the CPU oracle instead (the
-reference arm of this repository: a plain FP64 NumPy replay of the paper's
-algorithms) on a bounded sample of the same workload.
+every einsumsvd of Algorithms 2-4), inputs resident in HBM.  The default
+workload is the 16 x 16, D = 8 (double-layer bond 64), m = 256, p = 16, q = 2
+complex64 norm on the mixed-precision tensor-core path.  Prints one JSON line
+(rank 0).  ``--impl reference`` times the CPU oracle instead (the reference
+arm of this repository: a plain FP64 NumPy replay of the paper's algorithms)
+on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -177,9 +179,14 @@ def run_ours(args, cfg):
     plan.execute()
     la, ph = plan.result()
     if args.launch_list:
-        # one more contraction for an external launch-list capture, then stop
+        # one more contraction, bracketed for an external launch-list capture
+        # (ncu --profile-from-start off), then stop
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
         plan.execute()
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"launch_list": cfg.name, "kernel_launches": plan.kernel_launches()}), flush=True)
         return
     run = plan.execute
     graph = None
@@ -237,21 +244,29 @@ def run_ours(args, cfg):
 
     # per-launch device times of one more execute (CUDA events on the stream)
     prof = plan.profile()
-    by_tag = {}
-    for (tag, fl, by), t in zip(launches, prof):
+    kern = plan.kernels()
+    by_tag, by_kern = {}, {}
+    for (tag, fl, by), kname, t in zip(launches, kern, prof):
         d = by_tag.setdefault(tag, [0.0, 0.0, 0.0, 0])
         d[0] += t; d[1] += fl; d[2] += by; d[3] += 1
-    dom = max(by_tag.items(), key=lambda kv: kv[1][0])
+        d = by_kern.setdefault(kname, [0.0, 0.0, 0.0, 0])
+        d[0] += t; d[1] += fl; d[2] += by; d[3] += 1
     shapes = step_shapes(cfg)
     flops = algorithmic_flops(shapes, cfg.q, cfg.dtype == "c64")
     value = world * flops / (ms_step * 1e-3) / 1e12
     peaks, peak_src = measured_peaks()
-    tag, (dt_ms, dfl, dby, dn) = dom
-    if prec != libpeps.PREC_PLAIN and dfl > 0 and ("product" in tag or "adjoint" in tag):
+    # the dominant kernel: the family with the largest device time
+    kname, (dt_ms, dfl, dby, dn) = max(by_kern.items(), key=lambda kv: kv[1][0])
+    if kname == "tc_gemm":
         bound, unit = "tensor", "TFLOP/s"
         achieved = dfl / (dt_ms * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained", 1700.0) / 2.0      # TF32 = half the bf16 rate
-        peak_note = f"TF32 = bf16 sustained/2 ({peak_src})"
+        tf32 = peaks.get("bf16_tflops_sustained", 1700.0) / 2.0      # TF32 = half the bf16 rate
+        if prec == libpeps.PREC_FAST:
+            peak, peak_note = tf32, f"TF32 dense = bf16 sustained x 1/2 ({peak_src})"
+        else:
+            peak = tf32 / 3.0
+            peak_note = (f"FP32-level products as 3 TF32 MMAs: bf16 sustained x 1/2 x 1/3 ({peak_src}); "
+                         f"algorithmic FP32 flops counted once")
     elif dfl / max(dby, 1) > 12:
         bound, unit = "alu", "TFLOP/s"
         achieved = dfl / (dt_ms * 1e-3) / 1e12
@@ -263,6 +278,22 @@ def run_ours(args, cfg):
         achieved = dby / (dt_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         peak_note = f"HBM copy bandwidth ({peak_src})"
+    plain_s = None
+    if args.compare_plain and prec != libpeps.PREC_PLAIN:
+        pplan = libpeps.ContractPlan(kt, kt if cfg.two_layer else None,
+                                     libpeps.make_opts(cfg.m, cfg.p, cfg.q, cfg.omega_seed,
+                                                       prec=libpeps.PREC_PLAIN))
+        pplan.execute()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pplan.execute()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_s = e0.elapsed_time(e1) / 1e3
+        plain_la, _ = pplan.result()
+        del pplan
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -275,16 +306,22 @@ def run_ours(args, cfg):
                    "l2": "flushed between steps (2x L2 write outside the timed events)",
                    "parallelism": f"replicas x{world}", "log_norm": la,
                    "cuda_graph": graph is not None},
-        "gpu_launches": nlaunch * args.steps,
+        "gpu_launches": plan.kernel_launches() * args.steps,
         "e2e": {"value": round(world * flops / e2e_s / 1e12, 4), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16},
-        "roofline": {"bound": bound, "kernel": tag, "achieved": round(achieved, 3),
+        "roofline": {"bound": bound, "kernel": kname, "achieved": round(achieved, 3),
                      "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
                      "traffic": None, "launches_per_step": dn,
                      "avg_launch_ms": round(dt_ms / dn, 5), "peak_source": peak_note,
-                     "algorithmic_per_launch": round((dfl if unit == "TFLOP/s" else dby) / dn, 1)},
+                     "algorithmic_per_launch": round((dfl if unit == "TFLOP/s" else dby) / dn, 1),
+                     "share_of_step": round(dt_ms / max(sum(v[0] for v in by_kern.values()), 1e-9), 4)},
+        "kernel_ms": {k: round(v[0], 4) for k, v in sorted(by_kern.items(), key=lambda kv: -kv[1][0])},
         "stage_ms": {k: round(v[0], 4) for k, v in sorted(by_tag.items(), key=lambda kv: -kv[1][0])},
     }
+    if plain_s is not None:
+        line["config"]["plain_fp32_contraction_s"] = round(plain_s, 4)
+        line["config"]["mixed_speedup_vs_plain"] = round(plain_s / (ms_step / 1e3), 3)
+        line["config"]["plain_log_norm"] = plain_la
     clk = clk.summary()
     if clk:
         line["clocks"] = clk
@@ -309,23 +346,29 @@ def cpu_baseline(cfg, args):
         fl = algorithmic_flops(shapes, cfg.q, cfg.dtype == "c64")
         sample = "one full contraction"
     else:
-        # the largest einsumsvd step of the sweep, on its own inputs
+        # one implicit product A X of the largest einsumsvd step (the operation
+        # that carries most of the flops), on all of its l sketch columns
+        from oracle.implicit import ImplicitOp
         big = max(shapes, key=lambda s: s["prod_macs"])
         rng = np.random.default_rng(0)
-        kL = big["M"] // (cfg.D ** 2)
-        a = b = cfg.m
         R = cfg.D ** 2
+        kL = big["M"] // R
+        a = b = cfg.m
 
         def cg(shape):
             z = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
             return synth.round_to(z / np.linalg.norm(z), cfg.dtype)
         V, S = cg((kL, R, a, R)), cg((a, R, b))
         K = cg((cfg.d, cfg.D, cfg.D, cfg.D, cfg.D))
+        op = ImplicitOp(V, S, K, K)
+        cols = big["ell"]
+        X = rng.standard_normal((op.N, cols)) + 1j * rng.standard_normal((op.N, cols))
         t0 = time.perf_counter()
-        rsvd.einsumsvd(V, S, K, K, cfg.m, cfg.p, cfg.q, cfg.omega_seed, 0)
+        op.matvec(X)
         dt = time.perf_counter() - t0
-        fl = algorithmic_flops([big], cfg.q, True)
-        sample = f"one middle einsumsvd step (M={big['M']}, N={big['N']}, l={big['ell']})"
+        fl = 8.0 * big["prod_macs"] * cols / big["ell"]
+        sample = (f"one implicit product A X of the largest einsumsvd step (M={big['M']}, N={big['N']}) "
+                  f"on {cols} of its {big['ell']} sketch columns")
     return {"value": round(fl / dt / 1e12, 6), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
             "sample": sample, "seconds": round(dt, 3)}
 
@@ -360,11 +403,13 @@ def run_reference(args, cfg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c2", "c5", "c4"])
-    ap.add_argument("--prec", default="plain", choices=["plain", "mixed", "fast"])
+    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4"])
+    ap.add_argument("--prec", default="mixed", choices=["plain", "mixed", "fast"])
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="also time one plain FP32 contraction (reported in config)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--launch-list", action="store_true",

@@ -266,6 +266,17 @@ peps_status peps_plan_launch_count(const peps_plan *plan, int64_t *count);
 peps_status peps_plan_launch_info(const peps_plan *plan, int64_t i, const char **tag,
                                   double *flops, double *bytes);
 
+/* CUDA kernel launches one execute of the plan enqueues (an entry of the
+ * ledger may launch more than one kernel: the Cholesky and Jacobi entries
+ * launch a one-CTA and a cluster kernel, the Jacobi entry its singular value
+ * refinement too). */
+peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count);
+
+/* Kernel family of launch i (static string): "tc_gemm" (tcgen05 GEMM),
+ * "gemm", "gemm_gram", "sandwich", "chol", "jacobi", "finalize", "sketch",
+ * "permute", "site", "strip", "scalar", "zero", "fill". */
+peps_status peps_plan_launch_kernel(const peps_plan *plan, int64_t i, const char **kernel);
+
 /* Execute once more (same rules as the execute calls; the plan must have
  * been executed before) with a CUDA event after every launch, synchronise,
  * and write launch i's device time in milliseconds to ms[i]. */

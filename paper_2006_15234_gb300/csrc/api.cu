@@ -1339,6 +1339,46 @@ peps_status peps_plan_launch_info(const peps_plan *plan, int64_t i, const char *
   return PEPS_OK;
 }
 
+peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count) {
+  if (!plan || !count) return fail(PEPS_ERR_ARG, "NULL argument");
+  int64_t n = 0;
+  for (const Op &op : plan->ops) {
+    switch (op.kind) {
+      case Op::JACOBI: n += 1 + (op.smem2 > 0) + (op.blocks > 0); break;   // one CTA, cluster, refinement
+      case Op::CHOL: n += 1 + (op.smem2 > 0); break;                         // one CTA, cluster
+      case Op::TC: n += op.tc.tiles_m * op.tc.tiles_n > 0; break;
+      case Op::SKETCH: case Op::GEMM: case Op::GEMM_ATOMIC: case Op::SANDWICH: case Op::ZERO: case Op::SITE:
+      case Op::PERMUTE: n += op.blocks > 0; break;
+      default: n += 1; break;
+    }
+  }
+  *count = n;
+  return PEPS_OK;
+}
+
+peps_status peps_plan_launch_kernel(const peps_plan *plan, int64_t i, const char **kernel) {
+  if (!plan || !kernel) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (i < 0 || i >= (int64_t)plan->ops.size()) return fail(PEPS_ERR_ARG, "launch index out of range");
+  switch (plan->ops[i].kind) {
+    case Op::SKETCH: *kernel = "sketch"; break;
+    case Op::GEMM: *kernel = "gemm"; break;
+    case Op::GEMM_ATOMIC: *kernel = "gemm_gram"; break;
+    case Op::SANDWICH: *kernel = "sandwich"; break;
+    case Op::CHOL: *kernel = "chol"; break;
+    case Op::JACOBI: *kernel = "jacobi"; break;
+    case Op::FINALIZE: *kernel = "finalize"; break;
+    case Op::ZERO: *kernel = "zero"; break;
+    case Op::SITE: *kernel = "site"; break;
+    case Op::SCALAR: *kernel = "scalar"; break;
+    case Op::FILL: *kernel = "fill"; break;
+    case Op::TC: *kernel = "tc_gemm"; break;
+    case Op::PERMUTE: *kernel = "permute"; break;
+    case Op::STRIP: *kernel = "strip"; break;
+    default: *kernel = "unknown"; break;
+  }
+  return PEPS_OK;
+}
+
 peps_status peps_plan_profile(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream,
                               double *ms) {
   g_last_error.clear();

@@ -31,7 +31,8 @@ EXPORTED_SYMBOLS = [
     "peps_plan_launch_count", "peps_plan_launch_info", "peps_plan_profile", "peps_plan_validate",
     "peps_debug_tc_gemm", "peps_boundary_contract_static",
     "peps_expectation_plan", "peps_expectation_execute", "peps_expectation_result",
-    "peps_expectation_workspace", "peps_expectation",
+    "peps_expectation_workspace", "peps_expectation", "peps_plan_launch_kernel",
+    "peps_plan_kernel_launches",
 ]
 
 # Size of the library's fixed device scratch used by boundary_contract_static.
@@ -126,6 +127,10 @@ def load():
     lib.peps_plan_launch_info.restype = st
     lib.peps_plan_launch_info.argtypes = [vp, C.c_int64, C.POINTER(C.c_char_p),
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.peps_plan_kernel_launches.restype = st
+    lib.peps_plan_kernel_launches.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.peps_plan_launch_kernel.restype = st
+    lib.peps_plan_launch_kernel.argtypes = [vp, C.c_int64, C.POINTER(C.c_char_p)]
     lib.peps_plan_profile.restype = st
     lib.peps_plan_profile.argtypes = [vp, vp, C.c_size_t, vp, C.POINTER(C.c_double)]
     lib.peps_debug_tc_gemm.restype = st
@@ -236,6 +241,21 @@ class _Ledger:
             _check(self._lib.peps_plan_launch_info(self._plan, i, C.byref(tag), C.byref(fl),
                                                    C.byref(by)))
             out.append((tag.value.decode(), fl.value, by.value))
+        return out
+
+    def kernel_launches(self):
+        """CUDA kernel launches of one execute."""
+        n = C.c_int64()
+        _check(self._lib.peps_plan_kernel_launches(self._plan, C.byref(n)))
+        return n.value
+
+    def kernels(self):
+        """Kernel family of every launch ("tc_gemm", "chol", ...)."""
+        out = []
+        for i in range(self.launch_count()):
+            k = C.c_char_p()
+            _check(self._lib.peps_plan_launch_kernel(self._plan, i, C.byref(k)))
+            out.append(k.value.decode())
         return out
 
     def profile(self, stream=None):
