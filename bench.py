@@ -333,10 +333,184 @@ def run_ours(args, cfg):
         dist.destroy_process_group()
 
 
+def batched_shapes(cfg, rank=0):
+    """(shape tuple, algorithmic flops) of every instance of the batched
+    workload: one zip-up step per instance, kL = a = b = m, t = h = D^2,
+    rank k = m (the paper's per-step einsumsvd with its own m)."""
+    out = []
+    for m, D in synth.batched_dims(cfg):
+        R = D * D
+        M, N = m * R, m * R * R
+        k = min(m, M, N)
+        ell = min(k + cfg.p, M, N)
+        prod = ell * (m * cfg.d * (R * R * R + R * R * R) + m * R * R * m + M * m * R)
+        shp = dict(M=M, N=N, ell=ell, k=k, prod_macs=prod)
+        out.append(((m, R, m, m, cfg.d, D, D, D, D, D, D, D, D, m), algorithmic_flops([shp], cfg.q, False)))
+    return out
+
+
+def run_batched(args, cfg):
+    """Batched einsumsvd: 512 independent instances in one plan, replayed as
+    one CUDA graph (a step = all instances once)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2006_15234_gb300 import libpeps
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shp = batched_shapes(cfg)
+    n = len(shp)
+    flops = sum(f for _, f in shp)
+    prec = {"plain": libpeps.PREC_PLAIN, "mixed": libpeps.PREC_MIXED, "fast": libpeps.PREC_FAST}[args.prec]
+    # weak scaling: every rank its own 512 instances (instance seeds offset by rank)
+    host, io = [], []
+    plan = libpeps.EinsumsvdPlan(torch.float32, [s for s, _ in shp],
+                                 libpeps.make_opts(128, cfg.p, cfg.q, cfg.omega_seed, prec=prec),
+                                 instance_ids=[rank * n + i for i in range(n)], device=dev)
+    for i, (s, _) in enumerate(shp):
+        m, D = s[0], s[5]
+        inst = synth.batched_instance(cfg, rank * n + i, m, D)
+        h = [torch.from_numpy(np.ascontiguousarray(inst[k], dtype=np.float32)).pin_memory()
+             for k in ("V", "S", "ket", "bra")]
+        host.append(h)
+        k = plan.ranks[i]
+        U = torch.empty((s[0] * s[1], k), dtype=torch.float32, device=dev)
+        W = torch.empty((k, s[7] * s[11] * s[3] * s[8] * s[12]), dtype=torch.float32, device=dev)
+        sg = torch.empty(k, dtype=torch.float64, device=dev)
+        lg = torch.empty(1, dtype=torch.float64, device=dev)
+        io.append(tuple(x.to(dev) for x in h) + (U, W, sg, lg))
+    launches = plan.launches()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    plan.execute(io)                      # descriptor upload
+    torch.cuda.synchronize()
+    run = lambda: plan.execute(io)        # noqa: E731
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                plan.execute(io)
+        stream.wait_stream(side)
+        run = graph.replay
+    for _ in range(max(0, args.warmup - 1)):
+        run()
+    barrier()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            times.append((e0, e1))
+        barrier()
+    ms_step = float(np.mean([a.elapsed_time(b) for a, b in times]))
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    # end to end: H2D of every instance's operands, the batch, D2H of all singular values
+    h2d = sum(x.numel() * x.element_size() for h in host for x in h)
+    d2h = sum(x[6].numel() * 8 for x in io)
+    sig_host = [torch.empty(x[6].numel(), dtype=torch.float64).pin_memory() for x in io]
+    e2e = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for h, x in zip(host, io):
+            for a, b in zip(h, x[:4]):
+                b.copy_(a, non_blocking=True)
+        run()
+        for hs, x in zip(sig_host, io):
+            hs.copy_(x[6], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = float(np.median(e2e))
+    prof = plan.profile()
+    kern = plan.kernels()
+    by_kern = {}
+    for (tag, fl, by), kname, t in zip(launches, kern, prof):
+        d = by_kern.setdefault(kname, [0.0, 0.0, 0.0, 0])
+        d[0] += t; d[1] += fl; d[2] += by; d[3] += 1
+    kname, (dt_ms, dfl, dby, dn) = max(by_kern.items(), key=lambda kv: kv[1][0])
+    peaks, peak_src = measured_peaks()
+    if kname == "tc_gemm" or dfl / max(dby, 1) > 12:
+        bound, unit = ("tensor", "TFLOP/s") if kname == "tc_gemm" else ("alu", "TFLOP/s")
+        achieved = dfl / (dt_ms * 1e-3) / 1e12
+        if kname == "tc_gemm":
+            peak = peaks.get("bf16_tflops_sustained", 1700.0) / 2.0 / 3.0
+            peak_note = f"FP32-level products as 3 TF32 MMAs: bf16 sustained x 1/2 x 1/3 ({peak_src})"
+        else:
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            peak_note = "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock"
+    else:
+        bound, unit = "hbm", "GB/s"
+        achieved = dby / (dt_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        peak_note = f"HBM copy bandwidth ({peak_src})"
+    line = {
+        "metric": METRIC, "value": round(world * flops / (ms_step * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded N(0,1) operands, instance sizes of the workload)",
+        "config": {"workload": cfg.name, "instances": n, "m_range": cfg.extra["m_range"],
+                   "D_range": cfg.extra["D_range"], "p": cfg.p, "q": cfg.q, "rank": "k = m per instance",
+                   "precision": args.prec, "algorithmic_tflop_per_step": round(flops / 1e12, 6),
+                   "l2": "flushed between steps (2x L2 write outside the timed events)",
+                   "parallelism": f"instances per rank x{world}", "cuda_graph": graph is not None},
+        "gpu_launches": plan.kernel_launches() * args.steps,
+        "e2e": {"value": round(world * flops / e2e_s / 1e12, 4), "unit": "TFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": bound, "kernel": kname, "achieved": round(achieved, 3), "peak": round(peak, 1),
+                     "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
+                     "launches_per_step": dn, "avg_launch_ms": round(dt_ms / dn, 5), "peak_source": peak_note,
+                     "share_of_step": round(dt_ms / max(sum(v[0] for v in by_kern.values()), 1e-9), 4)},
+        "kernel_ms": {k: round(v[0], 4) for k, v in sorted(by_kern.items(), key=lambda kv: -kv[1][0])},
+    }
+    clk = clk.summary()
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(cfg, args):
     """The oracle as it stands, on a bounded sample of the workload."""
     from oracle import bmps, rsvd
     cores = os.cpu_count()
+    if cfg.name.startswith("c3"):
+        # instances in order until about 15 s of oracle time
+        fl, dt, cnt = 0.0, 0.0, 0
+        for i, ((s, f), (m, D)) in enumerate(zip(batched_shapes(cfg), synth.batched_dims(cfg))):
+            inst = synth.batched_instance(cfg, i, m, D)
+            t0 = time.perf_counter()
+            rsvd.einsumsvd(inst["V"], inst["S"], inst["ket"], inst["bra"], m, cfg.p, cfg.q, cfg.omega_seed, i)
+            dt += time.perf_counter() - t0
+            fl += f
+            cnt += 1
+            if dt > 15.0:
+                break
+        return {"value": round(fl / dt / 1e12, 6), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                "sample": f"the first {cnt} of the 512 instances", "seconds": round(dt, 3)}
     ket = synth.peps_for(cfg)
     shapes = step_shapes(cfg)
     if cfg.nrow * cfg.ncol <= 64:
@@ -406,7 +580,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4"])
+    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3"])
     ap.add_argument("--prec", default="mixed", choices=["plain", "mixed", "fast"])
     ap.add_argument("--compare-plain", action="store_true",
                     help="also time one plain FP32 contraction (reported in config)")
@@ -418,6 +592,8 @@ def main():
     cfg = synth.config(args.config)
     if args.impl == "reference":
         run_reference(args, cfg)
+    elif args.config == "c3":
+        run_batched(args, cfg)
     else:
         run_ours(args, cfg)
 

@@ -115,6 +115,7 @@ typedef struct {
   int32_t kL, t, a, b;
   int32_t d, Dl, Du, Dx, De;   /* ket site dims */
   int32_t DL, DU, DX, DE;      /* bra site dims */
+  int32_t m;                   /* this instance's truncation rank; 0: opts->m */
 } peps_einsumsvd_shape;
 
 typedef struct {

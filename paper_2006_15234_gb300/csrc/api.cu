@@ -1059,7 +1059,10 @@ peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch
     I.DL = s.DL; I.DU = s.DU; I.DX = s.DX; I.DE = s.DE;
     std::string e = inst_check(I, dtype);
     if (!e.empty()) return fail(PEPS_ERR_SHAPE, "instance %d: %s", i, e.c_str());
-    inst_derive(I, P->opts);
+    if (s.m < 0) return fail(PEPS_ERR_ARG, "instance %d: negative rank", i);
+    RsvdOpts oi = P->opts;
+    if (s.m > 0) oi.m = s.m;
+    inst_derive(I, oi);
     I.instance = instance_ids ? instance_ids[i] : (uint64_t)i;
     I.tc = P->opts.prec != PEPS_PREC_PLAIN && inst_tc_ok(I, dtype);
     P->insts.push_back(I);

@@ -58,7 +58,7 @@ class RsvdOpts(C.Structure):
 
 class EinsumsvdShape(C.Structure):
     _fields_ = [(n, C.c_int32) for n in
-                ("kL", "t", "a", "b", "d", "Dl", "Du", "Dx", "De", "DL", "DU", "DX", "DE")]
+                ("kL", "t", "a", "b", "d", "Dl", "Du", "Dx", "De", "DL", "DU", "DX", "DE", "m")]
 
 
 class EinsumsvdIO(C.Structure):

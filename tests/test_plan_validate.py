@@ -46,7 +46,7 @@ def _einsumsvd_ok(lib, dt, shapes, m, p, q, prec=0):
     es = ES[dt]
     io = (L.EinsumsvdIO * n)()
     for i, s in enumerate(shapes):
-        kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE = s
+        kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE = s[:13]
         k = C.c_int32()
         lib.peps_einsumsvd_rank(plan, i, C.byref(k))
         M, N = kL * t, Dx * DX * b * De * DE
@@ -77,7 +77,8 @@ def test_einsumsvd_test_shapes(lib, dt, prec):
 def test_batched_workload_sample(lib, prec):
     cfg = synth.config("c3")
     dims = synth.batched_dims(cfg)[:64]
-    shapes = [(m, D * D, m, m, 2, D, D, D, D, D, D, D, D) for m, D in dims]
+    # per-instance rank k = m (the shape's rank field)
+    shapes = [(m, D * D, m, m, 2, D, D, D, D, D, D, D, D, m) for m, D in dims]
     r, msg, _ = _einsumsvd_ok(lib, 0, shapes, 128, cfg.p, cfg.q, prec)
     assert r == 0, msg
 
@@ -190,3 +191,18 @@ def test_expectation_rejects_long_range_terms(lib):
     opts = L.make_opts(4, 2, 1, 1)
     assert lib.peps_expectation_plan(C.byref(plan), C.byref(net), arr, 1, C.byref(opts), 1, C.byref(ws)) == 3
     assert b"nearest-neighbour" in lib.peps_last_error()
+
+
+def test_per_instance_rank(lib):
+    """The shape's rank field overrides opts.m for that instance only."""
+    shapes = [(16, 9, 16, 16, 2, 3, 3, 3, 3, 3, 3, 3, 3, 5), (16, 9, 16, 16, 2, 3, 3, 3, 3, 3, 3, 3, 3, 0)]
+    arr = (L.EinsumsvdShape * 2)(*[L.EinsumsvdShape(*s) for s in shapes])
+    plan, ws = C.c_void_p(), C.c_size_t()
+    opts = L.make_opts(12, 4, 1, 1)
+    assert lib.peps_einsumsvd_plan(C.byref(plan), 0, 2, arr, None, C.byref(opts), C.byref(ws)) == 0
+    k = C.c_int32()
+    lib.peps_einsumsvd_rank(plan, 0, C.byref(k))
+    assert k.value == 5
+    lib.peps_einsumsvd_rank(plan, 1, C.byref(k))
+    assert k.value == 12
+    lib.peps_plan_destroy(plan)
