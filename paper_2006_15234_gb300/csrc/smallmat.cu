@@ -89,6 +89,22 @@ __device__ double block_max(double v, double *red) {
   return r;
 }
 
+__device__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m += red[i];
+    red[0] = m;
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
 template <class T> __device__ __forceinline__ T real_scalar(double x) { return from_parts<T>(x, 0.0); }
 
 template <class T> __device__ __forceinline__ T div_real(T a, double r) {
@@ -563,30 +579,33 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NT)
 // 1 + O(eps)) scales the columns it touches, and over the ~n rotations per
 // sweep per column that drift reaches ~n eps relative; the product with the
 // unrotated upper-triangular Rb, summed in FP64, carries Rb's rounding only.
-// One warp per column.
+// One CTA per column; its warps take rows round-robin.
 template <class T>
-__global__ void __launch_bounds__(NT) sigma_refine_kernel(const JacobiDesc *__restrict__ descs, int cols_blocks) {
+__global__ void __launch_bounds__(NT) sigma_refine_kernel(const JacobiDesc *__restrict__ descs, int cols) {
   using Acc = typename Traits<T>::Acc;
-  const JacobiDesc &g = descs[blockIdx.x / cols_blocks];
+  __shared__ double red[32];
+  const JacobiDesc &g = descs[blockIdx.x / cols];
   const int n = g.n;
-  const int lane = threadIdx.x & 31;
-  const int c = (blockIdx.x % cols_blocks) * (NT / 32) + (threadIdx.x >> 5);
-  if (c >= n) return;
+  const int c = blockIdx.x % cols;
+  if (c >= n) return;                              // uniform over the CTA
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const T *m = (const T *)g.Mw + (int64_t)c * n;
   const T *Rb = (const T *)g.Rb;
   double s2 = 0.0;
-  for (int k = lane; k < n; k += 32) s2 += (double)abs2(m[k]);
-  s2 = warp_sum(s2);
+  for (int k = threadIdx.x; k < n; k += NT) s2 += (double)abs2(m[k]);
+  s2 = block_sum(s2, red);
   double v2 = 0.0;
   if (s2 > 0.0) {
-    for (int i = 0; i < n; ++i) {
+    for (int i = w; i < n; i += NT / 32) {
       Acc d = zero<Acc>();
       for (int k = i + lane; k < n; k += 32) d = fma_(widen(Rb[(int64_t)i * n + k]), widen(m[k]), d);
       d = warp_sum(d);
-      v2 += abs2(d);
+      v2 += abs2(d);                               // identical in every lane
     }
   }
-  if (lane == 0) g.sig[c] = s2 > 0.0 ? sqrt(v2 / s2) : 0.0;
+  if (lane != 0) v2 = 0.0;
+  v2 = block_sum(v2, red);
+  if (threadIdx.x == 0) g.sig[c] = s2 > 0.0 ? sqrt(v2 / s2) : 0.0;
 }
 
 template <class T>
@@ -678,8 +697,7 @@ void jacobi_t(const JacobiDesc *d, int nd, int smem, int cluster_smem, int nmax,
   }
   if (smem >= 0) jacobi_kernel<T><<<nd, NT, smem, s>>>(d);
   if (cluster_smem > 0) jacobi_cluster_kernel<T><<<nd * kClusterCTAs, NT, cluster_smem, s>>>(d);
-  const int cb = (nmax + NT / 32 - 1) / (NT / 32);
-  if (cb > 0) sigma_refine_kernel<T><<<nd * cb, NT, 0, s>>>(d, cb);
+  if (nmax > 0) sigma_refine_kernel<T><<<nd * nmax, NT, 0, s>>>(d, nmax);
 }
 template <class T> void finalize_t(const FinalizeDesc *d, int nd, cudaStream_t s) {
   // order (n ints) + h (n) + rho (k <= n): n <= 1024

@@ -215,10 +215,14 @@ double chol_shift(int dt, int ell, bool first_pass) {
   return 4.0 * ell * 5.9604644775390625e-08;
 }
 
-// CholeskyQR pass: G <- src^H src; T <- R^+; dst <- src T
+void emit_gram_tc(Builder &B, Inst &q, const void *src, int64_t L, const char *tag);
+
+// CholeskyQR pass: G <- src^H src; T <- R^+; dst <- src T.  tc_gram: the Gram
+// of a single tensor-core instance runs on the tensor cores (3xTF32, FP64
+// accumulation across K chunks).
 void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*src, void *Inst::*dst,
                    void *Inst::*Rdst, void *Inst::*Rprev, void *Inst::*Rout, bool apply, const char *tag,
-                   bool first_pass) {
+                   bool first_pass, bool tc_gram = false) {
   const int as = acc_size(B.dt);
   std::vector<std::pair<void *, int64_t>> z;
   std::vector<GemmDesc> gram, app;
@@ -240,9 +244,14 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
       app.push_back(mk_gemm(q.ell, (int)L, q.ell, 1, q.Tm, 1, q.ell, 0, false, q.*src, L, 1, 0, false,
                             q.*dst, L, 1, 0));
   }
-  for (auto &g : gram) set_ksplit(g, (int)gram.size());
-  push_zero(B, z, tag);
-  push_gemm(B, gram, true, tag);
+  const int64_t Lr = I.empty() ? 0 : (mside ? I[0]->M : I[0]->N);
+  if (tc_gram && I.size() == 1 && (Lr * dtype_size(B.dt)) % 16 == 0) {
+    emit_gram_tc(B, *I[0], I[0]->*src, Lr, tag);
+  } else {
+    for (auto &g : gram) set_ksplit(g, (int)gram.size());
+    push_zero(B, z, tag);
+    push_gemm(B, gram, true, tag);
+  }
   Op op;
   op.kind = Op::CHOL;
   op.desc_off = B.put(ch);
@@ -258,12 +267,12 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
 
 void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I);
 
-void emit_orth(Builder &B, std::vector<Inst *> &I, bool mside) {
+void emit_orth(Builder &B, std::vector<Inst *> &I, bool mside, bool tc_gram = false) {
   void *Inst::*a = mside ? &Inst::Y : &Inst::Z;
   void *Inst::*t = mside ? &Inst::P : &Inst::X;
   const char *tag = mside ? "orth_m" : "orth_n";
-  emit_cqr_pass(B, I, mside, a, t, &Inst::R1, nullptr, nullptr, true, tag, true);
-  emit_cqr_pass(B, I, mside, t, a, &Inst::R1, nullptr, nullptr, true, tag, false);
+  emit_cqr_pass(B, I, mside, a, t, &Inst::R1, nullptr, nullptr, true, tag, true, tc_gram);
+  emit_cqr_pass(B, I, mside, t, a, &Inst::R1, nullptr, nullptr, true, tag, false, tc_gram);
 }
 
 void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
@@ -394,7 +403,11 @@ void emit_gram_tc(Builder &B, Inst &q, const void *src, int64_t L, const char *t
   Op &op = B.ops.back();
   const int64_t kr = op.tc_kr;
   const int64_t nkb = ceil_div(kr, 32);
-  const int64_t chunk_kb = dtype_complex(B.dt) ? 128 : 64;   // 2048 complex / 2048 real K values
+  // K chunks of at most 128 K blocks, and small enough that about two items
+  // per SM exist; 8 K blocks at least
+  const int64_t tiles = (int64_t)op.tc.tiles_m * op.tc.tiles_n;
+  const int64_t want = std::max<int64_t>(1, ceil_div(2 * kSMs, tiles));
+  const int64_t chunk_kb = std::max<int64_t>(std::min<int64_t>(8, nkb), std::min<int64_t>(128, ceil_div(nkb, want)));
   op.tc.atomic64 = 1;
   op.tc.kb_per_split = (int32_t)chunk_kb;
   op.tc.ksplit = (int32_t)ceil_div(nkb, chunk_kb);
@@ -500,13 +513,13 @@ void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {
   // products before the last A Q of the power iteration on plain TF32
   const bool fast = o.prec == 2;
   emit_product_tc(B, q, q.X, q.Y, !fast || o.q == 0);
-  emit_orth(B, one, true);
+  emit_orth(B, one, true, true);
   for (int it = 0; it < o.q; ++it) {
     const bool last = it == o.q - 1;
     emit_adjoint_tc(B, q, q.Y, q.ell, q.Z, false, !fast);
     if (o.orth_q) emit_orth(B, one, false);
     emit_product_tc(B, q, q.Z, q.Y, !fast || last);
-    emit_orth(B, one, true);
+    emit_orth(B, one, true, true);
   }
   emit_adjoint_tc(B, q, q.Y, q.ell, q.Z, false, true);      // Z = A^H P = B^H
   // R_B: Cholesky factor of the Gram Z^H Z (= B B^H, B = P^H A).  3xTF32
