@@ -150,6 +150,54 @@ peps_status peps_einsumsvd_execute(peps_plan *plan, const peps_einsumsvd_io *io,
 peps_status peps_plan_destroy(peps_plan *plan);
 
 /* ------------------------------------------------------------------------
+ * einsumsvd adjoint (reverse mode of Algorithm 4 with the sketch held
+ * fixed; the paper has no gradient, this carries the method toward
+ * variational optimisation).  Real data (PEPS_R32, PEPS_R64), CUDA-core
+ * arithmetic, one instance per plan.
+ *
+ * Given cotangents of the step's outputs U, W and log_scale, returns those of
+ * its operands V, S, ket and bra: the gradient of
+ *     L = <U_bar, U> + <W_bar, W> + log_scale_bar * log(sigma_1).
+ * The forward (executed again by the call) keeps the orthonormal bases of
+ * the power iteration and the inverses of their R factors; the reverse sweep
+ * runs the QR and SVD adjoints
+ *     Ybar = (Qbar + Q copyltu(-Qbar^T Q)) R^-T,
+ *     Bbar = U~ [(F o (U~^T Ubar - Ubar^T U~)) S + diag(sbar)] S^-1 U~^T B
+ *            (+ the direct dependence of W on B),  F_ij = 1/(s_j^2 - s_i^2),
+ * accumulates A's cotangent as a sum of rank-l outer products (one per
+ * product of the forward) and contracts it into the four operands with the
+ * same stage kernels as the forward products.  Valid where the kept
+ * singular values are distinct and nonzero (the gradient of a truncated SVD
+ * is otherwise undefined).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  const void *U_bar;              /* [kL][t][k], may be NULL (zero) */
+  const void *W_bar;              /* [k][Dx*DX][b][De*DE], may be NULL (zero) */
+  const double *log_scale_bar;    /* one double, may be NULL (zero) */
+} peps_einsumsvd_cotangent;
+
+typedef struct {
+  void *V_bar, *S_bar, *ket_bar, *bra_bar;   /* operand shapes; overwritten */
+} peps_einsumsvd_grads;
+
+/* Plan one instance with its adjoint (opts->prec must be PEPS_PREC_PLAIN). */
+peps_status peps_einsumsvd_grad_plan(peps_plan **out, peps_dtype dtype, const peps_einsumsvd_shape *shape,
+                                     const peps_rsvd_opts *opts, size_t *workspace_bytes);
+
+/* Host only: record the cotangent and gradient pointers in the plan without
+ * enqueueing anything (peps_plan_validate then checks the adjoint's launches
+ * against them; peps_einsumsvd_grad_execute records them too). */
+peps_status peps_einsumsvd_grad_bind(peps_plan *plan, const peps_einsumsvd_cotangent *ct,
+                                     const peps_einsumsvd_grads *gr);
+
+/* Forward (outputs in io as for peps_einsumsvd_execute) and reverse sweep
+ * (cotangents in gr); all pointers DEVICE pointers.  Same descriptor-upload
+ * rule as the execute calls (keyed on io, ct, gr and the workspace). */
+peps_status peps_einsumsvd_grad_execute(peps_plan *plan, const peps_einsumsvd_io *io,
+                                        const peps_einsumsvd_cotangent *ct, const peps_einsumsvd_grads *gr,
+                                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Boundary-MPS contraction of a PEPS network (Algorithms 2 and 3).
  * ------------------------------------------------------------------------ */
 typedef struct {

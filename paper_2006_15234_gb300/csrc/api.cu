@@ -115,12 +115,16 @@ peps_status read_net(const peps_network *n, Net &out, const char *which) {
 // ---- plans ------------------------------------------------------------------
 
 struct peps_plan {
-  enum Kind { EINSUMSVD, CONTRACT, EXPECT } kind;
+  enum Kind { EINSUMSVD, CONTRACT, EXPECT, EGRAD } kind;
   int dt = 0;
   RsvdOpts opts{};
   // einsumsvd
   std::vector<Inst> insts;
   std::vector<peps_einsumsvd_io> io_cache;
+  // einsumsvd adjoint (one instance)
+  peps_einsumsvd_cotangent ct{};
+  peps_einsumsvd_grads gr{};
+  bool grad_bound = false;
   // contraction
   Net ket, bra;
   bool one_layer = false;
@@ -170,6 +174,38 @@ std::string build_einsumsvd(peps_plan *P, uintptr_t base, const peps_einsumsvd_i
     ptrs.push_back(&I);
   }
   emit_einsumsvd(B, ptrs, P->opts);
+  return "";
+}
+
+// One einsumsvd with its adjoint: forward keeping the power iteration's
+// bases, then the reverse sweep into the operand cotangents.
+std::string build_egrad(peps_plan *P, uintptr_t base, const peps_einsumsvd_io *io, Builder &B) {
+  B.base = base;
+  B.dt = P->dt;
+  Inst &I = P->insts[0];
+  inst_alloc_scratch(B, I, P->dt);
+  I.logp = (double *)B.buf(8);
+  GradBufs G;
+  grad_alloc(B, I, P->opts, G, P->dt);
+  double *lzero = (double *)B.buf(8);
+  if (io) {
+    I.V = io->V; I.S = io->S; I.K = io->ket; I.Kb = io->bra;
+    I.U = io->U; I.W = io->W; I.sigma = io->sigma;
+    if (io->log_scale) I.logp = io->log_scale;
+  }
+  const double *lbar = P->ct.log_scale_bar ? P->ct.log_scale_bar : lzero;
+  {
+    std::vector<std::pair<void *, int64_t>> z{{lzero, 1}};
+    std::vector<ZeroDesc> d{ZeroDesc{lzero, 1}};
+    std::vector<int64_t> prefix{0};
+    Op op;
+    op.kind = Op::ZERO; op.desc_off = B.put(d); op.prefix_off = B.put(prefix); op.nd = 1; op.blocks = 1;
+    op.tag = "init";
+    B.ops.push_back(op);
+  }
+  emit_einsumsvd_save(B, I, P->opts, G);
+  emit_einsumsvd_bwd(B, I, P->opts, G, P->ct.U_bar, P->ct.W_bar, lbar, P->gr.V_bar, P->gr.S_bar, P->gr.ket_bar,
+                     P->gr.bra_bar);
   return "";
 }
 
@@ -914,6 +950,40 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         if (op.tc_kr % 4 || t.Kr != op.tc_kr) C.err = std::string(tag) + ": TMA rows not 16-byte aligned";
         break;
       }
+      case Op::COPY:
+        C.need(op.aux_ptr, (double)op.fill_n, tag, "src");
+        C.need(op.fill_ptr, (double)op.fill_n, tag, "dst");
+        break;
+      case Op::LTU:
+        C.need(op.aux_ptr, es * (double)op.fill_n * op.fill_n, tag, "M");
+        C.need(op.fill_ptr, es * (double)op.fill_n * op.fill_n, tag, "out");
+        break;
+      case Op::SVDBWD: {
+        const SvdBwdDesc &x = *(const SvdBwdDesc *)d;
+        const double n = x.n, k = x.k;
+        C.need(x.Mw, es * n * n, tag, "Mw");
+        C.need(x.sig, 8 * n, tag, "sig");
+        C.need(x.Ut, es * n * k, tag, "Ut");
+        C.need(x.Utbar, es * n * k, tag, "Utbar");
+        C.need(x.WW, es * k * k, tag, "WW");
+        C.need(x.H, es * n * n, tag, "H");
+        C.need(x.scratch, 8 * (3 * n * n + n) + 4 * n, tag, "scratch");
+        C.need(x.lbar, 8, tag, "lbar");
+        C.need(x.inv_s1, 8, tag, "inv_s1");
+        break;
+      }
+      case Op::TGRAD: {
+        const TensorGradDesc &x = *(const TensorGradDesc *)d;
+        const double nk = (double)x.d * x.Dl * x.Du * x.Dx * x.De, nkb = (double)x.d * x.DL * x.DU * x.DX * x.DE;
+        const double N = (double)x.Dx * x.DX * x.b * x.De * x.DE;
+        C.need(x.Z2, es * x.P * (double)x.Dl * x.DL * x.Du * x.DU * x.b, tag, "Z2");
+        C.need(x.R, es * x.P * N, tag, "R");
+        C.need(x.K, es * nk, tag, "K");
+        C.need(x.Kb, es * nkb, tag, "Kb");
+        C.need(x.Kbar, es * nk, tag, "Kbar");
+        C.need(x.Kbbar, es * nkb, tag, "Kbbar");
+        break;
+      }
       case Op::STRIP: {
         const StripCol *cl = (const StripCol *)(blob + op.aux_off[0]);
         for (int i = 0; i < op.nd; ++i) {
@@ -956,6 +1026,7 @@ peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool en
   B.encode = encode;
   std::string e = P->kind == peps_plan::EINSUMSVD ? build_einsumsvd(P, (uintptr_t)ws, io, B)
                   : P->kind == peps_plan::CONTRACT ? build_contract(P, (uintptr_t)ws, B)
+                  : P->kind == peps_plan::EGRAD    ? build_egrad(P, (uintptr_t)ws, io, B)
                                                    : build_expect(P, (uintptr_t)ws, B);
   if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
   if (!B.err.empty()) return fail(PEPS_ERR_UNSUPPORTED, "%s", B.err.c_str());
@@ -1009,6 +1080,12 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
         launch_strip(dt, (const StripDesc *)d, (const StripCol *)(blob + op.aux_off[0]), blob + op.aux_off[1], op.nd,
                      s);
         break;
+      case Op::COPY:
+        CUDA_TRY(cudaMemcpyAsync(op.fill_ptr, op.aux_ptr, (size_t)op.fill_n, cudaMemcpyDeviceToDevice, s));
+        break;
+      case Op::SVDBWD: launch_svd_bwd(dt, *(const SvdBwdDesc *)(P->blob.data() + op.desc_off), s); break;
+      case Op::LTU: launch_copyltu(dt, op.aux_ptr, op.fill_ptr, (int)op.fill_n, s); break;
+      case Op::TGRAD: launch_tensor_grad(dt, *(const TensorGradDesc *)(P->blob.data() + op.desc_off), s); break;
     }
     if (events) CUDA_TRY(cudaEventRecord(events[&op - P->ops.data() + 1], s));
   }
@@ -1075,7 +1152,8 @@ peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch
 
 peps_status peps_einsumsvd_rank(const peps_plan *plan, int32_t i, int32_t *k) {
   if (!plan || !k) return fail(PEPS_ERR_ARG, "NULL argument");
-  if (plan->kind != peps_plan::EINSUMSVD) return fail(PEPS_ERR_ARG, "not an einsumsvd plan");
+  if (plan->kind != peps_plan::EINSUMSVD && plan->kind != peps_plan::EGRAD)
+    return fail(PEPS_ERR_ARG, "not an einsumsvd plan");
   if (i < 0 || i >= (int)plan->insts.size()) return fail(PEPS_ERR_ARG, "instance index out of range");
   *k = plan->insts[i].k;
   return PEPS_OK;
@@ -1096,6 +1174,72 @@ peps_status peps_einsumsvd_execute(peps_plan *plan, const peps_einsumsvd_io *io,
   if (!same) {
     if (peps_status s = rebuild(plan, workspace, io, true)) return s;
     plan->io_cache.assign(io, io + n);
+    plan->built_base = (uintptr_t)workspace;
+    plan->built = true;
+  }
+  return enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, !same);
+}
+
+peps_status peps_einsumsvd_grad_plan(peps_plan **out, peps_dtype dtype, const peps_einsumsvd_shape *shape,
+                                     const peps_rsvd_opts *opts, size_t *workspace_bytes) {
+  g_last_error.clear();
+  if (!out || !shape || !workspace_bytes) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (dtype != PEPS_R32 && dtype != PEPS_R64) return fail(PEPS_ERR_UNSUPPORTED, "the adjoint takes real data");
+  if (peps_status s = check_opts(opts)) return s;
+  if (opts->prec != PEPS_PREC_PLAIN) return fail(PEPS_ERR_UNSUPPORTED, "the adjoint runs the plain arithmetic");
+  std::unique_ptr<peps_plan> P(new (std::nothrow) peps_plan());
+  if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
+  P->kind = peps_plan::EGRAD;
+  P->dt = dtype;
+  P->opts = to_opts(opts);
+  const peps_einsumsvd_shape &s = *shape;
+  Inst I{};
+  I.kL = s.kL; I.t = s.t; I.a = s.a; I.b = s.b; I.d = s.d;
+  I.Dl = s.Dl; I.Du = s.Du; I.Dx = s.Dx; I.De = s.De;
+  I.DL = s.DL; I.DU = s.DU; I.DX = s.DX; I.DE = s.DE;
+  std::string e = inst_check(I, dtype);
+  if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
+  if (s.m < 0) return fail(PEPS_ERR_ARG, "negative rank");
+  RsvdOpts oi = P->opts;
+  if (s.m > 0) oi.m = s.m;
+  inst_derive(I, oi);
+  I.instance = 0;
+  I.tc = false;
+  P->insts.push_back(I);
+  if (peps_status st = rebuild(P.get(), nullptr, nullptr)) return st;
+  *workspace_bytes = P->ws_bytes;
+  *out = P.release();
+  return PEPS_OK;
+}
+
+peps_status peps_einsumsvd_grad_bind(peps_plan *plan, const peps_einsumsvd_cotangent *ct,
+                                     const peps_einsumsvd_grads *gr) {
+  if (!plan || !ct || !gr) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (plan->kind != peps_plan::EGRAD) return fail(PEPS_ERR_ARG, "not an adjoint plan");
+  plan->ct = *ct;
+  plan->gr = *gr;
+  plan->built = false;
+  return PEPS_OK;
+}
+
+peps_status peps_einsumsvd_grad_execute(peps_plan *plan, const peps_einsumsvd_io *io,
+                                        const peps_einsumsvd_cotangent *ct, const peps_einsumsvd_grads *gr,
+                                        void *workspace, size_t workspace_bytes, void *stream) {
+  g_last_error.clear();
+  if (!plan || !io || !ct || !gr) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (plan->kind != peps_plan::EGRAD) return fail(PEPS_ERR_ARG, "not an adjoint plan");
+  if (!io->V || !io->S || !io->ket || !io->bra || !io->U || !io->W || !io->sigma)
+    return fail(PEPS_ERR_ARG, "NULL tensor pointer");
+  if (!gr->V_bar || !gr->S_bar || !gr->ket_bar || !gr->bra_bar) return fail(PEPS_ERR_ARG, "NULL gradient pointer");
+  if (!ct->U_bar || !ct->W_bar) return fail(PEPS_ERR_ARG, "U_bar and W_bar are required (pass zeros for none)");
+  bool same = plan->built && plan->built_base == (uintptr_t)workspace && plan->io_cache.size() == 1 &&
+              memcmp(&plan->io_cache[0], io, sizeof *io) == 0 && memcmp(&plan->ct, ct, sizeof *ct) == 0 &&
+              memcmp(&plan->gr, gr, sizeof *gr) == 0;
+  if (!same) {
+    plan->ct = *ct;
+    plan->gr = *gr;
+    if (peps_status s = rebuild(plan, workspace, io, true)) return s;
+    plan->io_cache.assign(io, io + 1);
     plan->built_base = (uintptr_t)workspace;
     plan->built = true;
   }
@@ -1350,6 +1494,7 @@ peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count) {
       case Op::JACOBI: n += 1 + (op.smem2 > 0) + (op.blocks > 0); break;   // one CTA, cluster, refinement
       case Op::CHOL: n += 1 + (op.smem2 > 0); break;                         // one CTA, cluster
       case Op::TC: n += op.tc.tiles_m * op.tc.tiles_n > 0; break;
+      case Op::COPY: break;                                                   // a copy, not a kernel
       case Op::SKETCH: case Op::GEMM: case Op::GEMM_ATOMIC: case Op::SANDWICH: case Op::ZERO: case Op::SITE:
       case Op::PERMUTE: n += op.blocks > 0; break;
       default: n += 1; break;
@@ -1377,6 +1522,10 @@ peps_status peps_plan_launch_kernel(const peps_plan *plan, int64_t i, const char
     case Op::TC: *kernel = "tc_gemm"; break;
     case Op::PERMUTE: *kernel = "permute"; break;
     case Op::STRIP: *kernel = "strip"; break;
+    case Op::COPY: *kernel = "copy"; break;
+    case Op::SVDBWD: *kernel = "svd_bwd"; break;
+    case Op::LTU: *kernel = "copyltu"; break;
+    case Op::TGRAD: *kernel = "tensor_grad"; break;
     default: *kernel = "unknown"; break;
   }
   return PEPS_OK;
@@ -1411,12 +1560,27 @@ peps_status peps_plan_validate(peps_plan *plan, void *workspace, size_t workspac
                                const peps_einsumsvd_io *io) {
   g_last_error.clear();
   if (!plan || !workspace) return fail(PEPS_ERR_ARG, "NULL argument");
-  if (plan->kind == peps_plan::EINSUMSVD && !io) return fail(PEPS_ERR_ARG, "einsumsvd plans need io");
-  if (peps_status s = rebuild(plan, workspace, plan->kind == peps_plan::EINSUMSVD ? io : nullptr)) return s;
+  if ((plan->kind == peps_plan::EINSUMSVD || plan->kind == peps_plan::EGRAD) && !io)
+    return fail(PEPS_ERR_ARG, "einsumsvd plans need io");
+  const bool with_io = plan->kind == peps_plan::EINSUMSVD || plan->kind == peps_plan::EGRAD;
+  if (peps_status s = rebuild(plan, workspace, with_io ? io : nullptr)) return s;
   plan->built = false;            // force an upload at the next execute
   Checker C;
   const double es = dtype_size(plan->dt);
-  if (plan->kind == peps_plan::EINSUMSVD) {
+  if (plan->kind == peps_plan::EGRAD) {
+    const Inst &I = plan->insts[0];
+    auto add = [&](const void *p, double n) {
+      if (p) C.ext.push_back(Extent{(uintptr_t)p, (uintptr_t)p + (uintptr_t)n, "operand"});
+    };
+    add(plan->ct.U_bar, es * (double)I.M * I.k);
+    add(plan->ct.W_bar, es * (double)I.k * I.N);
+    add(plan->ct.log_scale_bar, 8);
+    add(plan->gr.V_bar, es * I.kL * I.t * I.a * I.h);
+    add(plan->gr.S_bar, es * I.a * I.v * I.b);
+    add(plan->gr.ket_bar, es * I.d * I.Dl * I.Du * I.Dx * I.De);
+    add(plan->gr.bra_bar, es * I.d * I.DL * I.DU * I.DX * I.DE);
+  }
+  if (plan->kind == peps_plan::EINSUMSVD || plan->kind == peps_plan::EGRAD) {
     for (size_t i = 0; i < plan->insts.size(); ++i) {
       const Inst &I = plan->insts[i];
       auto add = [&](const void *p, double n) { C.ext.push_back(Extent{(uintptr_t)p, (uintptr_t)p + (uintptr_t)n, "io"}); };

@@ -191,5 +191,29 @@ struct StripDesc {
 };
 void launch_strip(int dt, const StripDesc *d, const StripCol *cols, const void *ops, int nd, cudaStream_t s);
 
+// ---- einsumsvd adjoint (real data) ----
+struct SvdBwdDesc {
+  const void *Mw;          // Jacobi output, n x n column-major, columns sigma_c u_c (unsorted)
+  const double *sig;       // n refined singular values (unsorted)
+  const void *Ut;          // n x k gauge-fixed kept vectors [j][c]
+  const void *Utbar;       // n x k cotangent of Ut
+  const void *WW;          // k x k: Wbar W^T
+  const double *lbar;      // cotangent of log sigma_1
+  const double *inv_s1;    // 1 / sigma_1
+  void *H;                 // out: n x n
+  double *scratch;         // 3 n^2 + n doubles, then n ints
+  int32_t n, k;
+};
+struct TensorGradDesc {
+  const void *Z2;          // [P][(l,L)][(u,U),b]
+  const void *R;           // [P][N], N = (x,X,b,e,E)
+  const void *K, *Kb;
+  void *Kbar, *Kbbar;
+  int32_t P, b, d, Dl, Du, Dx, De, DL, DU, DX, DE;
+};
+void launch_svd_bwd(int dt, const SvdBwdDesc &d, cudaStream_t s);
+void launch_copyltu(int dt, const void *M, void *out, int n, cudaStream_t s);
+void launch_tensor_grad(int dt, const TensorGradDesc &d, cudaStream_t s);
+
 
 }  // namespace peps

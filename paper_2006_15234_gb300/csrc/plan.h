@@ -15,7 +15,7 @@ namespace peps {
 
 struct Op {
   enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL, TC,
-              PERMUTE, STRIP } kind;
+              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD } kind;
   size_t desc_off = 0;    // byte offset of the descriptor array in the blob
   size_t prefix_off = 0;  // byte offset of the int64 block prefix array in the blob
   int nd = 0;
@@ -26,7 +26,8 @@ struct Op {
   ScalarDesc scalar{};
   size_t aux_off[3] = {0, 0, 0};  // blob offsets of the scalar's device arrays
   void *fill_ptr = nullptr;
-  int64_t fill_n = 0;
+  const void *aux_ptr = nullptr;  // COPY / LTU source
+  int64_t fill_n = 0;             // FILL: elements; COPY: bytes; LTU: n
   double fill_value = 0.0;
   std::string tag;        // stage name (profiling ledger)
   double flops = 0.0;     // algorithmic flops of the launch
@@ -117,6 +118,28 @@ void inst_share_scratch(Inst &I, const Inst &owner);
 std::string inst_check(const Inst &I, int dt);
 // Whether every stage GEMM of the instance meets the TMA alignment rules.
 bool inst_tc_ok(const Inst &I, int dt);
+// Saved forward data and scratch of the einsumsvd adjoint (plain path, real
+// data): the orthonormal bases P_i (M x l) and Q_i (N x l) of the power
+// iteration with the inverses of their R factors, the sketch, and the
+// buffers of the reverse sweep.
+struct GradBufs {
+  std::vector<void *> Ps, Qs, Tp, Tq;
+  void *Om = nullptr, *T1s = nullptr;
+  void *Pbar = nullptr, *Xbar = nullptr, *Qbar = nullptr, *Utbar = nullptr, *WW = nullptr, *H = nullptr;
+  void *Ms = nullptr, *Cq = nullptr;
+  double *svd_scr = nullptr;
+  void *Lall = nullptr, *Rall = nullptr;
+  void *T2g = nullptr, *T3g = nullptr, *Z3g = nullptr, *Z3p = nullptr, *Z2g = nullptr;
+  int Pw = 0;
+};
+void grad_alloc(Builder &B, const Inst &q, const RsvdOpts &o, GradBufs &G, int dt);
+// Forward of one plain-path instance that keeps what the adjoint needs.
+void emit_einsumsvd_save(Builder &B, Inst &q, const RsvdOpts &o, GradBufs &G);
+// Reverse sweep: cotangents of U ([M][k]), W ([k][N]) and log sigma_1 to
+// those of V, S, K and Kb (same layouts as the operands).
+void emit_einsumsvd_bwd(Builder &B, Inst &q, const RsvdOpts &o, GradBufs &G, const void *Ubar, const void *Wbar,
+                        const double *lbar, void *dV, void *dS, void *dK, void *dKb);
+
 // Emit every stage of one einsumsvd over a group of instances.
 void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);
 void emit_einsumsvd_simt(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);

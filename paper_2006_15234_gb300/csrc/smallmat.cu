@@ -645,9 +645,15 @@ __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__rest
     const double si = sig[c];
     const bool zero_dir = !(si > g.rtol * s1);
     T s = zero<T>();
+    double nrm2 = 0.0;
     if (!zero_dir)
-      for (int j = lane; j < n; j += 32) s = fma_(conj_(h[j]), M[(int64_t)c * n + j], s);
+      for (int j = lane; j < n; j += 32) {
+        const T mv = M[(int64_t)c * n + j];
+        s = fma_(conj_(h[j]), mv, s);
+        nrm2 += (double)abs2(mv);
+      }
     s = warp_sum(s);
+    nrm2 = warp_sum(nrm2);
     if (lane == 0) {
       T r;
       const double mag = sqrt((double)abs2(s));
@@ -655,8 +661,10 @@ __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__rest
         r = mag > 0 ? from_parts<T>(re(s) / mag, im(s) / mag) : from_parts<T>(1.0, 0.0);
       else
         r = re(s) < 0 ? from_parts<T>(-1.0, 0.0) : from_parts<T>(1.0, 0.0);
-      // coefficient of u_i in Ut: conj(rho) / sigma_i (zero for dropped directions)
-      rho[i] = zero_dir ? zero<T>() : div_real(conj_(r), si);
+      // coefficient of column c of Mw in Ut: the phase over the column's own
+      // norm (the rotated column's length, not the refined sigma), so u_i is
+      // a unit vector; zero for dropped directions
+      rho[i] = zero_dir || !(nrm2 > 0.0) ? zero<T>() : div_real(conj_(r), sqrt(nrm2));
       g.sigma_out[i] = zero_dir ? 0.0 : si;
     }
   }

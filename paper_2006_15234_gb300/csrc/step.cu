@@ -662,6 +662,225 @@ std::string inst_check(const Inst &I, int dt) {
   return "";
 }
 
+// ===========================================================================
+// einsumsvd adjoint (plain path, real data).  Reverse mode of the same
+// function the forward computes, the sketch held fixed:
+//   Y0 = A Om, P0 R0 = Y0;  Z_i = A^T P_{i-1}, Q_i S_i = Z_i, Y_i = A Q_i,
+//   P_i R_i = Y_i;  Z = A^T P_q, B = Z^T = U~ S V~^T;  U = P_q Ut, W = Ut^T B / s1,
+//   log s1  (Ut = the kept, gauge-fixed U~ columns)
+// Cotangent of A: sum over the pairs (L_t, R_t) of L_t R_t^T, contracted
+// into the operands at the end.
+// ===========================================================================
+
+namespace {
+
+void push_copy(Builder &B, void *dst, const void *src, int64_t bytes, const char *tag) {
+  Op op;
+  op.kind = Op::COPY; op.fill_ptr = dst; op.aux_ptr = src; op.fill_n = bytes; op.tag = tag;
+  B.ops.push_back(op);
+}
+
+GemmDesc gemm_acc(GemmDesc g, bool acc) {
+  g.accumulate = acc ? 1 : 0;
+  return g;
+}
+
+void push_one(Builder &B, GemmDesc g, const char *tag) {
+  std::vector<GemmDesc> v{g};
+  push_gemm(B, v, false, tag);
+}
+
+// CholeskyQR2 of src into dst (M- or N-side), saving R^-1 = T1 T2 in Tsave.
+void orth_save(Builder &B, Inst &q, bool mside, void *Tsave, GradBufs &G) {
+  std::vector<Inst *> one{&q};
+  void *Inst::*a = mside ? &Inst::Y : &Inst::Z;
+  void *Inst::*t = mside ? &Inst::P : &Inst::X;
+  const char *tag = mside ? "orth_m" : "orth_n";
+  const int64_t es = dtype_size(B.dt), l = q.ell;
+  emit_cqr_pass(B, one, mside, a, t, &Inst::R1, nullptr, nullptr, true, tag, true);
+  push_copy(B, G.T1s, q.Tm, l * l * es, tag);
+  emit_cqr_pass(B, one, mside, t, a, &Inst::R1, nullptr, nullptr, true, tag, false);
+  // Tsave = T1 T2 (row-major l x l)
+  push_one(B, mk_gemm((int)l, (int)l, (int)l, 1, G.T1s, l, 1, 0, false, q.Tm, l, 1, 0, false, Tsave, l, 1, 0), tag);
+}
+
+// QR adjoint on the [j][row] layout: Ybar = (Qbar + Q copyltu(-Qbar^T Q)) R^-T,
+// R^-1 = T; rows = M or N.
+void qr_bwd(Builder &B, GradBufs &G, int64_t l, int64_t rows, const void *Q, const void *Qbar, const void *T,
+            void *Ybar, const char *tag) {
+  // Ms[a][b] = -sum_r Qbar[a][r] Q[b][r]
+  GemmDesc m = mk_gemm((int)l, (int)l, (int)rows, 1, Qbar, rows, 1, 0, false, Q, 1, rows, 0, false, G.Ms, l, 1, 0);
+  m.alpha = -1.0;
+  push_one(B, m, tag);
+  Op lt;
+  lt.kind = Op::LTU; lt.aux_ptr = G.Ms; lt.fill_ptr = G.Cq; lt.fill_n = l; lt.tag = tag;
+  B.ops.push_back(lt);
+  // Xbar[j][r] = Qbar[j][r] + sum_i Cq[i][j] Q[i][r]
+  push_copy(B, G.Xbar, Qbar, l * rows * dtype_size(B.dt), tag);
+  push_one(B, gemm_acc(mk_gemm((int)l, (int)rows, (int)l, 1, G.Cq, 1, l, 0, false, Q, rows, 1, 0, false, G.Xbar,
+                               rows, 1, 0), true), tag);
+  // Ybar[j][r] = sum_i T[j][i] Xbar[i][r]
+  push_one(B, mk_gemm((int)l, (int)rows, (int)l, 1, T, l, 1, 0, false, G.Xbar, rows, 1, 0, false, Ybar, rows, 1, 0),
+           tag);
+}
+
+}  // namespace
+
+void grad_alloc(Builder &B, const Inst &q, const RsvdOpts &o, GradBufs &G, int dt) {
+  const int64_t es = dtype_size(dt), l = q.ell, M = q.M, N = q.N, k = q.k;
+  G.Ps.clear(); G.Qs.clear(); G.Tp.clear(); G.Tq.clear();
+  for (int i = 0; i <= o.q; ++i) { G.Ps.push_back(B.buf(M * l * es)); G.Tp.push_back(B.buf(l * l * es)); }
+  for (int i = 0; i < o.q; ++i) { G.Qs.push_back(B.buf(N * l * es)); G.Tq.push_back(B.buf(l * l * es)); }
+  G.Om = B.buf(N * l * es);
+  G.T1s = B.buf(l * l * es);
+  G.Pbar = B.buf(M * l * es);
+  G.Xbar = B.buf(std::max(M, N) * l * es);
+  G.Qbar = B.buf(N * l * es);
+  G.Utbar = B.buf(l * k * es);
+  G.WW = B.buf(k * k * es);
+  G.H = B.buf(l * l * es);
+  G.Ms = B.buf(l * l * es);
+  G.Cq = B.buf(l * l * es);
+  G.svd_scr = (double *)B.buf((3 * l * l + l) * 8 + l * 4);
+  G.Pw = (int)((2 * o.q + 2) * l);
+  const int64_t Pw = G.Pw;
+  G.Lall = B.buf(Pw * M * es);
+  G.Rall = B.buf(Pw * N * es);
+  G.T2g = B.buf(Pw * q.h * q.v * q.b * es);
+  G.T3g = B.buf(Pw * q.a * q.h * es);
+  G.Z3g = B.buf(Pw * q.a * q.h * es);
+  G.Z3p = B.buf(Pw * q.a * q.h * es);
+  G.Z2g = B.buf(Pw * q.h * q.v * q.b * es);
+}
+
+void emit_einsumsvd_save(Builder &B, Inst &q, const RsvdOpts &o, GradBufs &G) {
+  std::vector<Inst *> one{&q};
+  const int64_t es = dtype_size(B.dt), l = q.ell;
+  emit_sketch(B, one, o);
+  push_copy(B, G.Om, q.X, q.N * l * es, "sketch");
+  emit_product(B, one, true);
+  orth_save(B, q, true, G.Tp[0], G);
+  push_copy(B, G.Ps[0], q.Y, q.M * l * es, "orth_m");
+  for (int it = 0; it < o.q; ++it) {
+    emit_adjoint(B, one);
+    orth_save(B, q, false, G.Tq[it], G);
+    push_copy(B, G.Qs[it], q.Z, q.N * l * es, "orth_n");
+    emit_product(B, one, false);
+    orth_save(B, q, true, G.Tp[it + 1], G);
+    push_copy(B, G.Ps[it + 1], q.Y, q.M * l * es, "orth_m");
+  }
+  emit_adjoint(B, one);
+  emit_small_svd(B, one);
+  emit_epilogue(B, one);
+}
+
+void emit_einsumsvd_bwd(Builder &B, Inst &q, const RsvdOpts &o, GradBufs &G, const void *Ubar, const void *Wbar,
+                        const double *lbar, void *dV, void *dS, void *dK, void *dKb) {
+  const int64_t es = dtype_size(B.dt), l = q.ell, M = q.M, N = q.N, k = q.k;
+  const char *tag = "backward";
+  auto Lslot = [&](int t) { return (uint8_t *)G.Lall + (size_t)t * l * M * es; };
+  auto Rslot = [&](int t) { return (uint8_t *)G.Rall + (size_t)t * l * N * es; };
+  // views of the instance whose products read / write the adjoint's buffers
+  auto product_into = [&](const void *src, void *dst) {
+    Inst v = q;
+    v.Z = (void *)src; v.Y = dst;
+    std::vector<Inst *> one{&v};
+    emit_product(B, one, false);
+  };
+  auto adjoint_into = [&](const void *src, void *dst) {
+    Inst v = q;
+    v.Y = (void *)src; v.Z = dst;
+    std::vector<Inst *> one{&v};
+    emit_adjoint(B, one);
+  };
+  const void *Pq = G.Ps[o.q];
+  // Utbar = Pq^T Ubar + Z^T Wbar^T / s1      ([j][c])
+  push_one(B, mk_gemm((int)l, (int)k, (int)M, 1, Pq, M, 1, 0, false, Ubar, k, 1, 0, false, G.Utbar, k, 1, 0), tag);
+  {
+    GemmDesc g = mk_gemm((int)l, (int)k, (int)N, 1, q.Z, N, 1, 0, false, Wbar, 1, N, 0, false, G.Utbar, k, 1, 0);
+    g.alpha_dev = q.inv_s1;
+    push_one(B, gemm_acc(g, true), tag);
+  }
+  // WW = Wbar W^T (k x k)
+  push_one(B, mk_gemm((int)k, (int)k, (int)N, 1, Wbar, N, 1, 0, false, q.W, 1, N, 0, false, G.WW, k, 1, 0), tag);
+  {
+    SvdBwdDesc d{};
+    d.Mw = q.Mw; d.sig = q.sig; d.Ut = q.Ut; d.Utbar = G.Utbar; d.WW = G.WW; d.lbar = lbar; d.inv_s1 = q.inv_s1;
+    d.H = G.H; d.scratch = G.svd_scr; d.n = (int)l; d.k = (int)k;
+    Op op;
+    op.kind = Op::SVDBWD; op.desc_off = B.put(std::vector<SvdBwdDesc>{d}); op.nd = 1; op.tag = tag;
+    B.ops.push_back(op);
+  }
+  // Zbar = Z H^T + Wbar^T Ut^T / s1, written as pair 0's right factor ([j][n])
+  void *Zbar = Rslot(0);
+  push_one(B, mk_gemm((int)l, (int)N, (int)l, 1, G.H, l, 1, 0, false, q.Z, N, 1, 0, false, Zbar, N, 1, 0), tag);
+  {
+    GemmDesc g = mk_gemm((int)l, (int)N, (int)k, 1, q.Ut, k, 1, 0, false, Wbar, N, 1, 0, false, Zbar, N, 1, 0);
+    g.alpha_dev = q.inv_s1;
+    push_one(B, gemm_acc(g, true), tag);
+  }
+  push_copy(B, Lslot(0), Pq, M * l * es, tag);
+  // Pbar = A Zbar + Ubar Ut^T     ([j][m])
+  product_into(Zbar, G.Pbar);
+  push_one(B, gemm_acc(mk_gemm((int)l, (int)M, (int)k, 1, q.Ut, k, 1, 0, false, Ubar, 1, k, 0, false, G.Pbar, M, 1, 0),
+                       true), tag);
+  int slot = 1;
+  for (int i = o.q; i >= 1; --i) {
+    void *Ybar = Lslot(slot);
+    qr_bwd(B, G, l, M, G.Ps[i], G.Pbar, G.Tp[i], Ybar, tag);
+    push_copy(B, Rslot(slot), G.Qs[i - 1], N * l * es, tag);
+    ++slot;
+    adjoint_into(Ybar, G.Qbar);
+    void *Zb = Rslot(slot);
+    qr_bwd(B, G, l, N, G.Qs[i - 1], G.Qbar, G.Tq[i - 1], Zb, tag);
+    push_copy(B, Lslot(slot), G.Ps[i - 1], M * l * es, tag);
+    ++slot;
+    product_into(Zb, G.Pbar);
+  }
+  qr_bwd(B, G, l, M, G.Ps[0], G.Pbar, G.Tp[0], Lslot(slot), tag);
+  push_copy(B, Rslot(slot), G.Om, N * l * es, tag);
+  // ---- operand cotangents from Abar = Lall^T-pairs ----
+  const int64_t Pw = G.Pw, ah = (int64_t)q.a * q.h, vb = (int64_t)q.v * q.b, hvb = (int64_t)q.h * vb;
+  {
+    // T2g, T3g: the first three product stages applied to Rall
+    Inst v = q;
+    v.ell = (int)Pw; v.X = G.Rall; v.T2 = G.T2g; v.T3 = G.T3g;
+    std::vector<SandwichDesc> sw{mk_sandwich(v, G.Rall, G.T2g, false)};
+    push_sandwich(B, sw, tag);
+    std::vector<GemmDesc> g3{mk_gemm(q.a, q.h, (int)vb, (int)Pw, q.S, vb, 1, 0, false, G.T2g, 1, vb, hvb, false,
+                                     G.T3g, q.h, 1, ah)};
+    push_gemm(B, g3, false, tag);
+  }
+  // dV[m][(a,h)] = sum_j Lall[j][m] T3g[j][(a,h)]
+  push_one(B, mk_gemm((int)M, (int)ah, (int)Pw, 1, G.Lall, 1, M, 0, false, G.T3g, ah, 1, 0, false, dV, ah, 1, 0), tag);
+  // Z3g[j][(a,h)] = sum_m Lall[j][m] V[m][(a,h)];  Z2g[j][h][(v,b)] = sum_a Z3g[j][a][h] S[a][(v,b)]
+  push_one(B, mk_gemm((int)Pw, (int)ah, (int)M, 1, G.Lall, M, 1, 0, false, q.V, ah, 1, 0, false, G.Z3g, ah, 1, 0), tag);
+  {
+    std::vector<GemmDesc> g3{mk_gemm(q.h, (int)vb, q.a, (int)Pw, G.Z3g, 1, q.h, ah, false, q.S, vb, 1, 0, false,
+                                     G.Z2g, vb, 1, hvb)};
+    push_gemm(B, g3, false, tag);
+  }
+  // dS[a][(v,b)] = sum_{j,h} Z3g[j][a][h] T2g[j][h][(v,b)]  (Z3g regrouped to [a][(j,h)])
+  {
+    std::vector<PermuteDesc> pd(1);
+    pd[0] = PermuteDesc{};
+    pd[0].in = G.Z3g; pd[0].out = G.Z3p; pd[0].nb = 1; pd[0].R = Pw; pd[0].Cc = q.a; pd[0].Q = q.h; pd[0].conj = 0;
+    std::vector<int64_t> bl{permute_blocks(pd[0])};
+    push_grouped(B, Op::PERMUTE, pd.data(), sizeof(PermuteDesc), 1, bl, tag);
+    push_one(B, mk_gemm(q.a, (int)vb, (int)(Pw * q.h), 1, G.Z3p, Pw * q.h, 1, 0, false, G.T2g, vb, 1, 0, false, dS,
+                        vb, 1, 0), tag);
+  }
+  {
+    TensorGradDesc d{};
+    d.Z2 = G.Z2g; d.R = G.Rall; d.K = q.K; d.Kb = q.Kb; d.Kbar = dK; d.Kbbar = dKb;
+    d.P = (int)Pw; d.b = q.b; d.d = q.d; d.Dl = q.Dl; d.Du = q.Du; d.Dx = q.Dx; d.De = q.De;
+    d.DL = q.DL; d.DU = q.DU; d.DX = q.DX; d.DE = q.DE;
+    Op op;
+    op.kind = Op::TGRAD; op.desc_off = B.put(std::vector<TensorGradDesc>{d}); op.nd = 1; op.tag = tag;
+    B.ops.push_back(op);
+  }
+}
+
 void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
   // tensor-core instances run one by one; the rest share grouped launches
   std::vector<Inst *> simt;

@@ -17,7 +17,7 @@ __all__ = [
     "Network", "ContractPlan", "EinsumsvdPlan", "boundary_contract", "dtype_code",
     "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "PREC_FAST", "SKETCH_GAUSS", "SKETCH_UNIFORM",
     "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
-    "Term", "ExpectationPlan", "expectation",
+    "Term", "ExpectationPlan", "expectation", "Cotangent", "Grads", "einsumsvd_grad",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -32,7 +32,8 @@ EXPORTED_SYMBOLS = [
     "peps_debug_tc_gemm", "peps_boundary_contract_static",
     "peps_expectation_plan", "peps_expectation_execute", "peps_expectation_result",
     "peps_expectation_workspace", "peps_expectation", "peps_plan_launch_kernel",
-    "peps_plan_kernel_launches",
+    "peps_plan_kernel_launches", "peps_einsumsvd_grad_plan", "peps_einsumsvd_grad_bind",
+    "peps_einsumsvd_grad_execute",
 ]
 
 # Size of the library's fixed device scratch used by boundary_contract_static.
@@ -71,6 +72,14 @@ class Network(C.Structure):
     _fields_ = [("nrow", C.c_int32), ("ncol", C.c_int32), ("d", C.c_int32), ("dtype", C.c_int32),
                 ("bond_h", C.POINTER(C.c_int32)), ("bond_v", C.POINTER(C.c_int32)),
                 ("site", C.POINTER(C.c_void_p))]
+
+
+class Cotangent(C.Structure):
+    _fields_ = [("U_bar", C.c_void_p), ("W_bar", C.c_void_p), ("log_scale_bar", C.c_void_p)]
+
+
+class Grads(C.Structure):
+    _fields_ = [("V_bar", C.c_void_p), ("S_bar", C.c_void_p), ("ket_bar", C.c_void_p), ("bra_bar", C.c_void_p)]
 
 
 class Term(C.Structure):
@@ -137,6 +146,14 @@ def load():
     lib.peps_debug_tc_gemm.argtypes = [C.c_int32] * 7 + [vp, vp, vp, vp]
     lib.peps_plan_validate.restype = st
     lib.peps_plan_validate.argtypes = [vp, vp, C.c_size_t, C.POINTER(EinsumsvdIO)]
+    lib.peps_einsumsvd_grad_plan.restype = st
+    lib.peps_einsumsvd_grad_plan.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(EinsumsvdShape),
+                                             C.POINTER(RsvdOpts), C.POINTER(C.c_size_t)]
+    lib.peps_einsumsvd_grad_bind.restype = st
+    lib.peps_einsumsvd_grad_bind.argtypes = [vp, C.POINTER(Cotangent), C.POINTER(Grads)]
+    lib.peps_einsumsvd_grad_execute.restype = st
+    lib.peps_einsumsvd_grad_execute.argtypes = [vp, C.POINTER(EinsumsvdIO), C.POINTER(Cotangent),
+                                                C.POINTER(Grads), vp, C.c_size_t, vp]
     lib.peps_expectation_plan.restype = st
     lib.peps_expectation_plan.argtypes = [C.POINTER(vp), C.POINTER(Network), C.POINTER(Term), C.c_int32,
                                           C.POINTER(RsvdOpts), C.c_int32, C.POINTER(C.c_size_t)]
@@ -433,6 +450,45 @@ def expectation(ket, terms, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN,
     plan = ExpectationPlan(ket, terms, make_opts(m, p, q, seed, sketch, prec, flags), use_cache)
     plan.execute(stream)
     return plan.result(stream)
+
+
+def einsumsvd_grad(V, S, ket, bra, m, p, q, seed, U_bar, W_bar, log_scale_bar=0.0, stream=None):
+    """One einsumsvd (real data) and its adjoint: returns (U, W, sigma,
+    log sigma_1) and the cotangents (V_bar, S_bar, ket_bar, bra_bar) of
+    L = <U_bar, U> + <W_bar, W> + log_scale_bar * log sigma_1."""
+    import torch
+    lib = load()
+    kL, t, a, h = V.shape
+    _, v, b = S.shape
+    d, Dl, Du, Dx, De = ket.shape
+    _, DL, DU, DX, DE = bra.shape
+    shape = EinsumsvdShape(kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE, m)
+    plan = C.c_void_p()
+    ws = C.c_size_t()
+    _check(lib.peps_einsumsvd_grad_plan(C.byref(plan), dtype_code(V.dtype), C.byref(shape),
+                                        C.byref(make_opts(m, p, q, seed)), C.byref(ws)))
+    try:
+        k = C.c_int32()
+        _check(lib.peps_einsumsvd_rank(plan, 0, C.byref(k)))
+        k = k.value
+        dev = V.device
+        U = torch.empty((kL, t, k), dtype=V.dtype, device=dev)
+        W = torch.empty((k, Dx * DX, b, De * DE), dtype=V.dtype, device=dev)
+        sg = torch.empty(k, dtype=torch.float64, device=dev)
+        lg = torch.empty(1, dtype=torch.float64, device=dev)
+        lb = torch.tensor([float(log_scale_bar)], dtype=torch.float64, device=dev)
+        gV, gS, gK, gKb = (torch.empty_like(x) for x in (V, S, ket, bra))
+        buf, wsp = _workspace(ws.value, dev)
+        io = EinsumsvdIO(V.data_ptr(), S.data_ptr(), ket.data_ptr(), bra.data_ptr(), U.data_ptr(),
+                         W.data_ptr(), sg.data_ptr(), lg.data_ptr())
+        ct = Cotangent(U_bar.data_ptr(), W_bar.data_ptr(), lb.data_ptr())
+        gr = Grads(gV.data_ptr(), gS.data_ptr(), gK.data_ptr(), gKb.data_ptr())
+        _check(lib.peps_einsumsvd_grad_execute(plan, C.byref(io), C.byref(ct), C.byref(gr), C.c_void_p(wsp),
+                                               ws, _stream_handle(stream)))
+        torch.cuda.synchronize(dev)
+        return (U, W, sg, lg), (gV, gS, gK, gKb)
+    finally:
+        lib.peps_plan_destroy(plan)
 
 
 def boundary_contract_static(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN,

@@ -206,3 +206,31 @@ def test_per_instance_rank(lib):
     lib.peps_einsumsvd_rank(plan, 1, C.byref(k))
     assert k.value == 12
     lib.peps_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("dt", [0, 2])
+@pytest.mark.parametrize("shape,m,q", [((3, 4, 5, 3, 2, 2, 2, 2, 2, 2, 2, 2, 2), 4, 1),
+                                       ((18, 9, 18, 18, 2, 3, 3, 3, 3, 3, 3, 3, 3), 18, 2)])
+def test_einsumsvd_adjoint_plan(lib, dt, shape, m, q):
+    """The adjoint's forward-with-saving and reverse sweep stay inside the
+    workspace, the operands, the cotangents and the gradient buffers."""
+    heap = FakeHeap()
+    es = ES[dt]
+    kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE = shape
+    sh = L.EinsumsvdShape(*shape, m)
+    plan, ws = C.c_void_p(), C.c_size_t()
+    assert lib.peps_einsumsvd_grad_plan(C.byref(plan), dt, C.byref(sh), C.byref(L.make_opts(m, 8, q, 1)),
+                                        C.byref(ws)) == 0, lib.peps_last_error()
+    k = C.c_int32()
+    lib.peps_einsumsvd_rank(plan, 0, C.byref(k))
+    M, N = kL * t, Dx * DX * b * De * DE
+    sizes = (es * kL * t * a * Dl * DL, es * a * Du * DU * b, es * d * Dl * Du * Dx * De, es * d * DL * DU * DX * DE)
+    io = L.EinsumsvdIO(*[heap(x) for x in sizes], heap(es * M * k.value), heap(es * k.value * N),
+                       heap(8 * k.value), heap(8))
+    ct = L.Cotangent(heap(es * M * k.value), heap(es * k.value * N), heap(8))
+    gr = L.Grads(*[heap(x) for x in sizes])
+    assert lib.peps_einsumsvd_grad_bind(plan, C.byref(ct), C.byref(gr)) == 0
+    wsp = heap(ws.value)
+    r = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, C.byref(io))
+    assert r == 0, lib.peps_last_error().decode()
+    lib.peps_plan_destroy(plan)
