@@ -291,6 +291,31 @@ peps_status peps_expectation_execute(peps_plan *plan, void *workspace, size_t wo
 peps_status peps_expectation_result(peps_plan *plan, void *workspace, void *stream, double *energy,
                                     double *log_norm, double *term_values);
 
+/* Energy gradient (hand-written reverse mode; the paper has no gradient):
+ * E = <psi|H|psi>/<psi|psi> as computed by peps_expectation (cached
+ * environments) and dE/d(site) for every site tensor of a REAL network
+ * (PEPS_R32 / PEPS_R64, plain arithmetic, at least 2 x 2).  The forward keeps
+ * every einsumsvd step of the four sweeps (per-step saved bases); the
+ * reverse sweep runs the strip adjoints, then every sweep backwards (the
+ * einsumsvd adjoint of peps_einsumsvd_grad_execute per step, the row-start
+ * site adjoints), then maps the row-reversed and transposed lattices' site
+ * cotangents back.  Sketches are held fixed (the gradient of the function
+ * the forward computes). */
+peps_status peps_grad_plan(peps_plan **out, const peps_network *ket, const peps_term *terms, int32_t nterms,
+                           const peps_rsvd_opts *opts, size_t *workspace_bytes);
+
+/* Run forward and reverse; grad_site is a HOST array of nrow*ncol DEVICE
+ * pointers (site shapes, overwritten with dE/d(site)); *energy receives E.
+ * Synchronises `stream` (the strip values are read back between the two
+ * phases), so it cannot be captured. */
+peps_status peps_grad_execute(peps_plan *plan, void *const *grad_site, void *workspace,
+                              size_t workspace_bytes, void *stream, double *energy);
+
+/* One-shot convenience: plan, execute, destroy. */
+peps_status peps_grad(const peps_network *ket, const peps_term *terms, int32_t nterms,
+                      const peps_rsvd_opts *opts, void *const *grad_site, void *workspace,
+                      size_t workspace_bytes, void *stream, double *energy);
+
 /* Workspace size of peps_expectation for these arguments. */
 peps_status peps_expectation_workspace(const peps_network *ket, const peps_term *terms, int32_t nterms,
                                        const peps_rsvd_opts *opts, int32_t use_cache,

@@ -115,7 +115,7 @@ peps_status read_net(const peps_network *n, Net &out, const char *which) {
 // ---- plans ------------------------------------------------------------------
 
 struct peps_plan {
-  enum Kind { EINSUMSVD, CONTRACT, EXPECT, EGRAD } kind;
+  enum Kind { EINSUMSVD, CONTRACT, EXPECT, EGRAD, GRAD } kind;
   int dt = 0;
   RsvdOpts opts{};
   // einsumsvd
@@ -141,6 +141,10 @@ struct peps_plan {
   int64_t lognorm_strip = 0;                // row 0 norm strip of the original lattice
   size_t lognorm_logs_off = 0;              // logs of the sweep below row 0
   int64_t lognorm_nlogs = 0;
+  // energy gradient: caller's gradient tensors, phase split, strip cotangents
+  std::vector<void *> grad_site;
+  size_t split = 0;                         // ops[0, split): forward; ops[split, end): reverse sweep
+  size_t sbar_off = 0;
   // built schedule
   uintptr_t built_base = 0;
   bool built = false;
@@ -526,11 +530,169 @@ LatticeCopy transpose_copy(Builder &B, const Net &src, size_t es, std::vector<Pe
   return L;
 }
 
+// ---- energy gradient: sweeps that keep every step, and their reverse -------
+
+struct StepRec {
+  Inst I;
+  GradBufs G;
+  void *tmpS = nullptr, *tmpK = nullptr, *tmpKb = nullptr;
+};
+
+struct SweepGrad {
+  std::vector<std::vector<void *>> crow;             // cotangents of the boundary after row r
+  std::vector<std::vector<void *>> carry, ccarry;    // [r][i]: carry entering step i (i >= 1) and its cotangent
+  std::vector<std::vector<StepRec>> steps;           // [r][i-1]
+  std::vector<std::vector<void *>> gsite;            // [r][q]: cotangent of the lattice's site tensors
+};
+
+void push_copy(Builder &B, void *dst, const void *src, int64_t bytes, const char *tag) {
+  Op op;
+  op.kind = Op::COPY; op.fill_ptr = dst; op.aux_ptr = src; op.fill_n = bytes; op.tag = tag;
+  B.ops.push_back(op);
+}
+
+void push_memset(Builder &B, void *p, int64_t bytes, const char *tag) {
+  Op op;
+  op.kind = Op::MEMSET; op.fill_ptr = p; op.fill_n = bytes; op.tag = tag;
+  B.ops.push_back(op);
+}
+
+void push_axpy(Builder &B, const void *x, void *y, int64_t n, const char *tag) {
+  Op op;
+  op.kind = Op::AXPY; op.aux_ptr = x; op.fill_ptr = y; op.fill_n = n; op.tag = tag;
+  B.ops.push_back(op);
+}
+
+int64_t bsite_elems(const BSite &x) { return (int64_t)x.left * x.vert * x.right; }
+
+// Buffers of a sweep's gradient pass (per-step scratch: the reverse sweep
+// needs every step's forward data).
+void sweep_grad_alloc(Builder &B, const Sweep &S, const RsvdOpts &opts, int dt, SweepGrad &SG) {
+  const size_t es = dtype_size(dt);
+  const Net &K = *S.ket;
+  const int ncol = K.ncol;
+  SG.crow.assign(S.last + 1, {});
+  for (int r = 0; r <= S.last; ++r)
+    for (auto &x : S.bound[r]) SG.crow[r].push_back(B.buf(bsite_elems(x) * es));
+  SG.carry.assign(S.last + 1, std::vector<void *>(ncol + 1, nullptr));
+  SG.ccarry.assign(S.last + 1, std::vector<void *>(ncol + 1, nullptr));
+  SG.steps.assign(S.last + 1, {});
+  for (int r = 1; r <= S.last; ++r)
+    for (int i = 1; i < ncol; ++i) {
+      const Inst &I0 = S.steps[r][i - 1];
+      const int64_t vsz = (int64_t)I0.kL * I0.t * I0.a * I0.h;
+      SG.carry[r][i] = B.buf(vsz * es);
+      SG.ccarry[r][i] = B.buf(vsz * es);
+      StepRec rec;
+      rec.I = I0;
+      inst_alloc_scratch(B, rec.I, dt);
+      rec.I.logp = (double *)B.buf(8);
+      grad_alloc(B, rec.I, opts, rec.G, dt);
+      rec.tmpS = B.buf((int64_t)I0.a * I0.v * I0.b * es);
+      rec.tmpK = B.buf((int64_t)I0.d * I0.Dl * I0.Du * I0.Dx * I0.De * es);
+      rec.tmpKb = B.buf((int64_t)I0.d * I0.DL * I0.DU * I0.DX * I0.DE * es);
+      SG.steps[r].push_back(rec);
+    }
+  SG.gsite.assign(K.nrow, std::vector<void *>(ncol, nullptr));
+}
+
+// Forward of a sweep keeping every step (same ops as emit_sweep otherwise).
+void emit_sweep_save(Builder &B, const Sweep &S, const RsvdOpts &opts, const std::vector<std::vector<void *>> &row,
+                     SweepGrad &SG, double *logs, double *sigma) {
+  const Net &K = *S.ket;
+  const int ncol = K.ncol;
+  {
+    std::vector<SiteDesc> d;
+    for (int q = 0; q < ncol; ++q) {
+      const SiteDims k = K.at(0, q), b = sweep_bra_dims(S, 0, q);
+      SiteDesc x{};
+      x.K = K.ptr(0, q); x.Kb = S.bra->ptr(0, q); x.S = nullptr; x.out = row[0][q]; x.mode = 0;
+      x.d = k.d; x.Dl = k.Dl; x.Du = k.Du; x.Dx = k.Dx; x.De = k.De;
+      x.DL = b.Dl; x.DU = b.Du; x.DX = b.Dx; x.DE = b.De; x.B = 1;
+      x.total = (int64_t)k.Dl * b.Dl * k.Dx * b.Dx * k.De * b.De;
+      d.push_back(x);
+    }
+    push_site(B, d, "first_row");
+  }
+  int64_t step_idx = 0, sig_pos = 0;
+  for (int r = 1; r <= S.last; ++r) {
+    {
+      const SiteDims k = K.at(r, 0), b = sweep_bra_dims(S, r, 0);
+      SiteDesc x{};
+      x.K = K.ptr(r, 0); x.Kb = S.bra->ptr(r, 0); x.S = row[r - 1][0];
+      x.out = ncol == 1 ? row[r][0] : SG.carry[r][1];
+      x.mode = 1;
+      x.d = k.d; x.Dl = k.Dl; x.Du = k.Du; x.Dx = k.Dx; x.De = k.De;
+      x.DL = b.Dl; x.DU = b.Du; x.DX = b.Dx; x.DE = b.De; x.B = S.bound[r - 1][0].right;
+      x.total = (int64_t)k.Dx * b.Dx * x.B * k.De * b.De;
+      std::vector<SiteDesc> d{x};
+      push_site(B, d, "zipup_start");
+    }
+    for (int i = 1; i < ncol; ++i) {
+      StepRec &rec = SG.steps[r][i - 1];
+      Inst &I = rec.I;
+      I.V = SG.carry[r][i];
+      I.S = row[r - 1][i];
+      I.K = K.ptr(r, i);
+      I.Kb = S.bra->ptr(r, i);
+      I.U = row[r][i - 1];
+      I.W = (i == ncol - 1) ? row[r][ncol - 1] : SG.carry[r][i + 1];
+      I.sigma = sigma + sig_pos;
+      I.logp = logs + step_idx;
+      sig_pos += I.k;
+      ++step_idx;
+      emit_einsumsvd_save(B, I, opts, rec.G);
+    }
+  }
+}
+
+// Reverse of a sweep: boundary cotangents SG.crow (complete for every row the
+// strips and later rows feed) to the lattice's site cotangents SG.gsite.
+void emit_sweep_bwd(Builder &B, const Sweep &S, const RsvdOpts &opts, const std::vector<std::vector<void *>> &row,
+                    SweepGrad &SG, const double *lzero) {
+  const Net &K = *S.ket;
+  const int ncol = K.ncol;
+  const char *tag = "sweep_reverse";
+  for (int r = S.last; r >= 1; --r) {
+    for (int i = ncol - 1; i >= 1; --i) {
+      StepRec &rec = SG.steps[r][i - 1];
+      Inst &I = rec.I;
+      const void *Ub = SG.crow[r][i - 1];
+      const void *Wb = (i == ncol - 1) ? SG.crow[r][ncol - 1] : SG.ccarry[r][i + 1];
+      emit_einsumsvd_bwd(B, I, opts, rec.G, Ub, Wb, lzero, SG.ccarry[r][i], rec.tmpS, rec.tmpK, rec.tmpKb);
+      push_axpy(B, rec.tmpS, SG.crow[r - 1][i], (int64_t)I.a * I.v * I.b, tag);
+      const int64_t nk = (int64_t)I.d * I.Dl * I.Du * I.Dx * I.De;
+      push_axpy(B, rec.tmpK, SG.gsite[r][i], nk, tag);
+      push_axpy(B, rec.tmpKb, SG.gsite[r][i], nk, tag);
+    }
+    // first zip-up carry of row r
+    const SiteDims k = K.at(r, 0);
+    SiteBwdDesc x{};
+    x.K = K.ptr(r, 0); x.S = row[r - 1][0];
+    x.cot = ncol == 1 ? SG.crow[r][0] : SG.ccarry[r][1];
+    x.Kbar = SG.gsite[r][0]; x.Sbar = SG.crow[r - 1][0];
+    x.mode = 1; x.d = k.d; x.Dl = k.Dl; x.Du = k.Du; x.Dx = k.Dx; x.De = k.De; x.B = S.bound[r - 1][0].right;
+    Op op;
+    op.kind = Op::SITEBWD; op.desc_off = B.put(std::vector<SiteBwdDesc>{x}); op.nd = 1; op.tag = tag;
+    B.ops.push_back(op);
+  }
+  for (int q = 0; q < ncol; ++q) {
+    const SiteDims k = K.at(0, q);
+    SiteBwdDesc x{};
+    x.K = K.ptr(0, q); x.cot = SG.crow[0][q]; x.Kbar = SG.gsite[0][q];
+    x.mode = 0; x.d = k.d; x.Dl = k.Dl; x.Du = k.Du; x.Dx = k.Dx; x.De = k.De; x.B = 1;
+    Op op;
+    op.kind = Op::SITEBWD; op.desc_off = B.put(std::vector<SiteBwdDesc>{x}); op.nd = 1; op.tag = tag;
+    B.ops.push_back(op);
+  }
+}
+
 // Cached environments of one lattice: boundaries above every row (top-down
 // sweep) and below every row (sweep of the row-reversed copy).
 struct EnvSet {
   Sweep top, bot;
   bool has_top = false, has_bot = false;
+  std::unique_ptr<SweepGrad> tg, bg;      // energy gradient only
   std::vector<std::vector<void *>> top_rows, bot_rows;
   double *top_logs = nullptr, *bot_logs = nullptr;
   double *top_sigma = nullptr, *bot_sigma = nullptr;
@@ -544,6 +706,7 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
   const bool cplx = dtype_complex(dt);
   const Net &H = P->ket;
   const int d = H.d;
+  const bool grad = P->kind == peps_plan::GRAD;
   if (d > 4) return "physical dimension above 4 is not supported by the strip kernel";
   if (H.ncol > kStripMaxCols || H.nrow > kStripMaxCols) return "lattice side above 32 is not supported";
 
@@ -627,7 +790,7 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
       envs.push_back(std::move(E));
       return (int)envs.size() - 1;
     };
-    if (P->use_cache) {
+    if (P->use_cache || grad) {
       const int e = make(nrow - 2, nrow - 2);
       for (int r = 0; r < nrow; ++r) env_of[l][r] = e;
     } else {
@@ -649,7 +812,7 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
     }
   }
   Inst owner{};
-  sweep_owner_scratch(B, all, dt, owner);
+  if (!grad) sweep_owner_scratch(B, all, dt, owner);
   size_t max_carry = 1;
   for (Sweep *S : all) max_carry = std::max(max_carry, S->max_carry);
   void *Vbuf[2] = {B.buf(max_carry * es), B.buf(max_carry * es)};
@@ -672,9 +835,35 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
       E->bot_sigma = (double *)B.buf(std::max<int64_t>(E->bot.nsigma, 1) * 8);
     }
   }
+  // energy gradient: site cotangents of the four lattices (0 H, 1 Vt, 2 Hf, 3 Vf) and the sweeps' buffers
+  std::vector<std::vector<void *>> gl[4];
+  const Net *glat[4] = {&H, need_v ? &Vt.net : nullptr, &Hf.net, need_v ? &Vf.net : nullptr};
+  if (grad) {
+    for (int l = 0; l < 4; ++l) {
+      if (!glat[l]) continue;
+      gl[l].assign(glat[l]->nrow, std::vector<void *>(glat[l]->ncol, nullptr));
+      for (int r = 0; r < glat[l]->nrow; ++r)
+        for (int q = 0; q < glat[l]->ncol; ++q) gl[l][r][q] = B.buf(site_elems(glat[l]->at(r, q)) * es);
+    }
+    for (int l = 0; l < 2; ++l) {
+      if (!lat[l]) continue;
+      EnvSet &E = *envs[env_of[l][0]];
+      if (E.has_top && !E.tg) {
+        E.tg = std::make_unique<SweepGrad>();
+        sweep_grad_alloc(B, E.top, P->opts, dt, *E.tg);
+        E.tg->gsite = gl[l];
+      }
+      if (E.has_bot && !E.bg) {
+        E.bg = std::make_unique<SweepGrad>();
+        sweep_grad_alloc(B, E.bot, P->opts, dt, *E.bg);
+        E.bg->gsite = gl[l + 2];
+      }
+    }
+  }
 
   // --- strips
   std::vector<StripCol> cols;
+  std::vector<StripBwdCol> bcols;
   std::vector<StripDesc> sd;
   int64_t l_cap = 1, a1_cap = 1, a2_cap = 1, a3_cap = 1;
   // column table of row r of lattice l (shared by all strips of that row)
@@ -711,6 +900,13 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
       a2_cap = std::max<int64_t>(a2_cap, (int64_t)x.Dl * c.c * x.Du * c.b * x.d * x.Dx * x.De);
       a3_cap = std::max<int64_t>(a3_cap, (int64_t)c.c * c.b * x.De * x.Dx * x.Dx * x.De);
       cols.push_back(c);
+      StripBwdCol bc{};
+      if (grad) {
+        bc.cot_up = r > 0 ? E.tg->crow[r - 1][q] : nullptr;
+        bc.cot_lo = r < nrow - 1 ? E.bg->crow[nrow - 2 - r][q] : nullptr;
+        bc.cot_ket = gl[l][r][q];
+      }
+      bcols.push_back(bc);
     }
     return "";
   };
@@ -773,6 +969,11 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
     push_permute(B, Vf.perm, "lattice_copy");
   }
   for (auto &E : envs) {
+    if (grad) {
+      if (E->has_top) emit_sweep_save(B, E->top, P->opts, E->top_rows, *E->tg, E->top_logs, E->top_sigma);
+      if (E->has_bot) emit_sweep_save(B, E->bot, P->opts, E->bot_rows, *E->bg, E->bot_logs, E->bot_sigma);
+      continue;
+    }
     if (E->has_top) emit_sweep(B, E->top, P->opts, ones, E->top_rows, Vbuf, E->top_logs, E->top_sigma, owner);
     if (E->has_bot) emit_sweep(B, E->bot, P->opts, ones, E->bot_rows, Vbuf, E->bot_logs, E->bot_sigma, owner);
   }
@@ -788,6 +989,82 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
   st.nd = (int)P->nstrips;
   st.tag = "strips";
   B.ops.push_back(st);
+  if (!grad) return "";
+
+  // ---- reverse sweep (second phase: the host sets the strip cotangents) ----
+  P->split = B.ops.size();
+  P->sbar_off = B.alloc((size_t)P->nstrips * 8);
+  double *lzero = (double *)B.buf(8);
+  push_memset(B, lzero, 8, "reverse_init");
+  for (int l = 0; l < 4; ++l)
+    for (int r = 0; r < (int)gl[l].size(); ++r)
+      for (int q = 0; q < (int)gl[l][r].size(); ++q)
+        push_memset(B, gl[l][r][q], site_elems(glat[l]->at(r, q)) * (int64_t)es, "reverse_init");
+  for (auto &E : envs)
+    for (SweepGrad *SGp : {E->tg.get(), E->bg.get()}) {
+      if (!SGp) continue;
+      const Sweep &S = SGp == E->tg.get() ? E->top : E->bot;
+      for (int r = 0; r <= S.last; ++r)
+        for (size_t q = 0; q < SGp->crow[r].size(); ++q)
+          push_memset(B, SGp->crow[r][q], bsite_elems(S.bound[r][q]) * (int64_t)es, "reverse_init");
+    }
+  {
+    const int64_t blk = l_cap, big = std::max(a1_cap, std::max(a2_cap, a3_cap));
+    int maxc = 1;
+    for (auto &x : sd) maxc = std::max(maxc, x.ncol);
+    StripBwdScratch sc{};
+    sc.blk = blk; sc.big = big;
+    sc.per_strip = 2 * (int64_t)(maxc + 1) * blk + 6 * big;
+    sc.base = (double *)B.buf((size_t)P->nstrips * sc.per_strip * 8);
+    Op sb;
+    sb.kind = Op::STRIPBWD;
+    sb.desc_off = st.desc_off;
+    sb.aux_off[0] = st.aux_off[0];
+    sb.aux_off[1] = st.aux_off[1];
+    sb.aux_off[2] = B.put(bcols);
+    sb.nd = (int)P->nstrips;
+    sb.sbar = (const double *)B.ptr(P->sbar_off);
+    sb.sbs = sc;
+    sb.tag = "strips_reverse";
+    B.ops.push_back(sb);
+  }
+  for (auto &E : envs) {
+    if (E->has_top) emit_sweep_bwd(B, E->top, P->opts, E->top_rows, *E->tg, lzero);
+    if (E->has_bot) emit_sweep_bwd(B, E->bot, P->opts, E->bot_rows, *E->bg, lzero);
+  }
+  // lattice copies back onto the caller's lattice: un-flip (the same axis swap), un-transpose
+  auto unflip = [&](const Net &src_dims, std::vector<std::vector<void *>> &gsrc, std::vector<std::vector<void *>> &gdst) {
+    // gsrc on the flipped lattice (row p = original row nrow-1-p, [d][l][x][u][e])
+    const int nrow = src_dims.nrow;
+    for (int p = 0; p < nrow; ++p)
+      for (int q = 0; q < src_dims.ncol; ++q) {
+        const SiteDims f = src_dims.at(p, q);        // flipped dims: Du = original Dx, Dx = original Du
+        void *tmp = B.buf(site_elems(f) * es);
+        std::vector<PermuteDesc> pd{mk_permute(gsrc[p][q], tmp, (int64_t)f.d * f.Dl, f.Du, f.Dx, f.De)};
+        push_permute(B, pd, "lattice_reverse");
+        push_axpy(B, tmp, gdst[nrow - 1 - p][q], site_elems(f), "lattice_reverse");
+      }
+  };
+  if (need_v) {
+    unflip(Vf.net, gl[3], gl[1]);
+    // Vt site (q,p) = [d][u][l][e][x] of H site (p,q): undo the (e,x) swap, then the (u,l) swap
+    for (int p = 0; p < H.nrow; ++p)
+      for (int q = 0; q < H.ncol; ++q) {
+        const SiteDims x = H.at(p, q);
+        void *t1 = B.buf(site_elems(x) * es), *t2 = B.buf(site_elems(x) * es);
+        std::vector<PermuteDesc> a{mk_permute(gl[1][q][p], t1, (int64_t)x.d * x.Du * x.Dl, x.De, x.Dx, 1)};
+        push_permute(B, a, "lattice_reverse");
+        std::vector<PermuteDesc> b{mk_permute(t1, t2, x.d, x.Du, x.Dl, (int64_t)x.Dx * x.De)};
+        push_permute(B, b, "lattice_reverse");
+        push_axpy(B, t2, gl[0][p][q], site_elems(x), "lattice_reverse");
+      }
+  }
+  unflip(Hf.net, gl[2], gl[0]);
+  for (int p = 0; p < H.nrow; ++p)
+    for (int q = 0; q < H.ncol; ++q) {
+      void *dst = P->grad_site.empty() ? nullptr : P->grad_site[(size_t)p * H.ncol + q];
+      if (dst) push_copy(B, dst, gl[0][p][q], site_elems(H.at(p, q)) * (int64_t)es, "gradient_out");
+    }
   return "";
 }
 
@@ -954,6 +1231,55 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         C.need(op.aux_ptr, (double)op.fill_n, tag, "src");
         C.need(op.fill_ptr, (double)op.fill_n, tag, "dst");
         break;
+      case Op::MEMSET:
+        C.need(op.fill_ptr, (double)op.fill_n, tag, "dst");
+        break;
+      case Op::AXPY:
+        C.need(op.aux_ptr, es * (double)op.fill_n, tag, "x");
+        C.need(op.fill_ptr, es * (double)op.fill_n, tag, "y");
+        break;
+      case Op::SITEBWD: {
+        const SiteBwdDesc &x = *(const SiteBwdDesc *)d;
+        if (x.mode == 0) {
+          const double nk = (double)x.d * x.Dl * x.Dx * x.De;
+          C.need(x.K, es * nk, tag, "K");
+          C.need(x.Kbar, es * nk, tag, "Kbar");
+          C.need(x.cot, es * (double)x.Dl * x.Dl * x.Dx * x.Dx * x.De * x.De, tag, "cot");
+        } else {
+          const double nk = (double)x.d * x.Du * x.Dx * x.De, ns = (double)x.Du * x.Du * x.B;
+          C.need(x.K, es * nk, tag, "K");
+          C.need(x.Kbar, es * nk, tag, "Kbar");
+          C.need(x.S, es * ns, tag, "S");
+          C.need(x.Sbar, es * ns, tag, "Sbar");
+          C.need(x.cot, es * (double)x.Dx * x.Dx * x.B * x.De * x.De, tag, "cot");
+        }
+        break;
+      }
+      case Op::STRIPBWD: {
+        const StripCol *cl = (const StripCol *)(blob + op.aux_off[0]);
+        const StripBwdCol *bl = (const StripBwdCol *)(blob + op.aux_off[2]);
+        C.need(op.sbar, 8.0 * op.nd, tag, "sbar");
+        C.need(op.sbs.base, 8.0 * op.nd * op.sbs.per_strip, tag, "scratch");
+        for (int i = 0; i < op.nd; ++i) {
+          const StripDesc &x = ((const StripDesc *)d)[i];
+          if (2 * (int64_t)(x.ncol + 1) * op.sbs.blk + 6 * op.sbs.big > op.sbs.per_strip)
+            C.err = std::string(tag) + ": scratch slice too small";
+          for (int q = 0; q < x.ncol && q < kStripMaxCols; ++q) {
+            const StripCol &c = cl[x.col0 + q];
+            const StripBwdCol &b = bl[x.col0 + q];
+            const double vu = (double)c.Du * c.Du, vd = (double)c.Dx * c.Dx;
+            if (b.cot_up) C.need(b.cot_up, es * c.a * vu * c.b, tag, "cot_up");
+            if (b.cot_lo) C.need(b.cot_lo, es * c.c * vd * c.f, tag, "cot_lo");
+            C.need(b.cot_ket, es * (double)c.d * c.Dl * c.Du * c.Dx * c.De, tag, "cot_ket");
+            const double blk = std::max((double)c.a * c.Dl * c.Dl * c.c, (double)c.b * c.De * c.De * c.f);
+            const double big = std::max({(double)c.Dl * c.Dl * c.c * vu * c.b,
+                                         (double)c.Dl * c.c * c.Du * c.b * c.d * c.Dx * c.De,
+                                         (double)c.c * c.b * c.De * c.Dx * c.Dx * c.De});
+            if (blk > op.sbs.blk || big > op.sbs.big) C.err = std::string(tag) + ": scratch blocks too small";
+          }
+        }
+        break;
+      }
       case Op::LTU:
         C.need(op.aux_ptr, es * (double)op.fill_n * op.fill_n, tag, "M");
         C.need(op.fill_ptr, es * (double)op.fill_n * op.fill_n, tag, "out");
@@ -1037,7 +1363,7 @@ peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool en
 }
 
 peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, bool upload,
-                    cudaEvent_t *events = nullptr) {
+                    cudaEvent_t *events = nullptr, size_t first = 0, size_t last = SIZE_MAX) {
   if (!ws) return fail(PEPS_ERR_WORKSPACE, "workspace is NULL");
   if ((uintptr_t)ws & 255) return fail(PEPS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   if (ws_bytes < P->ws_bytes)
@@ -1050,7 +1376,9 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
   }
   const int dt = P->dt;
   if (events) CUDA_TRY(cudaEventRecord(events[0], s));
-  for (const Op &op : P->ops) {
+  last = std::min(last, P->ops.size());
+  for (size_t oi = first; oi < last; ++oi) {
+    const Op &op = P->ops[oi];
     const void *d = blob + op.desc_off;
     const int64_t *pre = (const int64_t *)(blob + op.prefix_off);
     switch (op.kind) {
@@ -1086,6 +1414,14 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
       case Op::SVDBWD: launch_svd_bwd(dt, *(const SvdBwdDesc *)(P->blob.data() + op.desc_off), s); break;
       case Op::LTU: launch_copyltu(dt, op.aux_ptr, op.fill_ptr, (int)op.fill_n, s); break;
       case Op::TGRAD: launch_tensor_grad(dt, *(const TensorGradDesc *)(P->blob.data() + op.desc_off), s); break;
+      case Op::MEMSET: CUDA_TRY(cudaMemsetAsync(op.fill_ptr, 0, (size_t)op.fill_n, s)); break;
+      case Op::AXPY: launch_axpy(dt, op.aux_ptr, op.fill_ptr, op.fill_n, s); break;
+      case Op::SITEBWD: launch_site_bwd(dt, *(const SiteBwdDesc *)(P->blob.data() + op.desc_off), s); break;
+      case Op::STRIPBWD:
+        launch_strip_bwd(dt, (const StripDesc *)d, (const StripCol *)(blob + op.aux_off[0]),
+                         (const StripBwdCol *)(blob + op.aux_off[2]), (const double *)(blob + op.aux_off[1]), op.sbar,
+                         op.sbs, op.nd, s);
+        break;
     }
     if (events) CUDA_TRY(cudaEventRecord(events[&op - P->ops.data() + 1], s));
   }
@@ -1448,6 +1784,81 @@ peps_status peps_expectation_result(peps_plan *plan, void *workspace, void *stre
   return PEPS_OK;
 }
 
+peps_status peps_grad_plan(peps_plan **out, const peps_network *ket, const peps_term *terms, int32_t nterms,
+                           const peps_rsvd_opts *opts, size_t *workspace_bytes) {
+  g_last_error.clear();
+  if (!ket) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (ket->dtype != PEPS_R32 && ket->dtype != PEPS_R64)
+    return fail(PEPS_ERR_UNSUPPORTED, "the energy gradient takes real networks");
+  if (!opts) return fail(PEPS_ERR_ARG, "opts is NULL");
+  if (opts->prec != PEPS_PREC_PLAIN) return fail(PEPS_ERR_UNSUPPORTED, "the energy gradient runs the plain arithmetic");
+  if (ket->nrow < 2 || ket->ncol < 2) return fail(PEPS_ERR_UNSUPPORTED, "the energy gradient needs 2 rows and 2 columns");
+  peps_plan *p = nullptr;
+  if (peps_status s = peps_expectation_plan(&p, ket, terms, nterms, opts, 1, workspace_bytes)) return s;
+  std::unique_ptr<peps_plan> P(p);
+  P->kind = peps_plan::GRAD;
+  if (peps_status s = rebuild(P.get(), nullptr, nullptr)) return s;
+  *workspace_bytes = P->ws_bytes;
+  *out = P.release();
+  return PEPS_OK;
+}
+
+peps_status peps_grad_execute(peps_plan *plan, void *const *grad_site, void *workspace, size_t workspace_bytes,
+                              void *stream, double *energy) {
+  g_last_error.clear();
+  if (!plan || !grad_site) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (plan->kind != peps_plan::GRAD) return fail(PEPS_ERR_ARG, "not a gradient plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (in_capture(s)) return fail(PEPS_ERR_CAPTURE, "the gradient reads the strips back mid-way: no capture");
+  const size_t ns = (size_t)plan->ket.nrow * plan->ket.ncol;
+  for (size_t i = 0; i < ns; ++i)
+    if (!grad_site[i]) return fail(PEPS_ERR_ARG, "gradient tensor %zu is NULL", i);
+  bool same = plan->built && plan->built_base == (uintptr_t)workspace && plan->grad_site.size() == ns &&
+              std::equal(plan->grad_site.begin(), plan->grad_site.end(), grad_site);
+  if (!same) {
+    plan->grad_site.assign(grad_site, grad_site + ns);
+    if (peps_status st = rebuild(plan, workspace, nullptr, true)) return st;
+    plan->built_base = (uintptr_t)workspace;
+    plan->built = true;
+  }
+  // phase 1: forward (sweeps keeping every step, strips)
+  if (peps_status st = enqueue(plan, workspace, workspace_bytes, s, !same, nullptr, 0, plan->split)) return st;
+  // strip cotangents of E = sum_t c_t sum_x s_{t,x} / s_norm(t) on the host
+  std::vector<double> sv((size_t)plan->nstrips), sb((size_t)plan->nstrips, 0.0);
+  CUDA_TRY(cudaMemcpyAsync(sv.data(), (uint8_t *)workspace + plan->strip_off, sv.size() * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  double e = 0.0;
+  for (size_t t = 0; t < plan->terms.size(); ++t) {
+    double num = 0.0;
+    int64_t nrm = -1;
+    for (auto &pr : plan->term_strips[t]) { num += sv[(size_t)pr.first]; nrm = pr.second; }
+    if (nrm < 0) continue;
+    const double den = sv[(size_t)nrm], c = plan->terms[t].coeff;
+    if (!(den != 0.0)) return fail(PEPS_ERR_NUMERIC, "term %zu: vanishing strip norm", t);
+    e += c * num / den;
+    for (auto &pr : plan->term_strips[t]) sb[(size_t)pr.first] += c / den;
+    sb[(size_t)nrm] -= c * num / (den * den);
+  }
+  if (energy) *energy = e;
+  CUDA_TRY(cudaMemcpyAsync((uint8_t *)workspace + plan->sbar_off, sb.data(), sb.size() * 8, cudaMemcpyHostToDevice, s));
+  // phase 2: reverse sweep into the site cotangents; synchronise (sb is host memory)
+  if (peps_status st = enqueue(plan, workspace, workspace_bytes, s, false, nullptr, plan->split)) return st;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (!std::isfinite(e)) return fail(PEPS_ERR_NUMERIC, "non-finite energy");
+  return PEPS_OK;
+}
+
+peps_status peps_grad(const peps_network *ket, const peps_term *terms, int32_t nterms, const peps_rsvd_opts *opts,
+                      void *const *grad_site, void *workspace, size_t workspace_bytes, void *stream, double *energy) {
+  peps_plan *p = nullptr;
+  size_t need = 0;
+  peps_status s = peps_grad_plan(&p, ket, terms, nterms, opts, &need);
+  if (s != PEPS_OK) return s;
+  s = peps_grad_execute(p, grad_site, workspace, workspace_bytes, stream, energy);
+  peps_plan_destroy(p);
+  return s;
+}
+
 peps_status peps_expectation_workspace(const peps_network *ket, const peps_term *terms, int32_t nterms,
                                        const peps_rsvd_opts *opts, int32_t use_cache, size_t *workspace_bytes) {
   peps_plan *p = nullptr;
@@ -1494,7 +1905,7 @@ peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count) {
       case Op::JACOBI: n += 1 + (op.smem2 > 0) + (op.blocks > 0); break;   // one CTA, cluster, refinement
       case Op::CHOL: n += 1 + (op.smem2 > 0); break;                         // one CTA, cluster
       case Op::TC: n += op.tc.tiles_m * op.tc.tiles_n > 0; break;
-      case Op::COPY: break;                                                   // a copy, not a kernel
+      case Op::COPY: case Op::MEMSET: break;                                  // copies, not kernels
       case Op::SKETCH: case Op::GEMM: case Op::GEMM_ATOMIC: case Op::SANDWICH: case Op::ZERO: case Op::SITE:
       case Op::PERMUTE: n += op.blocks > 0; break;
       default: n += 1; break;
@@ -1526,6 +1937,10 @@ peps_status peps_plan_launch_kernel(const peps_plan *plan, int64_t i, const char
     case Op::SVDBWD: *kernel = "svd_bwd"; break;
     case Op::LTU: *kernel = "copyltu"; break;
     case Op::TGRAD: *kernel = "tensor_grad"; break;
+    case Op::MEMSET: *kernel = "memset"; break;
+    case Op::AXPY: *kernel = "axpy"; break;
+    case Op::SITEBWD: *kernel = "site_reverse"; break;
+    case Op::STRIPBWD: *kernel = "strip_reverse"; break;
     default: *kernel = "unknown"; break;
   }
   return PEPS_OK;

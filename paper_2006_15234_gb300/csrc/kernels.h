@@ -214,6 +214,23 @@ struct TensorGradDesc {
 void launch_svd_bwd(int dt, const SvdBwdDesc &d, cudaStream_t s);
 void launch_copyltu(int dt, const void *M, void *out, int n, cudaStream_t s);
 void launch_tensor_grad(int dt, const TensorGradDesc &d, cudaStream_t s);
+// ---- network-layer adjoint (real data) ----
+struct StripBwdCol { void *cot_up, *cot_lo, *cot_ket; };   // NULL: no target
+struct StripBwdScratch {
+  double *base;
+  int64_t per_strip, blk, big;
+};
+// Row-start sites: mode 0 = first row (K is [d][Dl][1][Dx][De]), mode 1 =
+// first zip-up carry (K is [d][1][Du][Dx][De], S the boundary site [1][(u,U)][B]).
+struct SiteBwdDesc {
+  const void *K, *S, *cot;
+  void *Kbar, *Sbar;
+  int32_t mode, d, Dl, Du, Dx, De, B;
+};
+void launch_strip_bwd(int dt, const StripDesc *d, const StripCol *cols, const StripBwdCol *bcols, const double *ops,
+                      const double *sbar, const StripBwdScratch &sc, int nd, cudaStream_t s);
+void launch_site_bwd(int dt, const SiteBwdDesc &d, cudaStream_t s);
+void launch_axpy(int dt, const void *x, void *y, int64_t n, cudaStream_t s);
 
 
 }  // namespace peps

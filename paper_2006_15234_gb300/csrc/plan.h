@@ -15,7 +15,7 @@ namespace peps {
 
 struct Op {
   enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL, TC,
-              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD } kind;
+              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD, MEMSET, STRIPBWD, SITEBWD, AXPY } kind;
   size_t desc_off = 0;    // byte offset of the descriptor array in the blob
   size_t prefix_off = 0;  // byte offset of the int64 block prefix array in the blob
   int nd = 0;
@@ -26,7 +26,9 @@ struct Op {
   ScalarDesc scalar{};
   size_t aux_off[3] = {0, 0, 0};  // blob offsets of the scalar's device arrays
   void *fill_ptr = nullptr;
-  const void *aux_ptr = nullptr;  // COPY / LTU source
+  const void *aux_ptr = nullptr;  // COPY / LTU / AXPY source
+  StripBwdScratch sbs{};          // STRIPBWD scratch
+  const double *sbar = nullptr;   // STRIPBWD strip cotangents
   int64_t fill_n = 0;             // FILL: elements; COPY: bytes; LTU: n
   double fill_value = 0.0;
   std::string tag;        // stage name (profiling ledger)

@@ -17,7 +17,8 @@ __all__ = [
     "Network", "ContractPlan", "EinsumsvdPlan", "boundary_contract", "dtype_code",
     "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "PREC_FAST", "SKETCH_GAUSS", "SKETCH_UNIFORM",
     "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
-    "Term", "ExpectationPlan", "expectation", "Cotangent", "Grads", "einsumsvd_grad",
+    "Term", "ExpectationPlan", "expectation", "Cotangent", "Grads", "einsumsvd_grad", "GradPlan",
+    "energy_grad",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -33,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "peps_expectation_plan", "peps_expectation_execute", "peps_expectation_result",
     "peps_expectation_workspace", "peps_expectation", "peps_plan_launch_kernel",
     "peps_plan_kernel_launches", "peps_einsumsvd_grad_plan", "peps_einsumsvd_grad_bind",
-    "peps_einsumsvd_grad_execute",
+    "peps_einsumsvd_grad_execute", "peps_grad_plan", "peps_grad_execute", "peps_grad",
 ]
 
 # Size of the library's fixed device scratch used by boundary_contract_static.
@@ -146,6 +147,14 @@ def load():
     lib.peps_debug_tc_gemm.argtypes = [C.c_int32] * 7 + [vp, vp, vp, vp]
     lib.peps_plan_validate.restype = st
     lib.peps_plan_validate.argtypes = [vp, vp, C.c_size_t, C.POINTER(EinsumsvdIO)]
+    lib.peps_grad_plan.restype = st
+    lib.peps_grad_plan.argtypes = [C.POINTER(vp), C.POINTER(Network), C.POINTER(Term), C.c_int32,
+                                   C.POINTER(RsvdOpts), C.POINTER(C.c_size_t)]
+    lib.peps_grad_execute.restype = st
+    lib.peps_grad_execute.argtypes = [vp, C.POINTER(vp), vp, C.c_size_t, vp, C.POINTER(C.c_double)]
+    lib.peps_grad.restype = st
+    lib.peps_grad.argtypes = [C.POINTER(Network), C.POINTER(Term), C.c_int32, C.POINTER(RsvdOpts), C.POINTER(vp),
+                              vp, C.c_size_t, vp, C.POINTER(C.c_double)]
     lib.peps_einsumsvd_grad_plan.restype = st
     lib.peps_einsumsvd_grad_plan.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(EinsumsvdShape),
                                              C.POINTER(RsvdOpts), C.POINTER(C.c_size_t)]
@@ -441,6 +450,61 @@ class ExpectationPlan(_Ledger):
                 self._plan = None
         except Exception:
             pass
+
+
+class GradPlan(_Ledger):
+    """Energy and its gradient with respect to every site tensor (real
+    networks): terms as for ExpectationPlan."""
+
+    def __init__(self, ket, terms, opts: RsvdOpts):
+        import numpy as np
+        self._lib = load()
+        self._ket = _network(ket)
+        self._sites = ket
+        ncol = len(ket[0])
+        n = len(terms)
+        self._tarr = (Term * max(1, n))()
+        self._keep = []
+        for i, (st, op, coeff) in enumerate(terms):
+            a = np.ascontiguousarray(np.asarray(op, dtype=np.float64))
+            self._keep.append(a)
+            t = self._tarr[i]
+            t.nsite = len(st)
+            for k, (p_, q_) in enumerate(st):
+                t.site[k] = p_ * ncol + q_
+            t.op = a.ctypes.data_as(C.POINTER(C.c_double))
+            t.coeff = float(coeff)
+        plan = C.c_void_p()
+        ws = C.c_size_t()
+        _check(self._lib.peps_grad_plan(C.byref(plan), C.byref(self._ket.net), self._tarr, n, C.byref(opts),
+                                        C.byref(ws)))
+        self._plan = plan
+        self.workspace_bytes = ws.value
+        self._buf, self._ws = _workspace(ws.value, ket[0][0].device)
+
+    def execute(self, stream=None):
+        """(energy, [[dE/d site]]) with gradients shaped like the sites."""
+        import torch
+        grads = [[torch.empty_like(t) for t in row] for row in self._sites]
+        ptrs = (C.c_void_p * sum(len(r) for r in grads))(*[g.data_ptr() for r in grads for g in r])
+        e = C.c_double()
+        _check(self._lib.peps_grad_execute(self._plan, ptrs, C.c_void_p(self._ws), C.c_size_t(self.workspace_bytes),
+                                           _stream_handle(stream), C.byref(e)))
+        return e.value, grads
+
+    def __del__(self):
+        try:
+            if getattr(self, "_plan", None):
+                self._lib.peps_plan_destroy(self._plan)
+                self._plan = None
+        except Exception:
+            pass
+
+
+def energy_grad(ket, terms, m, p, q, seed, stream=None):
+    """Energy of H = sum coeff * op and dE/d(site) on the GPU (real network)."""
+    plan = GradPlan(ket, terms, make_opts(m, p, q, seed))
+    return plan.execute(stream)
 
 
 def expectation(ket, terms, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN, use_cache=True,

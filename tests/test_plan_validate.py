@@ -234,3 +234,22 @@ def test_einsumsvd_adjoint_plan(lib, dt, shape, m, q):
     r = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, C.byref(io))
     assert r == 0, lib.peps_last_error().decode()
     lib.peps_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("dt,shape,D,m", [(0, (3, 3), 2, 4), (2, (3, 4), 2, 6), (0, (6, 6), 3, 18)])
+def test_energy_gradient_plans(lib, dt, shape, D, m):
+    """The gradient plan (sweeps keeping every step, strips, reverse sweep,
+    lattice adjoints) stays inside the workspace and the network."""
+    nr, nc = shape
+    shp = [[synth.site_shape(nr, nc, p, q, 2, D) for q in range(nc)] for p in range(nr)]
+    heap = FakeHeap()
+    net, keep = _net(heap, shp, dt)
+    terms = synth.tfi_terms(nr, nc, 1.0, 3.0)
+    arr, tkeep = _term_array(terms, nc, False)
+    plan, ws = C.c_void_p(), C.c_size_t()
+    assert lib.peps_grad_plan(C.byref(plan), C.byref(net), arr, len(terms), C.byref(L.make_opts(m, 8, 2, 1)),
+                              C.byref(ws)) == 0, lib.peps_last_error()
+    wsp = heap(ws.value)
+    r = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None)
+    assert r == 0, lib.peps_last_error().decode()
+    lib.peps_plan_destroy(plan)
