@@ -18,7 +18,7 @@ __all__ = [
     "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "PREC_FAST", "SKETCH_GAUSS", "SKETCH_UNIFORM",
     "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
     "Term", "ExpectationPlan", "expectation", "Cotangent", "Grads", "einsumsvd_grad", "GradPlan",
-    "energy_grad",
+    "energy_grad", "peps_energy",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -499,6 +499,45 @@ class GradPlan(_Ledger):
                 self._plan = None
         except Exception:
             pass
+
+
+def peps_energy(terms, m, p, q, seed, nrow, ncol, *sites):
+    """torch.autograd entry: the energy of H = sum coeff * op for a real PEPS
+    whose nrow x ncol site tensors are passed in row-major order; E.backward()
+    returns dE/d(site) from the library's hand-written adjoint (peps_grad)."""
+    return _PepsEnergy.apply(terms, m, p, q, seed, nrow, ncol, *sites)
+
+
+def _make_energy_function():
+    import torch
+
+    class PepsEnergyFunction(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, terms, m, p, q, seed, nrow, ncol, *flat):
+            sites = [[flat[r * ncol + c].contiguous() for c in range(ncol)] for r in range(nrow)]
+            e, g = energy_grad(sites, terms, m, p, q, seed)
+            ctx.save_for_backward(*[x for row in g for x in row])
+            return torch.tensor(e, dtype=torch.float64, device=flat[0].device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            grads = ctx.saved_tensors
+            scale = gout.to(grads[0].dtype)
+            return (None, None, None, None, None, None, None) + tuple(g * scale for g in grads)
+
+    return PepsEnergyFunction
+
+
+class _LazyFunction:
+    _f = None
+
+    def apply(self, *args):
+        if _LazyFunction._f is None:
+            _LazyFunction._f = _make_energy_function()
+        return _LazyFunction._f.apply(*args)
+
+
+_PepsEnergy = _LazyFunction()
 
 
 def energy_grad(ket, terms, m, p, q, seed, stream=None):

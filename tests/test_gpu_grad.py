@@ -123,3 +123,18 @@ def test_c4_energy_gradient():
     num = np.sqrt(sum(np.sum((g32[a][b] - g64[a][b]) ** 2) for a in range(cfg.nrow) for b in range(cfg.ncol)))
     den = np.sqrt(sum(np.sum(g64[a][b] ** 2) for a in range(cfg.nrow) for b in range(cfg.ncol)))
     assert num <= 1e-4 * den, num / den
+
+
+def test_autograd_function_backward():
+    """The torch.autograd entry gives peps_grad's gradient, scaled by the
+    incoming cotangent."""
+    ket = synth.random_peps(3, 3, 2, 2, "f64", "normal", 8)
+    terms = synth.tfi_terms(3, 3, 1.0, 3.0)
+    k = to_dev(ket, "f64")
+    flat = [t.clone().requires_grad_(True) for row in k for t in row]
+    E = libpeps.peps_energy(terms, 3, 2, 1, 9, 3, 3, *flat)
+    (2.5 * E).backward()
+    e, g = libpeps.energy_grad(k, terms, 3, 2, 1, 9)
+    assert float(E) == pytest.approx(e, abs=1e-12)
+    for x, gr in zip(flat, [t for row in g for t in row]):
+        assert torch.allclose(x.grad, 2.5 * gr, rtol=1e-12, atol=1e-14)
