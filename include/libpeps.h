@@ -371,13 +371,17 @@ peps_status peps_plan_validate(peps_plan *plan, void *workspace, size_t workspac
  *   C[m][n] = sum_k opA(A[m][k]) * opB(B[n][k]),  m < M, n < N, k < K
  * A (M x K), B (N x K) and C (M x N) are row-major DEVICE arrays of float
  * (cplx = 0) or interleaved complex float (cplx = 1); opA / opB conjugate
- * when conjA / conjB.  split3 = 1 forms FP32-level products from TF32 head
- * and tail parts (3xTF32), split3 = 0 plain TF32 products.  Rows must be
- * 16-byte aligned (K even for complex, K % 4 == 0 for real).  Enqueued on
- * `stream`; PEPS_ERR_UNSUPPORTED if TMA maps cannot be encoded. */
+ * when conjA / conjB.  split3 selects the products: 0 plain TF32; 1
+ * FP32-level products from TF32 head and tail parts (3xTF32), B expanded and
+ * split inside the GEMM; 2 the same products with B expanded and split
+ * beforehand into `scratch`, a DEVICE buffer of 32*N*K bytes (complex) or
+ * 8*N*K bytes (real), caller-owned, used for no other mode (may be NULL
+ * then).  Rows must be 16-byte aligned (K even for complex, K % 4 == 0 for
+ * real).  Enqueued on `stream`; PEPS_ERR_ARG for a NULL operand or a missing
+ * scratch, PEPS_ERR_UNSUPPORTED if TMA maps cannot be encoded. */
 peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t conjB, int32_t split3, int32_t M,
                                int32_t N, int32_t K, const void *A, const void *B, void *C,
-                               void *stream);
+                               void *scratch, void *stream);
 
 /* ------------------------------------------------------------------------
  * Contraction without any allocation.  The paper has no counterpart: this

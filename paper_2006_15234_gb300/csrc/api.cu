@@ -1225,6 +1225,10 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           C.err = std::string(tag) + ": K chunks do not cover K";
         if (t.alpha_dev) C.need(t.alpha_dev, 8, tag, "alpha_dev");
         if (op.tc_kr % 4 || t.Kr != op.tc_kr) C.err = std::string(tag) + ": TMA rows not 16-byte aligned";
+        if (t.bpre) {
+          if (t.Braw != op.tcB || !t.split3 || op.tc_bn > 192) C.err = std::string(tag) + ": bad B pre-expansion";
+          C.need(t.Bx, (double)tc_bx_bytes(op.tcB_rows, op.tc_kr, t.cplx != 0), tag, "Bx");
+        }
         break;
       }
       case Op::COPY:
@@ -1355,6 +1359,7 @@ peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool en
                   : P->kind == peps_plan::EGRAD    ? build_egrad(P, (uintptr_t)ws, io, B)
                                                    : build_expect(P, (uintptr_t)ws, B);
   if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
+  tc_finish(B);
   if (!B.err.empty()) return fail(PEPS_ERR_UNSUPPORTED, "%s", B.err.c_str());
   P->ws_bytes = finish(B, &P->blob_off);   // needs the blob size: before the move
   P->ops = std::move(B.ops);
@@ -1904,7 +1909,7 @@ peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count) {
     switch (op.kind) {
       case Op::JACOBI: n += 1 + (op.smem2 > 0) + (op.blocks > 0); break;   // one CTA, cluster, refinement
       case Op::CHOL: n += 1 + (op.smem2 > 0); break;                         // one CTA, cluster
-      case Op::TC: n += op.tc.tiles_m * op.tc.tiles_n > 0; break;
+      case Op::TC: n += (op.tc.tiles_m * op.tc.tiles_n > 0) + (op.tc.bpre != 0); break;   // B expansion, GEMM
       case Op::COPY: case Op::MEMSET: break;                                  // copies, not kernels
       case Op::SKETCH: case Op::GEMM: case Op::GEMM_ATOMIC: case Op::SANDWICH: case Op::ZERO: case Op::SITE:
       case Op::PERMUTE: n += op.blocks > 0; break;

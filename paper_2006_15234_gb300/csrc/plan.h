@@ -58,6 +58,7 @@ struct Builder {
   int dt = 0;
   bool encode = false;            // encode TMA maps (real device pointers, driver present)
   std::string err;                // first encoding failure
+  size_t bx_need = 0;             // B scratch of the pre-expanded tensor-core operands (bytes)
 
   size_t alloc(size_t bytes) {
     size_t o = (top + 255) & ~(size_t)255;
@@ -114,6 +115,9 @@ void inst_derive(Inst &I, const RsvdOpts &o);
 size_t inst_scratch_bytes(const Inst &I, int dt);
 // Carve per-instance scratch out of the builder.
 void inst_alloc_scratch(Builder &B, Inst &I, int dt);
+// the B scratch of the pre-expanded tensor-core operands and their TMA maps;
+// called once after the whole schedule is emitted
+void tc_finish(Builder &B);
 // Point I's scratch at another instance's buffers (the sweep reuses one set).
 void inst_share_scratch(Inst &I, const Inst &owner);
 // Check the shape against the kernels' limits; returns "" when supported.

@@ -359,9 +359,11 @@ DigitMap mkmap(std::initializer_list<std::pair<int64_t, int64_t>> l) {
   return m;
 }
 
+// bpre: B expanded and split into the plan's B scratch before the GEMM (all
+// SPLIT3 products but the Grams, whose B is the whole N x l block)
 void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const void *Bm, int64_t rowsB, int64_t K,
              bool conjA, bool conjB, bool split3, void *C, DigitMap mm, DigitMap mn, bool conjC,
-             const double *alpha_dev) {
+             const double *alpha_dev, bool bpre = true) {
   Op op;
   op.kind = Op::TC;
   op.tag = tag;
@@ -369,11 +371,19 @@ void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const vo
   std::memset(&d, 0, sizeof d);
   const bool cplx = dtype_complex(B.dt);
   const int64_t kr = K * (cplx ? 2 : 1);
-  const int nmma = tc_pick_nmma((int)rowsB, cplx, tc_folds(split3, kr, 0));
+  const int nmma = tc_pick_nmma((int)rowsB, cplx, split3);
   const int bn = tc_tile_cols(nmma, cplx);
+  bpre = bpre && split3;
   if (B.encode) {
-    const bool ok = tc_encode_map(&d.ta, A, rowsA, kr, kr * 4, 128) && tc_encode_map(&d.tb, Bm, rowsB, kr, kr * 4, bn);
+    // bpre: B's maps point into the B scratch, encoded once its address is known (tc_finish)
+    const bool ok = tc_encode_map(&d.ta, A, rowsA, kr, kr * 4, 128) &&
+                    (bpre || tc_encode_map(&d.tb, Bm, rowsB, kr, kr * 4, bn));
     if (!ok && B.err.empty()) B.err = std::string("TMA map encoding failed for ") + tag;
+  }
+  if (bpre) {
+    d.bpre = 1;
+    d.Braw = Bm;
+    B.bx_need = std::max<size_t>(B.bx_need, (size_t)tc_bx_bytes(rowsB, kr, cplx));
   }
   d.M = (int32_t)rowsA; d.N = (int32_t)rowsB; d.Kr = (int32_t)kr;
   d.cplx = cplx; d.conjA = conjA; d.conjB = conjB; d.split3 = split3;
@@ -392,6 +402,27 @@ void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const vo
   B.ops.push_back(op);
 }
 
+}  // namespace
+
+// The plan's B scratch (after every buffer of the schedule) and the TMA maps
+// of the pre-expanded B operands, which point into it.
+void tc_finish(Builder &B) {
+  if (!B.bx_need) return;
+  void *bx = B.buf(B.bx_need);
+  for (Op &op : B.ops) {
+    if (op.kind != Op::TC || !op.tc.bpre) continue;
+    TcDesc &d = op.tc;
+    d.Bx = bx;
+    if (!B.encode) continue;
+    const int64_t nr = (int64_t)d.N * (d.cplx ? 2 : 1), pitch = (int64_t)d.Kr * 4;
+    const bool ok = tc_encode_map(&d.tb, bx, nr, d.Kr, pitch, op.tc_bn) &&
+                    tc_encode_map(&d.tb2, (char *)bx + nr * pitch, nr, d.Kr, pitch, op.tc_bn);
+    if (!ok && B.err.empty()) B.err = std::string("TMA map encoding failed for ") + op.tag;
+  }
+}
+
+namespace {
+
 // G = src^H src for an l x L block stored [j][n] (any order of n), FP64
 // accumulators, split over K.
 void emit_gram_tc(Builder &B, Inst &q, const void *src, int64_t L, const char *tag) {
@@ -399,7 +430,7 @@ void emit_gram_tc(Builder &B, Inst &q, const void *src, int64_t L, const char *t
   std::vector<std::pair<void *, int64_t>> zr{{q.G, (int64_t)q.ell * q.ell * as / 8}};
   push_zero(B, zr, tag);
   emit_tc(B, tag, src, q.ell, src, q.ell, L, true, false, true, q.G, mkmap({{BIG, q.ell}}), mkmap({{BIG, 1}}),
-          false, nullptr);
+          false, nullptr, false);
   Op &op = B.ops.back();
   const int64_t kr = op.tc_kr;
   const int64_t nkb = ceil_div(kr, 32);

@@ -59,18 +59,29 @@ using namespace peps;
 
 extern "C" peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t conjB, int32_t split3, int32_t M,
                                           int32_t N, int32_t K, const void *A, const void *B, void *C,
-                                          void *stream) {
-  if (!A || !B || !C || M < 1 || N < 1 || K < 1) return PEPS_ERR_ARG;
+                                          void *scratch, void *stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || split3 < 0 || split3 > 2) return PEPS_ERR_ARG;
+  if (split3 == 2 && !scratch) return PEPS_ERR_ARG;
   const int64_t kr = (int64_t)K * (cplx ? 2 : 1);
   const int64_t pitch = kr * 4;
   TcDesc d;
   std::memset(&d, 0, sizeof d);
-  const int nmma = tc_pick_nmma(N, cplx != 0, tc_folds(split3 != 0, kr, 0));
+  const int nmma = tc_pick_nmma(N, cplx != 0, split3 != 0);
   const int bn = tc_tile_cols(nmma, cplx != 0);
-  if (!tc_encode_map(&d.ta, A, M, kr, pitch, 128) || !tc_encode_map(&d.tb, B, N, kr, pitch, bn))
+  if (!tc_encode_map(&d.ta, A, M, kr, pitch, 128)) return PEPS_ERR_UNSUPPORTED;
+  if (split3 == 2) {
+    const int64_t nr = (int64_t)N * (cplx ? 2 : 1);
+    if (!tc_encode_map(&d.tb, scratch, nr, kr, pitch, nmma) ||
+        !tc_encode_map(&d.tb2, (char *)scratch + nr * pitch, nr, kr, pitch, nmma))
+      return PEPS_ERR_UNSUPPORTED;
+    d.bpre = 1;
+    d.Braw = B;
+    d.Bx = scratch;
+  } else if (!tc_encode_map(&d.tb, B, N, kr, pitch, bn)) {
     return PEPS_ERR_UNSUPPORTED;
+  }
   d.M = M; d.N = N; d.Kr = (int32_t)kr;
-  d.cplx = cplx; d.conjA = conjA; d.conjB = conjB; d.split3 = split3;
+  d.cplx = cplx; d.conjA = conjA; d.conjB = conjB; d.split3 = split3 != 0;
   d.tiles_m = (M + 127) / 128;
   d.tiles_n = (N + bn - 1) / bn;
   d.mm = digits1(N);

@@ -52,7 +52,9 @@ constexpr int BM = 128;
 constexpr int BKF = 32;              // floats of K per stage (one 128-byte swizzle row)
 constexpr int NWORK = 256;           // worker threads (warps 2..9)
 constexpr int NTHREADS = 64 + NWORK;
-constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a wait gives up (~1 s)
+constexpr uint32_t kWaitLimit = 1u << 24;   // polls of a teardown drain (~1 s)
+constexpr uint64_t kWaitNs = 2000000000ull;  // a pipeline wait gives up after 2 s
+constexpr uint32_t kSuspendNs = 1000;        // suspend-time hint of one pipeline poll
 constexpr int CK = 2;                // k blocks per tensor-memory accumulation chunk (SPLIT3)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -78,11 +80,32 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false (and the abort flag raised) when it gives up.
+// One poll that may suspend the thread (up to the hint) until the phase completes.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait (2 s of global time, and at most 2^26 polls); false (and the
+// abort flag raised) when it gives up.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if ((i & 1023) == 1023 && *abort_flag) return false;
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1; i < (1u << 26); ++i) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((i & 15) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kWaitNs) break;
+    }
   }
   *abort_flag = 1;
   return false;
@@ -121,6 +144,24 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// A from tensor memory: row i of the 128 x 8 operand in lane i, one 32-bit
+// column per K element, starting at column address a_tmem
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// this warp's 32 lanes, 8 consecutive columns from taddr
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -142,14 +183,16 @@ __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-__device__ __forceinline__ int64_t map_index(const DigitMap &m, int64_t i) {
+__device__ __forceinline__ int64_t map_index(const DigitMap &m, int64_t i64) {
+  uint32_t i = (uint32_t)i64;      // row / column indices are below 2^31
   int64_t off = 0;
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
     if (d >= m.n) break;
-    const int64_t r = m.radix[d];
-    off += (i % r) * m.stride[d];
-    i /= r;
+    // q = i / radix: t + i < 2^32 since t <= i < 2^31
+    const uint32_t q = (__umulhi(i, m.mul[d]) + i) >> m.shr[d];
+    off += (int64_t)(i - q * (uint32_t)m.radix[d]) * m.stride[d];
+    i = q;
   }
   return off;
 }
@@ -176,38 +219,52 @@ __device__ __forceinline__ float4 sub4(float4 a, float4 b) {
   return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
 
-template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD_> struct Layout {
+template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD_, bool BPRE_> struct Layout {
   static constexpr int BNR = CPLX ? NMMA / 2 : NMMA;   // output columns (complex or real) per tile
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = NMMA * 128;           // MMA-ready B tile
   static constexpr int RAW_BYTES = BNR * 128;          // B tile as TMA lands it
-  static constexpr int NA = SPLIT3 ? 2 : 1;            // A head (in place), A tail
+  // SPLIT3: A's head and tail go to tensor memory (ATMEM); only the raw A
+  // tile sits in shared memory.  Otherwise A is rounded in place.
+  static constexpr bool ATMEM = SPLIT3;
+  // B arrives as MMA-ready head and tail tiles (expanded and split beforehand)
+  static constexpr bool BPRE = SPLIT3 && BPRE_;
   static constexpr int NB = SPLIT3 ? 2 : 1;            // B head, B tail
   // complex: the raw B tile lands in the tail tile (read out before the tail
   // is written) or, without SPLIT3, in a buffer of its own
   static constexpr bool RAW_SEP = CPLX && !SPLIT3;
-  static constexpr int STAGE = NA * A_BYTES + NB * B_BYTES + (RAW_SEP ? RAW_BYTES : 0);
+  static constexpr int STAGE = A_BYTES + NB * B_BYTES + (RAW_SEP ? RAW_BYTES : 0);
   static constexpr int STAGES = (200 * 1024) / STAGE >= 4 ? 4 : (200 * 1024) / STAGE;
   static constexpr int SMEM = STAGES * STAGE + 1024;
   static constexpr bool FOLD = SPLIT3 && FOLD_;          // chunked accumulation (long K)
   static constexpr int ACC_COLS = NMMA;                // one accumulator set
   static constexpr int HALF = NMMA / 2;                // columns per epilogue thread
-  static constexpr int TMEM_NEED = 2 * NMMA;           // two accumulator buffers
+  // tensor-memory A stages after the two accumulator buffers: 32 head and 32
+  // tail columns (one 32-float k block of 128 rows) each
+  static constexpr int A_COLS = 64;
+  static constexpr int SA_FIT = ATMEM ? (512 - 2 * NMMA) / A_COLS : 0;
+  static constexpr int SA = SA_FIT > 4 ? 4 : SA_FIT;
+  static constexpr int A_COL0 = 2 * NMMA;
+  static constexpr int TMEM_NEED = 2 * NMMA + SA * A_COLS;
   static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   static_assert(STAGES >= 2, "two pipeline stages at least");
+  static_assert(!ATMEM || SA >= 2, "two tensor-memory A stages at least");
+  static_assert(TMEM_NEED <= 512, "tensor memory holds 512 columns");
   static_assert(NMMA % 16 == 0 && NMMA >= 16 && NMMA <= 256, "tcgen05 N for M = 128");
 };
 
 // 10 warps: each SM sub-partition (16K registers) holds 3 of them, so at most
 // 168 registers per thread
-template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD_>
+template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD_, bool BPRE_>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ TcDesc g) {
-  using L = Layout<NMMA, CPLX, SPLIT3, FOLD_>;
+  using L = Layout<NMMA, CPLX, SPLIT3, FOLD_, BPRE_>;
   constexpr int STAGES = L::STAGES;
   constexpr bool FOLD = L::FOLD;
   constexpr int HALF = L::HALF;
+  constexpr int SAD = L::SA > 0 ? L::SA : 1;   // tensor-memory A stages (ATMEM)
   __shared__ __align__(8) uint64_t full_bar[STAGES], ready_bar[STAGES], empty_bar[STAGES], done_bar;
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t a_empty[L::SA > 0 ? L::SA : 1];   // tensor-memory A stage free again
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ int64_t col_off[L::BNR];
@@ -234,11 +291,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   // accumulation chunks of an item: CK k blocks (SPLIT3) or the whole item
   auto nchunks_of = [&](int nkb) { return FOLD ? (nkb + CK - 1) / CK : 1; };
 
-  auto a_tile = [&](int s, int which) { return smem + s * L::STAGE + which * L::A_BYTES; };
-  auto b_tile = [&](int s, int which) { return smem + s * L::STAGE + L::NA * L::A_BYTES + which * L::B_BYTES; };
+  auto a_tile = [&](int s) { return smem + s * L::STAGE; };
+  auto b_tile = [&](int s, int which) { return smem + s * L::STAGE + L::A_BYTES + which * L::B_BYTES; };
   auto raw_tile = [&](int s) {
     if constexpr (!CPLX) return b_tile(s, 0);
-    else if constexpr (L::RAW_SEP) return smem + s * L::STAGE + L::NA * L::A_BYTES + L::NB * L::B_BYTES;
+    else if constexpr (L::RAW_SEP) return smem + s * L::STAGE + L::A_BYTES + L::NB * L::B_BYTES;
     else return b_tile(s, 1);
   };
 
@@ -254,6 +311,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], NWORK);
     }
+    for (int a = 0; a < L::SA; ++a) mbar_init(&a_empty[a], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -301,9 +359,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         for (int kb = 0; kb < it.nkb && !abort_flag; ++kb, ++gk) {
           const int s = gk % STAGES;
           if (gk >= STAGES && !mbar_wait(&empty_bar[s], ((gk / STAGES) - 1) & 1, &abort_flag)) break;
-          mbar_expect_tx(&full_bar[s], (uint32_t)(L::A_BYTES + L::RAW_BYTES));
-          tma_load_2d(a_tile(s, 0), &g.ta, (it.kb0 + kb) * BKF, it.m0, &full_bar[s]);
-          tma_load_2d(raw_tile(s), &g.tb, (it.kb0 + kb) * BKF, it.n0, &full_bar[s]);
+          const int x = (it.kb0 + kb) * BKF;
+          if constexpr (L::BPRE) {
+            const int nr0 = CPLX ? 2 * it.n0 : it.n0;      // first MMA row of B (Re / Im rows when complex)
+            mbar_expect_tx(&full_bar[s], (uint32_t)(L::A_BYTES + 2 * L::B_BYTES));
+            tma_load_2d(a_tile(s), &g.ta, x, it.m0, &full_bar[s]);
+            tma_load_2d(b_tile(s, 0), &g.tb, x, nr0, &full_bar[s]);
+            tma_load_2d(b_tile(s, 1), &g.tb2, x, nr0, &full_bar[s]);
+          } else {
+            mbar_expect_tx(&full_bar[s], (uint32_t)(L::A_BYTES + L::RAW_BYTES));
+            tma_load_2d(a_tile(s), &g.ta, x, it.m0, &full_bar[s]);
+            tma_load_2d(raw_tile(s), &g.tb, x, it.n0, &full_bar[s]);
+          }
           issued = gk + 1;
         }
       }
@@ -325,20 +392,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
           if (!mbar_wait(&ready_bar[s], (gk / STAGES) & 1, &abort_flag)) { alive = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t tacc = tmem + (uint32_t)(buf * L::ACC_COLS);
-          const uint32_t a0 = smem_u32(a_tile(s, 0)), b0 = smem_u32(b_tile(s, 0));
+          const uint32_t b0 = smem_u32(b_tile(s, 0));
+          if constexpr (L::ATMEM) {
+            // A head and tail from tensor memory stage gk % SA; B head and tail from shared memory
+            const uint32_t ah = tmem + (uint32_t)(L::A_COL0 + (gk % SAD) * L::A_COLS), at = ah + 32;
+            const uint32_t bt = smem_u32(b_tile(s, 1));
 #pragma unroll
-          for (int kk = 0; kk < BKF / 8; ++kk) {
-            const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
-            const uint32_t off = kk * 32;
-            mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc);
-            if (SPLIT3) {
-              const uint32_t at = smem_u32(a_tile(s, 1)), bt = smem_u32(b_tile(s, 1));
-              mma_tf32(tacc, sw128_desc(at + off), sw128_desc(b0 + off), idesc, 1u);
-              mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(bt + off), idesc, 1u);
+            for (int kk = 0; kk < BKF / 8; ++kk) {
+              const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+              const uint32_t off = kk * 32;
+              mma_tf32_ta(tacc, ah + kk * 8, sw128_desc(b0 + off), idesc, acc);
+              mma_tf32_ta(tacc, at + kk * 8, sw128_desc(b0 + off), idesc, 1u);
+              mma_tf32_ta(tacc, ah + kk * 8, sw128_desc(bt + off), idesc, 1u);
+            }
+          } else {
+            const uint32_t a0 = smem_u32(a_tile(s));
+#pragma unroll
+            for (int kk = 0; kk < BKF / 8; ++kk) {
+              const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+              const uint32_t off = kk * 32;
+              mma_tf32(tacc, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc);
             }
           }
           mma_any = true;
           mma_commit(&empty_bar[s]);
+          if (L::ATMEM) mma_commit(&a_empty[gk % SAD]);
           if (last) { mma_commit(&acc_full[buf]); ++gch; }
         }
       }
@@ -359,89 +437,111 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     const float alpha_f = (float)alpha;       // single-precision outputs: no FP64 multiplies per element
     bool alive = workers_all(!abort_flag);
     int gk = 0, items = 0;
-    for (int w = blockIdx.x; w < total && alive; w += gridDim.x, ++items) {
-      const Item it = item(w);
-      const int chunk0 = folded;              // first chunk of this item
+    // one k block: wait for its tiles (and, at a chunk boundary, read back the
+    // chunk before the last one), then prepare its operands for the MMA
+    auto kblock = [&](int kb) -> bool {
+      const int s = gk % STAGES;
+      bool ok = mbar_wait(&full_bar[s], (gk / STAGES) & 1, &abort_flag);
+      const bool fold_now = FOLD && kb % CK == 0 && kb >= 2 * CK;
+      if (fold_now) ok = ok && acc_wait();
+      // the tensor-memory A stage of this k block was last read by k block gk - SA
+      if (L::ATMEM && gk >= SAD)
+        ok = ok && mbar_wait(&a_empty[gk % SAD], ((gk / SAD) - 1) & 1, &abort_flag);
+      // a warp-wide decision suffices when no named barrier follows in the k loop (BPRE)
+      if (!(L::BPRE ? __all_sync(0xffffffffu, ok) : workers_all(ok))) return false;
+      if (fold_now) fold_body();
+      {
+        if constexpr (L::ATMEM) {
+          // A row r = 32q + lane, floats 16h .. 16h + 15 of the k block (swizzled
+          // 16-byte chunks 4h .. 4h + 3): head and tail into tensor memory
+          const int r = q * 32 + lane;
+          const unsigned char *arow = a_tile(s) + r * 128;
+          const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) +
+                                (uint32_t)(L::A_COL0 + (gk % SAD) * L::A_COLS + h * 16);
 #pragma unroll
-      for (int i = 0; i < (FOLD ? HALF : 1); ++i) facc[i] = 0.f;
-      for (int kb = 0; kb < it.nkb; ++kb, ++gk) {
-        const int s = gk % STAGES;
-        bool ok = mbar_wait(&full_bar[s], (gk / STAGES) & 1, &abort_flag);
-        // with this k block's operands in, read back the chunk before the last one
-        const bool fold_now = FOLD && kb % CK == 0 && kb >= 2 * CK;
-        if (fold_now) ok = ok && acc_wait();
-        if (!workers_all(ok)) { alive = false; break; }
-        if (fold_now) fold_body();
-        {
-          // A: head in place (+ tail tile), or nearest TF32 in place
-          float4 *A0 = (float4 *)a_tile(s, 0);
-          float4 *A1 = (float4 *)a_tile(s, 1);
+          for (int hv = 0; hv < 2; ++hv) {
+            const int c0 = 4 * h + 2 * hv;
+            const float4 x0 = *(const float4 *)(arow + ((c0 ^ (r & 7)) << 4));
+            const float4 x1 = *(const float4 *)(arow + (((c0 + 1) ^ (r & 7)) << 4));
+            const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            float hd[8], tl[8];
 #pragma unroll
-          for (int c = t; c < L::A_BYTES / 16; c += NWORK) {
-            const float4 v = A0[c];
+            for (int i = 0; i < 8; ++i) {
+              hd[i] = tf32_head(xv[i]);
+              tl[i] = xv[i] - hd[i];
+            }
+            tmem_st8(tcol + hv * 8, hd);
+            tmem_st8(tcol + 32 + hv * 8, tl);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        } else {
+          // A: nearest TF32 in place
+          float4 *A0 = (float4 *)a_tile(s);
+#pragma unroll
+          for (int c = t; c < L::A_BYTES / 16; c += NWORK) A0[c] = head4(A0[c]);
+        }
+        if constexpr (L::BPRE) {
+        } else if constexpr (CPLX) {
+          // B: complex row n -> real rows 2n (Re) and 2n+1 (Im), chunk by chunk
+          constexpr int RAWC = L::RAW_BYTES / 16;
+          constexpr int PER = (RAWC + NWORK - 1) / NWORK;
+          const unsigned char *raw = raw_tile(s);
+          unsigned char *BH = b_tile(s, 0);
+          unsigned char *BT = b_tile(s, 1);
+          float4 v[PER];
+#pragma unroll
+          for (int u = 0; u < PER; ++u) {
+            const int i = t + u * NWORK;
+            if (i < RAWC) v[u] = ((const float4 *)raw)[i];
+          }
+          if (!L::RAW_SEP) workers_sync(2);    // raw tile is the tail tile: read out before writing
+#pragma unroll
+          for (int u = 0; u < PER; ++u) {
+            const int i = t + u * NWORK;
+            if (i >= RAWC) continue;
+            const int n = i >> 3, c = (i & 7) ^ (n & 7);           // logical chunk of row n
+            const float4 x = v[u];
+            const float4 re = make_float4(x.x, sr * x.y, x.z, sr * x.w);
+            const float4 im = make_float4(s1 * x.y, s2 * x.x, s1 * x.w, s2 * x.z);
+            const int r0 = 2 * n, r1 = 2 * n + 1;
+            const float4 reh = head4(re), imh = head4(im);
+            *(float4 *)(BH + r0 * 128 + ((c ^ (r0 & 7)) << 4)) = reh;
+            *(float4 *)(BH + r1 * 128 + ((c ^ (r1 & 7)) << 4)) = imh;
+            if (SPLIT3) {
+              *(float4 *)(BT + r0 * 128 + ((c ^ (r0 & 7)) << 4)) = sub4(re, reh);
+              *(float4 *)(BT + r1 * 128 + ((c ^ (r1 & 7)) << 4)) = sub4(im, imh);
+            }
+          }
+        } else {
+          float4 *B0 = (float4 *)b_tile(s, 0);
+          float4 *B1 = (float4 *)b_tile(s, 1);
+#pragma unroll
+          for (int c = t; c < L::B_BYTES / 16; c += NWORK) {
+            const float4 v = B0[c];
             const float4 hd = head4(v);
-            if (SPLIT3) A1[c] = sub4(v, hd);
-            A0[c] = hd;
+            if (SPLIT3) B1[c] = sub4(v, hd);
+            B0[c] = hd;
           }
-          if constexpr (CPLX) {
-            // B: complex row n -> real rows 2n (Re) and 2n+1 (Im), chunk by chunk
-            constexpr int RAWC = L::RAW_BYTES / 16;
-            constexpr int PER = (RAWC + NWORK - 1) / NWORK;
-            const unsigned char *raw = raw_tile(s);
-            unsigned char *BH = b_tile(s, 0);
-            unsigned char *BT = b_tile(s, 1);
-            float4 v[PER];
-#pragma unroll
-            for (int u = 0; u < PER; ++u) {
-              const int i = t + u * NWORK;
-              if (i < RAWC) v[u] = ((const float4 *)raw)[i];
-            }
-            if (!L::RAW_SEP) workers_sync(2);    // raw tile is the tail tile: read out before writing
-#pragma unroll
-            for (int u = 0; u < PER; ++u) {
-              const int i = t + u * NWORK;
-              if (i >= RAWC) continue;
-              const int n = i >> 3, c = (i & 7) ^ (n & 7);           // logical chunk of row n
-              const float4 x = v[u];
-              const float4 re = make_float4(x.x, sr * x.y, x.z, sr * x.w);
-              const float4 im = make_float4(s1 * x.y, s2 * x.x, s1 * x.w, s2 * x.z);
-              const int r0 = 2 * n, r1 = 2 * n + 1;
-              const float4 reh = head4(re), imh = head4(im);
-              *(float4 *)(BH + r0 * 128 + ((c ^ (r0 & 7)) << 4)) = reh;
-              *(float4 *)(BH + r1 * 128 + ((c ^ (r1 & 7)) << 4)) = imh;
-              if (SPLIT3) {
-                *(float4 *)(BT + r0 * 128 + ((c ^ (r0 & 7)) << 4)) = sub4(re, reh);
-                *(float4 *)(BT + r1 * 128 + ((c ^ (r1 & 7)) << 4)) = sub4(im, imh);
-              }
-            }
-          } else {
-            float4 *B0 = (float4 *)b_tile(s, 0);
-            float4 *B1 = (float4 *)b_tile(s, 1);
-#pragma unroll
-            for (int c = t; c < L::B_BYTES / 16; c += NWORK) {
-              const float4 v = B0[c];
-              const float4 hd = head4(v);
-              if (SPLIT3) B1[c] = sub4(v, hd);
-              B0[c] = hd;
-            }
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        mbar_arrive(&ready_bar[s]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (L::ATMEM) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       }
-      if (!alive) break;
-      // the item's last chunks (FOLD), or its whole accumulator
-      const int chunk_end = chunk0 + nchunks_of(it.nkb);
+      mbar_arrive(&ready_bar[s]);
+      ++gk;
+      return true;
+    };
+    // final read-back and epilogue of an item whose k blocks were all prepared
+    auto finish = [&](const Item &it, int chunk_end) -> bool {
       if (FOLD) {
-        while (alive && folded < chunk_end) {
-          alive = workers_all(acc_wait());
-          if (alive) fold_body();
+        bool live = true;
+        while (live && folded < chunk_end) {
+          live = workers_all(acc_wait());
+          if (live) fold_body();
         }
-      } else {
-        alive = workers_all(acc_wait());
+        if (!live) return false;
+      } else if (!workers_all(acc_wait())) {
+        return false;
       }
-      if (!alive) break;
-
       // ---- epilogue of this item ----
       workers_sync(1);                        // previous item's column offsets no longer read
       for (int c = t; c < L::BNR; c += NWORK) col_off[c] = it.n0 + c < g.N ? map_index(g.mn, it.n0 + c) : 0;
@@ -495,7 +595,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         mbar_arrive(&acc_empty[folded & 1]);
         ++folded;
       }
+      return true;
+    };
+    // The epilogue of item i runs after the first k blocks of item i + 1 are
+    // prepared (lag: one chunk when folding, else the tensor-memory A stages),
+    // so that the MMAs of item i + 1 overlap it.  Every worker reaches the
+    // barrier reductions between the two k loops and at the item's end the
+    // same number of times, whichever k block it left at.
+    bool pend = false;
+    Item pit{};
+    int pend_end = 0, chunk_next = 0;
+    for (int w = blockIdx.x; w < total && alive; w += gridDim.x, ++items) {
+      const Item it = item(w);
+      const int chunk_end = chunk_next + nchunks_of(it.nkb);
+      chunk_next = chunk_end;
+      const int lag = min(it.nkb, FOLD ? CK : SAD);
+      bool ok = true;
+      for (int kb = 0; kb < lag && ok; ++kb) ok = kblock(kb);
+      if (!workers_all(ok)) { alive = false; break; }
+      if (pend && !finish(pit, pend_end)) { alive = false; break; }
+      pend = false;
+#pragma unroll
+      for (int i = 0; i < (FOLD ? HALF : 1); ++i) facc[i] = 0.f;
+      for (int kb = lag; kb < it.nkb && ok; ++kb) ok = kblock(kb);
+      if (!workers_all(ok)) { alive = false; break; }
+      pend = true;
+      pit = it;
+      pend_end = chunk_end;
     }
+    if (alive && pend) alive = finish(pit, pend_end);
     // the MMA thread's final completion signal lands before the CTA may exit
     if (alive && items > 0) mbar_wait(&done_bar, 0, &abort_flag);
   }
@@ -520,35 +648,86 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   }
 }
 
-template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD> void launch_tc(const TcDesc &d, cudaStream_t s) {
-  using L = Layout<NMMA, CPLX, SPLIT3, FOLD>;
+template <int NMMA, bool CPLX, bool SPLIT3, bool FOLD, bool BPRE>
+void launch_tc(const TcDesc &d, cudaStream_t s) {
+  using L = Layout<NMMA, CPLX, SPLIT3, FOLD, BPRE>;
+  auto kern = tc_gemm_kernel<NMMA, CPLX, SPLIT3, FOLD, BPRE>;
   static int resident = 0;     // CTAs of this instantiation that fit the whole GPU at once
   if (!resident) {
-    cudaFuncSetAttribute(tc_gemm_kernel<NMMA, CPLX, SPLIT3, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         L::SMEM);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tc_gemm_kernel<NMMA, CPLX, SPLIT3, FOLD>, NTHREADS, L::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NTHREADS, L::SMEM);
     resident = std::max(1, sms) * std::max(1, per);
   }
   const int64_t items = (int64_t)d.tiles_m * d.tiles_n * (d.ksplit > 1 ? d.ksplit : 1);
   const unsigned blocks = (unsigned)std::min<int64_t>(items, resident);
-  if (blocks) tc_gemm_kernel<NMMA, CPLX, SPLIT3, FOLD><<<blocks, NTHREADS, L::SMEM, s>>>(d);
+  if (blocks) kern<<<blocks, NTHREADS, L::SMEM, s>>>(d);
+}
+
+template <int NMMA, bool CPLX, bool FOLD> void launch_split3(const TcDesc &d, cudaStream_t s) {
+  if (d.bpre) launch_tc<NMMA, CPLX, true, FOLD, true>(d, s);
+  else launch_tc<NMMA, CPLX, true, FOLD, false>(d, s);
 }
 
 template <int NMMA> void launch_n(const TcDesc &d, cudaStream_t s) {
   // SPLIT3 items longer than two chunks fold; shorter ones keep one tensor-memory accumulation
   const bool fold = tc_folds(d.split3 != 0, d.Kr, d.ksplit > 1 ? d.kb_per_split : 0);
-  if (d.cplx) {
-    if (!d.split3) launch_tc<NMMA, true, false, false>(d, s);
-    else if (fold) launch_tc<NMMA, true, true, true>(d, s);
-    else launch_tc<NMMA, true, true, false>(d, s);
+  if constexpr (NMMA > 192) {
+    if (d.cplx) launch_tc<NMMA, true, false, false, false>(d, s);
+    else launch_tc<NMMA, false, false, false, false>(d, s);
+  } else if (d.cplx) {
+    if (!d.split3) launch_tc<NMMA, true, false, false, false>(d, s);
+    else if (fold) launch_split3<NMMA, true, true>(d, s);
+    else launch_split3<NMMA, true, false>(d, s);
   } else {
-    if (!d.split3) launch_tc<NMMA, false, false, false>(d, s);
-    else if (fold) launch_tc<NMMA, false, true, true>(d, s);
-    else launch_tc<NMMA, false, true, false>(d, s);
+    if (!d.split3) launch_tc<NMMA, false, false, false, false>(d, s);
+    else if (fold) launch_split3<NMMA, false, true>(d, s);
+    else launch_split3<NMMA, false, false>(d, s);
   }
+}
+
+// B -> Bx (bpre): each 16-byte chunk of B (two complex values, or four real
+// ones) gives its head and tail chunks; a complex row n becomes the real rows
+// 2n = (br, sr*bi) and 2n+1 = (s1*bi, s2*br), the signs encoding the
+// conjugation of A and/or B as in the in-kernel expansion.
+__global__ void tc_expand_kernel(const float4 *__restrict__ B, float4 *__restrict__ Bx, int64_t n, int64_t kr4,
+                                 int cplx, float sr, float s1, float s2) {
+  const int64_t total = n * kr4;
+  const int64_t nr = cplx ? 2 * n : n;       // MMA rows of one part (head or tail)
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / kr4, c = i - row * kr4;
+    const float4 x = B[i];
+    if (cplx) {
+      const float4 re = make_float4(x.x, sr * x.y, x.z, sr * x.w);
+      const float4 im = make_float4(s1 * x.y, s2 * x.x, s1 * x.w, s2 * x.z);
+      const float4 reh = head4(re), imh = head4(im);
+      Bx[(2 * row) * kr4 + c] = reh;
+      Bx[(2 * row + 1) * kr4 + c] = imh;
+      Bx[(nr + 2 * row) * kr4 + c] = sub4(re, reh);
+      Bx[(nr + 2 * row + 1) * kr4 + c] = sub4(im, imh);
+    } else {
+      const float4 hd = head4(x);
+      Bx[row * kr4 + c] = hd;
+      Bx[(nr + row) * kr4 + c] = sub4(x, hd);
+    }
+  }
+}
+
+void launch_expand(const TcDesc &d, cudaStream_t s) {
+  float sr = 1.f, s1 = 1.f, s2 = 1.f;
+  if (d.cplx) {
+    if (!d.conjA && !d.conjB) { sr = -1.f; s1 = 1.f; s2 = 1.f; }
+    else if (d.conjA && !d.conjB) { sr = 1.f; s1 = 1.f; s2 = -1.f; }
+    else if (!d.conjA && d.conjB) { sr = 1.f; s1 = -1.f; s2 = 1.f; }
+    else { sr = -1.f; s1 = -1.f; s2 = -1.f; }
+  }
+  const int64_t kr4 = d.Kr / 4, total = (int64_t)d.N * kr4;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+  if (blocks > 0)
+    tc_expand_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4 *)d.Braw, (float4 *)d.Bx, d.N, kr4, d.cplx,
+                                                       sr, s1, s2);
 }
 
 }  // namespace
@@ -558,14 +737,15 @@ bool tc_folds(bool split3, int64_t kr, int kb_per_split) {
   return split3 && nkb > 2 * CK;
 }
 
-int tc_pick_nmma(int N, bool cplx, bool fold) {
-  // fewest padded columns, a tile's fixed cost (its A rewrite) counted as 32
-  // columns; folding kernels keep half a tile row in registers: at most 192
+int tc_pick_nmma(int N, bool cplx, bool split3) {
+  // fewest padded columns, a tile's fixed cost (its A split) counted as 32
+  // columns; SPLIT3 kernels hold two accumulator buffers and the A stages in
+  // tensor memory (and folding ones half a tile row in registers): at most 192
   static const int cand[4] = {64, 128, 192, 256};
   int best = 64;
   int64_t best_cost = -1;
   for (int nm : cand) {
-    if (fold && nm > 192) continue;
+    if (split3 && nm > 192) continue;
     const int64_t bnr = cplx ? nm / 2 : nm;
     const int64_t tiles = (N + bnr - 1) / bnr;
     const int64_t cost = tiles * (bnr + 32);
@@ -574,13 +754,34 @@ int tc_pick_nmma(int N, bool cplx, bool fold) {
   return best;
 }
 
-void launch_tc_gemm(const TcDesc &d, int nmma, cudaStream_t s) {
+// Division by an invariant integer as multiply-high, add and shift
+// (Granlund and Montgomery, 1994): with l = ceil(log2 r) and
+// mul = floor(2^32 (2^l - r) / r) + 1, i / r = (umulhi(i, mul) + i) >> l for
+// every i < 2^31 (the sum then fits in 32 bits).
+static void fill_div(DigitMap &m) {
+  for (int d = 0; d < 4; ++d) {
+    const uint64_t r = m.radix[d] > 0 ? (uint64_t)m.radix[d] : 0x7fffffffull;
+    uint32_t l = 0;
+    while ((1ull << l) < r) ++l;
+    m.mul[d] = (uint32_t)(((1ull << 32) * ((1ull << l) - r)) / r + 1);
+    m.shr[d] = l;
+  }
+}
+
+void launch_tc_gemm(const TcDesc &desc, int nmma, cudaStream_t s) {
+  TcDesc d = desc;
+  fill_div(d.mm);
+  fill_div(d.mn);
+  if (d.bpre) {
+    if (!d.split3 || nmma > 192) return;   // never planned
+    launch_expand(d, s);
+  }
   switch (nmma) {
     case 64: launch_n<64>(d, s); break;
     case 128: launch_n<128>(d, s); break;
     case 192: launch_n<192>(d, s); break;
     default:
-      if (tc_folds(d.split3 != 0, d.Kr, d.ksplit > 1 ? d.kb_per_split : 0)) return;   // never planned
+      if (d.split3) return;   // never planned: tc_pick_nmma caps SPLIT3 at 192
       launch_n<256>(d, s);
       break;
   }

@@ -7,19 +7,28 @@
 
 namespace peps {
 
-// index -> sum_d digit_d * stride_d, digit 0 least significant (radix[d])
+// index -> sum_d digit_d * stride_d, digit 0 least significant (radix[d]).
+// mul / shr: division by radix[d] as a multiply-high and shift (filled by
+// the launcher; exact for indices below 2^31).
 struct DigitMap {
   int32_t n;
   int32_t radix[4];
   int64_t stride[4];
+  uint32_t mul[4], shr[4];
 };
 
 // C(m, n) (+)= alpha * sum_k opA(A[m][k]) opB(B[n][k]); A, B row-major with K
 // contiguous, complex interleaved when cplx.  C's element (m, n) sits at
 // C + mm(m) + mn(n) (elements of the output type: float2 or float).
+// bpre (SPLIT3 only): before the GEMM, B is rewritten once into Bx as the
+// MMA's real operand rows, head rows [0, NR) and tail rows [NR, 2 NR)
+// (NR = 2N for complex data: Re and Im rows of each complex row; N for real
+// data), so that the GEMM's B tiles arrive by TMA ready for the MMA (tb over
+// the head rows, tb2 over the tail rows).
 struct TcDesc {
   CUtensorMap ta;
   CUtensorMap tb;
+  CUtensorMap tb2;
   int32_t M, N, Kr;        // Kr = K extent in floats (2K for complex data)
   int32_t cplx, conjA, conjB, split3;
   int32_t tiles_m, tiles_n;
@@ -30,15 +39,22 @@ struct TcDesc {
   int32_t accumulate, conjC;
   int32_t atomic64;        // C holds FP64 accumulators (double / double2): atomicAdd
   int32_t ksplit, kb_per_split;   // K cut into ksplit chunks of kb_per_split 32-float blocks
+  int32_t bpre;
+  const void *Braw;        // bpre: B as given (N rows of Kr floats)
+  void *Bx;                // bpre: tc_bx_bytes(N, Kr, cplx) bytes
   uint32_t *status;
 };
 
-// MMA width (64, 128, 192 or 256 accumulator columns) for an N extent: a
-// tile covers nmma output columns (real) or nmma / 2 (complex, Re/Im pairs).
+// bytes of the pre-expanded B operand (head and tail rows)
+inline int64_t tc_bx_bytes(int64_t n, int64_t kr, bool cplx) { return n * kr * 4 * 2 * (cplx ? 2 : 1); }
+
+// MMA width (64, 128, 192 or 256 accumulator columns; SPLIT3 at most 192) for
+// an N extent: a tile covers nmma output columns (real) or nmma / 2 (complex,
+// Re/Im pairs).
 // Whether a SPLIT3 product folds its accumulation chunks (K longer than two
 // chunks); kb_per_split > 0 when K is split across CTAs.
 bool tc_folds(bool split3, int64_t kr, int kb_per_split);
-int tc_pick_nmma(int N, bool cplx, bool fold);
+int tc_pick_nmma(int N, bool cplx, bool split3);
 inline int tc_tile_cols(int nmma, bool cplx) { return cplx ? nmma / 2 : nmma; }
 void launch_tc_gemm(const TcDesc &d, int nmma, cudaStream_t s);
 

@@ -144,7 +144,7 @@ def load():
     lib.peps_plan_profile.restype = st
     lib.peps_plan_profile.argtypes = [vp, vp, C.c_size_t, vp, C.POINTER(C.c_double)]
     lib.peps_debug_tc_gemm.restype = st
-    lib.peps_debug_tc_gemm.argtypes = [C.c_int32] * 7 + [vp, vp, vp, vp]
+    lib.peps_debug_tc_gemm.argtypes = [C.c_int32] * 7 + [vp, vp, vp, vp, vp]
     lib.peps_plan_validate.restype = st
     lib.peps_plan_validate.argtypes = [vp, vp, C.c_size_t, C.POINTER(EinsumsvdIO)]
     lib.peps_grad_plan.restype = st
@@ -612,14 +612,24 @@ def boundary_contract_static(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=
 
 
 def debug_tc_gemm(A, B, conjA=False, conjB=False, split3=False, stream=None):
-    """C = opA(A) @ opB(B)^T on the tensor-core GEMM (A: M x K, B: N x K)."""
+    """C = opA(A) @ opB(B)^T on the tensor-core GEMM (A: M x K, B: N x K).
+    split3: False / 0 plain TF32, True / 1 3xTF32, 2 3xTF32 with B expanded
+    and split beforehand (scratch allocated here)."""
     import torch
     lib = load()
     cplx = A.is_complex()
     M, K = A.shape
     N = B.shape[0]
     C_ = torch.empty((M, N), dtype=A.dtype, device=A.device)
-    _check(lib.peps_debug_tc_gemm(int(cplx), int(conjA), int(conjB), int(split3), M, N, K,
+    mode = int(split3)
+    scratch = None
+    if mode == 2:
+        scratch = torch.empty((32 if cplx else 8) * N * K, dtype=torch.uint8, device=A.device)
+    _check(lib.peps_debug_tc_gemm(int(cplx), int(conjA), int(conjB), mode, M, N, K,
                                   C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
-                                  C.c_void_p(C_.data_ptr()), _stream_handle(stream)))
+                                  C.c_void_p(C_.data_ptr()),
+                                  C.c_void_p(scratch.data_ptr() if scratch is not None else None),
+                                  _stream_handle(stream)))
+    if scratch is not None:
+        torch.cuda.synchronize(A.device)     # scratch is released on return
     return C_

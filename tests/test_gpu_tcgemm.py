@@ -1,6 +1,7 @@
 """The tensor-core GEMM (tcgen05 kind::tf32, TMA-fed) against an FP64 torch
 reference: complex and real, every conjugation mode, plain TF32 and 3xTF32
-products, shapes spanning several 128-row tiles with ragged M, N and K tails.
+products (B expanded inside the GEMM, or beforehand: mode 2), shapes
+spanning several 128-row tiles with ragged M, N and K tails.
 
 Normwise bound |C - C_ref|_F <= tol |A|_F |B|_F: TF32 keeps 10+1 mantissa
 bits (relative rounding ~2^-11 per operand), 3xTF32 ~2^-21.
@@ -26,7 +27,7 @@ def _ref(A, B, cA, cB):
     return A64 @ B64.T
 
 
-@pytest.mark.parametrize("split3,tol", [(False, 2e-3), (True, 2e-6)])
+@pytest.mark.parametrize("split3,tol", [(False, 2e-3), (True, 2e-6), (2, 2e-6)])
 @pytest.mark.parametrize("cA,cB", [(False, False), (True, False), (False, True), (True, True)])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_complex(shape, cA, cB, split3, tol):
@@ -41,7 +42,7 @@ def test_complex(shape, cA, cB, split3, tol):
     assert err <= tol, float(err)
 
 
-@pytest.mark.parametrize("split3,tol", [(False, 2e-3), (True, 2e-6)])
+@pytest.mark.parametrize("split3,tol", [(False, 2e-3), (True, 2e-6), (2, 2e-6)])
 @pytest.mark.parametrize("shape", [(128, 64, 32), (300, 200, 92), (257, 129, 1000), (150, 190, 64),
                                    (100, 40, 36)])
 def test_real(shape, split3, tol):
@@ -56,9 +57,10 @@ def test_real(shape, split3, tol):
     assert err <= tol, float(err)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("K", [4096, 16384])
-def test_split3_long_sums_unbiased(cplx, K):
+def test_split3_long_sums_unbiased(cplx, K, mode):
     """Same-sign data, long K: an accumulator that truncates the low bits of
     every addend drifts by a relative ~1e-8 per K value (1.6e-4 at K = 16384);
     3xTF32 products accumulated with round-to-nearest stay at FP32 level.
@@ -71,7 +73,7 @@ def test_split3_long_sums_unbiased(cplx, K):
     if cplx:
         A = A * torch.exp(0.3j * torch.rand(M, K, device="cuda", generator=g))
         B = B * torch.exp(-0.3j * torch.rand(N, K, device="cuda", generator=g))
-    C = libpeps.debug_tc_gemm(A, B, False, False, True)
+    C = libpeps.debug_tc_gemm(A, B, False, False, mode)
     torch.cuda.synchronize()
     R = _ref(A, B, False, False)
     S = A.abs().double() @ B.abs().double().T
