@@ -36,9 +36,20 @@ constexpr int kCholCTAs = 8;     // CTAs of the cluster Cholesky
 // a cluster holding the rows in distributed shared memory, or one CTA on the
 // caller's global scratch (too large for either).
 enum CholRoute { kCholSmem = 0, kCholCluster = 1, kCholGlobal = 2 };
-__host__ __device__ inline int64_t chol_cluster_bytes(int n, int es, bool needT) {
+// Shared memory of the cluster Cholesky with panels of nb rows: the CTA's
+// rows of W (and T), one panel of nb rows and an nb x nb block.
+__host__ __device__ inline int64_t chol_cluster_bytes_nb(int n, int es, bool needT, int nb) {
   const int64_t cap = (n + kCholCTAs - 1) / kCholCTAs;
-  return (needT ? 2 : 1) * cap * n * es + (int64_t)n * es;
+  return ((needT ? 2 : 1) * cap * n + (int64_t)nb * n + (int64_t)nb * nb) * es;
+}
+// widest panel (16, 8, 4, 2 or 1 rows) that fits
+__host__ __device__ inline int chol_cluster_nb(int n, int es, bool needT) {
+  int nb = 16;
+  while (nb > 1 && chol_cluster_bytes_nb(n, es, needT, nb) > kSmemLimit) nb >>= 1;
+  return nb;
+}
+__host__ __device__ inline int64_t chol_cluster_bytes(int n, int es, bool needT) {
+  return chol_cluster_bytes_nb(n, es, needT, chol_cluster_nb(n, es, needT));
 }
 __host__ __device__ inline int chol_route(int n, int es, bool needT) {
   if ((int64_t)n * n * es <= kSmemLimit) return kCholSmem;
@@ -222,12 +233,15 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
 
 // Cluster Cholesky for l beyond one CTA's shared memory: the rows of W (then
 // R) and of T = R^+ are dealt round-robin to kCholCTAs CTAs (row i on CTA
-// i mod kCholCTAs), each in its own shared memory.  Right-looking over the
-// pivots: the owner of row j takes the square root and scales the row, one
-// cluster barrier publishes it, every CTA copies it through distributed
-// shared memory and updates its own rows below.  R^+ is formed the same way
-// from the last row up (row k of T is final once every later row has been
-// added into it).  Same outputs and pivot rule as chol_kernel.
+// i mod kCholCTAs), each in its own shared memory.  Blocked right-looking
+// over panels of nb pivots: after one cluster barrier every CTA copies the
+// panel's rows through distributed shared memory, factors the panel itself
+// (the same arithmetic in every CTA, so the copies agree), and applies the
+// panel to its own rows below; the owners keep the final panel rows.  R^+ is
+// formed the same way from the last panel up (a row of T is final once every
+// later row has been added into it).  Each element receives its updates in
+// the pivot order of the unblocked algorithm.  Same outputs and pivot rule as
+// chol_kernel.
 template <class T>
 __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
     chol_cluster_kernel(const CholDesc *__restrict__ descs) {
@@ -240,14 +254,18 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
   const int n = g.n;
   const bool needT = g.T != nullptr;
   if (chol_route(n, (int)sizeof(T), needT) != kCholCluster) return;   // uniform over the cluster
+  const int nb = chol_cluster_nb(n, (int)sizeof(T), needT);
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ double red[32];
   const int cap = (n + kCholCTAs - 1) / kCholCTAs;
   const int nloc = rank < n ? (n - rank + kCholCTAs - 1) / kCholCTAs : 0;   // rows rank + kCholCTAs * li
   T *Wl = (T *)dyn;
   T *Tl = Wl + (int64_t)cap * n;
-  T *buf = Tl + (needT ? (int64_t)cap * n : 0);
+  T *P = Tl + (needT ? (int64_t)cap * n : 0);    // nb panel rows, full width
+  T *B = P + (int64_t)nb * n;                     // nb x nb block of R (inverse phase)
   const Acc *G = (const Acc *)g.G;
+  // first local row index with global row >= r
+  auto first_li = [&](int r) { return r - rank <= 0 ? 0 : (r - rank + kCholCTAs - 1) / kCholCTAs; };
 
   double md = 0.0;
   for (int i = threadIdx.x; i < n; i += NT) md = fmax(md, re(G[(int64_t)i * n + i]));
@@ -263,12 +281,31 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
     Wl[t] = v;
     if (needT) Tl[t] = zero<T>();
   }
-  __syncthreads();
 
-  for (int j = 0; j < n; ++j) {
-    const int owner = j % kCholCTAs;
-    if (rank == owner) {
-      T *row = Wl + (int64_t)(j / kCholCTAs) * n;
+  // panel rows of this CTA back into its rows (after every CTA has copied the panel)
+  auto keep_panel = [&](T *dst, int j0, int jb, int c0) {
+    for (int p = 0; p < jb; ++p) {
+      const int j = j0 + p;
+      if (j % kCholCTAs != rank) continue;
+      T *row = dst + (int64_t)(j / kCholCTAs) * n;
+      for (int k = c0 + threadIdx.x; k < n; k += NT) row[k] = P[(int64_t)p * n + k];
+    }
+  };
+
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = min(nb, n - j0);
+    cluster.sync();                    // earlier panels applied everywhere and copied by everyone
+    if (j0 > 0) keep_panel(Wl, j0 - nb, nb, j0 - nb);
+    __syncthreads();                   // the panel buffer is read out
+    const int w = n - j0;
+    for (int64_t t = threadIdx.x; t < (int64_t)jb * w; t += NT) {
+      const int p = (int)(t / w), k = j0 + (int)(t % w), j = j0 + p;
+      P[(int64_t)p * n + k] = cluster.map_shared_rank(Wl, j % kCholCTAs)[(int64_t)(j / kCholCTAs) * n + k];
+    }
+    __syncthreads();
+    for (int p = 0; p < jb; ++p) {
+      const int j = j0 + p;
+      T *row = P + (int64_t)p * n;
       const double dj = re(row[j]);
       const bool dead = !(dj > thr) || !(md > 0.0);
       __syncthreads();                 // every thread has read the pivot before the row changes
@@ -279,51 +316,91 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
         const Real rinv = (Real)(1.0 / r);
         for (int k = j + threadIdx.x; k < n; k += NT) row[k] = k == j ? real_scalar<T>(r) : scale(row[k], rinv);
       }
+      __syncthreads();
+      // later rows of the panel: W[i][k] -= conj(R[j][i]) R[j][k], k >= i
+      const int rem = jb - p - 1;
+      for (int64_t t = threadIdx.x; t < (int64_t)rem * w; t += NT) {
+        const int pp = p + 1 + (int)(t / w), k = j0 + (int)(t % w), i = j0 + pp;
+        if (k < i) continue;
+        T *x = P + (int64_t)pp * n + k;
+        *x = sub(*x, mul(conj_(row[i]), row[k]));
+      }
+      __syncthreads();
     }
-    cluster.sync();                    // row j of R is final and visible
-    const T *src = cluster.map_shared_rank(Wl, owner) + (int64_t)(j / kCholCTAs) * n;
-    for (int k = j + threadIdx.x; k < n; k += NT) buf[k] = src[k];
-    __syncthreads();
-    // W[i][k] -= conj(R[j][i]) R[j][k] for this CTA's rows i > j, k >= i
-    const int li0 = j + 1 - rank <= 0 ? 0 : (j + 1 - rank + kCholCTAs - 1) / kCholCTAs;
+    // this CTA's rows below the panel
+    const int li0 = first_li(j0 + jb);
     for (int64_t t = threadIdx.x; t < (int64_t)(nloc - li0) * n; t += NT) {
       const int li = li0 + (int)(t / n), k = (int)(t % n), i = rank + kCholCTAs * li;
       if (k < i) continue;
-      T *w = Wl + (int64_t)li * n + k;
-      *w = sub(*w, mul(conj_(buf[i]), buf[k]));
+      T x = Wl[(int64_t)li * n + k];
+      for (int p = 0; p < jb; ++p) x = sub(x, mul(conj_(P[(int64_t)p * n + i]), P[(int64_t)p * n + k]));
+      Wl[(int64_t)li * n + k] = x;
     }
-    __syncthreads();
+  }
+  cluster.sync();                      // the last panel copied by everyone
+  {
+    const int j0 = ((n - 1) / nb) * nb;
+    keep_panel(Wl, j0, n - j0, j0);
   }
 
   if (needT) {
-    // right-looking R^+: Tl rows hold sum_{l > i, l done} R[i][l] T[l][c] until row i is finalised
-    for (int k = n - 1; k >= 0; --k) {
-      const int owner = k % kCholCTAs, lk = k / kCholCTAs;
-      if (rank == owner) {
-        const double rkk = re(Wl[(int64_t)lk * n + k]);
-        T *trow = Tl + (int64_t)lk * n;
+    cluster.sync();                    // every row of R final
+    // panels of rows [k0, k0 + kb) from the bottom; Tl rows hold
+    // sum_{l > i, l done} R[i][l] T[l][c] until row i is finalised
+    int prev0 = -1, prevb = 0;
+    for (int k1 = n; k1 > 0; k1 -= nb) {
+      const int k0 = max(0, k1 - nb), kb = k1 - k0;
+      if (prev0 >= 0) {
+        cluster.sync();                // previous panel applied everywhere and copied by everyone
+        keep_panel(Tl, prev0, prevb, prev0);
+        __syncthreads();               // the panel buffer is read out
+      }
+      const int w = n - k0;
+      for (int64_t t = threadIdx.x; t < (int64_t)kb * w; t += NT) {
+        const int p = (int)(t / w), c = k0 + (int)(t % w), k = k0 + p;
+        const int64_t o = (int64_t)(k / kCholCTAs) * n;
+        P[(int64_t)p * n + c] = cluster.map_shared_rank(Tl, k % kCholCTAs)[o + c];
+        if (c < k1) B[p * nb + (c - k0)] = cluster.map_shared_rank(Wl, k % kCholCTAs)[o + c];
+      }
+      __syncthreads();
+      for (int p = kb - 1; p >= 0; --p) {
+        const int k = k0 + p;
+        T *trow = P + (int64_t)p * n;
+        const double rkk = re(B[p * nb + p]);
         if (rkk == 0.0) {
           for (int c = k + threadIdx.x; c < n; c += NT) trow[c] = zero<T>();
         } else {
           const Real ninv = (Real)(-1.0 / rkk);
-          for (int c = k + threadIdx.x; c < n; c += NT)
-            trow[c] = c == k ? real_scalar<T>(1.0 / rkk) : scale(trow[c], ninv);
+          for (int c = k + threadIdx.x; c < n; c += NT) trow[c] = c == k ? real_scalar<T>(1.0 / rkk) : scale(trow[c], ninv);
         }
+        __syncthreads();
+        // earlier rows of the panel: T[i][c] += R[i][k] T[k][c], c >= k
+        const int m = n - k;
+        for (int64_t t = threadIdx.x; t < (int64_t)p * m; t += NT) {
+          const int pi = (int)(t / m), c = k + (int)(t % m);
+          T *x = P + (int64_t)pi * n + c;
+          *x = fma_(B[pi * nb + p], trow[c], *x);
+        }
+        __syncthreads();
       }
-      cluster.sync();                  // row k of T is final and visible
-      const T *src = cluster.map_shared_rank(Tl, owner) + (int64_t)lk * n;
-      for (int c = k + threadIdx.x; c < n; c += NT) buf[c] = src[c];
-      __syncthreads();
-      const int li1 = k - rank <= 0 ? 0 : (k - rank + kCholCTAs - 1) / kCholCTAs;   // rows i < k
-      const int m = n - k;
-      for (int64_t t = threadIdx.x; t < (int64_t)li1 * m; t += NT) {
-        const int li = (int)(t / m), c = k + (int)(t % m);
-        T *acc = Tl + (int64_t)li * n + c;
-        *acc = fma_(Wl[(int64_t)li * n + k], buf[c], *acc);
+      // this CTA's rows above the panel
+      const int li1 = first_li(k0);    // rows i < k0: local indices below li1
+      for (int64_t t = threadIdx.x; t < (int64_t)li1 * w; t += NT) {
+        const int li = (int)(t / w), c = k0 + (int)(t % w);
+        T x = Tl[(int64_t)li * n + c];
+        for (int p = kb - 1; p >= 0; --p) {
+          const int k = k0 + p;
+          if (c >= k) x = fma_(Wl[(int64_t)li * n + k], P[(int64_t)p * n + c], x);
+        }
+        Tl[(int64_t)li * n + c] = x;
       }
-      __syncthreads();
+      prev0 = k0;
+      prevb = kb;
     }
+    cluster.sync();
+    keep_panel(Tl, prev0, prevb, prev0);
   }
+  __syncthreads();
 
   // outputs: R (upper, zero below), T, R * Rprev, R in single precision
   T *R = (T *)g.R;
@@ -340,9 +417,9 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
       }
     }
     if (g.Rprev) {
-      const T *P = (const T *)g.Rprev;
+      const T *Rp = (const T *)g.Rprev;
       T sacc = zero<T>();
-      for (int l = i; l <= k; ++l) sacc = fma_(Wl[(int64_t)li * n + l], P[(int64_t)l * n + k], sacc);
+      for (int l = i; l <= k; ++l) sacc = fma_(Wl[(int64_t)li * n + l], Rp[(int64_t)l * n + k], sacc);
       ((T *)g.Rout)[o] = sacc;
     }
   }
@@ -373,11 +450,11 @@ __device__ __forceinline__ float jacobi_rotate_params(typename Traits<T>::Real a
   return rel;
 }
 
-template <class T>
+// kRegs: columns of up to 32 * kRegs rows stay in registers
+template <class T, int kRegs = (sizeof(T) <= 8 ? 16 : 8)>
 __device__ float jacobi_pair(T *a, T *b, int n, float tol) {
   using R = typename Traits<T>::Real;
   const int lane = threadIdx.x & 31;
-  constexpr int kRegs = sizeof(T) <= 8 ? 16 : 8;   // columns up to 32 * kRegs rows stay in registers
   R al = 0, be = 0;
   T ga = zero<T>();
   R c = 0, sn = 0;
@@ -493,11 +570,15 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict
 // one SM's shared memory, eight CTAs hold the columns in distributed shared
 // memory and all column pairs of a round-robin round rotate in parallel (one
 // warp per pair, any CTA reaching any column through the cluster window),
-// with a cluster barrier between rounds.
+// with a cluster barrier between rounds.  18 warps per CTA: the 144 warps of
+// the cluster take every pair of a round at once up to l = 288, with columns
+// of up to 288 rows (160 in FP64 complex) held in registers.
 constexpr int kClusterCTAs = 8;
+constexpr int NTJ = 576;
+template <class T> __host__ __device__ constexpr int jacobi_regs() { return sizeof(T) <= 8 ? 9 : 5; }
 
 template <class T>
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NT)
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NTJ)
     jacobi_cluster_kernel(const JacobiDesc *__restrict__ descs) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -511,7 +592,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NT)
   T *local = (T *)dyn;
   const int cpc = (n + kClusterCTAs - 1) / kClusterCTAs;     // columns per CTA
   const T *Rb = (const T *)g.Rb;
-  for (int64_t t = threadIdx.x; t < (int64_t)cpc * n; t += NT) {
+  for (int64_t t = threadIdx.x; t < (int64_t)cpc * n; t += NTJ) {
     const int lc = (int)(t / n), r = (int)(t % n), c = rank * cpc + lc;
     local[t] = c < n ? conj_(Rb[(int64_t)c * n + r]) : zero<T>();
   }
@@ -523,7 +604,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NT)
   };
   const int n2 = n + (n & 1);
   const int lane = threadIdx.x & 31;
-  const int gw = rank * (NT / 32) + (threadIdx.x >> 5), nwarps = kClusterCTAs * NT / 32;
+  const int gw = rank * (NTJ / 32) + (threadIdx.x >> 5), nwarps = kClusterCTAs * NTJ / 32;
   const double tol = 2.0 * sqrt((double)n) * Eps<T>::v;
   const double stop_tol = 8.0 * tol;
   float *root_max = cluster.map_shared_rank(&cluster_max, 0);
@@ -539,7 +620,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NT)
         else { a = (r + i) % (n2 - 1); b = (r - i + (n2 - 1)) % (n2 - 1); }
         if (a > b) { const int t = a; a = b; b = t; }
         if (b >= n) continue;
-        mine = fmaxf(mine, jacobi_pair(col(a), col(b), n, (float)tol));
+        mine = fmaxf(mine, jacobi_pair<T, jacobi_regs<T>()>(col(a), col(b), n, (float)tol));
       }
       cluster.sync();
     }
@@ -557,7 +638,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NT)
     atomicOr(g.status, STATUS_JACOBI_NOCONV);
   T *Mg = (T *)g.Mw;
   const int w = threadIdx.x >> 5;
-  for (int lc = w; lc < cpc; lc += NT / 32) {
+  for (int lc = w; lc < cpc; lc += NTJ / 32) {
     const int c = rank * cpc + lc;
     if (c >= n) break;
     double s2 = 0.0;
@@ -704,7 +785,7 @@ void jacobi_t(const JacobiDesc *d, int nd, int smem, int cluster_smem, int nmax,
     set = true;
   }
   if (smem >= 0) jacobi_kernel<T><<<nd, NT, smem, s>>>(d);
-  if (cluster_smem > 0) jacobi_cluster_kernel<T><<<nd * kClusterCTAs, NT, cluster_smem, s>>>(d);
+  if (cluster_smem > 0) jacobi_cluster_kernel<T><<<nd * kClusterCTAs, NTJ, cluster_smem, s>>>(d);
   if (nmax > 0) sigma_refine_kernel<T><<<nd * nmax, NT, 0, s>>>(d, nmax);
 }
 template <class T> void finalize_t(const FinalizeDesc *d, int nd, cudaStream_t s) {

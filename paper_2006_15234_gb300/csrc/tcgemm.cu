@@ -178,6 +178,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 columns without the wait (the caller waits once for several loads)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // nearest TF32 value (ties away from zero): exact input to the tensor core
 __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
@@ -583,13 +595,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((folded & 1) * L::ACC_COLS + h * HALF);
+        // up to 96 columns per round of loads (one wait per round)
+        constexpr int GRP = HALF > 96 ? 64 : HALF;
 #pragma unroll 1
-        for (int c0 = 0; c0 < HALF; c0 += 16) {
-          float v[16];
-          tmem_ld16(base + c0, v);
-          if (m >= g.M) continue;
+        for (int g0 = 0; g0 < HALF; g0 += GRP) {
+          float v[GRP];
 #pragma unroll
-          for (int i = 0; i < 16; i += STEP) store(c0 + i, v[i], CPLX ? v[(i + 1) & 15] : 0.f);
+          for (int c0 = 0; c0 < GRP; c0 += 16) tmem_ld16_nowait(base + g0 + c0, &v[c0]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (m < g.M) {
+#pragma unroll
+            for (int i = 0; i < GRP; i += STEP) store(g0 + i, v[i], CPLX ? v[i + 1] : 0.f);
+          }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&acc_empty[folded & 1]);
