@@ -1154,7 +1154,8 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           C.need(j.Rb, es * (double)j.n * j.n, tag, "Rb");
           C.need(j.Mw, es * (double)j.n * j.n, tag, "Mw");
           if (op.smem < small_smem_bytes(dt, j.n)) C.err = std::string(tag) + ": shared memory too small";
-          if (op.smem2 < jacobi_cluster_smem_bytes(dt, j.n)) C.err = std::string(tag) + ": cluster shared memory too small";
+          if (op.smem2 < jacobi_block_smem_bytes(dt, j.n) || op.smem3 < jacobi_cluster_smem_bytes(dt, j.n))
+            C.err = std::string(tag) + ": cluster shared memory too small";
           if (op.blocks < j.n) C.err = std::string(tag) + ": sigma refinement grid too small";
           C.need(j.sig, 8.0 * j.n, tag, "sig");
         }
@@ -1394,7 +1395,9 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
         launch_sandwich(dt, (const SandwichDesc *)d, pre, op.nd, op.blocks, op.smem, s);
         break;
       case Op::CHOL: launch_chol(op.wide ? (dt | 2) : dt, (const CholDesc *)d, op.nd, op.smem, op.smem2, s); break;
-      case Op::JACOBI: launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, (int)op.blocks, s); break;
+      case Op::JACOBI:
+        launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, op.smem3, (int)op.blocks, s);
+        break;
       case Op::FINALIZE: launch_finalize(dt, (const FinalizeDesc *)d, op.nd, s); break;
       case Op::ZERO: launch_zero((const ZeroDesc *)d, pre, op.nd, op.blocks, s); break;
       case Op::SITE: launch_site(dt, (const SiteDesc *)d, pre, op.nd, op.blocks, s); break;
@@ -1907,7 +1910,7 @@ peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count) {
   int64_t n = 0;
   for (const Op &op : plan->ops) {
     switch (op.kind) {
-      case Op::JACOBI: n += 1 + (op.smem2 > 0) + (op.blocks > 0); break;   // one CTA, cluster, refinement
+      case Op::JACOBI: n += 1 + (op.smem2 > 0) + (op.smem3 > 0) + (op.blocks > 0); break;   // one CTA, clusters, refinement
       case Op::CHOL: n += 1 + (op.smem2 > 0); break;                         // one CTA, cluster
       case Op::TC: n += (op.tc.tiles_m * op.tc.tiles_n > 0) + (op.tc.bpre != 0); break;   // B expansion, GEMM
       case Op::COPY: case Op::MEMSET: break;                                  // copies, not kernels

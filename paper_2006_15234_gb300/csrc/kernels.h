@@ -154,8 +154,11 @@ void launch_sketch(int dt, const SketchDesc *d, const int64_t *prefix, int nd,
 void launch_chol(int dt, const CholDesc *d, int nd, int smem, int cluster_smem, cudaStream_t s);
 // per-CTA shared memory of the cluster Cholesky for n x n (0: not routed there)
 int chol_cluster_smem_bytes(int dt, int n, bool needT);
-void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int cluster_smem, int nmax, cudaStream_t s);
-int jacobi_cluster_smem_bytes(int dt, int n);   // per-CTA shared memory of the cluster Jacobi (0: not used)
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int block_smem, int cluster_smem, int nmax,
+                   cudaStream_t s);
+// per-CTA shared memory of the block-cyclic / column-window cluster Jacobi (0: not used for n)
+int jacobi_block_smem_bytes(int dt, int n);
+int jacobi_cluster_smem_bytes(int dt, int n);
 int small_smem_bytes(int dt, int n);   // shared memory of chol / jacobi for n x n (0: global)
 void launch_finalize(int dt, const FinalizeDesc *d, int nd, cudaStream_t s);
 void launch_site(int dt, const SiteDesc *d, const int64_t *prefix, int nd, int64_t blocks,

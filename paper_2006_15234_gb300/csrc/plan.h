@@ -21,7 +21,8 @@ struct Op {
   int nd = 0;
   int64_t blocks = 0;
   int smem = 0;
-  int smem2 = 0;          // second kernel of the launch (cluster Jacobi)
+  int smem2 = 0;          // second kernel of the launch (cluster Cholesky, block-cyclic cluster Jacobi)
+  int smem3 = 0;          // third kernel of the launch (column-window cluster Jacobi)
   bool wide = false;      // CHOL: run in FP64 on single-precision data
   ScalarDesc scalar{};
   size_t aux_off[3] = {0, 0, 0};  // blob offsets of the scalar's device arrays

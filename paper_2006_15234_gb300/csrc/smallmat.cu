@@ -570,12 +570,22 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict
 // one SM's shared memory, eight CTAs hold the columns in distributed shared
 // memory and all column pairs of a round-robin round rotate in parallel (one
 // warp per pair, any CTA reaching any column through the cluster window),
-// with a cluster barrier between rounds.  18 warps per CTA: the 144 warps of
+// with a cluster barrier between rounds (for l whose four column blocks do
+// not fit the block-cyclic kernel below).  18 warps per CTA: the 144 warps of
 // the cluster take every pair of a round at once up to l = 288, with columns
 // of up to 288 rows (160 in FP64 complex) held in registers.
 constexpr int kClusterCTAs = 8;
 constexpr int NTJ = 576;
 template <class T> __host__ __device__ constexpr int jacobi_regs() { return sizeof(T) <= 8 ? 9 : 5; }
+// column blocks of the block-cyclic cluster Jacobi (below)
+constexpr int kJB = 2 * kClusterCTAs;
+__host__ __device__ inline int jacobi_bs(int n) { return (n + kJB - 1) / kJB; }
+__host__ __device__ inline int64_t jacobi_block_bytes(int n, int es) { return 4LL * jacobi_bs(n) * n * es; }
+// 0: one CTA; 1: block-cyclic cluster; 2: column-window cluster
+__host__ __device__ inline int jacobi_route(int n, int es) {
+  if ((int64_t)n * n * es <= kSmemLimit) return 0;
+  return jacobi_block_bytes(n, es) <= kSmemLimit ? 1 : 2;
+}
 
 template <class T>
 __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NTJ)
@@ -585,7 +595,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NTJ)
   const int rank = (int)cluster.block_rank();
   const JacobiDesc &g = descs[blockIdx.x / kClusterCTAs];
   const int n = g.n;
-  if ((int64_t)n * n * sizeof(T) <= kSmemLimit) return;      // handled by the one-CTA kernel
+  if (jacobi_route(n, (int)sizeof(T)) != 2) return;         // one CTA, or the block-cyclic kernel
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ float cta_max;
   __shared__ float cluster_max;
@@ -644,6 +654,129 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NTJ)
     double s2 = 0.0;
     for (int r = lane; r < n; r += 32) {
       const T v = local[(int64_t)lc * n + r];
+      Mg[(int64_t)c * n + r] = v;
+      s2 += (double)abs2(v);
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) g.sig[c] = sqrt(s2);
+  }
+  cluster.sync();   // keep this CTA's shared memory alive until every peer is done with it
+}
+
+// Block-cyclic one-sided Jacobi on a cluster: the l columns form 16 blocks;
+// each CTA holds two of them in its own shared memory and rotates all pairs
+// between (and once per sweep within) its two blocks with block-level
+// synchronisation only; between these stages the blocks move to other CTAs
+// on a round-robin tournament (block position p >= 1 goes to p + 1, 15 wraps
+// to 1), so that after 15 moves every pair of blocks has met once and each
+// block is back home.  One cluster barrier per move instead of one per
+// round, and column data crosses the cluster only when blocks move.
+
+template <class T>
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NTJ)
+    jacobi_block_kernel(const JacobiDesc *__restrict__ descs) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const JacobiDesc &g = descs[blockIdx.x / kClusterCTAs];
+  const int n = g.n;
+  if (jacobi_route(n, (int)sizeof(T)) != 1) return;          // uniform over the cluster
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ float cta_max;
+  __shared__ float cluster_max;
+  const int bs = jacobi_bs(n);
+  const int64_t bsz = (int64_t)bs * n;                       // elements of one block
+  T *const set0 = (T *)dyn, *const set1 = (T *)dyn + 2 * bsz; // current and next (two slots each)
+  const int pos0 = rank, pos1 = kJB - 1 - rank;               // tournament positions of the two slots
+  // block at position p after s moves (block b starts at position b)
+  auto block_at = [&](int p, int s) { return p == 0 ? 0 : 1 + ((p - 1 - s) % (kJB - 1) + (kJB - 1)) % (kJB - 1); };
+  auto valid = [&](int b) { return max(0, min(bs, n - b * bs)); };
+  const T *Rb = (const T *)g.Rb;
+  T *cs = set0;
+  for (int sl = 0; sl < 2; ++sl)
+    for (int64_t t = threadIdx.x; t < bsz; t += NTJ) {
+      const int j = (int)(t / n), r = (int)(t % n), c = (sl ? pos1 : pos0) * bs + j;
+      cs[sl * bsz + t] = c < n ? conj_(Rb[(int64_t)c * n + r]) : zero<T>();
+    }
+  if (threadIdx.x == 0) cluster_max = 0.f;
+  cluster.sync();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nw = NTJ / 32;
+  const double tol = 2.0 * sqrt((double)n) * Eps<T>::v;
+  const double stop_tol = 8.0 * tol;
+  float *root_max = cluster.map_shared_rank(&cluster_max, 0);
+  int sweep = 0;
+  for (; sweep < g.max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) cta_max = 0.f;
+    __syncthreads();
+    float mine = 0.f;
+    {
+      // pairs within each of the two blocks (round robin, a dummy player for odd sizes)
+      const int bsp = bs + (bs & 1), ppr = bsp / 2;
+      const int nva = valid(block_at(pos0, 0)), nvb = valid(block_at(pos1, 0));
+      for (int rr = 0; rr < bsp - 1; ++rr) {
+        for (int i = w; i < 2 * ppr; i += nw) {
+          const int sl = i / ppr, k = i % ppr;
+          int a, b;
+          if (k == 0) { a = rr; b = bsp - 1; }
+          else { a = (rr + k) % (bsp - 1); b = (rr - k + bsp - 1) % (bsp - 1); }
+          if (a > b) { const int t = a; a = b; b = t; }
+          if (b >= (sl ? nvb : nva)) continue;
+          T *base = cs + sl * bsz;
+          mine = fmaxf(mine, jacobi_pair<T, jacobi_regs<T>()>(base + (int64_t)a * n, base + (int64_t)b * n, n,
+                                                               (float)tol));
+        }
+        __syncthreads();
+      }
+    }
+    for (int s = 0; s < kJB - 1; ++s) {
+      // every pair between the two blocks: bs rounds of bs disjoint pairs
+      const int nv0 = valid(block_at(pos0, s)), nv1 = valid(block_at(pos1, s));
+      for (int t = 0; t < bs; ++t) {
+        for (int i = w; i < bs; i += nw) {
+          const int b = (i + t) % bs;
+          if (i >= nv0 || b >= nv1) continue;
+          mine = fmaxf(mine, jacobi_pair<T, jacobi_regs<T>()>(cs + (int64_t)i * n, cs + bsz + (int64_t)b * n, n,
+                                                               (float)tol));
+        }
+        __syncthreads();
+      }
+      // move: pull the blocks of the next positions into the other set
+      cluster.sync();                                        // every CTA is done with its current blocks
+      T *nx = cs == set0 ? set1 : set0;
+      const T *src0 = rank == 0   ? cs
+                      : rank == 1 ? cluster.map_shared_rank(cs, 0) + bsz
+                                  : cluster.map_shared_rank(cs, rank - 1);
+      const T *src1 = rank <= kClusterCTAs - 2 ? cluster.map_shared_rank(cs, rank + 1) + bsz
+                                               : cluster.map_shared_rank(cs, kClusterCTAs - 1);
+      for (int64_t t = threadIdx.x; t < bsz; t += NTJ) {
+        nx[t] = src0[t];
+        nx[bsz + t] = src1[t];
+      }
+      cs = nx;
+      __syncthreads();
+    }
+    if (lane == 0) atomicMax((int *)&cta_max, __float_as_int(mine));
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax((int *)root_max, __float_as_int(cta_max));
+    cluster.sync();
+    const bool done = *root_max <= (float)stop_tol;
+    cluster.sync();                                          // all read before the reset
+    if (rank == 0 && threadIdx.x == 0) cluster_max = 0.f;
+    cluster.sync();
+    if (done) break;
+  }
+  if (sweep == g.max_sweeps && rank == 0 && threadIdx.x == 0 && g.status)
+    atomicOr(g.status, STATUS_JACOBI_NOCONV);
+  // every block is home again: slot 0 holds block pos0, slot 1 block pos1
+  T *Mg = (T *)g.Mw;
+  for (int i = w; i < 2 * bs; i += nw) {
+    const int sl = i / bs, j = i % bs, c = (sl ? pos1 : pos0) * bs + j;
+    if (c >= n) continue;
+    const T *col = cs + sl * bsz + (int64_t)j * n;
+    double s2 = 0.0;
+    for (int r = lane; r < n; r += 32) {
+      const T v = col[r];
       Mg[(int64_t)c * n + r] = v;
       s2 += (double)abs2(v);
     }
@@ -777,14 +910,16 @@ template <class T> void chol_t(const CholDesc *d, int nd, int smem, int cluster_
   if (cluster_smem > 0) chol_cluster_kernel<T><<<nd * kCholCTAs, NT, cluster_smem, s>>>(d);
 }
 template <class T>
-void jacobi_t(const JacobiDesc *d, int nd, int smem, int cluster_smem, int nmax, cudaStream_t s) {
+void jacobi_t(const JacobiDesc *d, int nd, int smem, int block_smem, int cluster_smem, int nmax, cudaStream_t s) {
   static bool set = false;
   if (!set) {
     set_smem(jacobi_kernel<T>, kSmemLimit);
+    set_smem(jacobi_block_kernel<T>, kSmemLimit);
     set_smem(jacobi_cluster_kernel<T>, kSmemLimit);
     set = true;
   }
   if (smem >= 0) jacobi_kernel<T><<<nd, NT, smem, s>>>(d);
+  if (block_smem > 0) jacobi_block_kernel<T><<<nd * kClusterCTAs, NTJ, block_smem, s>>>(d);
   if (cluster_smem > 0) jacobi_cluster_kernel<T><<<nd * kClusterCTAs, NTJ, cluster_smem, s>>>(d);
   if (nmax > 0) sigma_refine_kernel<T><<<nd * nmax, NT, 0, s>>>(d, nmax);
 }
@@ -803,8 +938,12 @@ int small_smem_bytes(int dt, int n) {
   return b <= kSmemLimit ? (int)b : 0;
 }
 
+int jacobi_block_smem_bytes(int dt, int n) {
+  return jacobi_route(n, dtype_size(dt)) == 1 ? (int)jacobi_block_bytes(n, dtype_size(dt)) : 0;
+}
+
 int jacobi_cluster_smem_bytes(int dt, int n) {
-  if ((int64_t)n * n * dtype_size(dt) <= kSmemLimit) return 0;
+  if (jacobi_route(n, dtype_size(dt)) != 2) return 0;
   const int64_t cpc = (n + kClusterCTAs - 1) / kClusterCTAs;
   return (int)(cpc * n * dtype_size(dt));
 }
@@ -824,13 +963,14 @@ void launch_chol(int dt, const CholDesc *d, int nd, int smem, int cluster_smem, 
   }
 }
 
-void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int cluster_smem, int nmax, cudaStream_t s) {
+void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int block_smem, int cluster_smem, int nmax,
+                   cudaStream_t s) {
   if (nd <= 0) return;
   switch (dt) {
-    case DT_R32: jacobi_t<float>(d, nd, smem, cluster_smem, nmax, s); break;
-    case DT_C64: jacobi_t<float2>(d, nd, smem, cluster_smem, nmax, s); break;
-    case DT_R64: jacobi_t<double>(d, nd, smem, cluster_smem, nmax, s); break;
-    case DT_C128: jacobi_t<double2>(d, nd, smem, cluster_smem, nmax, s); break;
+    case DT_R32: jacobi_t<float>(d, nd, smem, block_smem, cluster_smem, nmax, s); break;
+    case DT_C64: jacobi_t<float2>(d, nd, smem, block_smem, cluster_smem, nmax, s); break;
+    case DT_R64: jacobi_t<double>(d, nd, smem, block_smem, cluster_smem, nmax, s); break;
+    case DT_C128: jacobi_t<double2>(d, nd, smem, block_smem, cluster_smem, nmax, s); break;
   }
 }
 

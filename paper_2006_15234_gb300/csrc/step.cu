@@ -306,7 +306,8 @@ void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I) {
   oj.kind = Op::JACOBI; oj.desc_off = B.put(jd); oj.nd = (int)jd.size(); oj.tag = "svd_jacobi";
   for (auto &j : jd) {
     oj.smem = std::max(oj.smem, small_smem_bytes(B.dt, j.n));
-    oj.smem2 = std::max(oj.smem2, jacobi_cluster_smem_bytes(B.dt, j.n));
+    oj.smem2 = std::max(oj.smem2, jacobi_block_smem_bytes(B.dt, j.n));
+    oj.smem3 = std::max(oj.smem3, jacobi_cluster_smem_bytes(B.dt, j.n));
     oj.blocks = std::max<int64_t>(oj.blocks, j.n);       // largest n: column blocks of the sigma refinement
   }
   B.ops.push_back(oj);

@@ -152,13 +152,26 @@ def test_mixed_precision_tensor_core_step(dtype):
 def test_wide_sketch_cluster_factorisations(dtype, prec):
     """l = 264: the l x l Cholesky and Jacobi no longer fit one CTA's shared
     memory and run as 8-CTA clusters (rows / columns in distributed shared
-    memory); FP64 data take the global-memory Cholesky.  Same parity bar."""
+    memory; the Jacobi block-cyclic for single precision, a column window for
+    FP64 complex, with a ragged last column block); FP64 data take the
+    global-memory Cholesky.  Same parity bar."""
     rng = np.random.default_rng(21)
     D = 4
     # a * D^2 = 320 >= l: A has full rank 288 (no directions below rounding level)
     case = _operands(rng, 18, D * D, 20, 18, 2, (D,) * 4, (D,) * 4, dtype)
     out = _run_batch([case], dtype, 256, 8, 2, 77, prec=prec)
     _check(case, out[0], 256, 8, 2, 77, 100, dtype)
+
+
+def test_block_cyclic_jacobi_fp64_complex():
+    """l = 168 in complex FP64: the Jacobi runs on the block-cyclic cluster
+    kernel (16 column blocks of 11, two per CTA) rather than the column-window
+    one that l = 264 takes in FP64 complex."""
+    rng = np.random.default_rng(23)
+    D = 4
+    case = _operands(rng, 18, D * D, 20, 18, 2, (D,) * 4, (D,) * 4, "c128")
+    out = _run_batch([case], "c128", 160, 8, 2, 78, prec=libpeps.PREC_PLAIN)
+    _check(case, out[0], 160, 8, 2, 78, 100, "c128")
 
 
 @pytest.mark.parametrize("prec", [libpeps.PREC_PLAIN, libpeps.PREC_MIXED])
