@@ -574,6 +574,60 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def run_step_profile(args, cfg):
+    """One einsumsvd step of the workload's middle-step shape (kL = m, t = D^2,
+    a = m, every bond D, complex64) with the right boundary bond b reduced to
+    32 so that the step fits a few GB: per-stage and per-launch times from the
+    plan's own event ledger, then a second execute bracketed by
+    cudaProfilerStart / Stop for an ncu capture of single kernels
+    (ncu --profile-from-start off -k regex:<kernel> -s <n> -c <k>)."""
+    import numpy as np
+    import torch
+    from paper_2006_15234_gb300 import libpeps
+
+    D, m, d = cfg.D, cfg.m, cfg.d
+    shape = (m, D * D, m, 32, d) + (D,) * 8
+    kL, t, a, b = shape[:4]
+    prec = {"plain": libpeps.PREC_PLAIN, "mixed": libpeps.PREC_MIXED, "fast": libpeps.PREC_FAST}[args.prec]
+    opts = libpeps.make_opts(m, cfg.p, cfg.q, cfg.omega_seed, prec=prec)
+    plan = libpeps.EinsumsvdPlan(torch.complex64, [shape], opts)
+    g = torch.Generator(device="cuda").manual_seed(1)
+
+    def rnd(*sh):
+        return torch.randn(*sh, dtype=torch.complex64, device="cuda", generator=g) / np.sqrt(np.prod(sh[1:]))
+
+    V = rnd(kL, t, a, D * D)
+    S = rnd(a, D * D, b)
+    K = rnd(d, D, D, D, D)
+    Kb = rnd(d, D, D, D, D)
+    k = plan.ranks[0]
+    M, N = kL * t, D * D * b * D * D
+    U = torch.empty(M, k, dtype=torch.complex64, device="cuda")
+    W = torch.empty(k, N, dtype=torch.complex64, device="cuda")
+    sig = torch.empty(k, dtype=torch.float64, device="cuda")
+    ls = torch.empty(1, dtype=torch.float64, device="cuda")
+    io = [(V, S, K, Kb, U, W, sig, ls)]
+    plan.execute(io)
+    torch.cuda.synchronize()
+    ms = plan.profile()
+    launches = plan.launches()
+    tags = {}
+    for (tag, fl, by), t_ in zip(launches, ms):
+        x = tags.setdefault(tag, [0.0, 0.0])
+        x[0] += t_
+        x[1] += fl
+    stages = {tag: {"ms": round(t_, 4), "tflops": round(fl / max(t_, 1e-9) / 1e9, 2)}
+              for tag, (t_, fl) in sorted(tags.items(), key=lambda kv: -kv[1][0])}
+    per = [{"i": i, "tag": tag, "ms": round(t_, 4), "tflops": round(fl / max(t_, 1e-9) / 1e9, 2),
+            "gbs": round(by / max(t_, 1e-9) / 1e6, 1)} for i, ((tag, fl, by), t_) in enumerate(zip(launches, ms))]
+    torch.cuda.profiler.start()
+    plan.execute(io)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"step_profile": {"shape": shape, "workspace_gb": round(plan.workspace_bytes / 1e9, 3),
+                                       "stages": stages, "launches": per}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -588,9 +642,13 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--launch-list", action="store_true",
                     help="warm up, run one more contraction and exit (for an ncu launch list)")
+    ap.add_argument("--step-profile", action="store_true",
+                    help="one middle einsumsvd step (b = 32): stage ledger, then one execute for ncu")
     args = ap.parse_args()
     cfg = synth.config(args.config)
-    if args.impl == "reference":
+    if args.step_profile:
+        run_step_profile(args, cfg)
+    elif args.impl == "reference":
         run_reference(args, cfg)
     elif args.config == "c3":
         run_batched(args, cfg)
