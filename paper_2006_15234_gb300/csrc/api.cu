@@ -1168,6 +1168,7 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           C.need(f.P, es * (double)f.n * f.M, tag, "P");
           C.need(f.g, es * (double)f.M, tag, "g");
           C.need(f.Ut, es * (double)f.n * f.k, tag, "Ut");
+          C.need(f.h, as * (double)f.n, tag, "h");
           C.need(f.sigma_out, 8.0 * f.k, tag, "sigma_out");
           C.need(f.log_out, 8, tag, "log_out");
           C.need(f.inv_s1, 8, tag, "inv_s1");
@@ -1398,7 +1399,7 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
       case Op::JACOBI:
         launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, op.smem3, (int)op.blocks, s);
         break;
-      case Op::FINALIZE: launch_finalize(dt, (const FinalizeDesc *)d, op.nd, s); break;
+      case Op::FINALIZE: launch_finalize(dt, (const FinalizeDesc *)d, op.nd, (int)op.blocks, s); break;
       case Op::ZERO: launch_zero((const ZeroDesc *)d, pre, op.nd, op.blocks, s); break;
       case Op::SITE: launch_site(dt, (const SiteDesc *)d, pre, op.nd, op.blocks, s); break;
       case Op::SCALAR: {
@@ -1912,6 +1913,7 @@ peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count) {
     switch (op.kind) {
       case Op::JACOBI: n += 1 + (op.smem2 > 0) + (op.smem3 > 0) + (op.blocks > 0); break;   // one CTA, clusters, refinement
       case Op::CHOL: n += 1 + (op.smem2 > 0); break;                         // one CTA, cluster
+      case Op::FINALIZE: n += 1 + (op.blocks > 0); break;                    // gauge projections, finalize
       case Op::TC: n += (op.tc.tiles_m * op.tc.tiles_n > 0) + (op.tc.bpre != 0); break;   // B expansion, GEMM
       case Op::COPY: case Op::MEMSET: break;                                  // copies, not kernels
       case Op::SKETCH: case Op::GEMM: case Op::GEMM_ATOMIC: case Op::SANDWICH: case Op::ZERO: case Op::SITE:

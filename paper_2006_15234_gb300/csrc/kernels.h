@@ -111,6 +111,7 @@ struct FinalizeDesc {
   const void *P;                   // working type, [j][m], ld = M
   const void *g;                   // gauge vector, M entries
   void *Ut;                        // working type [j][c], n x k
+  void *h;                         // FP64 (complex) n entries: h_j = sum_m conj(P[j][m]) g[m]
   double *sigma_out;               // k values
   double *log_out;                 // log sigma_1
   double *inv_s1;                  // 1 / sigma_1 (device scalar for the W GEMM)
@@ -160,7 +161,8 @@ void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int block_smem
 int jacobi_block_smem_bytes(int dt, int n);
 int jacobi_cluster_smem_bytes(int dt, int n);
 int small_smem_bytes(int dt, int n);   // shared memory of chol / jacobi for n x n (0: global)
-void launch_finalize(int dt, const FinalizeDesc *d, int nd, cudaStream_t s);
+// nmax: largest n of the descriptors (CTAs per instance of the gauge projections)
+void launch_finalize(int dt, const FinalizeDesc *d, int nd, int nmax, cudaStream_t s);
 void launch_site(int dt, const SiteDesc *d, const int64_t *prefix, int nd, int64_t blocks,
                  cudaStream_t s);
 void launch_scalar(int dt, const ScalarDesc *d, cudaStream_t s);

@@ -822,14 +822,41 @@ __global__ void __launch_bounds__(NT) sigma_refine_kernel(const JacobiDesc *__re
   if (threadIdx.x == 0) g.sig[c] = s2 > 0.0 ? sqrt(v2 / s2) : 0.0;
 }
 
+// Gauge projections h_j = sum_m conj(P[j][m]) g[m] (P = the M-side basis,
+// g = the Philox gauge vector): one CTA per j, products exact and sums in
+// FP64 (the gauge phase fixes the next step's sketch, so h carries only P's
+// own rounding), partial sums in a fixed order.
+template <class T>
+__global__ void __launch_bounds__(NT) gauge_h_kernel(const FinalizeDesc *__restrict__ descs, int cols) {
+  using Acc = typename Traits<T>::Acc;
+  __shared__ Acc part[NT / 32];
+  const FinalizeDesc &g = descs[blockIdx.x / cols];
+  const int j = blockIdx.x % cols;
+  if (j >= g.n) return;                            // uniform over the CTA
+  const T *P = (const T *)g.P + (int64_t)j * g.M;
+  const T *gv = (const T *)g.g;
+  Acc acc = zero<Acc>();
+  for (int64_t m = threadIdx.x; m < g.M; m += NT) acc = fma_(conj_(widen(P[m])), widen(gv[m]), acc);
+  acc = warp_sum(acc);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) part[w] = acc;
+  __syncthreads();
+  if (w == 0) {
+    Acc v = lane < NT / 32 ? part[lane] : zero<Acc>();
+    v = warp_sum(v);
+    if (lane == 0) ((Acc *)g.h)[j] = v;
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__restrict__ descs) {
   const FinalizeDesc &g = descs[blockIdx.x];
   const int n = g.n, k = g.k;
   extern __shared__ __align__(16) unsigned char dyn[];
+  using Acc = typename Traits<T>::Acc;
   int *order = (int *)dyn;                                   // n
-  T *h = (T *)(dyn + ((n * sizeof(int) + 15) & ~15));        // n
-  T *rho = h + n;                                            // k
+  Acc *h = (Acc *)(dyn + ((n * sizeof(int) + 15) & ~15));    // n
+  T *rho = (T *)(h + n);                                     // k
   const double *sig = g.sig;
   const T *M = (const T *)g.Mw;
   for (int c = threadIdx.x; c < n; c += NT) {
@@ -841,16 +868,9 @@ __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__rest
     }
     order[rank] = c;
   }
-  // h_j = sum_m conj(P[j][m]) g[m]
-  const T *P = (const T *)g.P;
-  const T *gv = (const T *)g.g;
+  // h_j = sum_m conj(P[j][m]) g[m], formed by gauge_h_kernel
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = w; j < n; j += NT / 32) {
-    T s = zero<T>();
-    for (int64_t m = lane; m < g.M; m += 32) s = fma_(conj_(P[(int64_t)j * g.M + m]), gv[m], s);
-    s = warp_sum(s);
-    if (lane == 0) h[j] = s;
-  }
+  for (int j = threadIdx.x; j < n; j += NT) h[j] = ((const Acc *)g.h)[j];
   __syncthreads();
   const double s1 = sig[order[0]];
   // phi_i = sum_j conj(h_j) u_{j,i}, u_i = M[:, order[i]] / sigma_i
@@ -858,12 +878,12 @@ __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__rest
     const int c = order[i];
     const double si = sig[c];
     const bool zero_dir = !(si > g.rtol * s1);
-    T s = zero<T>();
+    Acc s = zero<Acc>();
     double nrm2 = 0.0;
     if (!zero_dir)
       for (int j = lane; j < n; j += 32) {
         const T mv = M[(int64_t)c * n + j];
-        s = fma_(conj_(h[j]), mv, s);
+        s = fma_(conj_(h[j]), widen(mv), s);
         nrm2 += (double)abs2(mv);
       }
     s = warp_sum(s);
@@ -923,11 +943,12 @@ void jacobi_t(const JacobiDesc *d, int nd, int smem, int block_smem, int cluster
   if (cluster_smem > 0) jacobi_cluster_kernel<T><<<nd * kClusterCTAs, NTJ, cluster_smem, s>>>(d);
   if (nmax > 0) sigma_refine_kernel<T><<<nd * nmax, NT, 0, s>>>(d, nmax);
 }
-template <class T> void finalize_t(const FinalizeDesc *d, int nd, cudaStream_t s) {
-  // order (n ints) + h (n) + rho (k <= n): n <= 1024
-  const int smem = 4096 + 16 + 2 * 1024 * (int)sizeof(T);
+template <class T> void finalize_t(const FinalizeDesc *d, int nd, int nmax, cudaStream_t s) {
+  // order (n ints) + h (n, FP64) + rho (k <= n): n <= 1024
+  const int smem = 4096 + 16 + 1024 * (int)(sizeof(typename Traits<T>::Acc) + sizeof(T));
   static bool set = false;
   if (!set) { set_smem(finalize_kernel<T>, smem); set = true; }
+  if (nmax > 0) gauge_h_kernel<T><<<nd * nmax, NT, 0, s>>>(d, nmax);
   finalize_kernel<T><<<nd, NT, smem, s>>>(d);
 }
 
@@ -974,13 +995,13 @@ void launch_jacobi(int dt, const JacobiDesc *d, int nd, int smem, int block_smem
   }
 }
 
-void launch_finalize(int dt, const FinalizeDesc *d, int nd, cudaStream_t s) {
+void launch_finalize(int dt, const FinalizeDesc *d, int nd, int nmax, cudaStream_t s) {
   if (nd <= 0) return;
   switch (dt) {
-    case DT_R32: finalize_t<float>(d, nd, s); break;
-    case DT_C64: finalize_t<float2>(d, nd, s); break;
-    case DT_R64: finalize_t<double>(d, nd, s); break;
-    case DT_C128: finalize_t<double2>(d, nd, s); break;
+    case DT_R32: finalize_t<float>(d, nd, nmax, s); break;
+    case DT_C64: finalize_t<float2>(d, nd, nmax, s); break;
+    case DT_R64: finalize_t<double>(d, nd, nmax, s); break;
+    case DT_C128: finalize_t<double2>(d, nd, nmax, s); break;
   }
 }
 

@@ -298,6 +298,7 @@ void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I) {
     jd.push_back(j);
     FinalizeDesc f{};
     f.Mw = q.Mw; f.sig = q.sig; f.P = q.Y; f.g = q.g; f.Ut = q.Ut; f.sigma_out = q.sigma;
+    f.h = q.G;                     // the Gram buffer is free once R_B is factored
     f.log_out = q.logp; f.inv_s1 = q.inv_s1; f.n = q.ell; f.k = q.k; f.M = q.M;
     f.rtol = 16.0 * q.ell * 2.220446049250313e-16; f.status = nullptr;
     fd.push_back(f);
@@ -313,6 +314,7 @@ void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I) {
   B.ops.push_back(oj);
   Op of;
   of.kind = Op::FINALIZE; of.desc_off = B.put(fd); of.nd = (int)fd.size(); of.tag = "svd_finalize";
+  for (auto &f : fd) of.blocks = std::max<int64_t>(of.blocks, f.n);
   B.ops.push_back(of);
 }
 
