@@ -63,7 +63,13 @@ struct SketchDesc {
   int32_t nd;
   int32_t radix[5];
   int64_t stride[5];
+  // multiply-shift division by N and by each radix (sketch_set_div), used
+  // when N * ell < 2^31
+  uint32_t nmul, nshr;
+  uint32_t rmul[5], rshr[5];
 };
+// fill the division constants of a sketch descriptor (after its radices)
+void sketch_set_div(SketchDesc &s);
 
 // out[b][c][r][q] = op(in[b][r][c][q]) for b < nb, r < R, c < Cc, q < Q
 // (op = conjugate when conj): swaps two index groups of a tensor.

@@ -86,10 +86,34 @@ __global__ void sketch_kernel(const SketchDesc *__restrict__ descs, const int64_
     for (int i = 0; i < 4; ++i) v[i] = (R)2 * Uni<R>::u(c[i]) - (R)1;
   }
   T *X = (T *)g.X;
+  const bool small = total < (1ll << 31);      // 32-bit index arithmetic (multiply-shift division)
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     const int64_t e = blk * PER + r;
     if (e >= total) break;
+    if (small) {
+      const uint32_t e32 = (uint32_t)e;
+      const uint32_t j = (__umulhi(e32, g.nmul) + e32) >> g.nshr;
+      uint32_t n = e32 - j * (uint32_t)g.N;
+      T val;
+      if constexpr (CPLX) {
+        const R sc = g.kind == 0 ? (R)0.70710678118654752440 : (R)1;
+        val = from_parts<T>((double)(v[2 * r] * sc), (double)(v[2 * r + 1] * sc));
+      } else {
+        val = from_parts<T>((double)v[r], 0.0);
+      }
+      int64_t off = n;
+      if (g.nd) {
+        off = 0;
+        for (int d = 0; d < g.nd; ++d) {
+          const uint32_t q = (__umulhi(n, g.rmul[d]) + n) >> g.rshr[d];
+          off += (int64_t)(n - q * (uint32_t)g.radix[d]) * g.stride[d];
+          n = q;
+        }
+      }
+      X[(int64_t)j * g.ld + off] = val;
+      continue;
+    }
     const int64_t j = e / g.N, n = e % g.N;
     T val;
     if constexpr (CPLX) {
@@ -233,6 +257,15 @@ template <class T> __global__ void scalar_kernel(ScalarDesc g) {
     g.out[1] = atan2((double)im(x), (double)re(x));
   }
 }
+
+}  // namespace
+
+void sketch_set_div(SketchDesc &s) {
+  div_magic((uint64_t)s.N, &s.nmul, &s.nshr);
+  for (int d = 0; d < 5; ++d) div_magic(s.radix[d] > 0 ? (uint64_t)s.radix[d] : 0, &s.rmul[d], &s.rshr[d]);
+}
+
+namespace {
 
 template <class T>
 void sketch_t(const SketchDesc *d, const int64_t *prefix, int nd, int64_t blocks, cudaStream_t s) {

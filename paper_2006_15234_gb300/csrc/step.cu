@@ -109,10 +109,12 @@ void emit_sketch(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
     s.X = p->X; s.N = p->N; s.ld = p->N; s.ell = p->ell; s.tag = 0; s.kind = o.sketch;
     s.seed = o.seed; s.instance = p->instance;
     s.nblocks = ceil_div(ceil_div(s.N * s.ell, per), 256);
+    sketch_set_div(s);
     d.push_back(s); bl.push_back(s.nblocks);
     SketchDesc gg = s;
     gg.X = p->g; gg.N = p->M; gg.ld = p->M; gg.ell = 1; gg.tag = 1; gg.kind = 0;
     gg.nblocks = ceil_div(ceil_div(gg.N, per), 256);
+    sketch_set_div(gg);
     d.push_back(gg); bl.push_back(gg.nblocks);
   }
   push_grouped(B, Op::SKETCH, d.data(), sizeof(SketchDesc), (int)d.size(), bl, "sketch");
@@ -537,6 +539,7 @@ void emit_sketch_xl(Builder &B, Inst &q, const RsvdOpts &o) {
   const int64_t rad[5] = {q.DE, q.De, q.b, q.DX, BIG};
   const int64_t str[5] = {Q1, 1, (int64_t)q.DX * q.DE * Q1, (int64_t)q.DE * Q1, q.De};
   for (int i = 0; i < 5; ++i) { d[0].radix[i] = (int32_t)rad[i]; d[0].stride[i] = str[i]; }
+  sketch_set_div(d[0]);
 }
 
 void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {

@@ -771,18 +771,9 @@ int tc_pick_nmma(int N, bool cplx, bool split3) {
   return best;
 }
 
-// Division by an invariant integer as multiply-high, add and shift
-// (Granlund and Montgomery, 1994): with l = ceil(log2 r) and
-// mul = floor(2^32 (2^l - r) / r) + 1, i / r = (umulhi(i, mul) + i) >> l for
-// every i < 2^31 (the sum then fits in 32 bits).
+// multiply-shift constants of the index maps' radices
 static void fill_div(DigitMap &m) {
-  for (int d = 0; d < 4; ++d) {
-    const uint64_t r = m.radix[d] > 0 ? (uint64_t)m.radix[d] : 0x7fffffffull;
-    uint32_t l = 0;
-    while ((1ull << l) < r) ++l;
-    m.mul[d] = (uint32_t)(((1ull << 32) * ((1ull << l) - r)) / r + 1);
-    m.shr[d] = l;
-  }
+  for (int d = 0; d < 4; ++d) div_magic(m.radix[d] > 0 ? (uint64_t)m.radix[d] : 0, &m.mul[d], &m.shr[d]);
 }
 
 void launch_tc_gemm(const TcDesc &desc, int nmma, cudaStream_t s) {

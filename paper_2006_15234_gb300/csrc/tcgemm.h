@@ -66,6 +66,18 @@ bool tc_encode_map(CUtensorMap *map, const void *base, int64_t rows, int64_t col
 // Whether a K-contiguous operand can be fed by TMA (alignment rules).
 bool tc_operand_ok(const void *base, int64_t pitch_bytes);
 
+// Division by an invariant integer r >= 1 as multiply-high, add and shift
+// (Granlund and Montgomery, 1994): with l = ceil(log2 r) and
+// mul = floor(2^32 (2^l - r) / r) + 1, i / r = (umulhi(i, mul) + i) >> l for
+// every i < 2^31 (the sum then fits in 32 bits).
+inline void div_magic(uint64_t r, uint32_t *mul, uint32_t *shr) {
+  if (r == 0) r = 0x7fffffffull;
+  uint32_t l = 0;
+  while ((1ull << l) < r) ++l;
+  *mul = (uint32_t)(((1ull << 32) * ((1ull << l) - r)) / r + 1);
+  *shr = l;
+}
+
 inline DigitMap digits1(int64_t stride) {
   DigitMap d{};
   d.n = 1;
