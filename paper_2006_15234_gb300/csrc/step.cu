@@ -218,10 +218,19 @@ double chol_shift(int dt, int ell, bool first_pass) {
 }
 
 void emit_gram_tc(Builder &B, Inst &q, const void *src, int64_t L, const char *tag);
+void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const void *Bm, int64_t rowsB, int64_t K,
+             bool conjA, bool conjB, bool split3, void *C, DigitMap mm, DigitMap mn, bool conjC,
+             const double *alpha_dev, bool bpre);
+void emit_permute(Builder &B, const char *tag, std::vector<PermuteDesc> d);
+PermuteDesc mk_perm(const void *in, void *out, int64_t nb, int64_t R, int64_t C, int64_t Q, bool conj);
+DigitMap mkmap(std::initializer_list<std::pair<int64_t, int64_t>> l);
+constexpr int64_t BIG = 0x7fffffff;          // radix of an index map's last digit
 
 // CholeskyQR pass: G <- src^H src; T <- R^+; dst <- src T.  tc_gram: the Gram
 // of a single tensor-core instance runs on the tensor cores (3xTF32, FP64
-// accumulation across K chunks).
+// accumulation across K chunks), and so does the M-side apply (src and T
+// transposed into free scratch first: the sketch block X, which the M-side
+// orthogonalisation never reads, and the Jacobi matrix).
 void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*src, void *Inst::*dst,
                    void *Inst::*Rdst, void *Inst::*Rprev, void *Inst::*Rout, bool apply, const char *tag,
                    bool first_pass, bool tc_gram = false) {
@@ -264,7 +273,18 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
     op.smem2 = std::max(op.smem2, chol_cluster_smem_bytes(B.dt, c.n, c.T != nullptr));
   }
   B.ops.push_back(op);
-  if (apply) push_gemm(B, app, false, tag);
+  if (!apply) return;
+  // (X holds l x N elements: room for the transposed M x l block when M <= N)
+  if (tc_gram && mside && I.size() == 1 && I[0]->M <= I[0]->N && (Lr * dtype_size(B.dt)) % 16 == 0 &&
+      ((int64_t)I[0]->ell * dtype_size(B.dt)) % 16 == 0) {
+    // dst[i][n] = sum_j T[j][i] src[j][n] as C(n, i) = sum_j srcT[n][j] TT[i][j]
+    Inst &q = *I[0];
+    emit_permute(B, tag, {mk_perm(q.*src, q.X, 1, q.ell, Lr, 1, false), mk_perm(q.Tm, q.Mw, 1, q.ell, q.ell, 1, false)});
+    emit_tc(B, tag, q.X, Lr, q.Mw, q.ell, q.ell, false, false, true, q.*dst, mkmap({{BIG, 1}}), mkmap({{BIG, Lr}}),
+            false, nullptr, true);
+    return;
+  }
+  push_gemm(B, app, false, tag);
 }
 
 void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I);
@@ -350,8 +370,6 @@ void emit_epilogue(Builder &B, std::vector<Inst *> &I) {
 //          S2' T1[(j,b,X,E)][(s,l,u)] = Z2 (.) Kb^T      over (U,L)
 //          S1' Z[(j,b,X,E)][(x,e)]    = T1 (.) conj(K^T) over (s,l,u)
 // ===========================================================================
-
-constexpr int64_t BIG = 0x7fffffff;
 
 DigitMap mkmap(std::initializer_list<std::pair<int64_t, int64_t>> l) {
   DigitMap m{};
