@@ -1,0 +1,180 @@
+"""Index logic of the two cluster kernels of the small-matrix stage, replayed
+on the CPU with the kernels' own formulas (csrc/smallmat.cu):
+
+* the block-cyclic Jacobi: 16 column blocks, two per CTA (slot 0 at
+  tournament position r, slot 1 at 15 - r), all pairs within the two blocks
+  once per sweep, then 15 rounds of cross-block pairs with the blocks pulled
+  to their next positions (position p >= 1 -> p + 1, 15 -> 1) between rounds.
+  Every column pair must be rotated exactly once per sweep, the block a slot
+  holds must match the closed form block_at(p, s), and every block must be
+  home after a sweep;
+* the blocked cluster Cholesky: row-cyclic rows over 8 CTAs, panels of nb
+  pivots copied and factored by every CTA, rank-nb updates of the own rows
+  below, and R^+ panel by panel from the bottom.  Replayed in FP64 on random
+  Hermitian positive definite matrices it must give R^H R = G and T R = I.
+"""
+import numpy as np
+import pytest
+
+CTAS = 8
+NB = 2 * CTAS
+
+
+def block_at(p, s):
+    return 0 if p == 0 else 1 + ((p - 1 - s) % (NB - 1))
+
+
+@pytest.mark.parametrize("n", [161, 200, 264, 272, 288, 300, 320])
+def test_block_cyclic_jacobi_visits_every_pair_once(n):
+    bs = (n + NB - 1) // NB
+    slots = {r: [r, NB - 1 - r] for r in range(CTAS)}
+    seen = {}
+
+    def rotate(a, b):
+        key = (min(a, b), max(a, b))
+        seen[key] = seen.get(key, 0) + 1
+
+    def valid(b):
+        return max(0, min(bs, n - b * bs))
+
+    # pairs within each slot's block (round robin with a dummy player for odd sizes)
+    bsp = bs + (bs & 1)
+    for r in range(CTAS):
+        for sl in range(2):
+            b0 = slots[r][sl]
+            assert b0 == block_at([r, NB - 1 - r][sl], 0)
+            for rr in range(bsp - 1):
+                used = set()
+                for k in range(bsp // 2):
+                    a, b = (rr, bsp - 1) if k == 0 else ((rr + k) % (bsp - 1), (rr - k + bsp - 1) % (bsp - 1))
+                    assert a not in used and b not in used      # disjoint pairs within a round
+                    used |= {a, b}
+                    a, b = min(a, b), max(a, b)
+                    if b < valid(b0):
+                        rotate(b0 * bs + a, b0 * bs + b)
+    for s in range(NB - 1):
+        for r in range(CTAS):
+            b0, b1 = slots[r]
+            assert b0 == block_at(r, s) and b1 == block_at(NB - 1 - r, s)
+            for t in range(bs):
+                for i in range(bs):
+                    b = (i + t) % bs
+                    if i < valid(b0) and b < valid(b1):
+                        rotate(b0 * bs + i, b1 * bs + b)
+        # pull the next blocks: slot 0 of CTA r from CTA r - 1 (CTA 1 from slot 1 of
+        # CTA 0, CTA 0 keeps its own), slot 1 from CTA r + 1 (CTA 7 from its own slot 0)
+        slots = {r: [slots[0][0] if r == 0 else (slots[0][1] if r == 1 else slots[r - 1][0]),
+                     slots[r + 1][1] if r <= CTAS - 2 else slots[CTAS - 1][0]] for r in range(CTAS)}
+    assert all(slots[r] == [r, NB - 1 - r] for r in range(CTAS))
+    assert len(seen) == n * (n - 1) // 2
+    assert set(seen.values()) == {1}
+
+
+def _blocked_cholesky(G, nb, shift=0.0, tol=1e-30):
+    """Replay of chol_cluster_kernel's panel logic (FP64, complex)."""
+    n = G.shape[0]
+    md = max(np.real(np.diag(G)).max(), 0.0)
+    thr = tol * md
+    cap = (n + CTAS - 1) // CTAS
+    nloc = [(n - r + CTAS - 1) // CTAS if r < n else 0 for r in range(CTAS)]
+    Wl = [np.zeros((cap, n), complex) for _ in range(CTAS)]
+    Tl = [np.zeros((cap, n), complex) for _ in range(CTAS)]
+    for r in range(CTAS):
+        for li in range(nloc[r]):
+            i = r + CTAS * li
+            Wl[r][li, i:] = G[i, i:]
+            Wl[r][li, i] += shift * md
+
+    def first_li(r, x):
+        return 0 if x - r <= 0 else (x - r + CTAS - 1) // CTAS
+
+    P = [np.zeros((nb, n), complex) for _ in range(CTAS)]
+
+    def keep(dst, r, j0, jb, c0):
+        for p in range(jb):
+            j = j0 + p
+            if j % CTAS == r:
+                dst[r][j // CTAS, c0:] = P[r][p, c0:]
+
+    for j0 in range(0, n, nb):
+        jb = min(nb, n - j0)
+        if j0 > 0:
+            for r in range(CTAS):
+                keep(Wl, r, j0 - nb, nb, j0 - nb)
+        for r in range(CTAS):                     # every CTA copies the panel ...
+            for p in range(jb):
+                j = j0 + p
+                P[r][p, j0:] = Wl[j % CTAS][j // CTAS, j0:]
+        for r in range(CTAS):                     # ... and factors it itself
+            for p in range(jb):
+                j = j0 + p
+                row = P[r][p]
+                dj = row[j].real
+                if not (dj > thr) or not (md > 0):
+                    row[j:] = 0
+                else:
+                    rr = np.sqrt(dj)
+                    row[j + 1:] /= rr
+                    row[j] = rr
+                for pp in range(p + 1, jb):
+                    i = j0 + pp
+                    P[r][pp, i:] -= np.conj(row[i]) * row[i:]
+        for r in range(CTAS):                     # own rows below the panel
+            for li in range(first_li(r, j0 + jb), nloc[r]):
+                i = r + CTAS * li
+                for p in range(jb):
+                    Wl[r][li, i:] -= np.conj(P[r][p, i]) * P[r][p, i:]
+    j0 = ((n - 1) // nb) * nb
+    for r in range(CTAS):
+        keep(Wl, r, j0, n - j0, j0)
+    B = [np.zeros((nb, nb), complex) for _ in range(CTAS)]
+    prev0 = prevb = None
+    for k1 in range(n, 0, -nb):
+        k0 = max(0, k1 - nb)
+        kb = k1 - k0
+        if prev0 is not None:
+            for r in range(CTAS):
+                keep(Tl, r, prev0, prevb, prev0)
+        for r in range(CTAS):
+            for p in range(kb):
+                k = k0 + p
+                P[r][p, k0:] = Tl[k % CTAS][k // CTAS, k0:]
+                B[r][p, :kb] = Wl[k % CTAS][k // CTAS, k0:k1]
+        for r in range(CTAS):
+            for p in range(kb - 1, -1, -1):
+                k = k0 + p
+                rkk = B[r][p, p].real
+                if rkk == 0:
+                    P[r][p, k:] = 0
+                else:
+                    P[r][p, k + 1:] *= -1.0 / rkk
+                    P[r][p, k] = 1.0 / rkk
+                for pi in range(p):
+                    P[r][pi, k:] += B[r][pi, p] * P[r][p, k:]
+        for r in range(CTAS):
+            for li in range(first_li(r, k0)):
+                for p in range(kb - 1, -1, -1):
+                    k = k0 + p
+                    Tl[r][li, k:] += Wl[r][li, k] * P[r][p, k:]
+        prev0, prevb = k0, kb
+    for r in range(CTAS):
+        keep(Tl, r, prev0, prevb, prev0)
+    R = np.zeros((n, n), complex)
+    T = np.zeros((n, n), complex)
+    for r in range(CTAS):
+        for li in range(nloc[r]):
+            R[r + CTAS * li] = Wl[r][li]
+            T[r + CTAS * li] = Tl[r][li]
+    return R, T
+
+
+@pytest.mark.parametrize("n,nb", [(37, 16), (50, 8), (64, 16), (19, 4), (33, 1), (70, 16)])
+def test_blocked_cluster_cholesky_panels(n, nb):
+    rng = np.random.default_rng(n * 100 + nb)
+    Y = rng.standard_normal((3 * n, n)) + 1j * rng.standard_normal((3 * n, n))
+    G = Y.conj().T @ Y
+    R, T = _blocked_cholesky(G, nb)
+    assert np.array_equal(np.tril(R, -1), np.zeros_like(R))
+    assert np.abs(R.conj().T @ R - G).max() <= 1e-12 * np.abs(G).max()
+    assert np.abs(T @ R - np.eye(n)).max() <= 1e-10
+    assert np.array_equal(np.tril(T, -1), np.zeros_like(T))
