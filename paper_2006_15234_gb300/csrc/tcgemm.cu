@@ -9,17 +9,26 @@
 // re/im).  Tiles arrive by TMA with the 128-byte swizzle; the accumulators
 // live in tensor memory.  A complex product runs as ONE real MMA chain: A's
 // interleaved rows (ar, ai) are used as they are, and each complex row b of
-// the B tile is expanded in shared memory into two real rows,
+// B becomes two real rows,
 //   (br, sr*bi) -> Re C,     (s1*bi, s2*br) -> Im C,
 // the signs encoding the conjugation of A and/or B.  The accumulator then
 // holds (Re, Im) column pairs, i.e. C's interleaved layout, and A is read
-// once per k step for both parts.  The expansion acts per 16-byte chunk (two
-// complex values), so it commutes with the swizzle up to the row-dependent
-// chunk permutation, which the rewrite applies.
+// once per k step for both parts.
 // SPLIT3 ("3xTF32") splits each operand into a TF32 head (round to nearest)
 // and an FP32 tail and accumulates head*head + tail*head + head*tail,
 // recovering FP32-level products on TF32 tensor cores.  Plain TF32 products
 // round both operands to the nearest TF32 value first (unbiased).
+// SPLIT3 operands:
+//  * A (128 rows per tile) goes to tensor memory: the worker warps read each
+//    raw row from shared memory, split it in registers and store head and
+//    tail with tcgen05.st; the MMA takes A from tensor memory (A stages after
+//    the two accumulator buffers), so the tensor core reads only B from
+//    shared memory;
+//  * B is expanded (complex) and split once before the GEMM into a scratch
+//    buffer (tc_expand_kernel, "bpre") and TMA delivers MMA-ready head and
+//    tail tiles; where B is too large for that (the Grams) the workers expand
+//    and split it in shared memory per 16-byte chunk, which commutes with the
+//    swizzle up to the row-dependent chunk permutation the rewrite applies.
 // The tensor core's FP32 accumulator drops the bits of each addend below the
 // running sum's last place (measured: a relative bias of about 1e-8 per
 // accumulated K value, growing linearly with K).  SPLIT3 products therefore
@@ -28,14 +37,16 @@
 // warps add each chunk into FP32 registers with round-to-nearest.
 //
 // Roles: warp 0 issues TMA, warp 1 owns tensor memory and issues MMAs from
-// one thread, warps 2-9 rewrite operand tiles, fold accumulator chunks and
-// run the epilogue (tensor memory or registers -> global through an arbitrary
+// one thread, warps 2-9 prepare operands, fold accumulator chunks and run the
+// epilogue (tensor memory or registers -> global through an arbitrary
 // mixed-radix index map; warp w owns lane quarter w % 4 and column half
-// (w - 2) / 4).  Every mbarrier wait is bounded: on expiry the kernel raises a
-// status bit, lets its own TMA copies and MMAs drain (again bounded), frees
-// its tensor memory and returns.  Decisions to leave a loop are taken by all
-// worker threads together (a barrier reduction), so no worker is left at a
-// named barrier.
+// (w - 2) / 4).  An item's epilogue runs after the first k blocks of the next
+// item are prepared, so that its MMAs overlap the epilogue.  Every mbarrier
+// wait is bounded: on expiry the kernel raises a status bit, lets its own TMA
+// copies and MMAs drain (again bounded), frees its tensor memory and returns.
+// Decisions to leave a loop are taken by all worker threads together (a
+// barrier reduction; a warp vote inside k loops that reach no named
+// barrier), so no worker is left at a named barrier.
 #include <cuda.h>
 
 #include <algorithm>
