@@ -341,9 +341,11 @@ peps_status peps_plan_launch_info(const peps_plan *plan, int64_t i, const char *
                                   double *flops, double *bytes);
 
 /* CUDA kernel launches one execute of the plan enqueues (an entry of the
- * ledger may launch more than one kernel: the Cholesky and Jacobi entries
- * launch a one-CTA and a cluster kernel, the Jacobi entry its singular value
- * refinement too). */
+ * ledger may launch more than one kernel: the Cholesky entry a one-CTA and a
+ * cluster kernel, the Jacobi entry a one-CTA kernel, the cluster kernels its
+ * sizes need and the singular value refinement, the finalize entry the gauge
+ * projections first, a tensor-core GEMM entry the pre-expansion of its B
+ * operand first). */
 peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count);
 
 /* Kernel family of launch i (static string): "tc_gemm" (tcgen05 GEMM),
