@@ -137,6 +137,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---- multi-rank host logic (weak scaling: every rank its own work, no data-path collective) ----
+
+def replica_seed(cfg, rank):
+    """Seed of rank `rank`'s replica of the workload's PEPS."""
+    return cfg.seed + 1000 * rank
+
+
+def rank_instance_ids(rank, n):
+    """Instance ids of rank `rank`'s batch of n instances (disjoint across ranks)."""
+    return [rank * n + i for i in range(n)]
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """The largest per-rank value over all ranks (the slowest rank's step time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, flops_per_rank, ms_step):
+    """Whole-job throughput in TFLOP/s: the work of every rank over the slowest rank's time."""
+    return world * flops_per_rank / (ms_step * 1e-3) / 1e12
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -159,7 +187,7 @@ def run_ours(args, cfg):
     dev = torch.device("cuda", local)
     tdt = {"c64": torch.complex64, "f32": torch.float32, "f64": torch.float64}[cfg.dtype]
     # weak scaling: every rank contracts its own PEPS (replicas of the workload)
-    ket = synth.random_peps(cfg.nrow, cfg.ncol, cfg.d, cfg.D, cfg.dtype, cfg.dist, cfg.seed + 1000 * rank)
+    ket = synth.random_peps(cfg.nrow, cfg.ncol, cfg.d, cfg.D, cfg.dtype, cfg.dist, replica_seed(cfg, rank))
     kt = [[torch.tensor(T, dtype=tdt, device=dev) for T in row] for row in ket]
     prec = {"plain": libpeps.PREC_PLAIN, "mixed": libpeps.PREC_MIXED, "fast": libpeps.PREC_FAST}[args.prec]
     opts = libpeps.make_opts(cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=prec)
@@ -220,11 +248,7 @@ def run_ours(args, cfg):
         barrier()
         t_wall = time.perf_counter() - t_wall
     ms = [a.elapsed_time(b) for a, b in times]
-    ms_step = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(float(np.mean(ms)), world, dev)
 
     # end-to-end through the public API with host buffers: H2D of every site,
     # the contraction, D2H of the result, every step inside the timed region
@@ -240,7 +264,7 @@ def run_ours(args, cfg):
         run()
         la2, _ = plan.result()
         e2e.append(time.perf_counter() - t0)
-    e2e_s = float(np.median(e2e))
+    e2e_s = max_over_ranks(float(np.median(e2e)), world, dev)
 
     # per-launch device times of one more execute (CUDA events on the stream)
     prof = plan.profile()
@@ -253,7 +277,7 @@ def run_ours(args, cfg):
         d[0] += t; d[1] += fl; d[2] += by; d[3] += 1
     shapes = step_shapes(cfg)
     flops = algorithmic_flops(shapes, cfg.q, cfg.dtype == "c64")
-    value = world * flops / (ms_step * 1e-3) / 1e12
+    value = whole_job_value(world, flops, ms_step)
     peaks, peak_src = measured_peaks()
     # the dominant kernel: the family with the largest device time
     kname, (dt_ms, dfl, dby, dn) = max(by_kern.items(), key=lambda kv: kv[1][0])
@@ -370,10 +394,10 @@ def run_batched(args, cfg):
     host, io = [], []
     plan = libpeps.EinsumsvdPlan(torch.float32, [s for s, _ in shp],
                                  libpeps.make_opts(128, cfg.p, cfg.q, cfg.omega_seed, prec=prec),
-                                 instance_ids=[rank * n + i for i in range(n)], device=dev)
+                                 instance_ids=rank_instance_ids(rank, n), device=dev)
     for i, (s, _) in enumerate(shp):
         m, D = s[0], s[5]
-        inst = synth.batched_instance(cfg, rank * n + i, m, D)
+        inst = synth.batched_instance(cfg, rank_instance_ids(rank, n)[i], m, D)
         h = [torch.from_numpy(np.ascontiguousarray(inst[k], dtype=np.float32)).pin_memory()
              for k in ("V", "S", "ket", "bra")]
         host.append(h)
@@ -419,11 +443,7 @@ def run_batched(args, cfg):
             e1.record(stream)
             times.append((e0, e1))
         barrier()
-    ms_step = float(np.mean([a.elapsed_time(b) for a, b in times]))
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in times])), world, dev)
     # end to end: H2D of every instance's operands, the batch, D2H of all singular values
     h2d = sum(x.numel() * x.element_size() for h in host for x in h)
     d2h = sum(x[6].numel() * 8 for x in io)
@@ -440,7 +460,7 @@ def run_batched(args, cfg):
             hs.copy_(x[6], non_blocking=True)
         torch.cuda.synchronize()
         e2e.append(time.perf_counter() - t0)
-    e2e_s = float(np.median(e2e))
+    e2e_s = max_over_ranks(float(np.median(e2e)), world, dev)
     prof = plan.profile()
     kern = plan.kernels()
     by_kern = {}
@@ -464,7 +484,7 @@ def run_batched(args, cfg):
         peak = peaks.get("hbm_gbs", 6800.0)
         peak_note = f"HBM copy bandwidth ({peak_src})"
     line = {
-        "metric": METRIC, "value": round(world * flops / (ms_step * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+        "metric": METRIC, "value": round(whole_job_value(world, flops, ms_step), 4), "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded N(0,1) operands, instance sizes of the workload)",
