@@ -253,3 +253,54 @@ def test_energy_gradient_plans(lib, dt, shape, D, m):
     r = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None)
     assert r == 0, lib.peps_last_error().decode()
     lib.peps_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dt", [0, 1])
+def test_random_single_instance_shapes(lib, dt, prec):
+    """Seeded random zip-up step shapes, one instance per plan, each validated
+    against its workspace with the workspace one byte short refused.  Half of
+    them are drawn with bond and boundary sizes that meet the tensor-core
+    path's alignment (the mixed path's schedule for single instances: B
+    pre-expansion scratch, tensor-core CholeskyQR apply, or its SIMT fallback
+    where M > N, Grams split over K); the mixed plans must use the tensor
+    cores for those."""
+    import numpy as np
+    rng = np.random.default_rng(20200619 + 10 * dt + prec)
+    tc_plans = tall = 0
+    for i in range(16):
+        if i % 2:
+            D = [int(x) for x in rng.choice([2, 4], size=8)]
+            kL, a, b = (4 * int(x) for x in rng.integers(1, 12, size=3))
+            t = int(rng.choice([4, 16]))
+            d = 2
+        else:
+            D = [int(x) for x in rng.integers(1, 5, size=8)]
+            kL, a, b = (int(x) for x in rng.integers(1, 40, size=3))
+            t = int(rng.integers(1, 17))
+            d = int(rng.integers(1, 3))
+        m = int(rng.integers(2, 48))
+        shape = (kL, t, a, b, d) + tuple(D)
+        r, msg, r2 = _einsumsvd_ok(lib, dt, [shape], m, 4, int(rng.integers(0, 3)), prec)
+        assert r == 0, (shape, m, msg)
+        assert r2 != 0, shape
+        arr = (L.EinsumsvdShape * 1)(L.EinsumsvdShape(*shape))
+        plan, ws = C.c_void_p(), C.c_size_t()
+        assert lib.peps_einsumsvd_plan(C.byref(plan), dt, 1, arr, None, C.byref(L.make_opts(m, 4, 1, 1, prec=prec)),
+                                       C.byref(ws)) == 0
+        n = C.c_int64()
+        lib.peps_plan_launch_count(plan, C.byref(n))
+        kinds = set()
+        for j in range(n.value):
+            kk = C.c_char_p()
+            lib.peps_plan_launch_kernel(plan, j, C.byref(kk))
+            kinds.add(kk.value.decode())
+        lib.peps_plan_destroy(plan)
+        if "tc_gemm" in kinds:
+            tc_plans += 1
+            M, N = kL * t, D[2] * D[6] * b * D[3] * D[7]
+            tall += M > N
+    if prec == 1:
+        assert tc_plans >= 4, tc_plans
+    else:
+        assert tc_plans == 0
