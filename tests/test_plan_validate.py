@@ -304,3 +304,53 @@ def test_random_single_instance_shapes(lib, dt, prec):
         assert tc_plans >= 4, tc_plans
     else:
         assert tc_plans == 0
+
+
+def _stage_flops(lib, dt, shape, m, p, q, prec):
+    arr = (L.EinsumsvdShape * 1)(L.EinsumsvdShape(*shape))
+    plan, ws = C.c_void_p(), C.c_size_t()
+    assert lib.peps_einsumsvd_plan(C.byref(plan), dt, 1, arr, None, C.byref(L.make_opts(m, p, q, 1, prec=prec)),
+                                   C.byref(ws)) == 0
+    n = C.c_int64()
+    lib.peps_plan_launch_count(plan, C.byref(n))
+    agg = {}
+    for i in range(n.value):
+        tag, fl, by = C.c_char_p(), C.c_double(), C.c_double()
+        lib.peps_plan_launch_info(plan, i, C.byref(tag), C.byref(fl), C.byref(by))
+        agg[tag.value.decode()] = agg.get(tag.value.decode(), 0.0) + fl.value
+    k = C.c_int32()
+    lib.peps_einsumsvd_rank(plan, 0, C.byref(k))
+    lib.peps_plan_destroy(plan)
+    return agg, k.value
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape,m,q", [((32, 16, 32, 32, 2, 4, 4, 4, 4, 4, 4, 4, 4), 32, 2),
+                                       ((256, 64, 256, 256, 2) + (8,) * 8, 256, 2),
+                                       ((20, 9, 20, 17, 2, 3, 3, 3, 3, 3, 3, 3, 3), 8, 1)])
+def test_product_flops_follow_table_2(lib, shape, m, q, prec):
+    """The planner's flop accounting of the implicit products (what the
+    benchmark's TFLOP/s and roofline rest on) equals Table 2's two-layer
+    terms: per product of c columns, c (b d (P1 Q1 Q2 + P1 Q2 P2) + a b h v
+    + M a h) complex MACs (the four contraction stages), q + 1 products A X
+    and q + 1 products A^H Y of l columns; W is one more implicit product of k
+    columns on the tensor-core path and a k x l x N GEMM on the plain path."""
+    kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE = shape
+    P1, Q1, P2, Q2 = Dl * Du, Dx * De, DL * DU, DX * DE
+    h, v = Dl * DL, Du * DU
+    M, N = kL * t, Dx * DX * b * De * DE
+    p = 8
+    agg, k = _stage_flops(lib, 1, shape, m, p, q, prec)
+    ell = min(k + p, M, N)
+
+    def prod(c):
+        return 8.0 * c * (b * d * (P1 * Q1 * Q2 + P1 * Q2 * P2) + a * b * h * v + M * a * h)
+
+    fwd = sum(v_ for t_, v_ in agg.items() if t_.startswith("product_"))
+    adj = sum(v_ for t_, v_ in agg.items() if t_.startswith("adjoint_"))
+    assert fwd == pytest.approx((q + 1) * prod(ell), rel=1e-12)
+    if "svd_gram" in agg:                      # tensor-core path
+        assert adj + agg["epilogue_w"] == pytest.approx((q + 1) * prod(ell) + prod(k), rel=1e-12)
+    else:
+        assert adj == pytest.approx((q + 1) * prod(ell), rel=1e-12)
+        assert agg["epilogue_w"] == pytest.approx(8.0 * k * ell * N, rel=1e-12)
