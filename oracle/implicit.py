@@ -23,6 +23,15 @@ from __future__ import annotations
 from dataclasses import dataclass
 
 import numpy as np
+import torch
+
+
+def _common(*arrays):
+    """The operands as CPU torch tensors of one FP64 type (complex128 if any
+    operand is complex), sharing memory with the NumPy arrays where possible."""
+    cplx = any(np.iscomplexobj(a) for a in arrays)
+    dt = np.complex128 if cplx else np.float64
+    return [torch.from_numpy(np.ascontiguousarray(a, dtype=dt)) for a in arrays]
 
 
 @dataclass
@@ -56,24 +65,30 @@ class ImplicitOp:
 
         Pairwise contractions in the cheap order of Table 2's two-layer
         column: ket, bra (the two d D^6 terms), then S and V (the m^2 terms).
+        Each pairwise sum is one torch.einsum on the CPU (FP64 arithmetic).
         """
         ell = X.shape[1]
+        X, K, Kb, S4, V6 = _common(X, self.K, self.Kb, self.S4, self.V6)
         X6 = X.reshape(*self.col_shape, ell)
-        T1 = np.einsum("xXbeEj,sluxe->XbEjslu", X6, self.K, optimize=True)
-        T2 = np.einsum("XbEjslu,sLUXE->bjluLU", T1, np.conj(self.Kb), optimize=True)
-        T3 = np.einsum("bjluLU,auUb->jlLa", T2, self.S4, optimize=True)
-        Y = np.einsum("jlLa,ktalL->ktj", T3, self.V6, optimize=True)
-        return Y.reshape(self.M, ell)
+        T1 = torch.einsum("xXbeEj,sluxe->XbEjslu", X6, K)
+        T2 = torch.einsum("XbEjslu,sLUXE->bjluLU", T1, Kb.conj())
+        del T1
+        T3 = torch.einsum("bjluLU,auUb->jlLa", T2, S4)
+        del T2
+        Y = torch.einsum("jlLa,ktalL->ktj", T3, V6)
+        return Y.reshape(self.M, ell).resolve_conj().numpy()
 
     def rmatvec(self, Y: np.ndarray) -> np.ndarray:
         """A^H Y for Y of shape (M, ell) -> (N, ell), the chain reversed."""
         ell = Y.shape[1]
+        Y, K, Kb, S4, V6 = _common(Y, self.K, self.Kb, self.S4, self.V6)
         Y3 = Y.reshape(self.dims["kL"], self.dims["t"], ell)
-        Z3 = np.einsum("ktj,ktalL->jalL", Y3, np.conj(self.V6), optimize=True)
-        Z2 = np.einsum("jalL,auUb->jlLuUb", Z3, np.conj(self.S4), optimize=True)
-        Z1 = np.einsum("jlLuUb,sluxe->jLUbsxe", Z2, np.conj(self.K), optimize=True)
-        X = np.einsum("jLUbsxe,sLUXE->xXbeEj", Z1, self.Kb, optimize=True)
-        return X.reshape(self.N, ell)
+        Z3 = torch.einsum("ktj,ktalL->jalL", Y3, V6.conj())
+        Z2 = torch.einsum("jalL,auUb->jlLuUb", Z3, S4.conj())
+        Z1 = torch.einsum("jlLuUb,sluxe->jLUbsxe", Z2, K.conj())
+        del Z2
+        X = torch.einsum("jLUbsxe,sLUXE->xXbeEj", Z1, Kb)
+        return X.reshape(self.N, ell).resolve_conj().numpy()
 
     def dense(self) -> np.ndarray:
         """The explicit M x N matrix (only for checks on small shapes)."""

@@ -6,7 +6,8 @@ Step order, with A given only through A X and A^H Y (Sec. IV-A):
   repeat q times:  Q <- orth(A^H P);  P <- orth(A Q)
   B <- P^H A  (formed as (A^H P)^H);  U~, Sigma, V^H <- SVD(B)
   U <- P U~
-"orthogonalize" is Householder QR (LAPACK); when the block is numerically
+"orthogonalize" is Householder QR (LAPACK, through torch.linalg); when the
+block is numerically
 rank deficient (|R_ii| <= rtol max|R_ii|) the orthonormal basis of its range
 comes from an SVD instead, padded with zero columns, which is the role of
 the Gram eigen-route of Algorithm 5 for a rank-deficient input.
@@ -24,6 +25,7 @@ Readings of points the paper leaves open (all shared with the GPU path):
 from __future__ import annotations
 
 import numpy as np
+import torch
 
 from . import philox
 from .implicit import ImplicitOp
@@ -38,7 +40,8 @@ def orthogonalize(Y: np.ndarray, rtol: float) -> np.ndarray:
     """Orthonormal basis of range(Y) with the same column count."""
     if Y.shape[1] == 0:
         return Y.copy()
-    Q, R = np.linalg.qr(Y)
+    Qt, Rt = torch.linalg.qr(torch.from_numpy(np.ascontiguousarray(Y)))
+    Q, R = Qt.numpy(), Rt.numpy()
     dg = np.abs(np.diag(R))
     big = dg.max() if dg.size else 0.0
     if big == 0.0:
@@ -71,8 +74,8 @@ def rsvd_implicit(op: ImplicitOp, k: int, ell: int, q: int, omega: np.ndarray,
         Q = orthogonalize(op.rmatvec(P), rtol)
         P = orthogonalize(op.matvec(Q), rtol)
     Z = op.rmatvec(P)                  # (P^H A)^H
-    B = Z.conj().T
-    Ut, s, Vh = np.linalg.svd(B, full_matrices=False)
+    B = torch.from_numpy(np.ascontiguousarray(Z)).mH
+    Ut, s, Vh = (x.resolve_conj().numpy() for x in torch.linalg.svd(B, full_matrices=False))
     return P, Ut[:, :k], s[:k], Vh[:k]
 
 
