@@ -7,9 +7,9 @@ Step order, with A given only through A X and A^H Y (Sec. IV-A):
   B <- P^H A  (formed as (A^H P)^H);  U~, Sigma, V^H <- SVD(B)
   U <- P U~
 "orthogonalize" is Householder QR (LAPACK, through torch.linalg); when the
-block is numerically
-rank deficient (|R_ii| <= rtol max|R_ii|) the orthonormal basis of its range
-comes from an SVD instead, padded with zero columns, which is the role of
+block is numerically rank deficient (|R_ii| <= rtol max|R_ii|) the
+orthonormal basis of its range comes from an SVD instead, padded with zero
+columns, which is the role of
 the Gram eigen-route of Algorithm 5 for a rank-deficient input.
 
 Readings of points the paper leaves open (all shared with the GPU path):
