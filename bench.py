@@ -30,23 +30,48 @@ L2_BYTES = 129 * 2 ** 20
 
 
 def algorithmic_flops(shapes, q, cplx):
-    """Algorithmic flops of one contraction from its einsumsvd step shapes.
+    """Algorithmic flops of one contraction from its einsumsvd step shapes,
+    counting the work the schedule executes.
 
     Per step (complex MAC = 8 flops, real MAC = 2):
       (2q+2) implicit products, each l*(b d D^6-type site stages + the two
       m^2 stages) as counted by the plan (Table 2's two-layer terms);
-      q+1 orthogonalisations of the M x l block and q of the N x l block at
-      2 L l^2 (Householder-equivalent); the R factor of the N x l block of
-      P^H A (L l^2); U = P U~ (M l k) and W = U~^H B (k l N).
+      q+1 orthogonalisations of the M x l block at 2 M l^2
+      (Householder-equivalent), and q of the N x l block at 2 N l^2 when the
+      step runs them (s["orth_n"]; the tensor-core schedule feeds A^H P to the
+      next product directly and skips them); the R factor of the N x l block
+      of P^H A (N l^2); U = P U~ (M l k) and W = U~^H B (k l N).
     """
     mult = 8.0 if cplx else 2.0
     tot = 0.0
     for s in shapes:
         M, N, ell, k, prod = s["M"], s["N"], s["ell"], s["k"], s["prod_macs"]
-        macs = (2 * q + 2) * prod + (q + 1) * 2 * M * ell ** 2 + q * 2 * N * ell ** 2
+        macs = (2 * q + 2) * prod + (q + 1) * 2 * M * ell ** 2
+        if s.get("orth_n", True):
+            macs += q * 2 * N * ell ** 2
         macs += N * ell ** 2 + M * ell * k + k * ell * N
         tot += mult * macs
     return tot
+
+
+def tc_eligible(d, Dl, Du, Dx, De, DL, DU, DX, DE, a, b, M, cplx, double=False):
+    """Whether the library runs a step on the tensor cores: every contracted
+    extent of its stage GEMMs keeps TMA rows 16-byte aligned (a multiple of 2
+    complex or 4 real single-precision values); FP64 data never do."""
+    if double:
+        return False
+    align = 2 if cplx else 4
+    P1, Q1, P2, Q2 = Dl * Du, Dx * De, DL * DU, DX * DE
+    ks = (Q1, d * Q2, Du * DU * b, a * Dl * DL, M, a, P2, d * P1)
+    return all(k % align == 0 for k in ks)
+
+
+def mark_schedule(shapes, prec_plain, orth_q=False):
+    """Record per step whether the N-side orthogonalisations run (plain
+    schedule, or a step that falls back to it, or an explicit request)."""
+    for s in shapes:
+        s["orth_n"] = bool(prec_plain or orth_q or not s.get("tc", False))
+    return shapes
 
 
 def step_shapes(cfg):
@@ -74,7 +99,9 @@ def step_shapes(cfg):
             dd = kc[0]
             P1, Q1, P2, Q2 = kc[1] * kc[2], kc[3] * kc[4], bc[1] * bc[2], bc[3] * bc[4]
             prod = ell * (b * dd * (P1 * Q1 * Q2 + P1 * Q2 * P2) + a * h * v * b + M * a * h)
-            out.append(dict(M=M, N=N, ell=ell, k=k, prod_macs=prod, row=r, col=i))
+            tc = tc_eligible(dd, kc[1], kc[2], kc[3], kc[4], bc[1], bc[2], bc[3], bc[4], a, b, M,
+                             cfg.dtype.startswith("c"), cfg.dtype in ("f64", "c128"))
+            out.append(dict(M=M, N=N, ell=ell, k=k, prod_macs=prod, row=r, col=i, tc=tc))
             new[i - 1] = (kprev, t, k)
             kprev = k
         kl, bl = dims[r][ncol - 1], bra(r, ncol - 1)
@@ -255,7 +282,7 @@ def run_ours(args, cfg):
     host = [[torch.tensor(T, dtype=tdt).pin_memory() for T in row] for row in ket]
     h2d = sum(T.numel() * T.element_size() for row in host for T in row)
     e2e = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 5)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for r, row in enumerate(host):
@@ -275,7 +302,7 @@ def run_ours(args, cfg):
         d[0] += t; d[1] += fl; d[2] += by; d[3] += 1
         d = by_kern.setdefault(kname, [0.0, 0.0, 0.0, 0])
         d[0] += t; d[1] += fl; d[2] += by; d[3] += 1
-    shapes = step_shapes(cfg)
+    shapes = mark_schedule(step_shapes(cfg), prec == libpeps.PREC_PLAIN)
     flops = algorithmic_flops(shapes, cfg.q, cfg.dtype == "c64")
     value = whole_job_value(world, flops, ms_step)
     peaks, peak_src = measured_peaks()
@@ -302,13 +329,16 @@ def run_ours(args, cfg):
         achieved = dby / (dt_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         peak_note = f"HBM copy bandwidth ({peak_src})"
-    plain_s = None
-    if args.compare_plain and prec != libpeps.PREC_PLAIN:
+    plain = None
+    if not args.no_compare_plain and prec != libpeps.PREC_PLAIN:
+        # the plain FP32 CUDA-core path on the same PEPS: one contraction after
+        # one untimed execute (descriptor upload), CUDA events on the stream
         pplan = libpeps.ContractPlan(kt, kt if cfg.two_layer else None,
                                      libpeps.make_opts(cfg.m, cfg.p, cfg.q, cfg.omega_seed,
                                                        prec=libpeps.PREC_PLAIN))
         pplan.execute()
         torch.cuda.synchronize()
+        flush.add_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -317,7 +347,24 @@ def run_ours(args, cfg):
         torch.cuda.synchronize()
         plain_s = e0.elapsed_time(e1) / 1e3
         plain_la, _ = pplan.result()
+        pflops = algorithmic_flops(mark_schedule(step_shapes(cfg), True), cfg.q, cfg.dtype == "c64")
+        plain = {"contraction_s": round(plain_s, 4), "tflops": round(pflops / plain_s / 1e12, 4),
+                 "log_norm": plain_la, "mixed_speedup": round(plain_s / (ms_step / 1e3), 3)}
         del pplan
+    # the contracted log-norm against the FP64 oracle's stored value (rank 0's
+    # PEPS is the stored workload's): |d log|v|| and the relative error on v
+    parity = None
+    gold = load_golden(f"{cfg.name.split('_')[0]}_sweep.json") if rank == 0 else None
+    if gold is not None and "log_norm" in gold:
+        def err(x):
+            d = abs(x - gold["log_norm"])
+            return {"dlog": d, "rel_v": float(np.expm1(d)), "rel_log": d / abs(gold["log_norm"])}
+        parity = {"oracle_log_norm": gold["log_norm"], args.prec: err(la)}
+        if plain is not None:
+            parity["plain"] = err(plain["log_norm"])
+    c3 = None
+    if args.config == "c5" and not args.no_c3 and world == 1:
+        c3 = batched_subrecord(dev)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -342,10 +389,12 @@ def run_ours(args, cfg):
         "kernel_ms": {k: round(v[0], 4) for k, v in sorted(by_kern.items(), key=lambda kv: -kv[1][0])},
         "stage_ms": {k: round(v[0], 4) for k, v in sorted(by_tag.items(), key=lambda kv: -kv[1][0])},
     }
-    if plain_s is not None:
-        line["config"]["plain_fp32_contraction_s"] = round(plain_s, 4)
-        line["config"]["mixed_speedup_vs_plain"] = round(plain_s / (ms_step / 1e3), 3)
-        line["config"]["plain_log_norm"] = plain_la
+    if plain is not None:
+        line["plain_fp32"] = plain
+    if parity is not None:
+        line["parity_vs_oracle"] = parity
+    if c3 is not None:
+        line["batched_c3"] = c3
     clk = clk.summary()
     if clk:
         line["clocks"] = clk
@@ -358,9 +407,10 @@ def run_ours(args, cfg):
 
 
 def batched_shapes(cfg, rank=0):
-    """(shape tuple, algorithmic flops) of every instance of the batched
-    workload: one zip-up step per instance, kL = a = b = m, t = h = D^2,
-    rank k = m (the paper's per-step einsumsvd with its own m)."""
+    """(shape tuple, algorithmic flops, tensor-core eligible) of every
+    instance of the batched workload: one zip-up step per instance,
+    kL = a = b = m, t = h = D^2, rank k = m (the paper's per-step einsumsvd
+    with its own m)."""
     out = []
     for m, D in synth.batched_dims(cfg):
         R = D * D
@@ -368,8 +418,141 @@ def batched_shapes(cfg, rank=0):
         k = min(m, M, N)
         ell = min(k + cfg.p, M, N)
         prod = ell * (m * cfg.d * (R * R * R + R * R * R) + m * R * R * m + M * m * R)
-        shp = dict(M=M, N=N, ell=ell, k=k, prod_macs=prod)
-        out.append(((m, R, m, m, cfg.d, D, D, D, D, D, D, D, D, m), algorithmic_flops([shp], cfg.q, False)))
+        tc = tc_eligible(cfg.d, D, D, D, D, D, D, D, D, m, m, M, False)
+        shp = dict(M=M, N=N, ell=ell, k=k, prod_macs=prod, tc=tc)
+        out.append(((m, R, m, m, cfg.d, D, D, D, D, D, D, D, D, m), shp))
+    return out
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def load_golden(name):
+    try:
+        with open(os.path.join(GOLDEN, name)) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def measure_batched(cfg, prec, steps, warmup, dev, rank=0, world=1, use_graph=True, e2e=False, clock=None):
+    """One plan over the 512 instances (rank's ids), replayed as one CUDA
+    graph; returns the device time per batch, the executed algorithmic flops,
+    every instance's singular values and the plan's kernel ledger."""
+    import torch
+    from paper_2006_15234_gb300 import libpeps
+    shp = batched_shapes(cfg)
+    n = len(shp)
+    plain = prec == libpeps.PREC_PLAIN
+    flops = sum(algorithmic_flops(mark_schedule([dict(x)], plain), cfg.q, False) for _, x in shp)
+    host, io = [], []
+    ids = rank_instance_ids(rank, n)
+    plan = libpeps.EinsumsvdPlan(torch.float32, [s for s, _ in shp],
+                                 libpeps.make_opts(128, cfg.p, cfg.q, cfg.omega_seed, prec=prec),
+                                 instance_ids=ids, device=dev)
+    for i, (s, _) in enumerate(shp):
+        m, D = s[0], s[5]
+        inst = synth.batched_instance(cfg, ids[i], m, D)
+        h = [torch.from_numpy(np.ascontiguousarray(inst[k], dtype=np.float32)).pin_memory()
+             for k in ("V", "S", "ket", "bra")]
+        host.append(h)
+        k = plan.ranks[i]
+        U = torch.empty((s[0] * s[1], k), dtype=torch.float32, device=dev)
+        W = torch.empty((k, s[7] * s[11] * s[3] * s[8] * s[12]), dtype=torch.float32, device=dev)
+        sg = torch.empty(k, dtype=torch.float64, device=dev)
+        lg = torch.empty(1, dtype=torch.float64, device=dev)
+        io.append(tuple(x.to(dev) for x in h) + (U, W, sg, lg))
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    plan.execute(io)                      # descriptor upload
+    torch.cuda.synchronize()
+    run = lambda: plan.execute(io)        # noqa: E731
+    graph = None
+    if use_graph:
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                plan.execute(io)
+        stream.wait_stream(side)
+        run = graph.replay
+    for _ in range(max(0, warmup - 1)):
+        run()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    import contextlib
+    with (clock if clock is not None else contextlib.nullcontext()):
+        for _ in range(steps):
+            flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            times.append((e0, e1))
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in times]))
+    sig = [x[6].cpu().numpy() for x in io]
+    out = {"ms": ms, "flops": flops, "sig": sig, "plan": plan, "io": io, "host": host, "run": run,
+           "graph": graph is not None, "n": n, "tc_instances": sum(1 for _, x in shp if x["tc"])}
+    if e2e:
+        # end to end: H2D of every instance's operands, the batch, D2H of all singular values
+        out["h2d"] = sum(x.numel() * x.element_size() for h in host for x in h)
+        out["d2h"] = sum(x[6].numel() * 8 for x in io)
+        sig_host = [torch.empty(x[6].numel(), dtype=torch.float64).pin_memory() for x in io]
+        t = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for h, x in zip(host, io):
+                for a, b in zip(h, x[:4]):
+                    b.copy_(a, non_blocking=True)
+            run()
+            for hs, x in zip(sig_host, io):
+                hs.copy_(x[6], non_blocking=True)
+            torch.cuda.synchronize()
+            t.append(time.perf_counter() - t0)
+        out["e2e_s"] = float(np.median(t))
+    return out
+
+
+def batched_sigma_error(sig, gold):
+    """Largest normwise singular-value error max_i |s_i - s_i^ref| / s_1^ref
+    over the instances against the oracle's stored values (None without them)."""
+    if gold is None:
+        return None
+    worst = 0.0
+    for g, ref in zip(sig, gold["instances"]):
+        r = np.asarray(ref["sigma"])
+        worst = max(worst, float(np.max(np.abs(g[: len(r)] - r)) / max(r[0], 1e-300)))
+    return worst
+
+
+def batched_subrecord(dev, steps=3, warmup=3):
+    """The 512-instance batched einsumsvd in both precisions (one CUDA graph
+    per batch): device seconds per batch, executed algorithmic TFLOP/s and
+    the largest singular-value error against the oracle's stored values."""
+    import torch
+    from paper_2006_15234_gb300 import libpeps
+    cfg = synth.config("c3")
+    gold = load_golden("c3_sigma.json")
+    out = {"workload": cfg.name}
+    for name, prec in (("mixed", libpeps.PREC_MIXED), ("plain", libpeps.PREC_PLAIN)):
+        r = measure_batched(cfg, prec, steps, warmup, dev)
+        out[name] = {"batch_s": round(r["ms"] / 1e3, 5), "tflops": round(r["flops"] / (r["ms"] * 1e-3) / 1e12, 4),
+                     "sigma_err_vs_oracle": batched_sigma_error(r["sig"], gold),
+                     "kernel_launches": r["plan"].kernel_launches()}
+        if name == "mixed":
+            out["tensor_core_instances"] = r["tc_instances"]
+        del r
+        torch.cuda.empty_cache()
+    out["mixed_speedup"] = round(out["plain"]["batch_s"] / out["mixed"]["batch_s"], 3)
     return out
 
 
@@ -386,81 +569,15 @@ def run_batched(args, cfg):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    shp = batched_shapes(cfg)
-    n = len(shp)
-    flops = sum(f for _, f in shp)
     prec = {"plain": libpeps.PREC_PLAIN, "mixed": libpeps.PREC_MIXED, "fast": libpeps.PREC_FAST}[args.prec]
     # weak scaling: every rank its own 512 instances (instance seeds offset by rank)
-    host, io = [], []
-    plan = libpeps.EinsumsvdPlan(torch.float32, [s for s, _ in shp],
-                                 libpeps.make_opts(128, cfg.p, cfg.q, cfg.omega_seed, prec=prec),
-                                 instance_ids=rank_instance_ids(rank, n), device=dev)
-    for i, (s, _) in enumerate(shp):
-        m, D = s[0], s[5]
-        inst = synth.batched_instance(cfg, rank_instance_ids(rank, n)[i], m, D)
-        h = [torch.from_numpy(np.ascontiguousarray(inst[k], dtype=np.float32)).pin_memory()
-             for k in ("V", "S", "ket", "bra")]
-        host.append(h)
-        k = plan.ranks[i]
-        U = torch.empty((s[0] * s[1], k), dtype=torch.float32, device=dev)
-        W = torch.empty((k, s[7] * s[11] * s[3] * s[8] * s[12]), dtype=torch.float32, device=dev)
-        sg = torch.empty(k, dtype=torch.float64, device=dev)
-        lg = torch.empty(1, dtype=torch.float64, device=dev)
-        io.append(tuple(x.to(dev) for x in h) + (U, W, sg, lg))
+    clk = ClockSampler(local)
+    r = measure_batched(cfg, prec, args.steps, args.warmup, dev, rank, world, not args.no_graph, e2e=True,
+                        clock=clk)
+    ms_step = max_over_ranks(r["ms"], world, dev)
+    e2e_s = max_over_ranks(r["e2e_s"], world, dev)
+    flops, plan, n = r["flops"], r["plan"], r["n"]
     launches = plan.launches()
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    plan.execute(io)                      # descriptor upload
-    torch.cuda.synchronize()
-    run = lambda: plan.execute(io)        # noqa: E731
-    graph = None
-    if not args.no_graph:
-        graph = torch.cuda.CUDAGraph()
-        side = torch.cuda.Stream()
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            with torch.cuda.graph(graph, stream=side):
-                plan.execute(io)
-        stream.wait_stream(side)
-        run = graph.replay
-    for _ in range(max(0, args.warmup - 1)):
-        run()
-    barrier()
-    times = []
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.add_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            run()
-            e1.record(stream)
-            times.append((e0, e1))
-        barrier()
-    ms_step = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in times])), world, dev)
-    # end to end: H2D of every instance's operands, the batch, D2H of all singular values
-    h2d = sum(x.numel() * x.element_size() for h in host for x in h)
-    d2h = sum(x[6].numel() * 8 for x in io)
-    sig_host = [torch.empty(x[6].numel(), dtype=torch.float64).pin_memory() for x in io]
-    e2e = []
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for h, x in zip(host, io):
-            for a, b in zip(h, x[:4]):
-                b.copy_(a, non_blocking=True)
-        run()
-        for hs, x in zip(sig_host, io):
-            hs.copy_(x[6], non_blocking=True)
-        torch.cuda.synchronize()
-        e2e.append(time.perf_counter() - t0)
-    e2e_s = max_over_ranks(float(np.median(e2e)), world, dev)
     prof = plan.profile()
     kern = plan.kernels()
     by_kern = {}
@@ -483,6 +600,7 @@ def run_batched(args, cfg):
         achieved = dby / (dt_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         peak_note = f"HBM copy bandwidth ({peak_src})"
+    err = batched_sigma_error(r["sig"], load_golden("c3_sigma.json")) if rank == 0 else None
     line = {
         "metric": METRIC, "value": round(whole_job_value(world, flops, ms_step), 4), "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -491,11 +609,12 @@ def run_batched(args, cfg):
         "config": {"workload": cfg.name, "instances": n, "m_range": cfg.extra["m_range"],
                    "D_range": cfg.extra["D_range"], "p": cfg.p, "q": cfg.q, "rank": "k = m per instance",
                    "precision": args.prec, "algorithmic_tflop_per_step": round(flops / 1e12, 6),
+                   "tensor_core_instances": r["tc_instances"], "sigma_err_vs_oracle": err,
                    "l2": "flushed between steps (2x L2 write outside the timed events)",
-                   "parallelism": f"instances per rank x{world}", "cuda_graph": graph is not None},
+                   "parallelism": f"instances per rank x{world}", "cuda_graph": r["graph"]},
         "gpu_launches": plan.kernel_launches() * args.steps,
         "e2e": {"value": round(world * flops / e2e_s / 1e12, 4), "unit": "TFLOP/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "roofline": {"bound": bound, "kernel": kname, "achieved": round(achieved, 3), "peak": round(peak, 1),
                      "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
                      "launches_per_step": dn, "avg_launch_ms": round(dt_ms / dn, 5), "peak_source": peak_note,
@@ -520,7 +639,8 @@ def cpu_baseline(cfg, args):
     if cfg.name.startswith("c3"):
         # instances in order until about 15 s of oracle time
         fl, dt, cnt = 0.0, 0.0, 0
-        for i, ((s, f), (m, D)) in enumerate(zip(batched_shapes(cfg), synth.batched_dims(cfg))):
+        for i, ((s, x), (m, D)) in enumerate(zip(batched_shapes(cfg), synth.batched_dims(cfg))):
+            f = algorithmic_flops([dict(x, orth_n=True)], cfg.q, False)
             inst = synth.batched_instance(cfg, i, m, D)
             t0 = time.perf_counter()
             rsvd.einsumsvd(inst["V"], inst["S"], inst["ket"], inst["bra"], m, cfg.p, cfg.q, cfg.omega_seed, i)
@@ -656,8 +776,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3"])
     ap.add_argument("--prec", default="mixed", choices=["plain", "mixed", "fast"])
-    ap.add_argument("--compare-plain", action="store_true",
-                    help="also time one plain FP32 contraction (reported in config)")
+    ap.add_argument("--no-compare-plain", action="store_true",
+                    help="skip the plain FP32 contraction timed beside the mixed one")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the batched-einsumsvd sub-record of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--launch-list", action="store_true",

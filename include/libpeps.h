@@ -327,6 +327,40 @@ peps_status peps_expectation(const peps_network *ket, const peps_term *terms, in
                              size_t workspace_bytes, void *stream, double *energy, double *log_norm);
 
 /* ------------------------------------------------------------------------
+ * Device status word.  Every plan keeps one 32-bit word at the start of its
+ * workspace; the first launch of every execute clears it and the kernels
+ * or in these bits (Algorithm 4's operations whose failure they report):
+ *   PEPS_STATUS_NONFINITE     a non-finite largest singular value (the
+ *                             small SVD of Algorithm 4 met NaN / Inf data)
+ *   PEPS_STATUS_JACOBI_NOCONV the one-sided Jacobi SVD stopped at its sweep
+ *                             limit (30) before converging
+ *   PEPS_STATUS_TIMEOUT       a bounded wait of the tensor-core GEMM gave
+ *                             up; that kernel left its output incomplete,
+ *                             drained its own copies, freed its tensor
+ *                             memory and returned
+ * The synchronising result calls (peps_contract_result,
+ * peps_expectation_result, peps_grad_execute) read the word too and return
+ * PEPS_ERR_TIMEOUT or PEPS_ERR_NUMERIC for the first two error bits (their
+ * outputs are written all the same, but are not meaningful).
+ * ------------------------------------------------------------------------ */
+#define PEPS_STATUS_NONFINITE     1u
+#define PEPS_STATUS_JACOBI_NOCONV 2u
+#define PEPS_STATUS_TIMEOUT       4u
+
+/* Synchronise `stream`, read the status word of the plan's last execute in
+ * `workspace` into *flags (may be NULL) and return PEPS_ERR_TIMEOUT if the
+ * TIMEOUT bit is set, else PEPS_ERR_NUMERIC if the NONFINITE bit is set,
+ * else PEPS_OK.  PEPS_ERR_ARG if the plan was never executed;
+ * PEPS_ERR_CAPTURE on a capturing stream. */
+peps_status peps_poll(const peps_plan *plan, const void *workspace, void *stream, uint32_t *flags);
+
+/* Limit of one wait of the tensor-core GEMM's pipeline (TMA arrival, MMA
+ * completion, operand preparation) in nanoseconds; 0 restores the default
+ * of 2 s.  Applies to the plan's later executes.  A wait that gives up sets
+ * PEPS_STATUS_TIMEOUT (see above).  Host only. */
+peps_status peps_plan_set_wait_limit(peps_plan *plan, uint64_t ns);
+
+/* ------------------------------------------------------------------------
  * Launch ledger (profiling).  A plan's execute is a fixed list of grouped
  * kernel launches, each tagged with the stage of Algorithm 4 it serves
  * ("product_sites", "orth_m", "svd_jacobi", ...).
@@ -385,6 +419,20 @@ peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t conjB, int32
                                int32_t N, int32_t K, const void *A, const void *B, void *C,
                                void *scratch, void *stream);
 
+/* Verification entry point of the sketch generator (Algorithm 4's first
+ * line): writes elements e = j*N + n (n < N, j < ell) of the (instance, tag)
+ * Philox4x64-10 stream (counter (block, instance, tag, 0), key (seed, 0))
+ * to X[j*N + n], as the einsumsvd plans draw Omega (tag 0) and the gauge
+ * vector (tag 1).  kind PEPS_SKETCH_GAUSS: Box-Muller normals (complex:
+ * (a + i b)/sqrt 2 per pair); PEPS_SKETCH_UNIFORM: 2u - 1 with the 53-bit
+ * uniform u = ((x >> 11) + 1/2) 2^-53, rounded once to single precision for
+ * PEPS_R32 / PEPS_C64.  X is a DEVICE array of N*ell elements of dtype;
+ * desc_scratch a DEVICE buffer of at least 256 bytes (16-byte aligned) for
+ * the launch descriptor.  Synchronises `stream` before it returns.
+ * PEPS_ERR_ARG for NULL buffers or bad sizes, kinds or dtypes. */
+peps_status peps_debug_sketch(int32_t dtype, int64_t N, int32_t ell, uint64_t seed, uint64_t instance, int32_t tag,
+                              int32_t kind, void *X, void *desc_scratch, void *stream);
+
 /* ------------------------------------------------------------------------
  * Contraction without any allocation.  The paper has no counterpart: this
  * is a service of this library for callers that cannot obtain device
@@ -400,20 +448,22 @@ peps_status peps_debug_tc_gemm(int32_t cplx, int32_t conjA, int32_t conjB, int32
  * exits. */
 #define PEPS_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 
-/* Same contraction and result as peps_boundary_contract (Algorithms 2 and 3
- * with the einsumsvd of Algorithm 4), but the workspace is the library's
- * static device array instead of caller memory, and the call allocates no
- * device memory (no cudaMalloc, cudaFree or allocating library routine).
- * The site tensors in ket / bra are device arrays as for
+/* Same contraction and result as peps_boundary_contract, but the workspace
+ * is the library's static device array instead of caller memory, and the
+ * call allocates no device memory (no cudaMalloc, cudaFree or allocating
+ * library routine).  The site tensors in ket / bra are device arrays as for
  * peps_contract_plan; log_abs and phase are host pointers (either may be
- * NULL).  The call synchronises `stream` before it returns.
+ * NULL).  On success the call has synchronised `stream` before it returns;
+ * on an error it returns the status without waiting for work already
+ * enqueued.
  *  - PEPS_ERR_WORKSPACE, before anything is enqueued, when the contraction
  *    needs more than PEPS_STATIC_SCRATCH_BYTES of workspace (the need is
  *    what peps_boundary_workspace reports; the message states both sizes).
  *    Such contractions must use peps_boundary_contract with caller memory.
  *  - Set-up: the first call on a device looks up the array's device
- *    address, with that device current, and keeps it for later calls.
- *    Make that first call before any stream capture is begun.
+ *    address, with that device current, and keeps it for later calls in
+ *    the same CUDA context (a new context, e.g. after a device reset, looks
+ *    it up again).  Make that first call before any stream capture begins.
  *  - Sharing: every call on a device uses the same array, which keeps what
  *    the previous call left in it.  Each call clears the bytes it uses
  *    before its kernels run.  Calls whose work can overlap on the GPU

@@ -16,6 +16,9 @@ fixes neither generator nor layout; this is the library's reading):
     c = e & 1 of block e >> 1;
   * the 'uniform' variant (the paper's [-1, 1] draw) uses 2u - 1 instead.
 tag 0 draws sketches, tag 1 draws the gauge vector.
+A single-precision sketch rounds each 53-bit uniform once to FP32 before it
+is used (draw_elements(..., single=True)); the FP64 oracle itself draws with
+the 53-bit uniforms.
 """
 from __future__ import annotations
 
@@ -87,8 +90,25 @@ def _uniform(x: np.ndarray) -> np.ndarray:
     return ((x >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
 
 
-def _normals(words):
-    u0, u1, u2, u3 = (_uniform(w) for w in words)
+def _uniform_single(x: np.ndarray) -> np.ndarray:
+    """The uniform ((x >> 11) + 1/2) 2^-53 = (2 (x >> 11) + 1) 2^-54 rounded
+    once, to nearest with ties to even, to 24 significant bits (FP32), in
+    integer arithmetic; returned as float64 values."""
+    v = ((x >> np.uint64(11)) << np.uint64(1)) | np.uint64(1)         # odd, below 2^54
+    out = np.empty(v.shape, dtype=np.float64)
+    for i, vi in enumerate(v.tolist()):
+        shift = max(vi.bit_length() - 24, 0)
+        q = vi >> shift
+        if shift:
+            rem, half = vi & ((1 << shift) - 1), 1 << (shift - 1)
+            if rem > half or (rem == half and q & 1):
+                q += 1
+        out[i] = float(q << shift) * 2.0 ** -54
+    return out
+
+
+def _normals(uniforms):
+    u0, u1, u2, u3 = uniforms
     r0 = np.sqrt(-2.0 * np.log(u0))
     r1 = np.sqrt(-2.0 * np.log(u2))
     t0 = 2.0 * np.pi * u1
@@ -97,16 +117,20 @@ def _normals(words):
 
 
 def draw_elements(count: int, seed: int, instance: int, tag: int,
-                  is_complex: bool, kind: str = "gauss") -> np.ndarray:
-    """Elements e = 0..count-1 of the (instance, tag) stream."""
+                  is_complex: bool, kind: str = "gauss", single: bool = False) -> np.ndarray:
+    """Elements e = 0..count-1 of the (instance, tag) stream.
+
+    single: round every uniform once to FP32 first (the draw of a
+    single-precision sketch); the arithmetic after it stays in FP64."""
     per_block = 2 if is_complex else 4
     nblk = (count + per_block - 1) // per_block
     blocks = np.arange(nblk, dtype=np.uint64)
     words = philox4x64(blocks, instance, tag, 0, seed, 0)
+    us = [_uniform_single(w) if single else _uniform(w) for w in words]
     if kind == "gauss":
-        v = _normals(words)
+        v = _normals(us)
     elif kind == "uniform":
-        v = tuple(2.0 * _uniform(w) - 1.0 for w in words)
+        v = tuple(2.0 * u - 1.0 for u in us)
     else:
         raise ValueError(kind)
     if is_complex:

@@ -1,11 +1,13 @@
 // C ABI of libpeps (declared in include/libpeps.h): argument checking, plan
 // objects, descriptor upload and launch of the static schedules built by
 // step.cu (one einsumsvd) and by the boundary sweep below (Algorithms 2, 3).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <map>
 #include <memory>
@@ -145,6 +147,10 @@ struct peps_plan {
   std::vector<void *> grad_site;
   size_t split = 0;                         // ops[0, split): forward; ops[split, end): reverse sweep
   size_t sbar_off = 0;
+  // device status word (STATUS_* bits) at this workspace offset, cleared by
+  // the first launch of every execute; limit of one tensor-core pipeline wait
+  size_t status_off = 0;
+  uint64_t wait_ns = 0;
   // built schedule
   uintptr_t built_base = 0;
   bool built = false;
@@ -1142,6 +1148,7 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           if (c.Rlow) C.need(c.Rlow, es * n2, tag, "Rlow");
           if (c.Rlow && !op.wide) C.err = std::string(tag) + ": Rlow needs an FP64 factorisation";
           if (c.n > 1024) C.err = std::string(tag) + ": n above the pivot-flag buffer";
+          if (c.status) C.need(c.status, 4, tag, "status");
           if (op.smem < small_smem_bytes(op.wide ? (dt | 2) : dt, c.n))
             C.err = std::string(tag) + ": shared memory too small";
           if (op.smem2 < chol_cluster_smem_bytes(op.wide ? (dt | 2) : dt, c.n, c.T != nullptr))
@@ -1158,6 +1165,7 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
             C.err = std::string(tag) + ": cluster shared memory too small";
           if (op.blocks < j.n) C.err = std::string(tag) + ": sigma refinement grid too small";
           C.need(j.sig, 8.0 * j.n, tag, "sig");
+          if (j.status) C.need(j.status, 4, tag, "status");
         }
         break;
       case Op::FINALIZE:
@@ -1169,6 +1177,7 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           C.need(f.g, es * (double)f.M, tag, "g");
           C.need(f.Ut, es * (double)f.n * f.k, tag, "Ut");
           C.need(f.h, as * (double)f.n, tag, "h");
+          if (f.status) C.need(f.status, 4, tag, "status");
           C.need(f.sigma_out, 8.0 * f.k, tag, "sigma_out");
           C.need(f.log_out, 8, tag, "log_out");
           C.need(f.inv_s1, 8, tag, "inv_s1");
@@ -1226,6 +1235,7 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         if (t.ksplit > 1 && (int64_t)t.ksplit * t.kb_per_split * 32 < t.Kr)
           C.err = std::string(tag) + ": K chunks do not cover K";
         if (t.alpha_dev) C.need(t.alpha_dev, 8, tag, "alpha_dev");
+        if (t.status) C.need(t.status, 4, tag, "status");
         if (op.tc_kr % 4 || t.Kr != op.tc_kr) C.err = std::string(tag) + ": TMA rows not 16-byte aligned";
         if (t.bpre) {
           if (t.Braw != op.tcB || !t.split3 || op.tc_bn > 192) C.err = std::string(tag) + ": bad B pre-expansion";
@@ -1356,6 +1366,19 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
 peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool encode = false) {
   Builder B;
   B.encode = encode;
+  // the status word first (workspace offset 0), cleared by the first launch
+  B.base = (uintptr_t)ws;
+  B.dt = P->dt;
+  P->status_off = B.alloc(256);
+  B.status = (uint32_t *)B.ptr(P->status_off);
+  {
+    std::vector<ZeroDesc> d{ZeroDesc{B.status, 1}};
+    std::vector<int64_t> prefix{0};
+    Op op;
+    op.kind = Op::ZERO; op.desc_off = B.put(d); op.prefix_off = B.put(prefix); op.nd = 1; op.blocks = 1;
+    op.tag = "status";
+    B.ops.push_back(op);
+  }
   std::string e = P->kind == peps_plan::EINSUMSVD ? build_einsumsvd(P, (uintptr_t)ws, io, B)
                   : P->kind == peps_plan::CONTRACT ? build_contract(P, (uintptr_t)ws, B)
                   : P->kind == peps_plan::EGRAD    ? build_egrad(P, (uintptr_t)ws, io, B)
@@ -1363,9 +1386,23 @@ peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool en
   if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
   tc_finish(B);
   if (!B.err.empty()) return fail(PEPS_ERR_UNSUPPORTED, "%s", B.err.c_str());
+  for (Op &op : B.ops)
+    if (op.kind == Op::TC) op.tc.wait_ns = P->wait_ns;
   P->ws_bytes = finish(B, &P->blob_off);   // needs the blob size: before the move
   P->ops = std::move(B.ops);
   P->blob = std::move(B.blob);
+  return PEPS_OK;
+}
+
+// Status of the device word read back after a synchronisation: a wait that
+// gave up outranks a non-finite value; Jacobi non-convergence alone is not an
+// error (peps_poll reports it).
+static_assert(PEPS_STATUS_NONFINITE == STATUS_NONFINITE && PEPS_STATUS_JACOBI_NOCONV == STATUS_JACOBI_NOCONV &&
+                  PEPS_STATUS_TIMEOUT == STATUS_TIMEOUT,
+              "status bits of the ABI and the kernels differ");
+peps_status status_of(uint32_t w) {
+  if (w & STATUS_TIMEOUT) return fail(PEPS_ERR_TIMEOUT, "a tensor-core pipeline wait gave up (status 0x%x)", w);
+  if (w & STATUS_NONFINITE) return fail(PEPS_ERR_NUMERIC, "non-finite singular value met (status 0x%x)", w);
   return PEPS_OK;
 }
 
@@ -1646,6 +1683,28 @@ peps_status peps_contract_sigma_count(const peps_plan *plan, int64_t *count) {
   return PEPS_OK;
 }
 
+peps_status peps_poll(const peps_plan *plan, const void *workspace, void *stream, uint32_t *flags) {
+  g_last_error.clear();
+  if (!plan || !workspace) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (!plan->built) return fail(PEPS_ERR_ARG, "plan was never executed");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (in_capture(s)) return fail(PEPS_ERR_CAPTURE, "status read during stream capture");
+  uint32_t word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&word, (const uint8_t *)workspace + plan->status_off, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (flags) *flags = word;
+  return status_of(word);
+}
+
+peps_status peps_plan_set_wait_limit(peps_plan *plan, uint64_t ns) {
+  g_last_error.clear();
+  if (!plan) return fail(PEPS_ERR_ARG, "plan is NULL");
+  plan->wait_ns = ns;
+  for (Op &op : plan->ops)
+    if (op.kind == Op::TC) op.tc.wait_ns = ns;
+  return PEPS_OK;
+}
+
 peps_status peps_contract_result(peps_plan *plan, void *workspace, void *stream, double *log_abs,
                                  double *phase, double *sigma_out) {
   g_last_error.clear();
@@ -1654,13 +1713,16 @@ peps_status peps_contract_result(peps_plan *plan, void *workspace, void *stream,
   cudaStream_t s = (cudaStream_t)stream;
   if (in_capture(s)) return fail(PEPS_ERR_CAPTURE, "result read during stream capture");
   double res[2];
+  uint32_t word = 0;
   CUDA_TRY(cudaMemcpyAsync(res, (uint8_t *)workspace + plan->result_off, 16, cudaMemcpyDeviceToHost, s));
   if (sigma_out && plan->nsigma > 0)
     CUDA_TRY(cudaMemcpyAsync(sigma_out, (uint8_t *)workspace + plan->sigma_off, plan->nsigma * 8,
                              cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&word, (uint8_t *)workspace + plan->status_off, 4, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (log_abs) *log_abs = res[0];
   if (phase) *phase = res[1];
+  if (peps_status st = status_of(word)) return st;
   if (!std::isfinite(res[0]) && res[0] != -INFINITY)
     return fail(PEPS_ERR_NUMERIC, "non-finite contraction result");
   return PEPS_OK;
@@ -1760,7 +1822,10 @@ peps_status peps_expectation_result(peps_plan *plan, void *workspace, void *stre
   if (plan->lognorm_nlogs > 0)
     CUDA_TRY(cudaMemcpyAsync(lg.data(), (uint8_t *)workspace + plan->lognorm_logs_off,
                              (size_t)plan->lognorm_nlogs * 8, cudaMemcpyDeviceToHost, s));
+  uint32_t word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&word, (uint8_t *)workspace + plan->status_off, 4, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (peps_status st = status_of(word)) return st;
   auto re_ = [&](int64_t i) { return sv[(size_t)i * vals]; };
   auto im_ = [&](int64_t i) { return cplx ? sv[(size_t)i * vals + 1] : 0.0; };
   double e = 0.0;
@@ -1852,7 +1917,10 @@ peps_status peps_grad_execute(peps_plan *plan, void *const *grad_site, void *wor
   CUDA_TRY(cudaMemcpyAsync((uint8_t *)workspace + plan->sbar_off, sb.data(), sb.size() * 8, cudaMemcpyHostToDevice, s));
   // phase 2: reverse sweep into the site cotangents; synchronise (sb is host memory)
   if (peps_status st = enqueue(plan, workspace, workspace_bytes, s, false, nullptr, plan->split)) return st;
+  uint32_t word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&word, (uint8_t *)workspace + plan->status_off, 4, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (peps_status st = status_of(word)) return st;
   if (!std::isfinite(e)) return fail(PEPS_ERR_NUMERIC, "non-finite energy");
   return PEPS_OK;
 }
@@ -2050,24 +2118,54 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+
 std::mutex g_static_mu;
-void *g_static_addr[kMaxDevices] = {};
+struct StaticSlot {
+  CUcontext ctx = nullptr;  // context the address was looked up in
+  void *addr = nullptr;
+};
+StaticSlot g_static_slot[kMaxDevices];
+
+// The driver's cuCtxGetCurrent, fetched through the runtime (no libcuda link).
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return (CtxGetCurrentFn)p;
+  }();
+  return fn;
+}
 
 // Device address of g_static_scratch on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// array's name is only a host-side stand-in, so the address is looked up with
+// the device current and cached per device ordinal AND context: a device reset
+// (or a primary context torn down and made again) reloads the module, and the
+// array may then sit at another address, which the new context's lookup finds.
 peps_status static_scratch(void **addr) {
   int dev = -1;
   CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(PEPS_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return fail(PEPS_ERR_CUDA, "cannot identify the current CUDA context");
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) return fail(PEPS_ERR_CUDA, "cuCtxGetCurrent failed");
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  StaticSlot &slot = g_static_slot[dev];
+  if (!ctx || slot.ctx != ctx || !slot.addr) {
     void *p = nullptr;
+    // with the device current; also makes its primary context current if none was
     CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
     if (!p || ((uintptr_t)p & 255)) return fail(PEPS_ERR_CUDA, "static scratch address %p unusable", p);
-    g_static_addr[dev] = p;
+    if (!ctx && (get(&ctx) != CUDA_SUCCESS || !ctx))
+      return fail(PEPS_ERR_CUDA, "no current CUDA context after the symbol lookup");
+    slot.ctx = ctx;
+    slot.addr = p;
   }
-  *addr = g_static_addr[dev];
+  *addr = slot.addr;
   return PEPS_OK;
 }
 
@@ -2086,11 +2184,43 @@ extern "C" peps_status peps_boundary_contract_static(const peps_network *ket, co
                 "contraction needs %zu bytes of workspace, more than the %zu-byte static scratch; "
                 "call peps_boundary_contract with caller memory instead",
                 need, (size_t)PEPS_STATIC_SCRATCH_BYTES);
+  cudaStream_t st = (cudaStream_t)stream;
+  // refused here, before the memset, as the plan's first execute would refuse it
+  if (in_capture(st)) return fail(PEPS_ERR_CAPTURE, "contraction during stream capture");
   void *ws = nullptr;
   if (peps_status s = static_scratch(&ws)) return s;
-  cudaStream_t st = (cudaStream_t)stream;
   // the array holds the previous call's values: start this one from zeros
   CUDA_TRY(cudaMemsetAsync(ws, 0, need, st));
   if (peps_status s = peps_contract_execute(plan.get(), ws, PEPS_STATIC_SCRATCH_BYTES, stream)) return s;
   return peps_contract_result(plan.get(), ws, stream, log_abs, phase, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Verification entry of the sketch generator (Algorithm 4's first line).
+// ---------------------------------------------------------------------------
+extern "C" peps_status peps_debug_sketch(int32_t dtype, int64_t N, int32_t ell, uint64_t seed, uint64_t instance,
+                                         int32_t tag, int32_t kind, void *X, void *desc_scratch, void *stream) {
+  g_last_error.clear();
+  if (!X || !desc_scratch) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (dtype < PEPS_R32 || dtype > PEPS_C128) return fail(PEPS_ERR_ARG, "bad dtype %d", dtype);
+  if (N < 1 || ell < 1) return fail(PEPS_ERR_ARG, "N and ell must be >= 1");
+  if (kind != PEPS_SKETCH_GAUSS && kind != PEPS_SKETCH_UNIFORM) return fail(PEPS_ERR_ARG, "bad kind %d", kind);
+  if (tag < 0) return fail(PEPS_ERR_ARG, "bad tag %d", tag);
+  if (((uintptr_t)desc_scratch & 15) != 0) return fail(PEPS_ERR_ARG, "desc_scratch must be 16-byte aligned");
+  const int per = dtype_complex(dtype) ? 2 : 4;
+  const int64_t total = N * (int64_t)ell;
+  const int64_t blocks = ceil_div(ceil_div(total, per), 256);
+  if (blocks > 0x7fffffffll) return fail(PEPS_ERR_UNSUPPORTED, "block too large");
+  SketchDesc d{};
+  d.X = X; d.N = N; d.ld = N; d.ell = ell; d.tag = tag; d.kind = kind;
+  d.seed = seed; d.instance = instance; d.nblocks = blocks; d.nd = 0;
+  sketch_set_div(d);
+  struct { SketchDesc d; int64_t prefix[2]; } host{d, {0, blocks}};
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(desc_scratch, &host, sizeof host, cudaMemcpyHostToDevice, s));
+  uint8_t *dev = (uint8_t *)desc_scratch;
+  launch_sketch(dtype, (const SketchDesc *)dev, (const int64_t *)(dev + offsetof(decltype(host), prefix)), 1, blocks, s);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));   // the host copy of the descriptor dies with this call
+  return PEPS_OK;
 }

@@ -94,6 +94,7 @@ struct CholDesc {
   double tol;       // pivot threshold relative to the largest diagonal entry
   double shift;     // diagonal shift relative to the largest diagonal entry
   void *Rlow;       // optional: R rounded to single precision (FP64 kernels only)
+  uint32_t *status; // STATUS_NONFINITE when a Gram diagonal entry is not finite (may be NULL)
 };
 
 // One-sided Jacobi SVD of Mw = Rb^H (n x n, working type, column-major, built

@@ -4,7 +4,7 @@
 //    block, counter (block, instance, tag, 0), key (seed, 0); element
 //    e = j*N + n; Box-Muller on word pairs (real: 4 normals per block;
 //    complex: 2 values per block, scaled by 1/sqrt 2).  The uniform is
-//    ((x >> 11) + 1/2) 2^-53, rounded to the working precision.
+//    ((x >> 11) + 1/2) 2^-53, rounded once to the working precision.
 //  * site: the untruncated first row of the two-layer network (Algorithm 2,
 //    first line) and the zip-up start V1 = S1 O1 (Algorithm 3, first line).
 //  * scalar: the final contraction of a boundary with trivial vertical bonds
@@ -51,10 +51,11 @@ template <> struct Uni<double> {
   }
 };
 template <> struct Uni<float> {
-  // same 53-bit uniform as the double path, rounded once to 24 bits, so the
-  // relative difference stays below 2^-24 even for the smallest draws
+  // same 53-bit uniform as the double path, ((x >> 11) + 1/2) 2^-53 =
+  // (2 (x >> 11) + 1) 2^-54 exactly, rounded once to 24 bits by the integer
+  // conversion (the scaling by a power of two is exact)
   __device__ static float u(uint64_t x) {
-    return __fadd_rn(__ull2float_rn(x >> 11), 0.5f) * 0x1.0p-53f;
+    return __ull2float_rn(((x >> 11) << 1) | 1ull) * 0x1.0p-54f;
   }
   __device__ static void bm(float u0, float u1, float &a, float &b) {
     const float r = sqrtf(-2.0f * logf(u0));

@@ -60,6 +60,7 @@ struct Builder {
   bool encode = false;            // encode TMA maps (real device pointers, driver present)
   std::string err;                // first encoding failure
   size_t bx_need = 0;             // B scratch of the pre-expanded tensor-core operands (bytes)
+  uint32_t *status = nullptr;     // the plan's device status word (STATUS_* bits), in the workspace
 
   size_t alloc(size_t bytes) {
     size_t o = (top + 255) & ~(size_t)255;

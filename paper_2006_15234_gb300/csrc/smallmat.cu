@@ -138,7 +138,12 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
   T *R = (T *)g.R;
 
   double md = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) md = fmax(md, re(G[(int64_t)i * n + i]));
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const double gi = re(G[(int64_t)i * n + i]);
+    md = fmax(md, gi);
+    // a NaN / Inf diagonal would otherwise count as a dead pivot and vanish
+    if (!isfinite(gi) && g.status) atomicOr(g.status, STATUS_NONFINITE);
+  }
   md = block_max(md, red);
   const double shift = g.shift * md;
   for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
@@ -268,7 +273,12 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
   auto first_li = [&](int r) { return r - rank <= 0 ? 0 : (r - rank + kCholCTAs - 1) / kCholCTAs; };
 
   double md = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) md = fmax(md, re(G[(int64_t)i * n + i]));
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const double gi = re(G[(int64_t)i * n + i]);
+    md = fmax(md, gi);
+    // a NaN / Inf diagonal would otherwise count as a dead pivot and vanish
+    if (!isfinite(gi) && g.status) atomicOr(g.status, STATUS_NONFINITE);
+  }
   md = block_max(md, red);
   const double shift = g.shift * md, thr = g.tol * md;
   for (int64_t t = threadIdx.x; t < (int64_t)nloc * n; t += NT) {

@@ -250,6 +250,7 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
     c.shift = chol_shift(B.dt, q.ell, first_pass);
     c.Rprev = Rprev ? q.*Rprev : nullptr;
     c.Rout = Rout ? q.*Rout : nullptr;
+    c.status = B.status;
     ch.push_back(c);
     if (apply)
       app.push_back(mk_gemm(q.ell, (int)L, q.ell, 1, q.Tm, 1, q.ell, 0, false, q.*src, L, 1, 0, false,
@@ -316,13 +317,13 @@ void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I) {
   for (Inst *p : I) {
     Inst &q = *p;
     JacobiDesc j{};
-    j.Rb = q.Rout; j.Mw = q.Mw; j.sig = q.sig; j.n = q.ell; j.max_sweeps = 30; j.status = nullptr;
+    j.Rb = q.Rout; j.Mw = q.Mw; j.sig = q.sig; j.n = q.ell; j.max_sweeps = 30; j.status = B.status;
     jd.push_back(j);
     FinalizeDesc f{};
     f.Mw = q.Mw; f.sig = q.sig; f.P = q.Y; f.g = q.g; f.Ut = q.Ut; f.sigma_out = q.sigma;
     f.h = q.G;                     // the Gram buffer is free once R_B is factored
     f.log_out = q.logp; f.inv_s1 = q.inv_s1; f.n = q.ell; f.k = q.k; f.M = q.M;
-    f.rtol = 16.0 * q.ell * 2.220446049250313e-16; f.status = nullptr;
+    f.rtol = 16.0 * q.ell * 2.220446049250313e-16; f.status = B.status;
     fd.push_back(f);
   }
   Op oj;
@@ -417,6 +418,7 @@ void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const vo
   d.alpha = 1.0;
   d.alpha_dev = alpha_dev;
   d.conjC = conjC;
+  d.status = B.status;
   op.tc_bn = nmma;
   op.tcA = A; op.tcB = Bm; op.tcA_rows = rowsA; op.tcB_rows = rowsB; op.tc_kr = kr;
   const double mult = cplx ? 8.0 : 2.0, es = dtype_size(B.dt);
@@ -593,6 +595,7 @@ void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {
     ch[0] = CholDesc{};
     ch[0].G = q.G; ch[0].T = nullptr; ch[0].R = q.R2; ch[0].n = q.ell; ch[0].tol = chol_tol(B.dt, q.ell);
     ch[0].Rlow = wdt != B.dt ? q.Rout : nullptr;
+    ch[0].status = B.status;
     if (wdt == B.dt) ch[0].R = q.Rout;
     Op op;
     op.kind = Op::CHOL; op.desc_off = B.put(ch); op.nd = 1; op.tag = "svd_gram";

@@ -106,16 +106,19 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait (2 s of global time, and at most 2^26 polls); false (and the
-// abort flag raised) when it gives up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+// Bounded wait (limit_ns of global time, checked every 16 polls or, for limits
+// under 64 us, after every poll; and at most 2^26 polls); false (and the abort
+// flag raised) when it gives up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint64_t limit_ns) {
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = global_ns();
+  const uint32_t every = limit_ns < 65536 ? 0u : 15u;
   for (uint32_t i = 1; i < (1u << 26); ++i) {
     if (mbar_test_wait(bar, parity)) return true;
-    if ((i & 15) == 0) {
+    if ((i & every) == 0) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > kWaitNs) break;
+      if (global_ns() - t0 > limit_ns) break;
     }
   }
   *abort_flag = 1;
@@ -346,6 +349,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  const uint64_t wns = g.wait_ns ? g.wait_ns : kWaitNs;
 
   int issued = 0;          // producer: k blocks whose TMA was issued (over all items)
   bool mma_any = false;    // MMA thread: at least one MMA issued
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     ++folded;
   };
   auto acc_wait = [&]() -> bool {
-    return !abort_flag && mbar_wait(&acc_full[folded & 1], (folded >> 1) & 1, &abort_flag);
+    return !abort_flag && mbar_wait(&acc_full[folded & 1], (folded >> 1) & 1, &abort_flag, wns);
   };
 
   if (warp == 0) {
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         const Item it = item(w);
         for (int kb = 0; kb < it.nkb && !abort_flag; ++kb, ++gk) {
           const int s = gk % STAGES;
-          if (gk >= STAGES && !mbar_wait(&empty_bar[s], ((gk / STAGES) - 1) & 1, &abort_flag)) break;
+          if (gk >= STAGES && !mbar_wait(&empty_bar[s], ((gk / STAGES) - 1) & 1, &abort_flag, wns)) break;
           const int x = (it.kb0 + kb) * BKF;
           if constexpr (L::BPRE) {
             const int nr0 = CPLX ? 2 * it.n0 : it.n0;      // first MMA row of B (Re / Im rows when complex)
@@ -411,8 +415,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
           const bool last = FOLD ? (kb % CK == CK - 1 || kb == it.nkb - 1) : (kb == it.nkb - 1);
           const int buf = gch & 1;
           // a buffer is reused once the workers have read back the chunk two before
-          if (first && gch >= 2 && !mbar_wait(&acc_empty[buf], ((gch >> 1) - 1) & 1, &abort_flag)) { alive = false; break; }
-          if (!mbar_wait(&ready_bar[s], (gk / STAGES) & 1, &abort_flag)) { alive = false; break; }
+          if (first && gch >= 2 && !mbar_wait(&acc_empty[buf], ((gch >> 1) - 1) & 1, &abort_flag, wns)) { alive = false; break; }
+          if (!mbar_wait(&ready_bar[s], (gk / STAGES) & 1, &abort_flag, wns)) { alive = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t tacc = tmem + (uint32_t)(buf * L::ACC_COLS);
           const uint32_t b0 = smem_u32(b_tile(s, 0));
@@ -464,12 +468,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     // chunk before the last one), then prepare its operands for the MMA
     auto kblock = [&](int kb) -> bool {
       const int s = gk % STAGES;
-      bool ok = mbar_wait(&full_bar[s], (gk / STAGES) & 1, &abort_flag);
+      bool ok = mbar_wait(&full_bar[s], (gk / STAGES) & 1, &abort_flag, wns);
       const bool fold_now = FOLD && kb % CK == 0 && kb >= 2 * CK;
       if (fold_now) ok = ok && acc_wait();
       // the tensor-memory A stage of this k block was last read by k block gk - SA
       if (L::ATMEM && gk >= SAD)
-        ok = ok && mbar_wait(&a_empty[gk % SAD], ((gk / SAD) - 1) & 1, &abort_flag);
+        ok = ok && mbar_wait(&a_empty[gk % SAD], ((gk / SAD) - 1) & 1, &abort_flag, wns);
       // a warp-wide decision suffices when no named barrier follows in the k loop (BPRE)
       if (!(L::BPRE ? __all_sync(0xffffffffu, ok) : workers_all(ok))) return false;
       if (fold_now) fold_body();
@@ -653,7 +657,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     }
     if (alive && pend) alive = finish(pit, pend_end);
     // the MMA thread's final completion signal lands before the CTA may exit
-    if (alive && items > 0) mbar_wait(&done_bar, 0, &abort_flag);
+    if (alive && items > 0) mbar_wait(&done_bar, 0, &abort_flag, wns);
   }
 
   // ---- teardown: drain own copies and MMAs if a wait gave up ----

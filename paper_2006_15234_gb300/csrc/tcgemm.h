@@ -42,7 +42,8 @@ struct TcDesc {
   int32_t bpre;
   const void *Braw;        // bpre: B as given (N rows of Kr floats)
   void *Bx;                // bpre: tc_bx_bytes(N, Kr, cplx) bytes
-  uint32_t *status;
+  uint32_t *status;        // STATUS_TIMEOUT is or-ed in when a wait gives up (may be NULL)
+  uint64_t wait_ns;        // limit of one pipeline wait in ns (0: the default of 2 s)
 };
 
 // bytes of the pre-expanded B operand (head and tail rows)

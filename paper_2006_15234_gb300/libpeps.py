@@ -18,7 +18,8 @@ __all__ = [
     "EXPORTED_SYMBOLS", "PREC_PLAIN", "PREC_MIXED", "PREC_FAST", "SKETCH_GAUSS", "SKETCH_UNIFORM",
     "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
     "Term", "ExpectationPlan", "expectation", "Cotangent", "Grads", "einsumsvd_grad", "GradPlan",
-    "energy_grad", "peps_energy",
+    "energy_grad", "peps_energy", "STATUS_NONFINITE", "STATUS_JACOBI_NOCONV", "STATUS_TIMEOUT",
+    "ERR_NUMERIC", "ERR_TIMEOUT",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -35,7 +36,13 @@ EXPORTED_SYMBOLS = [
     "peps_expectation_workspace", "peps_expectation", "peps_plan_launch_kernel",
     "peps_plan_kernel_launches", "peps_einsumsvd_grad_plan", "peps_einsumsvd_grad_bind",
     "peps_einsumsvd_grad_execute", "peps_grad_plan", "peps_grad_execute", "peps_grad",
+    "peps_poll", "peps_plan_set_wait_limit", "peps_debug_sketch",
 ]
+
+# Bits of a plan's device status word (peps_poll).
+STATUS_NONFINITE, STATUS_JACOBI_NOCONV, STATUS_TIMEOUT = 1, 2, 4
+# Status codes the synchronising calls return for them.
+ERR_NUMERIC, ERR_TIMEOUT = 6, 7
 
 # Size of the library's fixed device scratch used by boundary_contract_static.
 STATIC_SCRATCH_BYTES = 32 << 20
@@ -182,6 +189,13 @@ def load():
     lib.peps_boundary_contract_static.argtypes = [C.POINTER(Network), C.POINTER(Network),
                                                   C.POINTER(RsvdOpts), vp, C.POINTER(C.c_double),
                                                   C.POINTER(C.c_double)]
+    lib.peps_debug_sketch.restype = st
+    lib.peps_debug_sketch.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
+                                      C.c_int32, vp, vp, vp]
+    lib.peps_poll.restype = st
+    lib.peps_poll.argtypes = [vp, vp, vp, C.POINTER(C.c_uint32)]
+    lib.peps_plan_set_wait_limit.restype = st
+    lib.peps_plan_set_wait_limit.argtypes = [vp, C.c_uint64]
     _lib = lib
     return lib
 
@@ -254,6 +268,16 @@ def _network(sites, d=None) -> _NetHolder:
 
 
 class _Ledger:
+    def poll(self, stream=None):
+        """(status code, status word) of the last execute, after a synchronisation."""
+        w = C.c_uint32()
+        r = self._lib.peps_poll(self._plan, C.c_void_p(self._ws), _stream_handle(stream), C.byref(w))
+        return r, w.value
+
+    def set_wait_limit(self, ns: int):
+        """Limit (ns) of one tensor-core pipeline wait for later executes; 0: default."""
+        _check(self._lib.peps_plan_set_wait_limit(self._plan, int(ns)))
+
     def launch_count(self) -> int:
         n = C.c_int64()
         _check(self._lib.peps_plan_launch_count(self._plan, C.byref(n)))
@@ -609,6 +633,22 @@ def boundary_contract_static(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=
     _check(lib.peps_boundary_contract_static(C.byref(k.net), C.byref(b.net) if b else None, C.byref(opts),
                                              _stream_handle(stream), C.byref(la), C.byref(ph)))
     return la.value, ph.value
+
+
+def debug_sketch(N, ell, seed, instance, dtype, tag=0, kind=SKETCH_GAUSS, device="cuda", stream=None):
+    """The GPU's (instance, tag) Philox stream as an (ell, N) tensor of dtype
+    (row j holds elements j*N .. j*N + N - 1)."""
+    import torch
+    lib = load()
+    X = torch.empty((int(ell), int(N)), dtype=dtype, device=device)
+    scratch = torch.empty(256, dtype=torch.uint8, device=device)
+    _check(lib.peps_debug_sketch(dtype_code(dtype), int(N), int(ell), int(seed) & (2 ** 64 - 1),
+                                 int(instance) & (2 ** 64 - 1), int(tag), int(kind), X.data_ptr(),
+                                 scratch.data_ptr(), _stream_handle(stream)))
+    return X
+
+
+__all__.append("debug_sketch")
 
 
 def debug_tc_gemm(A, B, conjA=False, conjB=False, split3=False, stream=None):

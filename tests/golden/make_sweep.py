@@ -1,12 +1,13 @@
-"""Write tests/golden/c5_sweep.json: the singular values and log(sigma_1) of
-every einsumsvd step of the whole boundary sweep (Algorithm 2 over all rows,
-Algorithm 3 per row, Algorithm 4 per step) of the 16 x 16, D = 8, m = 256
-norm workload, and the contracted log-norm, computed by the FP64 oracle only.
+"""Write tests/golden/<config>_sweep.json: the singular values and
+log(sigma_1) of every einsumsvd step of a whole boundary sweep (Algorithm 2
+over all rows, Algorithm 3 per row, Algorithm 4 per step) of a norm
+workload, and the contracted log-norm, computed by the FP64 oracle only.
 Run from the repository root:
 
-    python tests/golden/make_c5_sweep.py --cache DIR
+    python tests/golden/make_sweep.py --config c5 --cache DIR   # 16 x 16, D = 8, m = 256
+    python tests/golden/make_sweep.py --config c2               # 8 x 8, D = 4, m = 32
 
-The run takes hours on a few cores.  After every finished row the JSON is
+The 16 x 16 run takes hours on a few cores.  After every finished row the JSON is
 rewritten with the rows done so far, and (with --cache) the boundary left by
 that row is saved, so an interrupted run resumes at the next row.  The
 log-norm is written once the last row is contracted.
@@ -25,13 +26,13 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 from oracle import bmps  # noqa: E402
 
-OUT = os.path.join(ROOT, "tests", "golden", "c5_sweep.json")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def _write(path, cfg, steps, rows_done, seconds, result=None):
     out = {
         "workload": cfg.name, "m": cfg.m, "p": cfg.p, "q": cfg.q, "seed": cfg.omega_seed,
-        "generator": "tests/golden/make_c5_sweep.py (oracle.bmps: first_row_boundary, "
+        "generator": "tests/golden/make_sweep.py (oracle.bmps: first_row_boundary, "
                      "zipup per row, boundary_scalar)",
         "rows_done": rows_done, "nrow": cfg.nrow, "seconds": seconds,
         "steps": steps,
@@ -48,8 +49,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--cache", default=None, help="directory for the per-row boundary checkpoint")
     ap.add_argument("--config", default="c5", help="workload key of synth.CONFIGS")
-    ap.add_argument("--out", default=OUT)
+    ap.add_argument("--out", default=None, help="default: tests/golden/<config>_sweep.json")
     args = ap.parse_args()
+    if args.out is None:
+        args.out = os.path.join(GOLDEN, "%s_sweep.json" % args.config)
     cfg = synth.config(args.config)
     ket = synth.peps_for(cfg)
     steps, total, start, spent = [], 0.0, 1, 0.0

@@ -84,3 +84,38 @@ def test_streams_are_distinct():
     b = philox.draw_elements(64, 1, 3, 0, True)
     c = philox.draw_elements(64, 1, 2, 1, True)
     assert not np.allclose(a, b) and not np.allclose(a, c)
+
+
+def test_single_precision_uniform_is_one_correct_rounding():
+    """Reading of the single-precision sketch: each 53-bit uniform
+    ((x >> 11) + 1/2) 2^-53 is rounded once to FP32 (nearest, ties to even).
+    Checked against exact rational arithmetic: the result is an FP32 value
+    within half an FP32 unit of the exact uniform, ties going to the even
+    significand (a tie needs 2 (x >> 11) + 1 = 2^24 + 1: x >> 11 = 2^23)."""
+    from fractions import Fraction
+    words = philox.philox4x64(np.arange(600, dtype=np.uint64), 5, 0, 0, 99, 0)
+    xs = np.concatenate(list(words) + [np.array([0, 1 << 34, ((1 << 53) - 1) << 11, (1 << 52) << 11],
+                                                dtype=np.uint64)])
+    got = philox._uniform_single(xs)
+    for x, g in zip(xs.tolist(), got.tolist()):
+        assert float(np.float32(g)) == g
+        exact = Fraction(2 * (x >> 11) + 1, 1 << 54)
+        m, e = np.frexp(np.float32(g if g < 1.0 else 0.9999999))
+        ulp = Fraction(2) ** (int(e) - 24)
+        err = abs(Fraction(g) - exact)
+        assert err <= ulp / 2
+        if err == ulp / 2:
+            assert (Fraction(g) / ulp).denominator == 1 and int(Fraction(g) / ulp) % 2 == 0
+    assert philox._uniform_single(np.array([1 << 34], dtype=np.uint64))[0] == 2.0 ** -30
+
+
+def test_single_draw_differs_from_double_by_the_uniform_rounding_only():
+    """draw_elements(single=True) = the same Box-Muller / affine map applied to
+    the FP32-rounded uniforms: uniform variant equals 2 u32 - 1 exactly."""
+    a = philox.draw_elements(4000, 3, 7, 0, False, "uniform", single=True)
+    words = philox.philox4x64(np.arange(1000, dtype=np.uint64), 7, 0, 0, 3, 0)
+    u = np.stack([philox._uniform_single(w) for w in words], axis=1).reshape(-1)
+    assert np.array_equal(a, 2.0 * u - 1.0)
+    g64 = philox.draw_elements(4000, 3, 7, 0, False, "gauss")
+    g32 = philox.draw_elements(4000, 3, 7, 0, False, "gauss", single=True)
+    assert 0 < np.max(np.abs(g32 - g64)) < 1e-3

@@ -6,7 +6,9 @@ synchronisation).  It runs in the library's fixed 32 MiB device scratch array.
 
 The GPU test checks it against peps_boundary_contract (caller-provided
 workspace) on two calls in a row, the second one starting from the scratch
-the first one left behind.  The file is named to be collected last.
+the first one left behind, and checks that the second call changes neither
+the device's free memory nor any allocation count of PyTorch's caching
+allocator.  The file is named to be collected last.
 """
 import ctypes as C
 
@@ -62,7 +64,15 @@ def test_static_scratch_matches_caller_workspace(case):
     k = to_dev(ket, "c64")
     ref_la, ref_ph = libpeps.boundary_contract(k, k, m, p, q, seed, prec=prec)
     torch.cuda.synchronize()
+    keys = ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current")
     for call in range(2):
+        if call == 1:
+            free0 = torch.cuda.mem_get_info()[0]
+            st0 = torch.cuda.memory_stats()
         la, ph = libpeps.boundary_contract_static(k, k, m, p, q, seed, prec=prec)
         assert abs(la - ref_la) <= LOG_TOL * abs(ref_la), (call, la, ref_la)
         assert abs(ph - ref_ph) <= 1e-5, (call, ph, ref_ph)
+    torch.cuda.synchronize()
+    st1 = torch.cuda.memory_stats()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert [st1.get(x, 0) for x in keys] == [st0.get(x, 0) for x in keys]
