@@ -82,7 +82,14 @@ typedef enum { PEPS_SKETCH_GAUSS = 0, PEPS_SKETCH_UNIFORM = 1 } peps_sketch;
  *  sketch, prec  see the enums above
  *  flags PEPS_FLAG_ORTH_Q: in the MIXED / FAST paths, orthogonalise A^H P
  *        explicitly (Algorithm 4 literally; the default feeds it to the next
- *        product directly, which spans the same subspace) */
+ *        product directly, which spans the same subspace)
+ *        PEPS_FLAG_FP64_SMALL: single-precision data only (ignored for FP64
+ *        data and by the gradient plans): every Cholesky factorisation of
+ *        CholeskyQR2 (Algorithm 4's "orthogonalize", both sides) and the
+ *        one-sided Jacobi SVD of R_B (Algorithm 4's "SVD") run in FP64 on the
+ *        FP64-accumulated Grams, their outputs rounded once to the working
+ *        precision; the default runs them in single precision (with R_B's
+ *        factor in FP64 on the MIXED / FAST paths) */
 typedef struct {
   int32_t m, p, q;
   uint64_t seed;
@@ -91,6 +98,7 @@ typedef struct {
   uint32_t flags;
 } peps_rsvd_opts;
 #define PEPS_FLAG_ORTH_Q 1u
+#define PEPS_FLAG_FP64_SMALL 2u
 
 /* ------------------------------------------------------------------------
  * Batched einsumsvd (Algorithm 3's einsumsvd line, Algorithm 4 inside).
@@ -294,11 +302,15 @@ peps_status peps_expectation_result(peps_plan *plan, void *workspace, void *stre
 /* Energy gradient (hand-written reverse mode; the paper has no gradient):
  * E = <psi|H|psi>/<psi|psi> as computed by peps_expectation (cached
  * environments) and dE/d(site) for every site tensor of a REAL network
- * (PEPS_R32 / PEPS_R64, plain arithmetic, at least 2 x 2).  The forward keeps
- * every einsumsvd step of the four sweeps (per-step saved bases); the
- * reverse sweep runs the strip adjoints, then every sweep backwards (the
- * einsumsvd adjoint of peps_einsumsvd_grad_execute per step, the row-start
- * site adjoints), then maps the row-reversed and transposed lattices' site
+ * (PEPS_R32 / PEPS_R64, plain arithmetic, at least 2 x 2).  The rows of
+ * Algorithm 2 are the checkpoints: the forward keeps the boundary after every
+ * row of the four sweeps (the cached environments) and the einsumsvd steps'
+ * saved bases of the last row only; the reverse sweep runs the strip
+ * adjoints, then every sweep backwards row by row, first recomputing the
+ * row's zip-up from the boundary above it with its steps' forward data kept
+ * (one row's worth of step scratch, shared by all rows), then the einsumsvd
+ * adjoint of peps_einsumsvd_grad_execute per step and the row-start site
+ * adjoints; finally it maps the row-reversed and transposed lattices' site
  * cotangents back.  Sketches are held fixed (the gradient of the function
  * the forward computes). */
 peps_status peps_grad_plan(peps_plan **out, const peps_network *ket, const peps_term *terms, int32_t nterms,

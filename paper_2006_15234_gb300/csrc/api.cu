@@ -55,7 +55,8 @@ peps_status check_opts(const peps_rsvd_opts *o) {
     return fail(PEPS_ERR_ARG, "unknown sketch kind %d", o->sketch);
   if (o->prec != PEPS_PREC_PLAIN && o->prec != PEPS_PREC_MIXED && o->prec != PEPS_PREC_FAST)
     return fail(PEPS_ERR_ARG, "unknown precision %d", o->prec);
-  if (o->flags & ~PEPS_FLAG_ORTH_Q) return fail(PEPS_ERR_ARG, "unknown flag bits %#x", o->flags);
+  if (o->flags & ~(PEPS_FLAG_ORTH_Q | PEPS_FLAG_FP64_SMALL))
+    return fail(PEPS_ERR_ARG, "unknown flag bits %#x", o->flags);
   return PEPS_OK;
 }
 
@@ -63,6 +64,7 @@ RsvdOpts to_opts(const peps_rsvd_opts *o) {
   RsvdOpts r;
   r.m = o->m; r.p = o->p; r.q = o->q; r.seed = o->seed; r.sketch = o->sketch; r.prec = o->prec;
   r.orth_q = (o->flags & PEPS_FLAG_ORTH_Q) != 0;
+  r.fp64_small = (o->flags & PEPS_FLAG_FP64_SMALL) != 0;
   return r;
 }
 
@@ -122,6 +124,14 @@ struct peps_plan {
   RsvdOpts opts{};
   // einsumsvd
   std::vector<Inst> insts;
+  std::vector<Inst> embeds;                 // zero-padded copies of instances with embed set
+  // side streams of the plan's branches and their fork / join events
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_ev;
+  ~peps_plan() {
+    for (cudaEvent_t e : side_ev) cudaEventDestroy(e);
+    for (cudaStream_t st : side) cudaStreamDestroy(st);
+  }
   std::vector<peps_einsumsvd_io> io_cache;
   // einsumsvd adjoint (one instance)
   peps_einsumsvd_cotangent ct{};
@@ -167,23 +177,79 @@ size_t finish(Builder &B, size_t *blob_off) {
   return *blob_off + B.blob.size();
 }
 
-// Build the einsumsvd schedule (io may be null while sizing).
+// Side streams of a batched plan's tensor-core chains.
+constexpr int kBranches = 16;
+
+// Multiply-adds of one implicit product of an instance (Table 2's two-layer
+// terms): the cost the tensor-core chains are balanced on.
+double inst_cost(const Inst &q) {
+  const double P1 = (double)q.Dl * q.Du, Q1 = (double)q.Dx * q.De, P2 = (double)q.DL * q.DU,
+               Q2 = (double)q.DX * q.DE;
+  return (double)q.ell * ((double)q.b * q.d * (P1 * Q1 * Q2 + P1 * Q2 * P2) + (double)q.a * q.h * q.v * q.b +
+                          (double)q.M * q.a * q.h);
+}
+
+// Build the einsumsvd schedule (io may be null while sizing).  Instances on
+// the CUDA cores share grouped launches on the caller's stream (branch 0).
+// Instances on the tensor cores (extents aligned, or through a zero-padded
+// copy) each run as one chain of launches; the chains are dealt to
+// kBranches side streams by longest-processing-time-first on their product
+// cost, so that independent chains overlap on the GPU, and the chains of
+// one branch, which run one after the other, share one scratch region.
 std::string build_einsumsvd(peps_plan *P, uintptr_t base, const peps_einsumsvd_io *io, Builder &B) {
   B.base = base;
   B.dt = P->dt;
-  std::vector<Inst *> ptrs;
-  for (size_t i = 0; i < P->insts.size(); ++i) {
+  const size_t n = P->insts.size();
+  P->embeds.assign(n, Inst{});
+  std::vector<Inst *> simt;
+  std::vector<size_t> chains;
+  for (size_t i = 0; i < n; ++i) {
     Inst &I = P->insts[i];
-    inst_alloc_scratch(B, I, P->dt);
     I.logp = (double *)B.buf(8);
     if (io) {
       I.V = io[i].V; I.S = io[i].S; I.K = io[i].ket; I.Kb = io[i].bra;
       I.U = io[i].U; I.W = io[i].W; I.sigma = io[i].sigma;
       if (io[i].log_scale) I.logp = io[i].log_scale;
     }
-    ptrs.push_back(&I);
+    if (I.embed && !inst_embed_dims(I, P->dt, P->opts, P->embeds[i])) return "padded copy out of range";
+    if (I.tc || I.embed) {
+      chains.push_back(i);
+    } else {
+      inst_alloc_scratch(B, I, P->dt);
+      simt.push_back(&I);
+    }
   }
-  emit_einsumsvd(B, ptrs, P->opts);
+  if (!simt.empty()) emit_einsumsvd_simt(B, simt, P->opts);
+  if (chains.empty()) return "";
+  auto exec = [&](size_t i) -> Inst & { return P->insts[i].embed ? P->embeds[i] : P->insts[i]; };
+  std::sort(chains.begin(), chains.end(), [&](size_t x, size_t y) {
+    const double cx = inst_cost(exec(x)), cy = inst_cost(exec(y));
+    return cx != cy ? cx > cy : x < y;
+  });
+  const int nb = (int)std::min<size_t>(kBranches, chains.size());
+  std::vector<double> load(nb, 0.0);
+  std::vector<std::vector<size_t>> br(nb);
+  for (size_t i : chains) {
+    const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[b] += inst_cost(exec(i));
+    br[b].push_back(i);
+  }
+  for (int b = 0; b < nb; ++b) {
+    const size_t region = B.alloc(0);
+    size_t end = region;
+    for (size_t i : br[b]) {
+      B.top = region;
+      Inst &I = P->insts[i];
+      if (I.embed) inst_embed_alloc(B, P->embeds[i], P->dt);
+      else inst_alloc_scratch(B, I, P->dt);
+      end = std::max(end, B.top);
+      const size_t first = B.ops.size();
+      if (I.embed) emit_einsumsvd_embedded(B, I, P->embeds[i], P->opts);
+      else emit_einsumsvd_tc_one(B, I, P->opts);
+      for (size_t k = first; k < B.ops.size(); ++k) B.ops[k].branch = b + 1;
+    }
+    B.top = end;
+  }
   return "";
 }
 
@@ -571,8 +637,12 @@ void push_axpy(Builder &B, const void *x, void *y, int64_t n, const char *tag) {
 
 int64_t bsite_elems(const BSite &x) { return (int64_t)x.left * x.vert * x.right; }
 
-// Buffers of a sweep's gradient pass (per-step scratch: the reverse sweep
-// needs every step's forward data).
+// Buffers of a sweep's gradient pass with per-row checkpointing: the
+// boundary after every row (the cached environments) is the checkpoint; a
+// row's einsumsvd steps keep their forward data only while that row is being
+// reversed, so every row's step at column i (its scratch, saved bases, carry
+// and carry cotangent) is carved out of one region per column that all rows
+// share.  The boundary cotangents stay per row (they accumulate across rows).
 void sweep_grad_alloc(Builder &B, const Sweep &S, const RsvdOpts &opts, int dt, SweepGrad &SG) {
   const size_t es = dtype_size(dt);
   const Net &K = *S.ket;
@@ -583,8 +653,11 @@ void sweep_grad_alloc(Builder &B, const Sweep &S, const RsvdOpts &opts, int dt, 
   SG.carry.assign(S.last + 1, std::vector<void *>(ncol + 1, nullptr));
   SG.ccarry.assign(S.last + 1, std::vector<void *>(ncol + 1, nullptr));
   SG.steps.assign(S.last + 1, {});
-  for (int r = 1; r <= S.last; ++r)
-    for (int i = 1; i < ncol; ++i) {
+  for (int i = 1; i < ncol; ++i) {
+    const size_t region = B.alloc(0);
+    size_t end = region;
+    for (int r = 1; r <= S.last; ++r) {
+      B.top = region;
       const Inst &I0 = S.steps[r][i - 1];
       const int64_t vsz = (int64_t)I0.kL * I0.t * I0.a * I0.h;
       SG.carry[r][i] = B.buf(vsz * es);
@@ -598,11 +671,56 @@ void sweep_grad_alloc(Builder &B, const Sweep &S, const RsvdOpts &opts, int dt, 
       rec.tmpK = B.buf((int64_t)I0.d * I0.Dl * I0.Du * I0.Dx * I0.De * es);
       rec.tmpKb = B.buf((int64_t)I0.d * I0.DL * I0.DU * I0.DX * I0.DE * es);
       SG.steps[r].push_back(rec);
+      end = std::max(end, B.top);
     }
+    B.top = end;
+  }
   SG.gsite.assign(K.nrow, std::vector<void *>(ncol, nullptr));
 }
 
-// Forward of a sweep keeping every step (same ops as emit_sweep otherwise).
+// Row r of a sweep (r >= 1) keeping every step's forward data: the zip-up
+// start from the boundary after row r - 1, then the einsumsvd steps.
+void emit_row_save(Builder &B, const Sweep &S, const RsvdOpts &opts, const std::vector<std::vector<void *>> &row,
+                   SweepGrad &SG, double *logs, double *sigma, int r) {
+  const Net &K = *S.ket;
+  const int ncol = K.ncol;
+  int64_t step_idx = 0, sig_pos = 0;
+  for (int rr = 1; rr < r; ++rr)
+    for (const Inst &I : S.steps[rr]) {
+      ++step_idx;
+      sig_pos += I.k;
+    }
+  {
+    const SiteDims k = K.at(r, 0), b = sweep_bra_dims(S, r, 0);
+    SiteDesc x{};
+    x.K = K.ptr(r, 0); x.Kb = S.bra->ptr(r, 0); x.S = row[r - 1][0];
+    x.out = ncol == 1 ? row[r][0] : SG.carry[r][1];
+    x.mode = 1;
+    x.d = k.d; x.Dl = k.Dl; x.Du = k.Du; x.Dx = k.Dx; x.De = k.De;
+    x.DL = b.Dl; x.DU = b.Du; x.DX = b.Dx; x.DE = b.De; x.B = S.bound[r - 1][0].right;
+    x.total = (int64_t)k.Dx * b.Dx * x.B * k.De * b.De;
+    std::vector<SiteDesc> d{x};
+    push_site(B, d, "zipup_start");
+  }
+  for (int i = 1; i < ncol; ++i) {
+    StepRec &rec = SG.steps[r][i - 1];
+    Inst &I = rec.I;
+    I.V = SG.carry[r][i];
+    I.S = row[r - 1][i];
+    I.K = K.ptr(r, i);
+    I.Kb = S.bra->ptr(r, i);
+    I.U = row[r][i - 1];
+    I.W = (i == ncol - 1) ? row[r][ncol - 1] : SG.carry[r][i + 1];
+    I.sigma = sigma + sig_pos;
+    I.logp = logs + step_idx;
+    sig_pos += I.k;
+    ++step_idx;
+    emit_einsumsvd_save(B, I, opts, rec.G);
+  }
+}
+
+// Forward of a sweep (same ops as emit_sweep otherwise); the last row's
+// steps leave their forward data in place for the reverse sweep.
 void emit_sweep_save(Builder &B, const Sweep &S, const RsvdOpts &opts, const std::vector<std::vector<void *>> &row,
                      SweepGrad &SG, double *logs, double *sigma) {
   const Net &K = *S.ket;
@@ -620,46 +738,21 @@ void emit_sweep_save(Builder &B, const Sweep &S, const RsvdOpts &opts, const std
     }
     push_site(B, d, "first_row");
   }
-  int64_t step_idx = 0, sig_pos = 0;
-  for (int r = 1; r <= S.last; ++r) {
-    {
-      const SiteDims k = K.at(r, 0), b = sweep_bra_dims(S, r, 0);
-      SiteDesc x{};
-      x.K = K.ptr(r, 0); x.Kb = S.bra->ptr(r, 0); x.S = row[r - 1][0];
-      x.out = ncol == 1 ? row[r][0] : SG.carry[r][1];
-      x.mode = 1;
-      x.d = k.d; x.Dl = k.Dl; x.Du = k.Du; x.Dx = k.Dx; x.De = k.De;
-      x.DL = b.Dl; x.DU = b.Du; x.DX = b.Dx; x.DE = b.De; x.B = S.bound[r - 1][0].right;
-      x.total = (int64_t)k.Dx * b.Dx * x.B * k.De * b.De;
-      std::vector<SiteDesc> d{x};
-      push_site(B, d, "zipup_start");
-    }
-    for (int i = 1; i < ncol; ++i) {
-      StepRec &rec = SG.steps[r][i - 1];
-      Inst &I = rec.I;
-      I.V = SG.carry[r][i];
-      I.S = row[r - 1][i];
-      I.K = K.ptr(r, i);
-      I.Kb = S.bra->ptr(r, i);
-      I.U = row[r][i - 1];
-      I.W = (i == ncol - 1) ? row[r][ncol - 1] : SG.carry[r][i + 1];
-      I.sigma = sigma + sig_pos;
-      I.logp = logs + step_idx;
-      sig_pos += I.k;
-      ++step_idx;
-      emit_einsumsvd_save(B, I, opts, rec.G);
-    }
-  }
+  for (int r = 1; r <= S.last; ++r) emit_row_save(B, S, opts, row, SG, logs, sigma, r);
 }
 
 // Reverse of a sweep: boundary cotangents SG.crow (complete for every row the
 // strips and later rows feed) to the lattice's site cotangents SG.gsite.
 void emit_sweep_bwd(Builder &B, const Sweep &S, const RsvdOpts &opts, const std::vector<std::vector<void *>> &row,
-                    SweepGrad &SG, const double *lzero) {
+                    SweepGrad &SG, const double *lzero, double *logs, double *sigma) {
   const Net &K = *S.ket;
   const int ncol = K.ncol;
   const char *tag = "sweep_reverse";
   for (int r = S.last; r >= 1; --r) {
+    // checkpoint restart: row r's forward again from the boundary after row
+    // r - 1 (the same kernels on the same inputs rewrite the same values);
+    // the last row's forward data are still in place
+    if (r < S.last) emit_row_save(B, S, opts, row, SG, logs, sigma, r);
     for (int i = ncol - 1; i >= 1; --i) {
       StepRec &rec = SG.steps[r][i - 1];
       Inst &I = rec.I;
@@ -1035,8 +1128,8 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
     B.ops.push_back(sb);
   }
   for (auto &E : envs) {
-    if (E->has_top) emit_sweep_bwd(B, E->top, P->opts, E->top_rows, *E->tg, lzero);
-    if (E->has_bot) emit_sweep_bwd(B, E->bot, P->opts, E->bot_rows, *E->bg, lzero);
+    if (E->has_top) emit_sweep_bwd(B, E->top, P->opts, E->top_rows, *E->tg, lzero, E->top_logs, E->top_sigma);
+    if (E->has_bot) emit_sweep_bwd(B, E->bot, P->opts, E->bot_rows, *E->bg, lzero, E->bot_logs, E->bot_sigma);
   }
   // lattice copies back onto the caller's lattice: un-flip (the same axis swap), un-transpose
   auto unflip = [&](const Net &src_dims, std::vector<std::vector<void *>> &gsrc, std::vector<std::vector<void *>> &gdst) {
@@ -1147,6 +1240,8 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           if (c.Rprev) { C.need(c.Rprev, ws_ * n2, tag, "Rprev"); C.need(c.Rout, ws_ * n2, tag, "Rout"); }
           if (c.Rlow) C.need(c.Rlow, es * n2, tag, "Rlow");
           if (c.Rlow && !op.wide) C.err = std::string(tag) + ": Rlow needs an FP64 factorisation";
+          if (c.Tlow) C.need(c.Tlow, es * n2, tag, "Tlow");
+          if (c.Tlow && (!op.wide || !c.T)) C.err = std::string(tag) + ": Tlow needs an FP64 factorisation with T";
           if (c.n > 1024) C.err = std::string(tag) + ": n above the pivot-flag buffer";
           if (c.status) C.need(c.status, 4, tag, "status");
           if (op.smem < small_smem_bytes(op.wide ? (dt | 2) : dt, c.n))
@@ -1158,10 +1253,12 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
       case Op::JACOBI:
         for (int i = 0; i < op.nd; ++i) {
           const JacobiDesc &j = ((const JacobiDesc *)d)[i];
-          C.need(j.Rb, es * (double)j.n * j.n, tag, "Rb");
-          C.need(j.Mw, es * (double)j.n * j.n, tag, "Mw");
-          if (op.smem < small_smem_bytes(dt, j.n)) C.err = std::string(tag) + ": shared memory too small";
-          if (op.smem2 < jacobi_block_smem_bytes(dt, j.n) || op.smem3 < jacobi_cluster_smem_bytes(dt, j.n))
+          const int jdt = op.wide ? (dt | 2) : dt;
+          const double jes = dtype_size(jdt);
+          C.need(j.Rb, jes * (double)j.n * j.n, tag, "Rb");
+          C.need(j.Mw, jes * (double)j.n * j.n, tag, "Mw");
+          if (op.smem < small_smem_bytes(jdt, j.n)) C.err = std::string(tag) + ": shared memory too small";
+          if (op.smem2 < jacobi_block_smem_bytes(jdt, j.n) || op.smem3 < jacobi_cluster_smem_bytes(jdt, j.n))
             C.err = std::string(tag) + ": cluster shared memory too small";
           if (op.blocks < j.n) C.err = std::string(tag) + ": sigma refinement grid too small";
           C.need(j.sig, 8.0 * j.n, tag, "sig");
@@ -1249,6 +1346,10 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         break;
       case Op::MEMSET:
         C.need(op.fill_ptr, (double)op.fill_n, tag, "dst");
+        break;
+      case Op::NARROW:
+        C.need(op.aux_ptr, 8.0 * op.fill_n, tag, "src");
+        C.need(op.fill_ptr, 4.0 * op.fill_n, tag, "dst");
         break;
       case Op::AXPY:
         C.need(op.aux_ptr, es * (double)op.fill_n, tag, "x");
@@ -1348,6 +1449,21 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         }
         break;
       }
+      case Op::PAD:
+        for (int i = 0; i < op.nd; ++i) {
+          const PadDesc &q = ((const PadDesc *)d)[i];
+          double tot = 1, span = 0;
+          bool ok = q.nd >= 1 && q.nd <= 6;
+          for (int k = 0; ok && k < q.nd; ++k) {
+            ok = q.dims[k] >= 1 && q.lim[k] >= 1 && q.lim[k] <= q.dims[k] && q.in_stride[k] >= 0;
+            tot *= q.dims[k];
+            span += (double)(q.lim[k] - 1) * q.in_stride[k];
+          }
+          if (!ok || tot != (double)q.total) { C.err = std::string(tag) + ": bad pad descriptor"; break; }
+          C.need(q.in, es * (span + 1), tag, "in");
+          C.need(q.out, es * tot, tag, "out");
+        }
+        break;
       case Op::PERMUTE:
         for (int i = 0; i < op.nd; ++i) {
           const PermuteDesc &q = ((const PermuteDesc *)d)[i];
@@ -1406,8 +1522,9 @@ peps_status status_of(uint32_t w) {
   return PEPS_OK;
 }
 
-peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, bool upload,
+peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s0, bool upload,
                     cudaEvent_t *events = nullptr, size_t first = 0, size_t last = SIZE_MAX) {
+  cudaStream_t s = s0;
   if (!ws) return fail(PEPS_ERR_WORKSPACE, "workspace is NULL");
   if ((uintptr_t)ws & 255) return fail(PEPS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   if (ws_bytes < P->ws_bytes)
@@ -1421,8 +1538,29 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
   const int dt = P->dt;
   if (events) CUDA_TRY(cudaEventRecord(events[0], s));
   last = std::min(last, P->ops.size());
+  // branches > 0 run on the plan's side streams, forked from the caller's
+  // stream here and joined back after the last launch (the profiling replay
+  // keeps every launch on the caller's stream, one after the other)
+  int nbr = 1;
+  for (size_t oi = first; oi < last; ++oi) nbr = std::max(nbr, P->ops[oi].branch + 1);
+  const bool fork = nbr > 1 && !events;
+  if (fork) {
+    while ((int)P->side.size() < nbr - 1) {
+      cudaStream_t st = nullptr;
+      CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      P->side.push_back(st);
+    }
+    while ((int)P->side_ev.size() < nbr) {
+      cudaEvent_t ev = nullptr;
+      CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      P->side_ev.push_back(ev);
+    }
+    CUDA_TRY(cudaEventRecord(P->side_ev[0], s0));
+    for (int b = 1; b < nbr; ++b) CUDA_TRY(cudaStreamWaitEvent(P->side[b - 1], P->side_ev[0], 0));
+  }
   for (size_t oi = first; oi < last; ++oi) {
     const Op &op = P->ops[oi];
+    s = fork && op.branch > 0 ? P->side[op.branch - 1] : s0;
     const void *d = blob + op.desc_off;
     const int64_t *pre = (const int64_t *)(blob + op.prefix_off);
     switch (op.kind) {
@@ -1434,8 +1572,10 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
         break;
       case Op::CHOL: launch_chol(op.wide ? (dt | 2) : dt, (const CholDesc *)d, op.nd, op.smem, op.smem2, s); break;
       case Op::JACOBI:
-        launch_jacobi(dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, op.smem3, (int)op.blocks, s);
+        launch_jacobi(op.wide ? (dt | 2) : dt, (const JacobiDesc *)d, op.nd, op.smem, op.smem2, op.smem3,
+                      (int)op.blocks, s);
         break;
+      case Op::NARROW: launch_narrow((const double *)op.aux_ptr, (float *)op.fill_ptr, op.fill_n, s); break;
       case Op::FINALIZE: launch_finalize(dt, (const FinalizeDesc *)d, op.nd, (int)op.blocks, s); break;
       case Op::ZERO: launch_zero((const ZeroDesc *)d, pre, op.nd, op.blocks, s); break;
       case Op::SITE: launch_site(dt, (const SiteDesc *)d, pre, op.nd, op.blocks, s); break;
@@ -1450,6 +1590,7 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
       case Op::FILL: launch_fill(dt, op.fill_ptr, op.fill_n, op.fill_value, s); break;
       case Op::TC: launch_tc_gemm(op.tc, op.tc_bn, s); break;
       case Op::PERMUTE: launch_permute(dt, (const PermuteDesc *)d, pre, op.nd, op.blocks, s); break;
+      case Op::PAD: launch_pad(dt, (const PadDesc *)d, pre, op.nd, op.blocks, s); break;
       case Op::STRIP:
         launch_strip(dt, (const StripDesc *)d, (const StripCol *)(blob + op.aux_off[0]), blob + op.aux_off[1], op.nd,
                      s);
@@ -1471,6 +1612,11 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s, boo
     }
     if (events) CUDA_TRY(cudaEventRecord(events[&op - P->ops.data() + 1], s));
   }
+  if (fork)
+    for (int b = 1; b < nbr; ++b) {
+      CUDA_TRY(cudaEventRecord(P->side_ev[b], P->side[b - 1]));
+      CUDA_TRY(cudaStreamWaitEvent(s0, P->side_ev[b], 0));
+    }
   CUDA_TRY(cudaGetLastError());
   return PEPS_OK;
 }
@@ -1524,6 +1670,8 @@ peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch
     inst_derive(I, oi);
     I.instance = instance_ids ? instance_ids[i] : (uint64_t)i;
     I.tc = P->opts.prec != PEPS_PREC_PLAIN && inst_tc_ok(I, dtype);
+    Inst E{};
+    I.embed = P->opts.prec != PEPS_PREC_PLAIN && !I.tc && inst_embed_dims(I, dtype, oi, E);
     P->insts.push_back(I);
   }
   if (peps_status s = rebuild(P.get(), nullptr, nullptr)) return s;
@@ -1985,7 +2133,7 @@ peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count) {
       case Op::TC: n += (op.tc.tiles_m * op.tc.tiles_n > 0) + (op.tc.bpre != 0); break;   // B expansion, GEMM
       case Op::COPY: case Op::MEMSET: break;                                  // copies, not kernels
       case Op::SKETCH: case Op::GEMM: case Op::GEMM_ATOMIC: case Op::SANDWICH: case Op::ZERO: case Op::SITE:
-      case Op::PERMUTE: n += op.blocks > 0; break;
+      case Op::PERMUTE: case Op::PAD: n += op.blocks > 0; break;
       default: n += 1; break;
     }
   }
@@ -2010,6 +2158,8 @@ peps_status peps_plan_launch_kernel(const peps_plan *plan, int64_t i, const char
     case Op::FILL: *kernel = "fill"; break;
     case Op::TC: *kernel = "tc_gemm"; break;
     case Op::PERMUTE: *kernel = "permute"; break;
+    case Op::PAD: *kernel = "pad"; break;
+    case Op::NARROW: *kernel = "narrow"; break;
     case Op::STRIP: *kernel = "strip"; break;
     case Op::COPY: *kernel = "copy"; break;
     case Op::SVDBWD: *kernel = "svd_bwd"; break;

@@ -80,6 +80,24 @@ struct PermuteDesc {
   int32_t conj;
 };
 
+// Strided copy with zero fill over up to 6 index digits (most significant
+// first): out[o] for o < total (row-major over dims[]) takes
+// in[sum_d digit_d * in_stride[d]] when every digit_d < lim[d], else 0.
+// Zero-pads a tensor into larger bond dimensions (lim = source dims < dims)
+// or cuts the padding off again (lim = dims, strides of the padded source).
+struct PadDesc {
+  const void *in;
+  void *out;
+  int32_t nd;
+  int32_t dims[6], lim[6];
+  int64_t in_stride[6];
+  int64_t total;
+};
+constexpr int kPadPerBlock = 256;
+void launch_pad(int dt, const PadDesc *d, const int64_t *prefix, int nd, int64_t blocks, cudaStream_t s);
+// out[i] = in[i] rounded to single precision, i < n (real values)
+void launch_narrow(const double *in, float *out, int64_t n, cudaStream_t s);
+
 // Cholesky of a Hermitian Gram (FP64 accumulators, row-major n x n) with
 // pivot skipping and an optional diagonal shift, in the working precision:
 // upper factor R and T = R^+ (working type, n x n).  If Rprev != nullptr the
@@ -95,6 +113,7 @@ struct CholDesc {
   double shift;     // diagonal shift relative to the largest diagonal entry
   void *Rlow;       // optional: R rounded to single precision (FP64 kernels only)
   uint32_t *status; // STATUS_NONFINITE when a Gram diagonal entry is not finite (may be NULL)
+  void *Tlow;       // optional: T rounded to single precision (FP64 kernels only)
 };
 
 // One-sided Jacobi SVD of Mw = Rb^H (n x n, working type, column-major, built

@@ -215,6 +215,23 @@ __global__ void site_kernel(const SiteDesc *__restrict__ descs, const int64_t *_
   ((T *)g.out)[idx] = narrow<T>(acc);
 }
 
+template <class T>
+__global__ void pad_kernel(const PadDesc *__restrict__ descs, const int64_t *__restrict__ prefix, int nd) {
+  const int di = find_desc(prefix, nd, blockIdx.x);
+  const PadDesc &g = descs[di];
+  const int64_t o = (int64_t)(blockIdx.x - prefix[di]) * kPadPerBlock + threadIdx.x;
+  if (o >= g.total) return;
+  int64_t r = o, off = 0;
+  bool in_range = true;
+  for (int d = g.nd - 1; d >= 0; --d) {
+    const int64_t dig = r % g.dims[d];
+    r /= g.dims[d];
+    in_range = in_range && dig < g.lim[d];
+    off += dig * g.in_stride[d];
+  }
+  ((T *)g.out)[o] = in_range ? ((const T *)g.in)[off] : zero<T>();
+}
+
 __global__ void zero_kernel(const ZeroDesc *__restrict__ descs, const int64_t *__restrict__ prefix,
                             int nd) {
   const int di = find_desc(prefix, nd, blockIdx.x);
@@ -286,6 +303,27 @@ void launch_sketch(int dt, const SketchDesc *d, const int64_t *prefix, int nd, i
     case DT_C64: sketch_t<float2>(d, prefix, nd, blocks, s); break;
     case DT_R64: sketch_t<double>(d, prefix, nd, blocks, s); break;
     case DT_C128: sketch_t<double2>(d, prefix, nd, blocks, s); break;
+  }
+}
+
+namespace {
+__global__ void narrow_kernel(const double *__restrict__ in, float *__restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+}  // namespace
+
+void launch_narrow(const double *in, float *out, int64_t n, cudaStream_t s) {
+  if (n > 0) narrow_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(in, out, n);
+}
+
+void launch_pad(int dt, const PadDesc *d, const int64_t *prefix, int nd, int64_t blocks, cudaStream_t s) {
+  if (blocks <= 0) return;
+  switch (dt) {
+    case DT_R32: pad_kernel<float><<<(unsigned)blocks, kPadPerBlock, 0, s>>>(d, prefix, nd); break;
+    case DT_C64: pad_kernel<float2><<<(unsigned)blocks, kPadPerBlock, 0, s>>>(d, prefix, nd); break;
+    case DT_R64: pad_kernel<double><<<(unsigned)blocks, kPadPerBlock, 0, s>>>(d, prefix, nd); break;
+    case DT_C128: pad_kernel<double2><<<(unsigned)blocks, kPadPerBlock, 0, s>>>(d, prefix, nd); break;
   }
 }
 

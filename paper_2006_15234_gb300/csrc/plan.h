@@ -15,7 +15,7 @@ namespace peps {
 
 struct Op {
   enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL, TC,
-              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD, MEMSET, STRIPBWD, SITEBWD, AXPY } kind;
+              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD, MEMSET, STRIPBWD, SITEBWD, AXPY, PAD, NARROW } kind;
   size_t desc_off = 0;    // byte offset of the descriptor array in the blob
   size_t prefix_off = 0;  // byte offset of the int64 block prefix array in the blob
   int nd = 0;
@@ -23,18 +23,23 @@ struct Op {
   int smem = 0;
   int smem2 = 0;          // second kernel of the launch (cluster Cholesky, block-cyclic cluster Jacobi)
   int smem3 = 0;          // third kernel of the launch (column-window cluster Jacobi)
-  bool wide = false;      // CHOL: run in FP64 on single-precision data
+  bool wide = false;      // CHOL, JACOBI: run in FP64 on single-precision data
   ScalarDesc scalar{};
   size_t aux_off[3] = {0, 0, 0};  // blob offsets of the scalar's device arrays
   void *fill_ptr = nullptr;
   const void *aux_ptr = nullptr;  // COPY / LTU / AXPY source
   StripBwdScratch sbs{};          // STRIPBWD scratch
   const double *sbar = nullptr;   // STRIPBWD strip cotangents
-  int64_t fill_n = 0;             // FILL: elements; COPY: bytes; LTU: n
+  int64_t fill_n = 0;             // FILL: elements; COPY: bytes; LTU: n; NARROW: real values
   double fill_value = 0.0;
   std::string tag;        // stage name (profiling ledger)
   double flops = 0.0;     // algorithmic flops of the launch
   double bytes = 0.0;     // algorithmic DRAM bytes of the launch
+  // independent chain the launch belongs to: 0 runs on the caller's stream,
+  // b > 0 on the plan's side stream b (forked from and joined back into the
+  // caller's stream, so a captured execute holds the chains as parallel
+  // graph branches)
+  int branch = 0;
   // tensor-core GEMM (kind TC): descriptor passed by value, operand spans
   TcDesc tc{};
   int tc_bn = 0;
@@ -61,6 +66,8 @@ struct Builder {
   std::string err;                // first encoding failure
   size_t bx_need = 0;             // B scratch of the pre-expanded tensor-core operands (bytes)
   uint32_t *status = nullptr;     // the plan's device status word (STATUS_* bits), in the workspace
+  int branch = 0;                 // branch of the ops emitted next (Op::branch)
+  std::vector<size_t> bx_branch;  // B scratch need per branch > 0 (bytes)
 
   size_t alloc(size_t bytes) {
     size_t o = (top + 255) & ~(size_t)255;
@@ -69,6 +76,11 @@ struct Builder {
   }
   void *ptr(size_t off) const { return (void *)(base + off); }
   void *buf(size_t bytes) { return ptr(alloc(bytes)); }
+  int branches() const {
+    int n = 1;
+    for (const Op &o : ops) n = o.branch + 1 > n ? o.branch + 1 : n;
+    return n;
+  }
 
   size_t put_bytes(const void *p, size_t n) {
     size_t o = (blob.size() + 15) & ~(size_t)15;
@@ -101,6 +113,9 @@ struct Inst {
   // tensor-core path scratch
   void *T1, *VT, *ST, *UT, *KT, *KbP, *KbT;
   bool tc;                          // this instance runs its products on tensor cores
+  // runs as a zero-padded copy whose extents meet the tensor cores' alignment
+  // (set on the caller's instance; the copy is a separate Inst)
+  bool embed;
 };
 
 struct RsvdOpts {
@@ -109,6 +124,7 @@ struct RsvdOpts {
   int sketch;
   int prec;
   bool orth_q;
+  bool fp64_small;     // single-precision data: CholeskyQR2's factorisations and the Jacobi SVD in FP64
 };
 
 // Shape bookkeeping shared by every planner.
@@ -150,6 +166,20 @@ void emit_einsumsvd_bwd(Builder &B, Inst &q, const RsvdOpts &o, GradBufs &G, con
 
 // Emit every stage of one einsumsvd over a group of instances.
 void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);
+// Dimensions of the zero-padded copy of I that meets the tensor-core alignment
+// (every bond even; t and a multiples of 4 real / 2 complex values), with
+// I's rank k and sketch width l; false if the copy would exceed the kernels'
+// limits.
+bool inst_embed_dims(const Inst &I, int dt, const RsvdOpts &o, Inst &E);
+// Bytes of E's scratch plus its padded operands and outputs.
+size_t inst_embed_bytes(const Inst &E, int dt);
+// Carve E's scratch, padded operands and outputs out of the builder.
+void inst_embed_alloc(Builder &B, Inst &E, int dt);
+// One instance through its padded copy E: operands zero-padded into E, the
+// tensor-core einsumsvd of E with the sketch and gauge vector drawn at I's
+// element numbering, U and W cut back into I's outputs.
+void emit_einsumsvd_embedded(Builder &B, Inst &I, Inst &E, const RsvdOpts &o);
+void emit_einsumsvd_tc_one(Builder &B, Inst &q, const RsvdOpts &o);
 void emit_einsumsvd_simt(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);
 
 }  // namespace peps

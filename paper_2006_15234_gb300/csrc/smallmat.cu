@@ -224,6 +224,14 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
     }
     __syncthreads();
   }
+  if constexpr (sizeof(typename Traits<T>::Real) == 8) {
+    if (g.Tlow) {
+      for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+        if constexpr (sizeof(T) == 16) ((float2 *)g.Tlow)[t] = narrow<float2>(widen(Tm[t]));
+        else ((float *)g.Tlow)[t] = narrow<float>(widen(Tm[t]));
+      }
+    }
+  }
   if (g.Rprev) {
     const T *P = (const T *)g.Rprev;
     T *O = (T *)g.Rout;
@@ -424,6 +432,10 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
       if (g.Rlow) {
         if constexpr (sizeof(T) == 16) ((float2 *)g.Rlow)[o] = narrow<float2>(widen(Wl[t]));
         else ((float *)g.Rlow)[o] = narrow<float>(widen(Wl[t]));
+      }
+      if (needT && g.Tlow) {
+        if constexpr (sizeof(T) == 16) ((float2 *)g.Tlow)[o] = narrow<float2>(widen(Tl[t]));
+        else ((float *)g.Tlow)[o] = narrow<float>(widen(Tl[t]));
       }
     }
     if (g.Rprev) {

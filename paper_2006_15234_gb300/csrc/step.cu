@@ -231,9 +231,13 @@ constexpr int64_t BIG = 0x7fffffff;          // radix of an index map's last dig
 // accumulation across K chunks), and so does the M-side apply (src and T
 // transposed into free scratch first: the sketch block X, which the M-side
 // orthogonalisation never reads, and the Jacobi matrix).
+// wide (single-precision data): the Cholesky runs in FP64 on the FP64 Gram,
+// R into the FP64-sized Rdst, T = R^+ in FP64 into R2 and rounded once into
+// Tm for the apply (R2 is free during the orthogonalisations).
 void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*src, void *Inst::*dst,
                    void *Inst::*Rdst, void *Inst::*Rprev, void *Inst::*Rout, bool apply, const char *tag,
-                   bool first_pass, bool tc_gram = false) {
+                   bool first_pass, bool tc_gram = false, bool wide = false) {
+  wide = wide && !dtype_double(B.dt) && !Rprev;
   const int as = acc_size(B.dt);
   std::vector<std::pair<void *, int64_t>> z;
   std::vector<GemmDesc> gram, app;
@@ -251,6 +255,10 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
     c.Rprev = Rprev ? q.*Rprev : nullptr;
     c.Rout = Rout ? q.*Rout : nullptr;
     c.status = B.status;
+    if (wide) {
+      c.T = q.R2;
+      c.Tlow = q.Tm;
+    }
     ch.push_back(c);
     if (apply)
       app.push_back(mk_gemm(q.ell, (int)L, q.ell, 1, q.Tm, 1, q.ell, 0, false, q.*src, L, 1, 0, false,
@@ -269,9 +277,11 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
   op.desc_off = B.put(ch);
   op.nd = (int)ch.size();
   op.tag = tag;
+  op.wide = wide;
+  const int fdt = wide ? (B.dt | 2) : B.dt;
   for (auto &c : ch) {
-    op.smem = std::max(op.smem, small_smem_bytes(B.dt, c.n));
-    op.smem2 = std::max(op.smem2, chol_cluster_smem_bytes(B.dt, c.n, c.T != nullptr));
+    op.smem = std::max(op.smem, small_smem_bytes(fdt, c.n));
+    op.smem2 = std::max(op.smem2, chol_cluster_smem_bytes(fdt, c.n, c.T != nullptr));
   }
   B.ops.push_back(op);
   if (!apply) return;
@@ -288,22 +298,62 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
   push_gemm(B, app, false, tag);
 }
 
-void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I);
+void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I, bool wide = false);
 
-void emit_orth(Builder &B, std::vector<Inst *> &I, bool mside, bool tc_gram = false) {
+void emit_orth(Builder &B, std::vector<Inst *> &I, bool mside, bool tc_gram = false, bool wide = false) {
   void *Inst::*a = mside ? &Inst::Y : &Inst::Z;
   void *Inst::*t = mside ? &Inst::P : &Inst::X;
   const char *tag = mside ? "orth_m" : "orth_n";
-  emit_cqr_pass(B, I, mside, a, t, &Inst::R1, nullptr, nullptr, true, tag, true, tc_gram);
-  emit_cqr_pass(B, I, mside, t, a, &Inst::R1, nullptr, nullptr, true, tag, false, tc_gram);
+  emit_cqr_pass(B, I, mside, a, t, &Inst::R1, nullptr, nullptr, true, tag, true, tc_gram, wide);
+  emit_cqr_pass(B, I, mside, t, a, &Inst::R1, nullptr, nullptr, true, tag, false, tc_gram, wide);
 }
 
-void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
+// FP64 Cholesky of the FP64 Gram of Z (no apply): R_B in FP64 into R2 and
+// rounded once into Rout.
+void emit_rb_wide(Builder &B, std::vector<Inst *> &I, const char *tag) {
+  const int wdt = B.dt | 2;
+  std::vector<CholDesc> ch;
+  for (Inst *p : I) {
+    Inst &q = *p;
+    CholDesc c{};
+    c.G = q.G; c.T = nullptr; c.R = q.R2; c.n = q.ell; c.tol = chol_tol(B.dt, q.ell);
+    c.Rlow = q.Rout;
+    c.status = B.status;
+    ch.push_back(c);
+  }
+  Op op;
+  op.kind = Op::CHOL; op.desc_off = B.put(ch); op.nd = (int)ch.size(); op.tag = tag;
+  op.wide = true;
+  for (auto &c : ch) {
+    op.smem = std::max(op.smem, small_smem_bytes(wdt, c.n));
+    op.smem2 = std::max(op.smem2, chol_cluster_smem_bytes(wdt, c.n, false));
+  }
+  B.ops.push_back(op);
+}
+
+void emit_small_svd(Builder &B, std::vector<Inst *> &I, bool wide = false) {
   // R_B: CholeskyQR2 of Z = (P^H A)^H (R_B = R2 R1, R_B^H R_B = B B^H with
   // B = P^H A, so its singular values are those of B).  FP64 data: one
-  // Cholesky of the FP64 Gram is already accurate.
+  // Cholesky of the FP64 Gram is already accurate; so is one FP64 Cholesky
+  // of the FP64-accumulated Gram for single-precision data (wide).
   if (dtype_double(B.dt)) {
     emit_cqr_pass(B, I, false, &Inst::Z, nullptr, &Inst::Rout, nullptr, nullptr, false, "svd_qr", false);
+  } else if (wide) {
+    const int as = acc_size(B.dt);
+    std::vector<std::pair<void *, int64_t>> z;
+    std::vector<GemmDesc> gram;
+    for (Inst *p : I) {
+      Inst &q = *p;
+      z.push_back({q.G, (int64_t)q.ell * q.ell * as / 8});
+      gram.push_back(mk_gemm(q.ell, q.ell, (int)q.N, 1, q.Z, q.N, 1, 0, true, q.Z, 1, q.N, 0, false, q.G, q.ell, 1,
+                             0));
+    }
+    for (auto &g : gram) set_ksplit(g, (int)gram.size());
+    push_zero(B, z, "svd_qr");
+    push_gemm(B, gram, true, "svd_qr");
+    emit_rb_wide(B, I, "svd_qr");
+    emit_jacobi_finalize(B, I, true);
+    return;
   } else {
     emit_cqr_pass(B, I, false, &Inst::Z, &Inst::X, &Inst::R1, nullptr, nullptr, true, "svd_qr", true);
     emit_cqr_pass(B, I, false, &Inst::X, nullptr, &Inst::R2, &Inst::R1, &Inst::Rout, false, "svd_qr", false);
@@ -311,16 +361,20 @@ void emit_small_svd(Builder &B, std::vector<Inst *> &I) {
   emit_jacobi_finalize(B, I);
 }
 
-void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I) {
+// wide (single-precision data whose R_B was factored in FP64 into R2): the
+// Jacobi SVD runs in FP64 on R2 (Mw in FP64), its result is rounded once into
+// R1 for the finalize.
+void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I, bool wide) {
+  wide = wide && !dtype_double(B.dt);
   std::vector<JacobiDesc> jd;
   std::vector<FinalizeDesc> fd;
   for (Inst *p : I) {
     Inst &q = *p;
     JacobiDesc j{};
-    j.Rb = q.Rout; j.Mw = q.Mw; j.sig = q.sig; j.n = q.ell; j.max_sweeps = 30; j.status = B.status;
+    j.Rb = wide ? q.R2 : q.Rout; j.Mw = q.Mw; j.sig = q.sig; j.n = q.ell; j.max_sweeps = 30; j.status = B.status;
     jd.push_back(j);
     FinalizeDesc f{};
-    f.Mw = q.Mw; f.sig = q.sig; f.P = q.Y; f.g = q.g; f.Ut = q.Ut; f.sigma_out = q.sigma;
+    f.Mw = wide ? q.R1 : q.Mw; f.sig = q.sig; f.P = q.Y; f.g = q.g; f.Ut = q.Ut; f.sigma_out = q.sigma;
     f.h = q.G;                     // the Gram buffer is free once R_B is factored
     f.log_out = q.logp; f.inv_s1 = q.inv_s1; f.n = q.ell; f.k = q.k; f.M = q.M;
     f.rtol = 16.0 * q.ell * 2.220446049250313e-16; f.status = B.status;
@@ -328,13 +382,24 @@ void emit_jacobi_finalize(Builder &B, std::vector<Inst *> &I) {
   }
   Op oj;
   oj.kind = Op::JACOBI; oj.desc_off = B.put(jd); oj.nd = (int)jd.size(); oj.tag = "svd_jacobi";
+  oj.wide = wide;
+  const int jdt = wide ? (B.dt | 2) : B.dt;
   for (auto &j : jd) {
-    oj.smem = std::max(oj.smem, small_smem_bytes(B.dt, j.n));
-    oj.smem2 = std::max(oj.smem2, jacobi_block_smem_bytes(B.dt, j.n));
-    oj.smem3 = std::max(oj.smem3, jacobi_cluster_smem_bytes(B.dt, j.n));
+    oj.smem = std::max(oj.smem, small_smem_bytes(jdt, j.n));
+    oj.smem2 = std::max(oj.smem2, jacobi_block_smem_bytes(jdt, j.n));
+    oj.smem3 = std::max(oj.smem3, jacobi_cluster_smem_bytes(jdt, j.n));
     oj.blocks = std::max<int64_t>(oj.blocks, j.n);       // largest n: column blocks of the sigma refinement
   }
   B.ops.push_back(oj);
+  if (wide)
+    for (Inst *p : I) {
+      Op on;
+      on.kind = Op::NARROW; on.tag = "svd_jacobi";
+      on.aux_ptr = p->Mw; on.fill_ptr = p->R1;
+      on.fill_n = (int64_t)p->ell * p->ell * (dtype_complex(B.dt) ? 2 : 1);
+      on.bytes = 12.0 * on.fill_n;
+      B.ops.push_back(on);
+    }
   Op of;
   of.kind = Op::FINALIZE; of.desc_off = B.put(fd); of.nd = (int)fd.size(); of.tag = "svd_finalize";
   for (auto &f : fd) of.blocks = std::max<int64_t>(of.blocks, f.n);
@@ -433,10 +498,18 @@ void emit_tc(Builder &B, const char *tag, const void *A, int64_t rowsA, const vo
 // of the pre-expanded B operands, which point into it.
 void tc_finish(Builder &B) {
   if (!B.bx_need) return;
-  void *bx = B.buf(B.bx_need);
+  // one B scratch per branch (chains of different branches may run at once)
+  std::vector<size_t> need(B.branches(), 0);
+  for (const Op &op : B.ops)
+    if (op.kind == Op::TC && op.tc.bpre)
+      need[op.branch] = std::max<size_t>(need[op.branch], (size_t)tc_bx_bytes(op.tcB_rows, op.tc_kr, op.tc.cplx != 0));
+  std::vector<void *> bxs(need.size(), nullptr);
+  for (size_t b = 0; b < need.size(); ++b)
+    if (need[b]) bxs[b] = B.buf(need[b]);
   for (Op &op : B.ops) {
     if (op.kind != Op::TC || !op.tc.bpre) continue;
     TcDesc &d = op.tc;
+    void *bx = bxs[op.branch];
     d.Bx = bx;
     if (!B.encode) continue;
     const int64_t nr = (int64_t)d.N * (d.cplx ? 2 : 1), pitch = (int64_t)d.Kr * 4;
@@ -509,35 +582,54 @@ void emit_tc_prep(Builder &B, Inst &q) {
   emit_permute(B, "tc_prep", {mk_perm(q.Kb, q.KbP, 1, z.d, z.P2, z.Q2)});
 }
 
-void emit_product_tc(Builder &B, Inst &q, const void *src, void *dst, bool split3) {
+// Algorithmic flops and bytes of the last launch recomputed for the extents a
+// padded copy stands in for (the padding is not algorithmic work).
+void relabel(Builder &B, int64_t rowsA, int64_t rowsB, int64_t K) {
+  Op &op = B.ops.back();
+  const double mult = dtype_complex(B.dt) ? 8.0 : 2.0, es = dtype_size(B.dt);
+  op.flops = mult * (double)rowsA * rowsB * K;
+  op.bytes = es * ((double)rowsA * K + (double)rowsB * K + (double)rowsA * rowsB);
+}
+
+void emit_product_tc(Builder &B, Inst &q, const void *src, void *dst, bool split3, const Inst *lg = nullptr) {
   const Dims6 z = dims_of(q, q.ell);
+  const Dims6 y = lg ? dims_of(*lg, q.ell) : z;
   // T1 rows (j, l, u, b) with b fastest, columns (s, X, E)
   emit_tc(B, "product_sites", src, z.l * z.b * z.Q2, q.K, z.d * z.P1, z.Q1, false, false, split3, q.T1,
           mkmap({{z.Q2, 1}, {z.b, z.d * z.Q2}, {BIG, z.P1 * z.b * z.d * z.Q2}}),
           mkmap({{z.P1, z.b * z.d * z.Q2}, {BIG, z.Q2}}), false, nullptr);
+  if (lg) relabel(B, y.l * y.b * y.Q2, y.d * y.P1, y.Q1);
   emit_tc(B, "product_sites", q.T1, z.l * z.b * z.P1, q.KbP, z.P2, z.d * z.Q2, false, true, split3, q.T2,
           mkmap({{z.b, 1}, {q.Du, (int64_t)q.DU * z.b}, {q.Dl, (int64_t)q.DL * z.v * z.b}, {BIG, z.h * z.v * z.b}}),
           mkmap({{q.DU, z.b}, {BIG, z.v * z.b}}), false, nullptr);
+  if (lg) relabel(B, y.l * y.b * y.P1, y.P2, y.d * y.Q2);
   emit_tc(B, "product_boundary", q.T2, z.l * z.h, q.S, z.a, z.v * z.b, false, false, split3, q.T3,
           mkmap({{z.h, 1}, {BIG, z.a * z.h}}), mkmap({{BIG, z.h}}), false, nullptr);
+  if (lg) relabel(B, y.l * y.h, y.a, y.v * y.b);
   emit_tc(B, "product_carry", q.V, z.M, q.T3, z.l, z.a * z.h, false, false, split3, dst, mkmap({{BIG, 1}}),
           mkmap({{BIG, z.M}}), false, nullptr);
+  if (lg) relabel(B, y.M, y.l, y.a * y.h);
 }
 
 // A^H P for ncols columns of P ([j][mrow]); result in the XL layout, or (W
 // mode) conjugated, scaled by 1/sigma_1 and written in the carry layout.
-void emit_adjoint_tc(Builder &B, Inst &q, const void *Pin, int64_t ncols, void *dst, bool wmode, bool split3) {
+void emit_adjoint_tc(Builder &B, Inst &q, const void *Pin, int64_t ncols, void *dst, bool wmode, bool split3,
+                     const Inst *lg = nullptr) {
   const Dims6 z = dims_of(q, ncols);
+  const Dims6 y = lg ? dims_of(*lg, ncols) : z;
   emit_tc(B, "adjoint_carry", q.VT, z.a * z.h, Pin, z.l, z.M, true, false, split3, q.T3,
           mkmap({{z.h, z.a}, {BIG, 1}}), mkmap({{BIG, z.h * z.a}}), false, nullptr);
+  if (lg) relabel(B, y.a * y.h, y.l, y.M);
   // Z2 rows (j, b, l, u) with u fastest, columns (U, L) with L fastest;
   // computed as Z3 (.) conj(S^T) so that lanes write along L
   emit_tc(B, "adjoint_boundary", q.T3, z.l * z.h, q.ST, z.v * z.b, z.a, false, true, split3, q.T2,
           mkmap({{q.DL, 1}, {q.Dl, (int64_t)q.Du * z.P2}, {BIG, z.b * z.P1 * z.P2}}),
           mkmap({{z.b, z.P1 * z.P2}, {q.DU, q.DL}, {BIG, z.P2}}), false, nullptr);
+  if (lg) relabel(B, y.l * y.h, y.v * y.b, y.a);
   emit_tc(B, "adjoint_sites", q.T2, z.l * z.b * z.P1, q.KbT, z.d * z.Q2, z.P2, false, false, split3, q.T1,
           mkmap({{q.Du, 1}, {q.Dl, q.Du}, {z.b, z.Q2 * z.d * z.P1}, {BIG, z.b * z.Q2 * z.d * z.P1}}),
           mkmap({{z.Q2, z.d * z.P1}, {BIG, z.P1}}), false, nullptr);
+  if (lg) relabel(B, y.l * y.b * y.P1, y.d * y.Q2, y.P2);
   if (!wmode)
     emit_tc(B, "adjoint_sites", q.T1, z.l * z.b * z.Q2, q.KT, z.Q1, z.d * z.P1, false, true, split3, dst,
             mkmap({{BIG, z.Q1}}), mkmap({{BIG, 1}}), false, nullptr);
@@ -545,6 +637,7 @@ void emit_adjoint_tc(Builder &B, Inst &q, const void *Pin, int64_t ncols, void *
     emit_tc(B, "epilogue_w", q.T1, z.l * z.b * z.Q2, q.KT, z.Q1, z.d * z.P1, false, true, split3, dst,
             mkmap({{q.DE, 1}, {q.DX, z.b * q.De * q.DE}, {z.b, (int64_t)q.De * q.DE}, {BIG, z.N}}),
             mkmap({{q.De, q.DE}, {BIG, (int64_t)q.DX * z.b * q.De * q.DE}}), true, q.inv_s1);
+  if (lg) relabel(B, y.l * y.b * y.Q2, y.Q1, y.d * y.P1);
 }
 
 // Sketch in the XL layout: logical n = (x, X, b, e, E), least significant E.
@@ -562,23 +655,56 @@ void emit_sketch_xl(Builder &B, Inst &q, const RsvdOpts &o) {
   sketch_set_div(d[0]);
 }
 
-void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {
+// Sketch and gauge vector of the padded copy E drawn at the caller instance
+// I's element numbering: element e = j N + n of I's stream (n = (x, X, b, e,
+// E) in I's extents) lands at its place in E's XL layout, gauge entry (k, t)
+// at row k t_E + t; every padded position is zero.
+void emit_sketch_embedded(Builder &B, const Inst &I, Inst &E, const RsvdOpts &o) {
+  const int es = dtype_size(B.dt);
+  push_zero(B, {{E.X, (int64_t)E.ell * E.N * es / 8}, {E.g, E.M * es / 8}}, "sketch");
+  const int per = dtype_complex(B.dt) ? 2 : 4;
+  SketchDesc s{};
+  s.X = E.X; s.N = I.N; s.ld = E.N; s.ell = I.ell; s.tag = 0; s.kind = o.sketch;
+  s.seed = o.seed; s.instance = I.instance;
+  s.nblocks = ceil_div(ceil_div(s.N * s.ell, per), 256);
+  const int64_t Q1 = (int64_t)E.Dx * E.De;
+  s.nd = 5;
+  const int64_t rad[5] = {I.DE, I.De, I.b, I.DX, BIG};
+  const int64_t str[5] = {Q1, 1, (int64_t)E.DX * E.DE * Q1, (int64_t)E.DE * Q1, E.De};
+  for (int i = 0; i < 5; ++i) { s.radix[i] = (int32_t)rad[i]; s.stride[i] = str[i]; }
+  sketch_set_div(s);
+  SketchDesc gg{};
+  gg.X = E.g; gg.N = I.M; gg.ld = E.M; gg.ell = 1; gg.tag = 1; gg.kind = 0;
+  gg.seed = o.seed; gg.instance = I.instance;
+  gg.nblocks = ceil_div(ceil_div(gg.N, per), 256);
+  gg.nd = 2;
+  gg.radix[0] = I.t; gg.stride[0] = 1;
+  gg.radix[1] = (int32_t)BIG; gg.stride[1] = E.t;
+  sketch_set_div(gg);
+  std::vector<SketchDesc> d{s, gg};
+  std::vector<int64_t> bl{s.nblocks, gg.nblocks};
+  push_grouped(B, Op::SKETCH, d.data(), sizeof(SketchDesc), 2, bl, "sketch");
+  B.ops.back().bytes = (double)es * ((double)s.N * s.ell + gg.N);
+}
+
+void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o, const Inst *logical = nullptr) {
   std::vector<Inst *> one{&q};
   emit_tc_prep(B, q);
-  emit_sketch_xl(B, q, o);
+  if (logical) emit_sketch_embedded(B, *logical, q, o);
+  else emit_sketch_xl(B, q, o);
   // 3xTF32 (FP32-level) products throughout; the FAST precision runs the
   // products before the last A Q of the power iteration on plain TF32
   const bool fast = o.prec == 2;
-  emit_product_tc(B, q, q.X, q.Y, !fast || o.q == 0);
-  emit_orth(B, one, true, true);
+  emit_product_tc(B, q, q.X, q.Y, !fast || o.q == 0, logical);
+  emit_orth(B, one, true, true, o.fp64_small);
   for (int it = 0; it < o.q; ++it) {
     const bool last = it == o.q - 1;
-    emit_adjoint_tc(B, q, q.Y, q.ell, q.Z, false, !fast);
-    if (o.orth_q) emit_orth(B, one, false);
-    emit_product_tc(B, q, q.Z, q.Y, !fast || last);
-    emit_orth(B, one, true, true);
+    emit_adjoint_tc(B, q, q.Y, q.ell, q.Z, false, !fast, logical);
+    if (o.orth_q) emit_orth(B, one, false, false, o.fp64_small);
+    emit_product_tc(B, q, q.Z, q.Y, !fast || last, logical);
+    emit_orth(B, one, true, true, o.fp64_small);
   }
-  emit_adjoint_tc(B, q, q.Y, q.ell, q.Z, false, true);      // Z = A^H P = B^H
+  emit_adjoint_tc(B, q, q.Y, q.ell, q.Z, false, true, logical);      // Z = A^H P = B^H
   // R_B: Cholesky factor of the Gram Z^H Z (= B B^H, B = P^H A).  3xTF32
   // tensor-core products, FP32 partial sums over chunks of 2048 K values,
   // chunks combined in FP64, so the factor carries Z's own error only (a Gram
@@ -604,7 +730,7 @@ void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {
     op.smem2 = chol_cluster_smem_bytes(wdt, q.ell, false);
     B.ops.push_back(op);
   }
-  emit_jacobi_finalize(B, one);
+  emit_jacobi_finalize(B, one, o.fp64_small);
   // U = P U~ and its transpose (input of the W adjoint)
   {
     std::vector<GemmDesc> gu{mk_gemm((int)q.M, q.k, q.ell, 1, q.Y, 1, q.M, 0, false, q.Ut, q.k, 1, 0, false, q.U,
@@ -612,7 +738,7 @@ void emit_einsumsvd_tc(Builder &B, Inst &q, const RsvdOpts &o) {
     push_gemm(B, gu, false, "epilogue_u");
     emit_permute(B, "epilogue_u", {mk_perm(q.U, q.UT, 1, q.M, q.k, 1)});
   }
-  emit_adjoint_tc(B, q, q.UT, q.k, q.W, true, true);        // W = U^H A / sigma_1
+  emit_adjoint_tc(B, q, q.UT, q.k, q.W, true, true, logical);        // W = U^H A / sigma_1
 }
 
 }  // namespace
@@ -699,6 +825,104 @@ bool inst_tc_ok(const Inst &I, int dt) {
     if (k % align) return false;
   return true;
 }
+
+namespace {
+int round_up(int x, int q) { return (x + q - 1) / q * q; }
+void push_pad(Builder &B, std::vector<PadDesc> &d, const char *tag) {
+  std::vector<int64_t> bl;
+  double by = 0;
+  for (auto &p : d) {
+    bl.push_back(ceil_div(p.total, kPadPerBlock));
+    by += 2.0 * dtype_size(B.dt) * p.total;
+  }
+  const size_t before = B.ops.size();
+  push_grouped(B, Op::PAD, d.data(), sizeof(PadDesc), (int)d.size(), bl, tag);
+  if (B.ops.size() > before) B.ops.back().bytes = by;
+}
+PadDesc mk_pad(const void *in, void *out, std::initializer_list<int> dims, std::initializer_list<int> lim,
+               std::initializer_list<int64_t> in_stride) {
+  PadDesc p{};
+  p.in = in; p.out = out; p.nd = (int32_t)dims.size(); p.total = 1;
+  int i = 0;
+  for (int x : dims) { p.dims[i++] = x; p.total *= x; }
+  i = 0;
+  for (int x : lim) p.lim[i++] = x;
+  i = 0;
+  for (int64_t x : in_stride) p.in_stride[i++] = x;
+  return p;
+}
+}  // namespace
+
+bool inst_embed_dims(const Inst &I, int dt, const RsvdOpts &o, Inst &E) {
+  if (dtype_double(dt)) return false;
+  const int q = dtype_complex(dt) ? 2 : 4;
+  E = I;
+  E.embed = false;
+  E.Dl = round_up(I.Dl, 2); E.Du = round_up(I.Du, 2); E.Dx = round_up(I.Dx, 2); E.De = round_up(I.De, 2);
+  E.DL = round_up(I.DL, 2); E.DU = round_up(I.DU, 2); E.DX = round_up(I.DX, 2); E.DE = round_up(I.DE, 2);
+  E.t = round_up(I.t, q);
+  E.a = round_up(I.a, q);
+  inst_derive(E, o);
+  E.k = I.k;                      // the caller's rank and sketch width
+  E.ell = I.ell;
+  E.tc = true;
+  return inst_check(E, dt).empty() && inst_tc_ok(E, dt);
+}
+
+size_t inst_embed_bytes(const Inst &E, int dt) {
+  const size_t es = dtype_size(dt);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return inst_scratch_bytes(E, dt) + al((size_t)E.kL * E.t * E.a * E.h * es) + al((size_t)E.a * E.v * E.b * es) +
+         al((size_t)E.d * E.Dl * E.Du * E.Dx * E.De * es) + al((size_t)E.d * E.DL * E.DU * E.DX * E.DE * es) +
+         al((size_t)E.M * E.k * es) + al((size_t)E.k * E.N * es);
+}
+
+void inst_embed_alloc(Builder &B, Inst &E, int dt) {
+  const size_t es = dtype_size(dt);
+  inst_alloc_scratch(B, E, dt);
+  E.V = B.buf((size_t)E.kL * E.t * E.a * E.h * es);
+  E.S = B.buf((size_t)E.a * E.v * E.b * es);
+  E.K = B.buf((size_t)E.d * E.Dl * E.Du * E.Dx * E.De * es);
+  E.Kb = B.buf((size_t)E.d * E.DL * E.DU * E.DX * E.DE * es);
+  E.U = B.buf((size_t)E.M * E.k * es);
+  E.W = B.buf((size_t)E.k * E.N * es);
+}
+
+void emit_einsumsvd_embedded(Builder &B, Inst &I, Inst &E, const RsvdOpts &o) {
+  E.instance = I.instance;
+  E.sigma = I.sigma;
+  E.logp = I.logp;
+  // operands into the padded extents (zeros elsewhere)
+  std::vector<PadDesc> in{
+      mk_pad(I.V, (void *)E.V, {E.kL, E.t, E.a, E.Dl, E.DL}, {I.kL, I.t, I.a, I.Dl, I.DL},
+             {(int64_t)I.t * I.a * I.h, (int64_t)I.a * I.h, I.h, I.DL, 1}),
+      mk_pad(I.S, (void *)E.S, {E.a, E.Du, E.DU, E.b}, {I.a, I.Du, I.DU, I.b},
+             {(int64_t)I.v * I.b, (int64_t)I.DU * I.b, I.b, 1}),
+      mk_pad(I.K, (void *)E.K, {E.d, E.Dl, E.Du, E.Dx, E.De}, {I.d, I.Dl, I.Du, I.Dx, I.De},
+             {(int64_t)I.Dl * I.Du * I.Dx * I.De, (int64_t)I.Du * I.Dx * I.De, (int64_t)I.Dx * I.De, I.De, 1}),
+      mk_pad(I.Kb, (void *)E.Kb, {E.d, E.DL, E.DU, E.DX, E.DE}, {I.d, I.DL, I.DU, I.DX, I.DE},
+             {(int64_t)I.DL * I.DU * I.DX * I.DE, (int64_t)I.DU * I.DX * I.DE, (int64_t)I.DX * I.DE, I.DE, 1})};
+  push_pad(B, in, "pad");
+  const size_t first = B.ops.size();
+  emit_einsumsvd_tc(B, E, o, &I);
+  // the orthogonalisations and Grams count the caller's extents too
+  const double fm = (double)I.M / E.M, fn = (double)I.N / E.N;
+  for (size_t i = first; i < B.ops.size(); ++i) {
+    Op &op = B.ops[i];
+    const double f = (op.tag == "orth_m" || op.tag == "epilogue_u") ? fm
+                     : (op.tag == "orth_n" || op.tag == "svd_gram") ? fn : 1.0;
+    op.flops *= f;
+    op.bytes *= f;
+  }
+  // U [kL][t][k] and W [k][(x,X)][b][(e,E)] cut out of the padded results
+  std::vector<PadDesc> out{
+      mk_pad(E.U, I.U, {I.kL, I.t, I.k}, {I.kL, I.t, I.k}, {(int64_t)E.t * E.k, E.k, 1}),
+      mk_pad(E.W, I.W, {I.k, I.Dx, I.DX, I.b, I.De, I.DE}, {I.k, I.Dx, I.DX, I.b, I.De, I.DE},
+             {E.N, (int64_t)E.DX * E.b * E.De * E.DE, (int64_t)E.b * E.De * E.DE, (int64_t)E.De * E.DE, E.DE, 1})};
+  push_pad(B, out, "pad");
+}
+
+void emit_einsumsvd_tc_one(Builder &B, Inst &q, const RsvdOpts &o) { emit_einsumsvd_tc(B, q, o); }
 
 std::string inst_check(const Inst &I, int dt) {
   const int dims[] = {I.kL, I.t, I.a, I.b, I.d, I.Dl, I.Du, I.Dx, I.De, I.DL, I.DU, I.DX, I.DE};
@@ -953,15 +1177,15 @@ void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
 void emit_einsumsvd_simt(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) {
   emit_sketch(B, I, o);
   emit_product(B, I, true);
-  emit_orth(B, I, true);
+  emit_orth(B, I, true, false, o.fp64_small);
   for (int it = 0; it < o.q; ++it) {
     emit_adjoint(B, I);
-    emit_orth(B, I, false);
+    emit_orth(B, I, false, false, o.fp64_small);
     emit_product(B, I, false);
-    emit_orth(B, I, true);
+    emit_orth(B, I, true, false, o.fp64_small);
   }
   emit_adjoint(B, I);
-  emit_small_svd(B, I);
+  emit_small_svd(B, I, o.fp64_small);
   emit_epilogue(B, I);
 }
 

@@ -19,7 +19,7 @@ __all__ = [
     "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
     "Term", "ExpectationPlan", "expectation", "Cotangent", "Grads", "einsumsvd_grad", "GradPlan",
     "energy_grad", "peps_energy", "STATUS_NONFINITE", "STATUS_JACOBI_NOCONV", "STATUS_TIMEOUT",
-    "ERR_NUMERIC", "ERR_TIMEOUT",
+    "ERR_NUMERIC", "ERR_TIMEOUT", "FLAG_FP64_SMALL",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -213,6 +213,7 @@ def dtype_code(dtype) -> int:
 
 
 FLAG_ORTH_Q = 1
+FLAG_FP64_SMALL = 2
 
 
 def make_opts(m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN, flags=0) -> RsvdOpts:
@@ -539,6 +540,10 @@ def _make_energy_function():
         @staticmethod
         def forward(ctx, terms, m, p, q, seed, nrow, ncol, *flat):
             sites = [[flat[r * ncol + c].contiguous() for c in range(ncol)] for r in range(nrow)]
+            if not any(ctx.needs_input_grad[7:]):
+                # no gradient wanted: the expectation value alone (no reverse sweep)
+                e, _, _ = expectation(sites, terms, m, p, q, seed)
+                return torch.tensor(e, dtype=torch.float64, device=flat[0].device)
             e, g = energy_grad(sites, terms, m, p, q, seed)
             ctx.save_for_backward(*[x for row in g for x in row])
             return torch.tensor(e, dtype=torch.float64, device=flat[0].device)

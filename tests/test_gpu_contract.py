@@ -135,3 +135,21 @@ def test_c2_fast_precision_log_norm():
     la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=libpeps.PREC_FAST)
     ra, rp = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed)
     assert abs(la - ra) <= 1e-5 * abs(ra)
+
+
+@pytest.mark.parametrize("prec", [libpeps.PREC_PLAIN, libpeps.PREC_MIXED])
+def test_c2_fp64_small_factorisations(prec):
+    """PEPS_FLAG_FP64_SMALL (CholeskyQR2's Cholesky factorisations and the
+    Jacobi SVD in FP64 on single-precision data): the 8x8 log-norm stays
+    within 1e-5 of the FP64 oracle and the first row's steps (identical
+    inputs) keep their singular values within 1e-5 normwise."""
+    cfg = synth.config("c2")
+    ket = synth.peps_for(cfg)
+    rec = []
+    la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=prec,
+                       flags=libpeps.FLAG_FP64_SMALL)
+    ra, rp = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec)
+    assert abs(la - ra) <= 1e-5 * abs(ra)
+    errs = sigma_errors(sig, rec)
+    row1 = [i for i, r in enumerate(rec) if r["row"] == 1]
+    assert errs[row1].max() <= 1e-5

@@ -31,7 +31,7 @@ def _operands(rng, kL, t, a, b, d, Dk, Db, dtype):
             r((d, DL, DU, DX, DE)))
 
 
-def _run_batch(cases, dtype, m, p, q, seed, prec=libpeps.PREC_PLAIN, ranks=None):
+def _run_batch(cases, dtype, m, p, q, seed, prec=libpeps.PREC_PLAIN, ranks=None, flags=0):
     shapes, ios, outs = [], [], []
     for i, (V, S, K, Kb) in enumerate(cases):
         kL, t, a, h = V.shape
@@ -39,7 +39,7 @@ def _run_batch(cases, dtype, m, p, q, seed, prec=libpeps.PREC_PLAIN, ranks=None)
         d, Dl, Du, Dx, De = K.shape
         _, DL, DU, DX, DE = Kb.shape
         shapes.append((kL, t, a, b, d, Dl, Du, Dx, De, DL, DU, DX, DE, ranks[i] if ranks else 0))
-    plan = libpeps.EinsumsvdPlan(TORCH_DT[dtype], shapes, libpeps.make_opts(m, p, q, seed, prec=prec),
+    plan = libpeps.EinsumsvdPlan(TORCH_DT[dtype], shapes, libpeps.make_opts(m, p, q, seed, prec=prec, flags=flags),
                                  instance_ids=list(range(100, 100 + len(cases))))
     for i, (V, S, K, Kb) in enumerate(cases):
         k = plan.ranks[i]
@@ -193,3 +193,40 @@ def test_c3_batch_with_per_instance_ranks(prec):
         # (close singular values at its truncation edge: single-precision
         # singular vectors move by ~u sigma_1 / gap), so they get 1e-2
         _check(c, out[i], mm, cfg.p, cfg.q, cfg.omega_seed, 100 + i, "f32", ftol=1e-2)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "c64"])
+def test_padded_copy_on_tensor_cores(dtype):
+    """Instances whose contracted extents break the TMA row alignment (odd
+    bonds, t and a not multiples of 4) run on the tensor cores through a
+    zero-padded copy: the padded operator is the original one with zero rows
+    and columns added, the sketch and gauge vector are drawn at the original
+    element numbering, so every singular value, U and W match the oracle on
+    the original operands.  Several such instances share one plan (their
+    chains run as concurrent graph branches)."""
+    rng = np.random.default_rng(29)
+    cases = [_operands(rng, 6, 9, 7, 5, 2, (3, 3, 3, 3), (3, 3, 3, 3), dtype),
+             _operands(rng, 10, 25, 13, 6, 2, (5, 5, 5, 5), (5, 5, 5, 5), dtype),
+             _operands(rng, 12, 6, 10, 9, 2, (2, 3, 3, 2), (3, 2, 2, 3), dtype)]
+    out = _run_batch(cases, dtype, 24, 8, 2, 81, prec=libpeps.PREC_MIXED)
+    for i, c in enumerate(cases):
+        _check(c, out[i], 24, 8, 2, 81, 100 + i, dtype, ftol=1e-2)
+
+
+@pytest.mark.parametrize("dtype,prec", [("c64", libpeps.PREC_PLAIN), ("c64", libpeps.PREC_MIXED),
+                                        ("f32", libpeps.PREC_PLAIN), ("f32", libpeps.PREC_MIXED)])
+@pytest.mark.parametrize("ell_case", ["one_cta", "cluster"])
+def test_fp64_small_factorisations(dtype, prec, ell_case):
+    """PEPS_FLAG_FP64_SMALL: the CholeskyQR2 factorisations and the Jacobi SVD
+    run in FP64 on single-precision data (one-CTA kernels at l = 40, 8-CTA
+    cluster kernels at l = 264); same parity bar as the default."""
+    rng = np.random.default_rng(31)
+    D = 4
+    if ell_case == "one_cta":
+        case = _operands(rng, 6, D * D, 8, 6, 2, (D,) * 4, (D,) * 4, dtype)
+        m = 32
+    else:
+        case = _operands(rng, 18, D * D, 20, 18, 2, (D,) * 4, (D,) * 4, dtype)
+        m = 256
+    out = _run_batch([case], dtype, m, 8, 2, 79, prec=prec, flags=libpeps.FLAG_FP64_SMALL)
+    _check(case, out[0], m, 8, 2, 79, 100, dtype)

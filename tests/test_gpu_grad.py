@@ -138,3 +138,17 @@ def test_autograd_function_backward():
     assert float(E) == pytest.approx(e, abs=1e-12)
     for x, gr in zip(flat, [t for row in g for t in row]):
         assert torch.allclose(x.grad, 2.5 * gr, rtol=1e-12, atol=1e-14)
+
+
+def test_autograd_function_forward_only():
+    """With no input requiring a gradient the autograd entry runs the
+    expectation value alone (no reverse sweep) and returns the same energy."""
+    ket = synth.random_peps(3, 3, 2, 2, "f64", "normal", 8)
+    terms = synth.tfi_terms(3, 3, 1.0, 3.0)
+    k = to_dev(ket, "f64")
+    flat = [t for row in k for t in row]
+    with torch.no_grad():
+        E = libpeps.peps_energy(terms, 3, 2, 1, 9, 3, 3, *flat)
+    e, _ = libpeps.energy_grad(k, terms, 3, 2, 1, 9)
+    assert not E.requires_grad
+    assert float(E) == pytest.approx(e, abs=1e-12)
