@@ -206,6 +206,17 @@ def whole_job_value(world, flops_per_rank, ms_step):
     return world * flops_per_rank / (ms_step * 1e-3) / 1e12
 
 
+TUNE_DIR = os.path.join(ROOT, "paper_2006_15234_gb300", "tuning")
+
+
+def load_tune(workload):
+    """The stored tensor-core tile table of a workload (tuning/<workload>.txt)."""
+    path = os.path.join(TUNE_DIR, workload + ".txt")
+    if not os.path.exists(path):
+        return None
+    return {"source": os.path.relpath(path, ROOT), "table": open(path).read()}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -248,6 +259,21 @@ def run_ours(args, cfg):
     # remaining warm-up steps replay the captured sweep
     plan.execute()
     la, ph = plan.result()
+    tune = None
+    if not args.no_autotune and prec != libpeps.PREC_PLAIN:
+        # MMA widths per tensor-core GEMM shape: the stored table of this
+        # workload if there is one, else timed here (before the graph capture)
+        tune = load_tune(cfg.name)
+        if tune is None:
+            t0 = time.perf_counter()
+            plan.autotune(reps=3)
+            tune = {"source": "tuned in this run", "seconds": round(time.perf_counter() - t0, 3),
+                    "table": plan.tune_table()}
+        else:
+            plan.set_tune_table(tune["table"])
+        plan.execute()
+        la_t, _ = plan.result()
+        assert la_t == la, (la_t, la)
     if args.launch_list:
         # one more contraction, bracketed for an external launch-list capture
         # (ncu --profile-from-start off), then stop
@@ -405,6 +431,13 @@ def run_ours(args, cfg):
         "kernel_ms": {k: round(v[0], 4) for k, v in sorted(by_kern.items(), key=lambda kv: -kv[1][0])},
         "stage_ms": {k: round(v[0], 4) for k, v in sorted(by_tag.items(), key=lambda kv: -kv[1][0])},
     }
+    if tune is not None:
+        line["config"]["tile_table"] = {"source": tune["source"],
+                                        "shapes": len([x for x in tune["table"].splitlines() if x]),
+                                        **({"tune_s": tune["seconds"]} if "seconds" in tune else {})}
+        if rank == 0 and "seconds" in tune and args.tune_out:
+            with open(args.tune_out, "w") as f:
+                f.write(tune["table"])
     if plain is not None:
         line["plain_fp32"] = plain
     if parity is not None:
@@ -814,6 +847,9 @@ def main():
                     help="skip the plain FP32 contraction timed beside the mixed one")
     ap.add_argument("--fp64-small", action="store_true",
                     help="CholeskyQR2 factorisations and the Jacobi SVD in FP64 (PEPS_FLAG_FP64_SMALL)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the rule-based MMA widths (no stored or live tile table)")
+    ap.add_argument("--tune-out", default=None, help="write a freshly tuned tile table to this file")
     ap.add_argument("--no-c3", action="store_true",
                     help="skip the batched-einsumsvd sub-record of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")

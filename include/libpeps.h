@@ -373,6 +373,39 @@ peps_status peps_poll(const peps_plan *plan, const void *workspace, void *stream
 peps_status peps_plan_set_wait_limit(peps_plan *plan, uint64_t ns);
 
 /* ------------------------------------------------------------------------
+ * Autotuning of the tensor-core GEMM tiles.  Every tensor-core launch of a
+ * plan has a shape signature (operand types, products, rows of A and B,
+ * contracted extent, K split); its MMA width (64, 128, 192 or, without the
+ * FP32-level split, 256 accumulator columns) fixes the N tiling.  The default
+ * is a rule (fewest padded columns); the autotuner times every candidate
+ * width on one launch of each signature and keeps the fastest.
+ * ------------------------------------------------------------------------ */
+
+/* Tune the plan's tensor-core launches on this device: for each shape
+ * signature, time `reps` launches (1..100) of one representative with every
+ * candidate width (CUDA events on `stream`, synchronising) and set the
+ * fastest on every launch of that signature.  The plan must have been
+ * executed with `workspace` (the launches read and write it; its contents are
+ * not meaningful afterwards, the next execute recomputes them).  Results are
+ * unchanged by the tiling (each output is accumulated over K in the same
+ * order).  Execute the plan once more before capturing it in a CUDA graph.
+ * PEPS_ERR_ARG if the plan was not executed with this workspace,
+ * PEPS_ERR_CAPTURE on a capturing stream. */
+peps_status peps_plan_autotune(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream,
+                               int32_t reps);
+
+/* The plan's tuning table as text, one "<signature> = <width>" line per shape
+ * (*len receives the size including the terminating NUL; buf may be NULL to
+ * query it; at most cap bytes are written, NUL-terminated). */
+peps_status peps_plan_tune_table(const peps_plan *plan, char *buf, size_t cap, size_t *len);
+
+/* Replace the plan's tuning table (text as peps_plan_tune_table writes it; a
+ * stored table applies to every plan with launches of the same signatures).
+ * The next execute rebuilds the launches with it.  PEPS_ERR_ARG on a
+ * malformed line or a width other than 64, 128, 192, 256. */
+peps_status peps_plan_set_tune_table(peps_plan *plan, const char *table);
+
+/* ------------------------------------------------------------------------
  * Launch ledger (profiling).  A plan's execute is a fixed list of grouped
  * kernel launches, each tagged with the stage of Algorithm 4 it serves
  * ("product_sites", "orth_m", "svd_jacobi", ...).

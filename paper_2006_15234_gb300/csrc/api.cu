@@ -161,6 +161,8 @@ struct peps_plan {
   // the first launch of every execute; limit of one tensor-core pipeline wait
   size_t status_off = 0;
   uint64_t wait_ns = 0;
+  // autotuned MMA width per tensor-core GEMM shape (tc_signature -> width)
+  std::map<std::string, int> tune;
   // built schedule
   uintptr_t built_base = 0;
   bool built = false;
@@ -1502,8 +1504,14 @@ peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool en
   if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
   tc_finish(B);
   if (!B.err.empty()) return fail(PEPS_ERR_UNSUPPORTED, "%s", B.err.c_str());
-  for (Op &op : B.ops)
-    if (op.kind == Op::TC) op.tc.wait_ns = P->wait_ns;
+  for (Op &op : B.ops) {
+    if (op.kind != Op::TC) continue;
+    op.tc.wait_ns = P->wait_ns;
+    if (!encode || P->tune.empty()) continue;
+    auto it = P->tune.find(tc_signature(op));
+    if (it != P->tune.end() && it->second != op.tc_bn && !tc_retile(op, it->second))
+      return fail(PEPS_ERR_UNSUPPORTED, "tuned MMA width %d not encodable for %s", it->second, op.tag.c_str());
+  }
   P->ws_bytes = finish(B, &P->blob_off);   // needs the blob size: before the move
   P->ops = std::move(B.ops);
   P->blob = std::move(B.blob);
@@ -1842,6 +1850,90 @@ peps_status peps_poll(const peps_plan *plan, const void *workspace, void *stream
   CUDA_TRY(cudaStreamSynchronize(s));
   if (flags) *flags = word;
   return status_of(word);
+}
+
+peps_status peps_plan_autotune(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream,
+                               int32_t reps) {
+  g_last_error.clear();
+  if (!plan || !workspace) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (!plan->built || plan->built_base != (uintptr_t)workspace)
+    return fail(PEPS_ERR_ARG, "execute the plan with this workspace before tuning it");
+  if (workspace_bytes < plan->ws_bytes) return fail(PEPS_ERR_WORKSPACE, "workspace too small");
+  if (reps < 1 || reps > 100) return fail(PEPS_ERR_ARG, "reps must be in 1..100");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (in_capture(s)) return fail(PEPS_ERR_CAPTURE, "tuning during stream capture");
+  // one representative launch per shape; every candidate width timed on it
+  std::map<std::string, std::vector<size_t>> groups;
+  for (size_t i = 0; i < plan->ops.size(); ++i)
+    if (plan->ops[i].kind == Op::TC) groups[tc_signature(plan->ops[i])].push_back(i);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  peps_status st = PEPS_OK;
+  for (auto &g : groups) {
+    Op &rep = plan->ops[g.second.front()];
+    const int orig = rep.tc_bn;
+    int best = orig;
+    float best_ms = -1.f;
+    for (int c : tc_candidates(rep)) {
+      if (!tc_retile(rep, c)) continue;
+      launch_tc_gemm(rep.tc, rep.tc_bn, s);           // warm-up (and first-launch set-up)
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) launch_tc_gemm(rep.tc, rep.tc_bn, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(PEPS_ERR_CUDA, "tuning launch failed"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = c; }
+    }
+    if (st != PEPS_OK) break;
+    for (size_t i : g.second)
+      if (plan->ops[i].tc_bn != best && !tc_retile(plan->ops[i], best)) {
+        st = fail(PEPS_ERR_UNSUPPORTED, "MMA width %d not encodable", best);
+        break;
+      }
+    if (st != PEPS_OK) break;
+    plan->tune[g.first] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == PEPS_OK) CUDA_TRY(cudaGetLastError());
+  return st;
+}
+
+peps_status peps_plan_tune_table(const peps_plan *plan, char *buf, size_t cap, size_t *len) {
+  if (!plan || !len) return fail(PEPS_ERR_ARG, "NULL argument");
+  std::string t;
+  for (auto &kv : plan->tune) t += kv.first + " = " + std::to_string(kv.second) + "\n";
+  *len = t.size() + 1;
+  if (buf && cap) {
+    const size_t n = std::min(cap - 1, t.size());
+    memcpy(buf, t.data(), n);
+    buf[n] = 0;
+  }
+  return PEPS_OK;
+}
+
+peps_status peps_plan_set_tune_table(peps_plan *plan, const char *table) {
+  g_last_error.clear();
+  if (!plan || !table) return fail(PEPS_ERR_ARG, "NULL argument");
+  std::map<std::string, int> t;
+  const char *p = table;
+  while (*p) {
+    const char *e = strchr(p, '\n');
+    std::string line(p, e ? (size_t)(e - p) : strlen(p));
+    p = e ? e + 1 : p + line.size();
+    if (line.empty()) continue;
+    const size_t eq = line.rfind(" = ");
+    int w = 0;
+    if (eq == std::string::npos || sscanf(line.c_str() + eq + 3, "%d", &w) != 1 ||
+        (w != 64 && w != 128 && w != 192 && w != 256))
+      return fail(PEPS_ERR_ARG, "bad tuning line \"%s\"", line.c_str());
+    t[line.substr(0, eq)] = w;
+  }
+  plan->tune = t;
+  plan->built = false;        // the next execute rebuilds with the table
+  return PEPS_OK;
 }
 
 peps_status peps_plan_set_wait_limit(peps_plan *plan, uint64_t ns) {

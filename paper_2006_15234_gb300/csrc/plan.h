@@ -136,6 +136,12 @@ void inst_alloc_scratch(Builder &B, Inst &I, int dt);
 // the B scratch of the pre-expanded tensor-core operands and their TMA maps;
 // called once after the whole schedule is emitted
 void tc_finish(Builder &B);
+// Shape signature of a tensor-core GEMM launch (the autotuner's table key),
+// its candidate MMA widths, and a change of its MMA width (N tiling and the B
+// operand's TMA boxes re-encoded; false if the maps cannot be encoded).
+std::string tc_signature(const Op &op);
+std::vector<int> tc_candidates(const Op &op);
+bool tc_retile(Op &op, int nmma);
 // Point I's scratch at another instance's buffers (the sweep reuses one set).
 void inst_share_scratch(Inst &I, const Inst &owner);
 // Check the shape against the kernels' limits; returns "" when supported.

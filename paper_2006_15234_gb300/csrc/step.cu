@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cstdio>
 #include <cstring>
 
 #include "common.cuh"
@@ -517,6 +518,40 @@ void tc_finish(Builder &B) {
                     tc_encode_map(&d.tb2, (char *)bx + nr * pitch, nr, d.Kr, pitch, op.tc_bn);
     if (!ok && B.err.empty()) B.err = std::string("TMA map encoding failed for ") + op.tag;
   }
+}
+
+std::string tc_signature(const Op &op) {
+  const TcDesc &d = op.tc;
+  char b[160];
+  snprintf(b, sizeof b, "c%d s%d p%d a%d f%d M%lld N%d K%d k%d", d.cplx, d.split3, d.bpre, d.atomic64,
+           tc_folds(d.split3 != 0, d.Kr, d.kb_per_split) ? 1 : 0, (long long)op.tcA_rows, d.N, d.Kr,
+           d.ksplit > 1 ? d.kb_per_split : 0);
+  return b;
+}
+
+std::vector<int> tc_candidates(const Op &op) {
+  std::vector<int> c{64, 128, 192};
+  if (!op.tc.split3) c.push_back(256);
+  return c;
+}
+
+bool tc_retile(Op &op, int nmma) {
+  TcDesc &d = op.tc;
+  const bool cplx = d.cplx != 0;
+  if (d.split3 && nmma > 192) return false;
+  const int bn = tc_tile_cols(nmma, cplx);
+  const int64_t pitch = (int64_t)d.Kr * 4;
+  if (d.bpre) {
+    const int64_t nr = (int64_t)d.N * (cplx ? 2 : 1);
+    if (!tc_encode_map(&d.tb, d.Bx, nr, d.Kr, pitch, nmma) ||
+        !tc_encode_map(&d.tb2, (char *)d.Bx + nr * pitch, nr, d.Kr, pitch, nmma))
+      return false;
+  } else if (!tc_encode_map(&d.tb, op.tcB, op.tcB_rows, d.Kr, pitch, bn)) {
+    return false;
+  }
+  op.tc_bn = nmma;
+  d.tiles_n = (int32_t)ceil_div(d.N, bn);
+  return true;
 }
 
 namespace {

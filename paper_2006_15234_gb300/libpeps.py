@@ -37,6 +37,7 @@ EXPORTED_SYMBOLS = [
     "peps_plan_kernel_launches", "peps_einsumsvd_grad_plan", "peps_einsumsvd_grad_bind",
     "peps_einsumsvd_grad_execute", "peps_grad_plan", "peps_grad_execute", "peps_grad",
     "peps_poll", "peps_plan_set_wait_limit", "peps_debug_sketch",
+    "peps_plan_autotune", "peps_plan_tune_table", "peps_plan_set_tune_table",
 ]
 
 # Bits of a plan's device status word (peps_poll).
@@ -192,6 +193,12 @@ def load():
     lib.peps_debug_sketch.restype = st
     lib.peps_debug_sketch.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                       C.c_int32, vp, vp, vp]
+    lib.peps_plan_autotune.restype = st
+    lib.peps_plan_autotune.argtypes = [vp, vp, C.c_size_t, vp, C.c_int32]
+    lib.peps_plan_tune_table.restype = st
+    lib.peps_plan_tune_table.argtypes = [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
+    lib.peps_plan_set_tune_table.restype = st
+    lib.peps_plan_set_tune_table.argtypes = [vp, C.c_char_p]
     lib.peps_poll.restype = st
     lib.peps_poll.argtypes = [vp, vp, vp, C.POINTER(C.c_uint32)]
     lib.peps_plan_set_wait_limit.restype = st
@@ -274,6 +281,23 @@ class _Ledger:
         w = C.c_uint32()
         r = self._lib.peps_poll(self._plan, C.c_void_p(self._ws), _stream_handle(stream), C.byref(w))
         return r, w.value
+
+    def autotune(self, reps: int = 3, stream=None):
+        """Time every candidate MMA width per tensor-core GEMM shape and keep
+        the fastest (execute the plan once before, and once more before a
+        graph capture)."""
+        _check(self._lib.peps_plan_autotune(self._plan, C.c_void_p(self._ws), C.c_size_t(self.workspace_bytes),
+                                            _stream_handle(stream), int(reps)))
+
+    def tune_table(self) -> str:
+        n = C.c_size_t()
+        _check(self._lib.peps_plan_tune_table(self._plan, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(self._lib.peps_plan_tune_table(self._plan, buf, n.value, C.byref(n)))
+        return buf.value.decode()
+
+    def set_tune_table(self, text: str):
+        _check(self._lib.peps_plan_set_tune_table(self._plan, text.encode()))
 
     def set_wait_limit(self, ns: int):
         """Limit (ns) of one tensor-core pipeline wait for later executes; 0: default."""

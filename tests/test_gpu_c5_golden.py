@@ -1,18 +1,20 @@
-"""Full-size parity of the 16 x 16, D = 8, m = 256 norm contraction (complex64,
-mixed precision: tcgen05 3xTF32 products): the singular values of every
-einsumsvd step of the first zip-up row (Algorithm 3 on rows one and two,
-identical network inputs on both sides) against the FP64 oracle's values
-stored in tests/golden/c5_row1.json (written by tests/golden/make_c5_row1.py,
-which calls only the oracle).  Error per step: max_i |sigma_i - sigma_i^ref| /
-sigma_1^ref.
+"""Full-size parity of the 16 x 16, D = 8, m = 256 norm contraction (complex64)
+against the FP64 oracle's stored sweep (tests/golden/c5_sweep.json, written
+by tests/golden/make_sweep.py from the oracle alone, row by row; the file
+holds the rows finished so far and, once the last row is done, the
+log-norm).  Error per step: max_i |sigma_i - sigma_i^ref| / sigma_1^ref.
 
-The first step of the row sees exactly the oracle's inputs: bound 1e-5, the
-single-precision tolerance of the workload (measured 2.4e-6 mixed, 4.3e-6
-plain FP32).  Every later step takes the previous step's carry W, which the
-GPU holds in single precision and the oracle in FP64; that rounding alone
-moves the next singular values by up to ~1.2e-5 relative to sigma_1 on this
-workload (the plain FP32 path measures the same 1.2e-5), so those steps are
-held to 2e-5."""
+The first step of the first zip-up row sees exactly the oracle's inputs:
+bound 1e-5, the single-precision tolerance of the workload.  Every later
+step takes the previous steps' boundary and carry, which the GPU holds in
+single precision and the oracle in FP64; on the first row that rounding moves
+the singular values by up to ~1.3e-5 relative to sigma_1 on both paths, so
+those steps are held to 2e-5.  Later rows amplify the rounding row by row
+(on the 8 x 8 workload the single-precision replay's envelope grows from
+7.6e-7 in row 1 to 4.5e-5 in row 7, see tests/golden/c2_envelope.json): row r
+is held to 2e-5 * 3^(r - 1), the 8 x 8 envelope's growth per row rounded up,
+capped at 1e-3.  The log-norm, when stored, is held to 1e-5 relative on
+log|v|."""
 import json
 import os
 
@@ -25,11 +27,15 @@ from tests.gpu_util import to_dev
 
 pytestmark = pytest.mark.gpu
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c5_row1.json")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c5_sweep.json")
 
 
-@pytest.mark.parametrize("prec", [libpeps.PREC_MIXED])
-def test_c5_first_row_sigma_matches_oracle(prec):
+def row_bar(row):
+    return min(2e-5 * 3.0 ** (row - 1), 1e-3)
+
+
+@pytest.mark.parametrize("prec", [libpeps.PREC_MIXED, libpeps.PREC_PLAIN])
+def test_c5_stored_rows_match_oracle(prec):
     gold = json.load(open(GOLDEN))
     cfg = synth.config("c5")
     assert (gold["m"], gold["p"], gold["q"], gold["seed"]) == (cfg.m, cfg.p, cfg.q, cfg.omega_seed)
@@ -43,7 +49,14 @@ def test_c5_first_row_sigma_matches_oracle(prec):
         ref = np.asarray(st["sigma"])
         got = sig[pos:pos + len(ref)]
         pos += len(ref)
-        errs.append(np.max(np.abs(got - ref)) / ref[0])
-    msg = ["%.2e" % e for e in errs]
-    assert errs[0] <= 1e-5, msg
-    assert max(errs) <= 2e-5, msg
+        errs.append((st["row"], st["col"], float(np.max(np.abs(got - ref)) / ref[0])))
+    rows = sorted({r for r, _, _ in errs})
+    print(f"prec {prec}: rows {rows[0]}..{rows[-1]} stored; per-row max sigma error",
+          ["%.1e" % max(e for r2, _, e in errs if r2 == r) for r in rows])
+    assert errs[0][2] <= 1e-5, errs[0]
+    bad = [(r, c, "%.2e" % e) for r, c, e in errs[1:] if e > row_bar(r)]
+    assert not bad, bad
+    if "log_norm" in gold:
+        d = abs(la - gold["log_norm"])
+        print(f"log-norm {la} vs {gold['log_norm']}: |d log v| {d:.2e}, relative on log {d / abs(gold['log_norm']):.2e}")
+        assert d <= 1e-5 * abs(gold["log_norm"])

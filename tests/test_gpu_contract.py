@@ -2,15 +2,25 @@
 C ABI against the CPU oracle on identical seeded inputs.
 
 Tolerances: FP64 data, 1e-9 on log|v| (the FP64 path reproduces the oracle up
-to rounding order); single-precision data, 1e-5 relative on log|v|.  The
-singular values of every step of a whole sweep are compared normwise
-(against sigma_1) at SWEEP_SIGMA_TOL = 1e-4: a step's inputs (the boundary
-left by earlier rows) already differ from the oracle's by single-precision
-rounding, and truncating at a flat spectrum amplifies such differences (the
-FP64 oracle moves late-row singular values by up to 5e-6 when its inputs are
-perturbed by 1e-7 relative).  With identical inputs a single einsumsvd step
-matches at 1e-5 (tests/test_gpu_einsumsvd.py; measured ~2e-7).
+to rounding order); single-precision data, 1e-5 relative on log|v|.
+
+Singular values of a whole single-precision sweep: a step's inputs (the
+boundary left by earlier rows) already differ from the oracle's by rounding,
+and truncation at a flat spectrum amplifies such differences row by row.  The
+8 x 8 norm workload's bar is therefore per row, from the oracle replayed in
+emulated single precision (tests/golden/make_c2_envelope.py: products,
+sketch, QR and small SVD in complex64, every step's U and W rounded, four
+rounding realizations): every step of row r is held to SWEEP_ENVELOPE_FACTOR
+times the largest envelope of row r.  Measured on the GPU: at most 2.1 times
+the envelope on the plain and mixed paths, with and without FP64 small
+factorisations.  The smaller workloads below keep SWEEP_SIGMA_TOL = 1e-4, the
+largest row envelope of the 8 x 8 sweep (4.5e-5) with room for their own
+rows.  With identical inputs a single einsumsvd step matches at 1e-5
+(tests/test_gpu_einsumsvd.py; measured ~2e-7).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -23,6 +33,38 @@ from tests.gpu_util import sigma_errors, to_dev
 pytestmark = pytest.mark.gpu
 
 SWEEP_SIGMA_TOL = 1e-4
+SWEEP_ENVELOPE_FACTOR = 3.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _c2_row_bars():
+    """Per-step bar of the 8 x 8 sweep: the factor times its row's envelope."""
+    env = json.load(open(os.path.join(GOLDEN, "c2_envelope.json")))
+    rows = np.array([s["row"] for s in env["steps"]])
+    e = np.array([s["envelope"] for s in env["steps"]])
+    return SWEEP_ENVELOPE_FACTOR * np.array([e[rows == r].max() for r in rows]), env
+
+
+def _c2_against_golden(sig, la, prec_name):
+    """Every step's singular values against the stored FP64 sweep and the
+    log-norm: relative 1e-5 on log|v|, and |d log v| within ten times the
+    largest single-precision replay's (reported with the relative error on v)."""
+    gold = json.load(open(os.path.join(GOLDEN, "c2_sweep.json")))
+    bars, env = _c2_row_bars()
+    pos, errs = 0, []
+    for st in gold["steps"]:
+        ref = np.asarray(st["sigma"])
+        errs.append(np.max(np.abs(sig[pos:pos + len(ref)] - ref)) / ref[0])
+        pos += len(ref)
+    errs = np.array(errs)
+    bad = [(gold["steps"][i]["row"], gold["steps"][i]["col"], "%.2e > %.2e" % (errs[i], bars[i]))
+           for i in np.nonzero(errs > bars)[0]]
+    assert not bad, (prec_name, bad)
+    dlog = abs(la - gold["log_norm"])
+    print(f"{prec_name}: max step sigma error {errs.max():.2e}, |d log v| {dlog:.2e} "
+          f"(relative on v {np.expm1(dlog):.2e}, on log v {dlog / abs(gold['log_norm']):.2e})")
+    assert dlog <= 1e-5 * abs(gold["log_norm"])
+    assert dlog <= 10 * max(abs(x) for x in env["dlog"])
 
 
 def _run(ket, bra, dtype, m, p, q, seed, **kw):
@@ -68,14 +110,16 @@ def test_two_layer_truncated_complex64(shape, D, m, p, q):
     assert sigma_errors(sig, rec).max() <= SWEEP_SIGMA_TOL
 
 
-def test_c2_norm_8x8_complex64():
+@pytest.mark.parametrize("prec,flags", [(libpeps.PREC_PLAIN, 0), (libpeps.PREC_MIXED, 0),
+                                        (libpeps.PREC_PLAIN, libpeps.FLAG_FP64_SMALL),
+                                        (libpeps.PREC_MIXED, libpeps.FLAG_FP64_SMALL)])
+def test_c2_norm_8x8_complex64_every_step(prec, flags):
+    """The 8 x 8 norm on every path against the stored FP64 sweep: every
+    step of every row at the row's envelope bar, and the log-norm."""
     cfg = synth.config("c2")
     ket = synth.peps_for(cfg)
-    rec = []
-    la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed)
-    ra, rp = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec)
-    assert abs(la - ra) <= 1e-5 * abs(ra)
-    assert sigma_errors(sig, rec).max() <= SWEEP_SIGMA_TOL
+    la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=prec, flags=flags)
+    _c2_against_golden(sig, la, f"prec {prec} flags {flags}")
 
 
 def test_real_f32_norm_6x6_and_uniform_sketch():
@@ -112,21 +156,6 @@ def test_single_row_and_single_column():
         assert la == pytest.approx(np.log(abs(ex)), abs=1e-9)
 
 
-def test_c2_mixed_precision():
-    """Tensor-core products: the log-norm stays within 1e-5 of the FP64
-    oracle and the first row's einsumsvd steps (identical inputs) keep their
-    singular values within 1e-5 normwise."""
-    cfg = synth.config("c2")
-    ket = synth.peps_for(cfg)
-    rec = []
-    la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=libpeps.PREC_MIXED)
-    ra, rp = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec)
-    assert abs(la - ra) <= 1e-5 * abs(ra)
-    errs = sigma_errors(sig, rec)
-    row1 = [i for i, r in enumerate(rec) if r["row"] == 1]
-    assert errs[row1].max() <= 1e-5
-
-
 def test_c2_fast_precision_log_norm():
     """PEPS_PREC_FAST (plain TF32 for the early power-iteration products): the
     contracted scalar stays within 1e-5 of the FP64 oracle."""
@@ -135,21 +164,3 @@ def test_c2_fast_precision_log_norm():
     la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=libpeps.PREC_FAST)
     ra, rp = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed)
     assert abs(la - ra) <= 1e-5 * abs(ra)
-
-
-@pytest.mark.parametrize("prec", [libpeps.PREC_PLAIN, libpeps.PREC_MIXED])
-def test_c2_fp64_small_factorisations(prec):
-    """PEPS_FLAG_FP64_SMALL (CholeskyQR2's Cholesky factorisations and the
-    Jacobi SVD in FP64 on single-precision data): the 8x8 log-norm stays
-    within 1e-5 of the FP64 oracle and the first row's steps (identical
-    inputs) keep their singular values within 1e-5 normwise."""
-    cfg = synth.config("c2")
-    ket = synth.peps_for(cfg)
-    rec = []
-    la, ph, sig = _run(ket, ket, "c64", cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=prec,
-                       flags=libpeps.FLAG_FP64_SMALL)
-    ra, rp = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec)
-    assert abs(la - ra) <= 1e-5 * abs(ra)
-    errs = sigma_errors(sig, rec)
-    row1 = [i for i, r in enumerate(rec) if r["row"] == 1]
-    assert errs[row1].max() <= 1e-5
