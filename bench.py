@@ -491,7 +491,8 @@ def batched_costs(cfg, plain):
     return [algorithmic_flops(mark_schedule([dict(x)], plain), cfg.q, False) for _, x in batched_shapes(cfg)]
 
 
-def measure_batched(cfg, prec, steps, warmup, dev, rank=0, world=1, use_graph=True, e2e=False, clock=None):
+def measure_batched(cfg, prec, steps, warmup, dev, rank=0, world=1, use_graph=True, e2e=False, clock=None,
+                    tune_branches=True):
     """One plan over this rank's LPT share of the 512 instances, replayed as
     one CUDA graph; returns the device time per batch, the executed
     algorithmic flops, every instance's singular values and the plan's
@@ -522,6 +523,26 @@ def measure_batched(cfg, prec, steps, warmup, dev, rank=0, world=1, use_graph=Tr
         io.append(tuple(x.to(dev) for x in h) + (U, W, sg, lg))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    branches = None
+    if not plain and tune_branches:
+        # side streams of the tensor-core chains: the fastest of a few counts
+        best = None
+        for nb in (8, 16, 32, 64):
+            plan.set_branches(nb, dev)
+            plan.execute(io)              # descriptor upload
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                plan.execute(io)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 2
+            if best is None or t < best[1]:
+                best = (nb, t)
+        branches = best[0]
+        plan.set_branches(branches, dev)
     plan.execute(io)                      # descriptor upload
     torch.cuda.synchronize()
     run = lambda: plan.execute(io)        # noqa: E731
@@ -558,7 +579,7 @@ def measure_batched(cfg, prec, steps, warmup, dev, rank=0, world=1, use_graph=Tr
     ms = float(np.mean([a.elapsed_time(b) for a, b in times]))
     sig = [x[6].cpu().numpy() for x in io]
     out = {"ms": ms, "flops": flops, "sig": sig, "ids": ids, "plan": plan, "io": io, "host": host, "run": run,
-           "graph": graph is not None, "n": n, "tc_instances": 0 if plain else n,
+           "graph": graph is not None, "n": n, "tc_instances": 0 if plain else n, "branches": branches,
            "padded_instances": 0 if plain else sum(1 for _, x in shp if not x["aligned"])}
     if e2e:
         # end to end: H2D of every instance's operands, the batch, D2H of all singular values
@@ -611,6 +632,7 @@ def batched_subrecord(dev, steps=3, warmup=3):
         if name == "mixed":
             out["tensor_core_instances"] = r["tc_instances"]
             out["padded_instances"] = r["padded_instances"]
+            out["branches"] = r["branches"]
         del r
         torch.cuda.empty_cache()
     out["mixed_speedup"] = round(out["plain"]["batch_s"] / out["mixed"]["batch_s"], 3)
@@ -676,7 +698,7 @@ def run_batched(args, cfg):
                    "D_range": cfg.extra["D_range"], "p": cfg.p, "q": cfg.q, "rank": "k = m per instance",
                    "precision": args.prec, "algorithmic_tflop_per_step": round(flops_all / 1e12, 6),
                    "tensor_core_instances": r["tc_instances"], "padded_instances": r["padded_instances"],
-                   "sigma_err_vs_oracle": err,
+                   "branches": r["branches"], "sigma_err_vs_oracle": err,
                    "l2": "flushed between steps (2x L2 write outside the timed events)",
                    "parallelism": f"one batch split by LPT over {world} rank(s)", "cuda_graph": r["graph"]},
         "gpu_launches": plan.kernel_launches() * args.steps,
@@ -697,6 +719,65 @@ def run_batched(args, cfg):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_expect_cache(args, cfg):
+    """Expectation value <psi|H|psi>/<psi|psi> of the transverse-field Ising
+    Hamiltonian (one-site X on every site, ZZ on every bond) on the 12 x 12,
+    D = 4 PEPS with the cached environments of Sec. IV-B (two sweeps per
+    lattice, then one strip per term) and without them (fresh sweeps for the
+    environments of every row that holds a term): device seconds of each, the
+    speed-up, and the energies of both schedules."""
+    import torch
+    from paper_2006_15234_gb300 import libpeps
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prec = {"plain": libpeps.PREC_PLAIN, "mixed": libpeps.PREC_MIXED, "fast": libpeps.PREC_FAST}[args.prec]
+    ket = synth.peps_for(cfg)
+    kt = [[torch.tensor(T, dtype=torch.complex64, device=dev) for T in row] for row in ket]
+    terms = synth.tfi_terms(cfg.nrow, cfg.ncol, cfg.extra["J"], cfg.extra["h"])
+    opts = libpeps.make_opts(cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=prec)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    with ClockSampler(0) as clk:
+        for name, cache in (("cached", True), ("uncached", False)):
+            plan = libpeps.ExpectationPlan(kt, terms, opts, use_cache=cache)
+            for _ in range(max(1, args.warmup)):
+                plan.execute()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                flush.add_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.execute()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            e, lnorm, _ = plan.result()
+            fl = sum(f for _, f, _ in plan.launches())
+            out[name] = {"seconds": round(float(np.mean(ms)) / 1e3, 5), "energy": e, "log_norm": lnorm,
+                         "launch_flops_tflop": round(fl / 1e12, 4), "kernel_launches": plan.kernel_launches(),
+                         "workspace_gb": round(plan.workspace_bytes / 1e9, 3)}
+            del plan
+    t_c = out["cached"]["seconds"]
+    line = {
+        "metric": METRIC, "value": round(out["cached"]["launch_flops_tflop"] / t_c, 4), "unit": "TFLOP/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_c, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": cfg.dtype,
+        "data": "synthetic (seeded Gaussian PEPS, shapes of the workload)",
+        "config": {"workload": cfg.name, "nrow": cfg.nrow, "ncol": cfg.ncol, "bond": cfg.D, "m": cfg.m,
+                   "p": cfg.p, "q": cfg.q, "precision": args.prec, "terms": len(terms),
+                   "cache_speedup": round(out["uncached"]["seconds"] / t_c, 3),
+                   "l2": "flushed between steps (2x L2 write outside the timed events)"},
+        "cache": out,
+    }
+    clk = clk.summary()
+    if clk:
+        line["clocks"] = clk
+    print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(cfg, args):
@@ -841,7 +922,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3"])
+    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3", "f2"])
     ap.add_argument("--prec", default="mixed", choices=["plain", "mixed", "fast"])
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip the plain FP32 contraction timed beside the mixed one")
@@ -866,6 +947,8 @@ def main():
         run_reference(args, cfg)
     elif args.config == "c3":
         run_batched(args, cfg)
+    elif args.config == "f2":
+        run_expect_cache(args, cfg)
     else:
         run_ours(args, cfg)
 

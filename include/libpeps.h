@@ -144,6 +144,14 @@ peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch
                                 const uint64_t *instance_ids,
                                 const peps_rsvd_opts *opts, size_t *workspace_bytes);
 
+/* Number of side streams (1..64, default 16) over which a batched plan deals
+ * its tensor-core instances (longest-processing-time-first on each
+ * instance's product cost); each runs its chains one after another in one
+ * shared scratch region, and a captured execute holds them as parallel graph
+ * branches.  Host only: rebuilds the schedule and writes the new workspace
+ * size (more branches, more scratch regions) to *workspace_bytes. */
+peps_status peps_einsumsvd_set_branches(peps_plan *plan, int32_t branches, size_t *workspace_bytes);
+
 /* Output rank k of instance i of a plan (host query). */
 peps_status peps_einsumsvd_rank(const peps_plan *plan, int32_t i, int32_t *k);
 

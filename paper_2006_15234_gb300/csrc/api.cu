@@ -125,6 +125,7 @@ struct peps_plan {
   // einsumsvd
   std::vector<Inst> insts;
   std::vector<Inst> embeds;                 // zero-padded copies of instances with embed set
+  int branches = 16;                        // side streams of the tensor-core chains
   // side streams of the plan's branches and their fork / join events
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> side_ev;
@@ -179,8 +180,9 @@ size_t finish(Builder &B, size_t *blob_off) {
   return *blob_off + B.blob.size();
 }
 
-// Side streams of a batched plan's tensor-core chains.
+// Side streams of a batched plan's tensor-core chains (default and limit).
 constexpr int kBranches = 16;
+constexpr int kMaxBranches = 64;
 
 // Multiply-adds of one implicit product of an instance (Table 2's two-layer
 // terms): the cost the tensor-core chains are balanced on.
@@ -195,7 +197,7 @@ double inst_cost(const Inst &q) {
 // the CUDA cores share grouped launches on the caller's stream (branch 0).
 // Instances on the tensor cores (extents aligned, or through a zero-padded
 // copy) each run as one chain of launches; the chains are dealt to
-// kBranches side streams by longest-processing-time-first on their product
+// P->branches side streams by longest-processing-time-first on their product
 // cost, so that independent chains overlap on the GPU, and the chains of
 // one branch, which run one after the other, share one scratch region.
 std::string build_einsumsvd(peps_plan *P, uintptr_t base, const peps_einsumsvd_io *io, Builder &B) {
@@ -228,7 +230,7 @@ std::string build_einsumsvd(peps_plan *P, uintptr_t base, const peps_einsumsvd_i
     const double cx = inst_cost(exec(x)), cy = inst_cost(exec(y));
     return cx != cy ? cx > cy : x < y;
   });
-  const int nb = (int)std::min<size_t>(kBranches, chains.size());
+  const int nb = (int)std::min<size_t>(P->branches, chains.size());
   std::vector<double> load(nb, 0.0);
   std::vector<std::vector<size_t>> br(nb);
   for (size_t i : chains) {
@@ -1685,6 +1687,18 @@ peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch
   if (peps_status s = rebuild(P.get(), nullptr, nullptr)) return s;
   *workspace_bytes = P->ws_bytes;
   *out = P.release();
+  return PEPS_OK;
+}
+
+peps_status peps_einsumsvd_set_branches(peps_plan *plan, int32_t branches, size_t *workspace_bytes) {
+  g_last_error.clear();
+  if (!plan || !workspace_bytes) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (plan->kind != peps_plan::EINSUMSVD) return fail(PEPS_ERR_ARG, "not an einsumsvd plan");
+  if (branches < 1 || branches > kMaxBranches) return fail(PEPS_ERR_ARG, "branches must be in 1..%d", kMaxBranches);
+  plan->branches = branches;
+  plan->built = false;
+  if (peps_status s = rebuild(plan, nullptr, nullptr)) return s;
+  *workspace_bytes = plan->ws_bytes;
   return PEPS_OK;
 }
 

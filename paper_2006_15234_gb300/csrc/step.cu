@@ -280,9 +280,14 @@ void emit_cqr_pass(Builder &B, std::vector<Inst *> &I, bool mside, void *Inst::*
   op.tag = tag;
   op.wide = wide;
   const int fdt = wide ? (B.dt | 2) : B.dt;
+  const double mult = dtype_complex(B.dt) ? 8.0 : 2.0;
   for (auto &c : ch) {
     op.smem = std::max(op.smem, small_smem_bytes(fdt, c.n));
     op.smem2 = std::max(op.smem2, chol_cluster_smem_bytes(fdt, c.n, c.T != nullptr));
+    const double n = c.n;
+    // factor n^3/3 MACs (+ n^3/6 for R^+); Gram in, R (and R^+) out
+    op.flops += mult * (n * n * n / 3.0 + (c.T ? n * n * n / 6.0 : 0.0));
+    op.bytes += n * n * (acc_size(B.dt) + dtype_size(fdt) * (c.T ? 2.0 : 1.0));
   }
   B.ops.push_back(op);
   if (!apply) return;

@@ -37,7 +37,7 @@ EXPORTED_SYMBOLS = [
     "peps_plan_kernel_launches", "peps_einsumsvd_grad_plan", "peps_einsumsvd_grad_bind",
     "peps_einsumsvd_grad_execute", "peps_grad_plan", "peps_grad_execute", "peps_grad",
     "peps_poll", "peps_plan_set_wait_limit", "peps_debug_sketch",
-    "peps_plan_autotune", "peps_plan_tune_table", "peps_plan_set_tune_table",
+    "peps_plan_autotune", "peps_plan_tune_table", "peps_plan_set_tune_table", "peps_einsumsvd_set_branches",
 ]
 
 # Bits of a plan's device status word (peps_poll).
@@ -193,6 +193,8 @@ def load():
     lib.peps_debug_sketch.restype = st
     lib.peps_debug_sketch.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                       C.c_int32, vp, vp, vp]
+    lib.peps_einsumsvd_set_branches.restype = st
+    lib.peps_einsumsvd_set_branches.argtypes = [vp, C.c_int32, C.POINTER(C.c_size_t)]
     lib.peps_plan_autotune.restype = st
     lib.peps_plan_autotune.argtypes = [vp, vp, C.c_size_t, vp, C.c_int32]
     lib.peps_plan_tune_table.restype = st
@@ -413,6 +415,14 @@ class EinsumsvdPlan(_Ledger):
             k = C.c_int32()
             _check(self._lib.peps_einsumsvd_rank(plan, i, C.byref(k)))
             self.ranks.append(k.value)
+
+    def set_branches(self, n: int, device="cuda"):
+        """Side streams of the tensor-core chains; reallocates the workspace."""
+        ws = C.c_size_t()
+        _check(self._lib.peps_einsumsvd_set_branches(self._plan, int(n), C.byref(ws)))
+        self.workspace_bytes = ws.value
+        self._buf = None
+        self._buf, self._ws = _workspace(ws.value, device)
 
     def execute(self, io_list, stream=None):
         """io_list: per instance (V, S, ket, bra, U, W, sigma, log_scale) tensors."""

@@ -65,6 +65,11 @@ CONFIGS = {
     "c4": WorkloadConfig("c4_6x6_tfi_f32_D3_m18", 6, 6, 2, 3, "f32", True,
                          18, 8, 2, "normal_tenth", _BASE_SEED + 3, _BASE_SEED + 4,
                          {"J": 1.0, "h": 3.0}),
+    # 12x12 TFI expectation value, complex64, d=2, bond 4 (the cache-on /
+    # cache-off study's shape, Sec. IV-B); boundary bond 16 = D^2.
+    "f2": WorkloadConfig("f2_12x12_tfi_expectation_c64_D4_m16", 12, 12, 2, 4, "c64", True,
+                         16, 8, 2, "cgauss_scaled", _BASE_SEED + 5, _BASE_SEED + 6,
+                         {"J": 1.0, "h": 3.0}),
     # 16x16 norm, complex64, d=2, bond 8, per-tensor Frobenius-normalised.
     "c5": WorkloadConfig("c5_16x16_norm_c64_D8_m256", 16, 16, 2, 8, "c64", True,
                          256, 16, 2, "cgauss_fro", _BASE_SEED + 4, _BASE_SEED + 5),

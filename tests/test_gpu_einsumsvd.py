@@ -230,3 +230,35 @@ def test_fp64_small_factorisations(dtype, prec, ell_case):
         m = 256
     out = _run_batch([case], dtype, m, 8, 2, 79, prec=prec, flags=libpeps.FLAG_FP64_SMALL)
     _check(case, out[0], m, 8, 2, 79, 100, dtype)
+
+
+def test_branch_count_changes_no_result():
+    """Dealing the tensor-core chains to 1 or to 64 side streams (parallel
+    graph branches, per-branch scratch) runs the same kernels on the same
+    operands: bit-identical outputs."""
+    cfg = synth.config("c3")
+    dims = synth.batched_dims(cfg)[:24]
+    shapes, host = [], []
+    for i, (mm, D) in enumerate(dims):
+        inst = synth.batched_instance(cfg, i, mm, D)
+        host.append([inst[k] for k in ("V", "S", "ket", "bra")])
+        R = D * D
+        shapes.append((mm, R, mm, mm, cfg.d, D, D, D, D, D, D, D, D, mm))
+    plan = libpeps.EinsumsvdPlan(torch.float32, shapes,
+                                 libpeps.make_opts(128, cfg.p, cfg.q, cfg.omega_seed, prec=libpeps.PREC_MIXED))
+    outs = []
+    for nb in (1, 64):
+        plan.set_branches(nb)
+        ios = []
+        for (V, S, K, Kb), sh, k in zip(host, shapes, plan.ranks):
+            mm, R = sh[0], sh[1]
+            ios.append((tensor(V, "f32"), tensor(S, "f32"), tensor(K, "f32"), tensor(Kb, "f32"),
+                        torch.zeros((mm * R, k), device="cuda"), torch.zeros((k, R * mm * R), device="cuda"),
+                        torch.zeros(k, dtype=torch.float64, device="cuda"),
+                        torch.zeros(1, dtype=torch.float64, device="cuda")))
+        plan.execute(ios)
+        torch.cuda.synchronize()
+        outs.append([[t.cpu().numpy() for t in io[4:]] for io in ios])
+    for a, b in zip(*outs):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
