@@ -53,17 +53,25 @@ def zipup_start(S1, K, Kb):
     return V1.reshape(1, Dx * DX, b, De * DE)
 
 
+def absorb_side(row, alternate):
+    """Where a row's einsumsvd steps put Sigma: into the carry ("right") on
+    every row, or, with alternating canonicalisation (Sec. III-A), into the
+    finished boundary site ("left") on the even rows 2, 4, ..."""
+    return "left" if alternate and row % 2 == 0 else "right"
+
+
 def zipup(S_sites, ket_row, bra_row, m, p, q, seed, direction, row,
-          sketch_kind="gauss", rtol=None, record=None):
+          sketch_kind="gauss", rtol=None, record=None, alternate=False):
     """Algorithm 3 on one row; returns (new boundary sites, sum of logs)."""
     n = len(ket_row)
     V = zipup_start(S_sites[0], ket_row[0], bra_row[0])
     new = [None] * n
     total = 0.0
+    side = absorb_side(row, alternate)
     for i in range(1, n):
         inst = philox.instance_id(direction, row, i)
         U, W, s, logs1 = einsumsvd(V, S_sites[i], ket_row[i], bra_row[i],
-                                   m, p, q, seed, inst, sketch_kind, rtol)
+                                   m, p, q, seed, inst, sketch_kind, rtol, absorb=side)
         if record is not None:
             record.append(dict(row=row, col=i, sigma=s, logs1=logs1,
                                M=U.shape[0] * U.shape[1],
@@ -86,7 +94,7 @@ def boundary_scalar(S_sites):
 
 
 def sweep(ket, bra, m, p, q, seed, direction=0, upto=None, sketch_kind="gauss",
-          rtol=None, record=None):
+          rtol=None, record=None, alternate=False):
     """Boundaries after rows 0..r for r = 0..upto (list) and their log scales."""
     nrow = len(ket)
     if bra is None:
@@ -98,7 +106,7 @@ def sweep(ket, bra, m, p, q, seed, direction=0, upto=None, sketch_kind="gauss",
     total = 0.0
     for r in range(1, last + 1):
         S, lg = zipup(S, ket[r], bra[r], m, p, q, seed, direction, r,
-                      sketch_kind, rtol, record)
+                      sketch_kind, rtol, record, alternate)
         total += lg
         bounds.append(S)
         logs.append(total)
@@ -106,14 +114,15 @@ def sweep(ket, bra, m, p, q, seed, direction=0, upto=None, sketch_kind="gauss",
 
 
 def contract(ket, bra, m, p, q, seed, direction=0, sketch_kind="gauss",
-             rtol=None, record=None):
+             rtol=None, record=None, alternate=False):
     """Algorithm 2: returns (log|v|, arg v) of the contracted network.
 
     ``bra=None`` is the one-layer contraction (ket sites have d = 1); for a
-    norm pass ``bra=ket`` (the bra layer enters conjugated).
+    norm pass ``bra=ket`` (the bra layer enters conjugated).  ``alternate``
+    selects the alternating canonicalisation of Sec. III-A (absorb_side).
     """
     bounds, logs = sweep(ket, bra, m, p, q, seed, direction, None, sketch_kind,
-                         rtol, record)
+                         rtol, record, alternate)
     v = boundary_scalar(bounds[-1])
     if v == 0:
         return float("-inf"), 0.0

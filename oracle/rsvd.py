@@ -87,11 +87,15 @@ def block_sizes(m: int, p: int, M: int, N: int):
 
 def einsumsvd(V, S, K, Kb, m: int, p: int, q: int, seed: int, instance: int,
               sketch_kind: str = "gauss", rtol: float | None = None,
-              return_all: bool = False):
+              return_all: bool = False, absorb: str = "right"):
     """One zip-up einsumsvd step (Algorithm 3) with Algorithm 4 inside.
 
     Returns U [kL][t][k] (new boundary site), W [k][x X][b][e E] (new carry,
     divided by sigma_1), sigma (k values, unnormalised) and log(sigma_1).
+    absorb="right" puts Sigma into the carry (W = Sigma V^H / sigma_1, U with
+    orthonormal columns); absorb="left" into the finished site (U = U~ Sigma /
+    sigma_1, W = V^H with orthonormal rows), the other canonical choice of
+    Sec. III-A's zip-up.
     """
     op = ImplicitOp(V, S, K, Kb)
     is_c = op.is_complex
@@ -110,7 +114,13 @@ def einsumsvd(V, S, K, Kb, m: int, p: int, q: int, seed: int, instance: int,
     U, W = fix_gauge(U, W, g)
     s1 = s[0] if s.size else 0.0
     logs1 = float(np.log(s1)) if s1 > 0 else float("-inf")
-    if s1 > 0:
+    if absorb == "left":
+        # W rows back to V^H (zero rows stay zero), Sigma / sigma_1 into U
+        inv = np.where(s > 0, 1.0 / np.where(s > 0, s, 1.0), 0.0)
+        W = W * inv[:, None]
+        if s1 > 0:
+            U = U * (s / s1)[None, :]
+    elif s1 > 0:
         W = W / s1
     kL, t = op.dims["kL"], op.dims["t"]
     Dx, DX, b, De, DE = op.col_shape

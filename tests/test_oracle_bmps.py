@@ -79,7 +79,7 @@ def test_transposed_lattice_exact_regime():
     assert lf == pytest.approx(la, abs=1e-10)
 
 
-def _dense_einsumsvd(V, S, K, Kb, m, *args, **kw):
+def _dense_einsumsvd(V, S, K, Kb, m, *args, absorb="right", **kw):
     """Naive einsumsvd: form A explicitly and take LAPACK's truncated SVD."""
     op = ImplicitOp(V, S, K, Kb)
     A = op.dense()
@@ -109,3 +109,50 @@ def test_truncated_regime_close_to_exact():
     errs = [abs(bmps.contract(ket, ket, m, 4, 2, 6)[0] - ex) for m in (2, 8, 16)]
     assert errs[1] < errs[0]
     assert errs[2] < 1e-10          # m = 16 is the largest cut rank: exact
+
+
+def test_left_absorption_is_the_same_factorisation():
+    """absorb="left" (Sigma into the finished site) factorises the same
+    truncated matrix: U W is unchanged, the carry's rows are orthonormal
+    (V^H), U's column norms are sigma_c / sigma_1, the log-scale is the same,
+    and the gauge phases (<g, u_c> real and >= 0) still hold."""
+    rng = np.random.default_rng(4)
+    cplx = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)   # noqa: E731
+    V, S, K, Kb = cplx(3, 4, 5, 4), cplx(5, 4, 3), cplx(2, 2, 2, 2, 2), cplx(2, 2, 2, 2, 2)
+    Ur, Wr, sr, lr = rsvd.einsumsvd(V, S, K, Kb, 6, 4, 2, 11, 3)
+    Ul, Wl, sl, ll = rsvd.einsumsvd(V, S, K, Kb, 6, 4, 2, 11, 3, absorb="left")
+    k = len(sr)
+    assert np.array_equal(sr, sl) and lr == ll
+    UWr = Ur.reshape(-1, k) @ Wr.reshape(k, -1)
+    UWl = Ul.reshape(-1, k) @ Wl.reshape(k, -1)
+    assert np.linalg.norm(UWl - UWr) <= 1e-12 * np.linalg.norm(UWr)
+    Wm = Wl.reshape(k, -1)
+    assert np.allclose(Wm @ Wm.conj().T, np.eye(k), atol=1e-12)
+    assert np.allclose(np.linalg.norm(Ul.reshape(-1, k), axis=0), sl / sl[0], atol=1e-12)
+    g = rsvd.philox.gauge_vector(Ul.reshape(-1, k).shape[0], 11, 3, True)
+    ph = g.conj() @ Ul.reshape(-1, k)
+    assert np.all(np.abs(ph.imag) <= 1e-12 * np.abs(ph)) and np.all(ph.real >= 0)
+
+
+@pytest.mark.parametrize("shape,D,m", [((3, 3), 2, 16), ((4, 3), 2, 16)])
+def test_alternating_canonicalisation_exact_regime(shape, D, m):
+    """Alternating where Sigma goes (Sec. III-A) changes no exact contraction."""
+    nr, nc = shape
+    ket = synth.random_peps(nr, nc, 2, D, "c64", "cgauss_scaled", 41)
+    la, ph = bmps.contract(ket, ket, m, 4, 1, 77, alternate=True)
+    ex = bruteforce.exact_scalar(ket, ket)
+    assert la == pytest.approx(np.log(abs(ex)), abs=1e-10)
+    assert abs(np.sin(ph)) < 1e-10
+    assert [bmps.absorb_side(r, True) for r in (1, 2, 3, 4)] == ["right", "left", "right", "left"]
+
+
+def test_alternating_canonicalisation_truncated_regime():
+    """Truncated: a different (still valid) approximation of the same norm,
+    as close to the exact value as the right-absorbing sweep at each m."""
+    ket = synth.random_peps(4, 4, 2, 2, "c64", "cgauss_scaled", 43)
+    ex = np.log(abs(bruteforce.exact_scalar(ket, ket)))
+    for m in (3, 6):
+        lr = bmps.contract(ket, ket, m, 4, 2, 6)[0]
+        la = bmps.contract(ket, ket, m, 4, 2, 6, alternate=True)[0]
+        assert la != lr
+        assert abs(la - ex) < 5 * abs(lr - ex) + 1e-6
