@@ -89,7 +89,12 @@ typedef enum { PEPS_SKETCH_GAUSS = 0, PEPS_SKETCH_UNIFORM = 1 } peps_sketch;
  *        one-sided Jacobi SVD of R_B (Algorithm 4's "SVD") run in FP64 on the
  *        FP64-accumulated Grams, their outputs rounded once to the working
  *        precision; the default runs them in single precision (with R_B's
- *        factor in FP64 on the MIXED / FAST paths) */
+ *        factor in FP64 on the MIXED / FAST paths)
+ *        PEPS_FLAG_ALTERNATE: contraction plans only (PEPS_ERR_UNSUPPORTED
+ *        elsewhere): alternating canonicalisation of the zip-up (Sec. III-A):
+ *        on the even rows 2, 4, ... of a sweep every einsumsvd puts its
+ *        singular values into the finished boundary site (U = U~ Sigma /
+ *        sigma_1, carry W = V^H) instead of the carry */
 typedef struct {
   int32_t m, p, q;
   uint64_t seed;
@@ -99,6 +104,7 @@ typedef struct {
 } peps_rsvd_opts;
 #define PEPS_FLAG_ORTH_Q 1u
 #define PEPS_FLAG_FP64_SMALL 2u
+#define PEPS_FLAG_ALTERNATE 4u
 
 /* ------------------------------------------------------------------------
  * Batched einsumsvd (Algorithm 3's einsumsvd line, Algorithm 4 inside).

@@ -55,7 +55,7 @@ peps_status check_opts(const peps_rsvd_opts *o) {
     return fail(PEPS_ERR_ARG, "unknown sketch kind %d", o->sketch);
   if (o->prec != PEPS_PREC_PLAIN && o->prec != PEPS_PREC_MIXED && o->prec != PEPS_PREC_FAST)
     return fail(PEPS_ERR_ARG, "unknown precision %d", o->prec);
-  if (o->flags & ~(PEPS_FLAG_ORTH_Q | PEPS_FLAG_FP64_SMALL))
+  if (o->flags & ~(PEPS_FLAG_ORTH_Q | PEPS_FLAG_FP64_SMALL | PEPS_FLAG_ALTERNATE))
     return fail(PEPS_ERR_ARG, "unknown flag bits %#x", o->flags);
   return PEPS_OK;
 }
@@ -65,6 +65,7 @@ RsvdOpts to_opts(const peps_rsvd_opts *o) {
   r.m = o->m; r.p = o->p; r.q = o->q; r.seed = o->seed; r.sketch = o->sketch; r.prec = o->prec;
   r.orth_q = (o->flags & PEPS_FLAG_ORTH_Q) != 0;
   r.fp64_small = (o->flags & PEPS_FLAG_FP64_SMALL) != 0;
+  r.alternate = (o->flags & PEPS_FLAG_ALTERNATE) != 0;
   return r;
 }
 
@@ -467,6 +468,14 @@ void emit_sweep(Builder &B, const Sweep &S, const RsvdOpts &opts, const void *on
       ++step_idx;
       std::vector<Inst *> one{&I};
       emit_einsumsvd(B, one, opts);
+      if (opts.alternate && r % 2 == 0) {
+        // alternating canonicalisation: Sigma / sigma_1 into the finished site
+        Op op;
+        op.kind = Op::ABSORB; op.tag = "epilogue_u";
+        op.absorb = AbsorbDesc{I.U, I.W, I.sigma, I.M, I.N, I.k};
+        op.bytes = 2.0 * dtype_size(B.dt) * ((double)I.M * I.k + (double)I.k * I.N);
+        B.ops.push_back(op);
+      }
       cv = 1 - cv;
     }
   }
@@ -1355,6 +1364,11 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         C.need(op.aux_ptr, 8.0 * op.fill_n, tag, "src");
         C.need(op.fill_ptr, 4.0 * op.fill_n, tag, "dst");
         break;
+      case Op::ABSORB:
+        C.need(op.absorb.U, es * (double)op.absorb.M * op.absorb.k, tag, "U");
+        C.need(op.absorb.W, es * (double)op.absorb.k * op.absorb.N, tag, "W");
+        C.need(op.absorb.sigma, 8.0 * op.absorb.k, tag, "sigma");
+        break;
       case Op::AXPY:
         C.need(op.aux_ptr, es * (double)op.fill_n, tag, "x");
         C.need(op.fill_ptr, es * (double)op.fill_n, tag, "y");
@@ -1613,6 +1627,7 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s0, bo
       case Op::TGRAD: launch_tensor_grad(dt, *(const TensorGradDesc *)(P->blob.data() + op.desc_off), s); break;
       case Op::MEMSET: CUDA_TRY(cudaMemsetAsync(op.fill_ptr, 0, (size_t)op.fill_n, s)); break;
       case Op::AXPY: launch_axpy(dt, op.aux_ptr, op.fill_ptr, op.fill_n, s); break;
+      case Op::ABSORB: launch_absorb(dt, op.absorb, s); break;
       case Op::SITEBWD: launch_site_bwd(dt, *(const SiteBwdDesc *)(P->blob.data() + op.desc_off), s); break;
       case Op::STRIPBWD:
         launch_strip_bwd(dt, (const StripDesc *)d, (const StripCol *)(blob + op.aux_off[0]),
@@ -1666,6 +1681,8 @@ peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch
   P->kind = peps_plan::EINSUMSVD;
   P->dt = dtype;
   P->opts = to_opts(opts);
+  if (P->opts.alternate)
+    return fail(PEPS_ERR_UNSUPPORTED, "alternating canonicalisation applies to contraction plans only");
   for (int i = 0; i < batch; ++i) {
     const peps_einsumsvd_shape &s = shapes[i];
     Inst I{};
@@ -1744,6 +1761,8 @@ peps_status peps_einsumsvd_grad_plan(peps_plan **out, peps_dtype dtype, const pe
   P->kind = peps_plan::EGRAD;
   P->dt = dtype;
   P->opts = to_opts(opts);
+  if (P->opts.alternate)
+    return fail(PEPS_ERR_UNSUPPORTED, "alternating canonicalisation applies to contraction plans only");
   const peps_einsumsvd_shape &s = *shape;
   Inst I{};
   I.kL = s.kL; I.t = s.t; I.a = s.a; I.b = s.b; I.d = s.d;
@@ -2014,6 +2033,8 @@ peps_status peps_expectation_plan(peps_plan **out, const peps_network *ket, cons
   if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
   P->kind = peps_plan::EXPECT;
   P->opts = to_opts(opts);
+  if (P->opts.alternate)
+    return fail(PEPS_ERR_UNSUPPORTED, "alternating canonicalisation applies to contraction plans only");
   P->use_cache = use_cache != 0;
   if (peps_status s = read_net(ket, P->ket, "ket")) return s;
   P->dt = P->ket.dt;
@@ -2266,6 +2287,7 @@ peps_status peps_plan_launch_kernel(const peps_plan *plan, int64_t i, const char
     case Op::PERMUTE: *kernel = "permute"; break;
     case Op::PAD: *kernel = "pad"; break;
     case Op::NARROW: *kernel = "narrow"; break;
+    case Op::ABSORB: *kernel = "absorb"; break;
     case Op::STRIP: *kernel = "strip"; break;
     case Op::COPY: *kernel = "copy"; break;
     case Op::SVDBWD: *kernel = "svd_bwd"; break;

@@ -159,6 +159,17 @@ struct SiteDesc {
   int64_t total;
 };
 
+// Sigma moved from the carry into the finished site (alternating
+// canonicalisation): U[row][c] *= sigma_c / sigma_0 (U: M x k) and
+// W[c][n] *= sigma_0 / sigma_c, 0 where sigma_c = 0 (W: k x N).
+struct AbsorbDesc {
+  void *U, *W;
+  const double *sigma;
+  int64_t M, N;
+  int32_t k;
+};
+void launch_absorb(int dt, const AbsorbDesc &d, cudaStream_t s);
+
 // Contract a boundary MPS with trivial vertical bonds to a scalar:
 // v = S_0[0,0,:] S_1[:,0,:] ... ; result log|v| + sum(logs), arg v.
 struct ScalarDesc {

@@ -9,6 +9,8 @@
 //    first line) and the zip-up start V1 = S1 O1 (Algorithm 3, first line).
 //  * scalar: the final contraction of a boundary with trivial vertical bonds
 //    (Algorithm 2, last line), returned as log|v| plus the carried logs.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "plan.h"
@@ -315,6 +317,38 @@ __global__ void narrow_kernel(const double *__restrict__ in, float *__restrict__
 
 void launch_narrow(const double *in, float *out, int64_t n, cudaStream_t s) {
   if (n > 0) narrow_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(in, out, n);
+}
+
+namespace {
+template <class T> __global__ void absorb_kernel(AbsorbDesc g) {
+  const int64_t nu = g.M * g.k, total = nu + (int64_t)g.k * g.N;
+  const double s0 = g.sigma[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nu) {
+      const int c = (int)(i % g.k);
+      T *u = (T *)g.U + i;
+      *u = scale(*u, (typename Traits<T>::Real)(s0 > 0.0 ? g.sigma[c] / s0 : 0.0));
+    } else {
+      const int64_t j = i - nu;
+      const int c = (int)(j / g.N);
+      const double sc = g.sigma[c];
+      T *w = (T *)g.W + j;
+      *w = scale(*w, (typename Traits<T>::Real)(sc > 0.0 ? s0 / sc : 0.0));
+    }
+  }
+}
+}  // namespace
+
+void launch_absorb(int dt, const AbsorbDesc &d, cudaStream_t s) {
+  const int64_t total = d.M * d.k + (int64_t)d.k * d.N;
+  if (total <= 0) return;
+  const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 16);
+  switch (dt) {
+    case DT_R32: absorb_kernel<float><<<blocks, 256, 0, s>>>(d); break;
+    case DT_C64: absorb_kernel<float2><<<blocks, 256, 0, s>>>(d); break;
+    case DT_R64: absorb_kernel<double><<<blocks, 256, 0, s>>>(d); break;
+    case DT_C128: absorb_kernel<double2><<<blocks, 256, 0, s>>>(d); break;
+  }
 }
 
 void launch_pad(int dt, const PadDesc *d, const int64_t *prefix, int nd, int64_t blocks, cudaStream_t s) {

@@ -15,7 +15,7 @@ namespace peps {
 
 struct Op {
   enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL, TC,
-              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD, MEMSET, STRIPBWD, SITEBWD, AXPY, PAD, NARROW } kind;
+              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD, MEMSET, STRIPBWD, SITEBWD, AXPY, PAD, NARROW, ABSORB } kind;
   size_t desc_off = 0;    // byte offset of the descriptor array in the blob
   size_t prefix_off = 0;  // byte offset of the int64 block prefix array in the blob
   int nd = 0;
@@ -29,6 +29,7 @@ struct Op {
   void *fill_ptr = nullptr;
   const void *aux_ptr = nullptr;  // COPY / LTU / AXPY source
   StripBwdScratch sbs{};          // STRIPBWD scratch
+  AbsorbDesc absorb{};            // ABSORB
   const double *sbar = nullptr;   // STRIPBWD strip cotangents
   int64_t fill_n = 0;             // FILL: elements; COPY: bytes; LTU: n; NARROW: real values
   double fill_value = 0.0;
@@ -125,6 +126,7 @@ struct RsvdOpts {
   int prec;
   bool orth_q;
   bool fp64_small;     // single-precision data: CholeskyQR2's factorisations and the Jacobi SVD in FP64
+  bool alternate;      // contraction sweeps: Sigma into the finished site on even rows
 };
 
 // Shape bookkeeping shared by every planner.

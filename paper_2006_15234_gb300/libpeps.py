@@ -19,7 +19,7 @@ __all__ = [
     "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
     "Term", "ExpectationPlan", "expectation", "Cotangent", "Grads", "einsumsvd_grad", "GradPlan",
     "energy_grad", "peps_energy", "STATUS_NONFINITE", "STATUS_JACOBI_NOCONV", "STATUS_TIMEOUT",
-    "ERR_NUMERIC", "ERR_TIMEOUT", "FLAG_FP64_SMALL",
+    "ERR_NUMERIC", "ERR_TIMEOUT", "FLAG_FP64_SMALL", "FLAG_ALTERNATE",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -223,6 +223,7 @@ def dtype_code(dtype) -> int:
 
 FLAG_ORTH_Q = 1
 FLAG_FP64_SMALL = 2
+FLAG_ALTERNATE = 4
 
 
 def make_opts(m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN, flags=0) -> RsvdOpts:

@@ -4,6 +4,10 @@ D = 4, m = 32 norm sweep away from the FP64 oracle's (tests/golden/
 c2_sweep.json).  Run from the repository root:
 
     python tests/golden/make_c2_envelope.py
+    python tests/golden/make_c2_envelope.py --alternate   # c2_envelope_alternate.json
+
+(--alternate: the same for the sweep with alternating canonicalisation,
+against the FP64 oracle's alternating sweep, which is computed here.)
 
 Each realization replays the oracle's sweep (Algorithms 2-4) with the
 arithmetic of a single-precision implementation emulated around the oracle's
@@ -37,7 +41,7 @@ def _c64(a):
     return np.asarray(a).astype(np.complex64).astype(np.complex128)
 
 
-def replay(cfg, ket, seed):
+def replay(cfg, ket, seed, alternate=False):
     rng = np.random.default_rng(seed)
     Op = implicit.ImplicitOp
     mv, rmv, common = Op.matvec, Op.rmatvec, implicit._common
@@ -80,7 +84,7 @@ def replay(cfg, ket, seed):
     torch.linalg.qr, torch.linalg.svd = qr32, svd32
     try:
         rec = []
-        la, _ = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec)
+        la, _ = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec, alternate=alternate)
     finally:
         Op.matvec, Op.rmatvec = mv, rmv
         philox.sketch, bmps.einsumsvd = sketch, es
@@ -89,23 +93,30 @@ def replay(cfg, ket, seed):
 
 
 def main():
+    alternate = "--alternate" in sys.argv[1:]
     cfg = synth.config("c2")
     ket = synth.peps_for(cfg)
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "c2_sweep.json")))
+    if alternate:
+        rec = []
+        la, _ = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec, alternate=True)
+        gold = {"log_norm": la, "steps": [{"row": r["row"], "col": r["col"], "sigma": r["sigma"]} for r in rec]}
+    else:
+        gold = json.load(open(os.path.join(ROOT, "tests", "golden", "c2_sweep.json")))
     env = np.zeros(len(gold["steps"]))
     dlog = []
     for seed in SEEDS:
-        la, rec = replay(cfg, ket, seed)
+        la, rec = replay(cfg, ket, seed, alternate)
         dlog.append(la - gold["log_norm"])
         for i, (r, g) in enumerate(zip(rec, gold["steps"])):
             ref = np.asarray(g["sigma"])
             env[i] = max(env[i], float(np.max(np.abs(np.asarray(r["sigma"]) - ref)) / ref[0]))
-    out = {"workload": cfg.name, "seeds": list(SEEDS),
+    out = {"workload": cfg.name, "seeds": list(SEEDS), "alternate": alternate,
            "generator": "tests/golden/make_c2_envelope.py (oracle.bmps.contract with single-precision "
                         "emulation wrappers)",
            "steps": [{"row": g["row"], "col": g["col"], "envelope": float(e)} for g, e in zip(gold["steps"], env)],
            "dlog": dlog}
-    with open(os.path.join(ROOT, "tests", "golden", "c2_envelope.json"), "w") as f:
+    name = "c2_envelope_alternate.json" if alternate else "c2_envelope.json"
+    with open(os.path.join(ROOT, "tests", "golden", name), "w") as f:
         json.dump(out, f, indent=0)
 
 
