@@ -19,6 +19,9 @@ Modules and the passages they follow (arXiv:2006.15234):
   bruteforce  -- exact contraction used to pin the above on tiny lattices.
   expectation -- Eq. 6 with the cached-environment strips of Sec. IV-B.
   grad        -- central finite differences of the expectation energy.
+  qrsvd       -- operator application by QR-SVD (Algorithm 1) with the
+                 einsumsvd of G, R1, R2 (Eq. 5), and one TEBD layer over all
+                 nearest-neighbour bonds.
 
 Parity status: the final scalars of the larger lattices (8x8 and 16x16
 norms) have no closed form; they are pinned only through the checks of each
