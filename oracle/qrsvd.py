@@ -27,8 +27,14 @@ Readings of points the paper leaves open (all shared with the GPU path):
     directions with sigma <= 16 n eps sigma_1 are returned as zeros, so the
     new bond always has k = D_max entries when D_max <= the rank bound, or
     the full rank bound otherwise (static shapes);
-  * phases: each U column is multiplied by the conjugate phase of <g, u>
-    (g the Philox gauge vector of the bond's stream, tag 1), V compensating;
+  * phases: column c of the updated first site, as a matrix
+    [(outer bonds, s)][c], is multiplied by the conjugate phase of its inner
+    product with g (the Philox gauge vector of the bond's stream, tag 1, one
+    entry per row) and the second site's column c by that phase, so the
+    choice does not depend on the orthonormal basis the QR picks;
+  * a site with no more outer entries than d * shared is not factorised
+    (Q = identity, R = the site itself); the result is the same for any
+    orthonormal Q;
   * the stream of the bond between sites a and b (row-major indices) is
     (4 << 32) | (a << 16) | b;
   * a TEBD layer applies G to every horizontal bond (columns 0-1, 2-3, ...,
@@ -62,30 +68,23 @@ def _qr(Mmat: np.ndarray):
     return Q, R
 
 
-def _svd_truncate(Theta: np.ndarray, kmax: int, seed: int, stream: int):
+def _svd_truncate(Theta: np.ndarray, kmax: int):
     U, s, Vh = np.linalg.svd(Theta, full_matrices=False)
     k = min(kmax, len(s))
     U, s, Vh = U[:, :k], s[:k], Vh[:k]
     tol = 16.0 * max(Theta.shape) * np.finfo(np.float64).eps * (s[0] if s.size else 0.0)
     zero = s <= tol
-    U = U.copy()
-    Vh = Vh.copy()
-    U[:, zero] = 0
-    Vh[zero, :] = 0
     s = np.where(zero, 0.0, s)
-    g = philox.gauge_vector(U.shape[0], seed, stream, np.iscomplexobj(Theta))
-    phi = g.conj() @ U
-    mag = np.abs(phi)
-    if np.iscomplexobj(U):
-        rho = np.where(mag > 0, phi / np.where(mag > 0, mag, 1.0), 1.0)
-        U = U * np.conj(rho)[None, :]
-        Vh = Vh * rho[:, None]
-    else:
-        rho = np.where(phi < 0, -1.0, 1.0)
-        U = U * rho[None, :]
-        Vh = Vh * rho[:, None]
     r = np.sqrt(s)
     return U * r[None, :], r[:, None] * Vh, s
+
+
+def _factor(Amat: np.ndarray):
+    """QR of a site matrix, or (identity, itself) when it has no more rows
+    than columns."""
+    if Amat.shape[0] <= Amat.shape[1]:
+        return np.eye(Amat.shape[0], dtype=Amat.dtype), Amat.copy()
+    return _qr(Amat)
 
 
 def apply_two_site(M1, M2, G, D_max, vertical, seed, stream):
@@ -101,16 +100,27 @@ def apply_two_site(M1, M2, G, D_max, vertical, seed, stream):
         A2 = np.transpose(M2, (2, 3, 4, 0, 1))          # [u][x][e][s][l]
     o1, o2 = A1.shape[:3], A2.shape[:3]
     Db = A1.shape[4]
-    Q1, R1 = _qr(A1.reshape(-1, d * Db))
-    Q2, R2 = _qr(A2.reshape(-1, d * Db))
+    Q1, R1 = _factor(A1.reshape(-1, d * Db))
+    Q2, R2 = _factor(A2.reshape(-1, d * Db))
     r1, r2 = R1.shape[0], R2.shape[0]
     G4 = np.asarray(G).reshape(d, d, d, d)             # [i1][i2][j1][j2]
     T = np.einsum("abjk,rjx,tkx->ratb", G4, R1.reshape(r1, d, Db), R2.reshape(r2, d, Db))
     Theta = T.reshape(r1 * d, r2 * d)
     k = min(D_max, r1 * d, r2 * d)
-    R1t, R2t, s = _svd_truncate(Theta, k, seed, stream)
-    N1 = (Q1 @ R1t.reshape(r1, d * k)).reshape(*o1, d, k)      # [o1][s][k]
-    N2 = (Q2 @ R2t.T.reshape(r2, d * k)).reshape(*o2, d, k)    # [o2][s][k]
+    R1t, R2t, s = _svd_truncate(Theta, k)
+    N1 = (Q1 @ R1t.reshape(r1, d * k)).reshape(-1, k)          # [(o1, s)][k]
+    N2 = (Q2 @ R2t.T.reshape(r2, d * k)).reshape(-1, k)        # [(o2, s)][k]
+    g = philox.gauge_vector(N1.shape[0], seed, stream, np.iscomplexobj(N1))
+    phi = g.conj() @ N1
+    mag = np.abs(phi)
+    if np.iscomplexobj(N1):
+        rho = np.where(mag > 0, phi / np.where(mag > 0, mag, 1.0), 1.0)
+        N1, N2 = N1 * np.conj(rho)[None, :], N2 * rho[None, :]
+    else:
+        rho = np.where(phi < 0, -1.0, 1.0)
+        N1, N2 = N1 * rho[None, :], N2 * rho[None, :]
+    N1 = N1.reshape(*o1, d, k)
+    N2 = N2.reshape(*o2, d, k)
     if vertical:
         M1n = np.transpose(N1, (3, 0, 1, 4, 2))          # [s][l][u][k][e]
         M2n = np.transpose(N2, (3, 0, 4, 1, 2))          # [s][l][k][x][e]

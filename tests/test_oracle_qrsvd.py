@@ -65,18 +65,28 @@ def test_truncation_error_is_eckart_young(vertical):
 
 
 def test_gauge_rule():
+    """<g, column c of the updated first site> is real and >= 0, whatever
+    orthonormal basis the factorisation used (Q and -Q give the same sites)."""
     rng = np.random.default_rng(13)
     d, D = 2, 2
-    M1, M2 = _rand(rng, (d, 1, D, D, D)), _rand(rng, (d, D, D, D, 1))
-    N1, _, s = qrsvd.apply_two_site(M1, M2, _gate(rng), 3, False, 9, 21)
-    # U sqrt(Sigma) is N1's R factor times Q1: recover <g, u_c> through the R part
-    A1 = np.transpose(M1, (1, 2, 3, 0, 4)).reshape(-1, d * D)
-    Q1, R1 = qrsvd._qr(A1)
-    R1t = Q1.conj().T @ np.transpose(N1, (1, 2, 3, 0, 4)).reshape(-1, d * len(s))
-    U = R1t.reshape(R1.shape[0] * d, len(s)) / np.sqrt(s)[None, :]
-    g = philox.gauge_vector(U.shape[0], 9, 21, True)
-    ph = g.conj() @ U
+    M1, M2, G = _rand(rng, (d, 2, D, D, D)), _rand(rng, (d, D, D, D, 1)), _gate(rng)
+    N1, N2, s = qrsvd.apply_two_site(M1, M2, G, 3, False, 9, 21)
+    k = len(s)
+    N1m = np.transpose(N1, (1, 2, 3, 0, 4)).reshape(-1, k)
+    g = philox.gauge_vector(N1m.shape[0], 9, 21, True)
+    ph = g.conj() @ N1m
     assert np.all(np.abs(ph.imag) <= 1e-10 * np.abs(ph)) and np.all(ph.real >= 0)
+    real_qr = qrsvd._qr
+
+    def flipped(A):
+        Q, R = real_qr(A)
+        return -Q, -R
+    qrsvd._qr = flipped
+    try:
+        F1, F2, _ = qrsvd.apply_two_site(M1, M2, G, 3, False, 9, 21)
+    finally:
+        qrsvd._qr = real_qr
+    assert np.allclose(F1, N1, atol=1e-12) and np.allclose(F2, N2, atol=1e-12)
 
 
 def _apply_gate_dense(psi, G, a, b, n):
