@@ -780,6 +780,57 @@ def run_expect_cache(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def run_tebd(args, cfg):
+    """One TEBD layer (Algorithm 1 on every nearest-neighbour bond, four
+    passes of disjoint bonds) of the imaginary-time TFI gate on the 16 x 16,
+    D = 8 complex64 PEPS, in place: device seconds per layer (each step
+    evolves the state by one more layer) and the algorithmic flops of the
+    site QR factorisations and the N = Q R~ products."""
+    import torch
+    from paper_2006_15234_gb300 import libpeps
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ket = synth.peps_for(cfg)
+    kt = [[torch.tensor(T, dtype=torch.complex64, device=dev) for T in row] for row in ket]
+    G = synth.tfi_bond_gate(cfg.extra["J"], cfg.extra["h"], cfg.extra["tau"])
+    plan = libpeps.TebdPlan(kt, G, cfg.omega_seed)
+    nbonds = cfg.nrow * (cfg.ncol - 1) + (cfg.nrow - 1) * cfg.ncol
+    flops = sum(f for _, f, _ in plan.launches())
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, args.warmup)):
+        plan.execute()
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.execute()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    t = float(np.mean(ms))
+    finite = all(bool(torch.isfinite(T).all()) for row in kt for T in row)
+    line = {
+        "metric": METRIC, "value": round(flops / (t * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": cfg.dtype,
+        "data": "synthetic (seeded Gaussian PEPS, imaginary-time TFI gate)",
+        "config": {"workload": cfg.name, "nrow": cfg.nrow, "ncol": cfg.ncol, "bond": cfg.D, "bonds": nbonds,
+                   "tau": cfg.extra["tau"], "layer_s": round(t / 1e3, 6), "us_per_bond": round(1e3 * t / nbonds, 3),
+                   "kernel_launches": plan.launch_count(), "launch_flops_gflop": round(flops / 1e9, 3),
+                   "sites_finite": finite,
+                   "l2": "flushed between steps (2x L2 write outside the timed events)"},
+    }
+    clk = clk.summary()
+    if clk:
+        line["clocks"] = clk
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(cfg, args):
     """The oracle as it stands, on a bounded sample of the workload."""
     from oracle import bmps, rsvd
@@ -922,7 +973,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3", "f2"])
+    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3", "f1", "f2"])
     ap.add_argument("--prec", default="mixed", choices=["plain", "mixed", "fast"])
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip the plain FP32 contraction timed beside the mixed one")
@@ -949,6 +1000,8 @@ def main():
         run_batched(args, cfg)
     elif args.config == "f2":
         run_expect_cache(args, cfg)
+    elif args.config == "f1":
+        run_tebd(args, cfg)
     else:
         run_ours(args, cfg)
 

@@ -265,6 +265,42 @@ peps_status peps_boundary_workspace(const peps_network *ket, const peps_network 
                                     const peps_rsvd_opts *opts, size_t *workspace_bytes);
 
 /* ------------------------------------------------------------------------
+ * Operator application by QR-SVD (Algorithm 1) and one TEBD layer.
+ *
+ * A two-site operator G (gate) acts on every nearest-neighbour bond of the
+ * network, in place: two passes over the horizontal bonds (those starting at
+ * even, then at odd columns), then two over the vertical ones (starting at
+ * even, then odd rows); the bonds of one pass share no site and run as
+ * grouped launches.  On each bond (sites M1, M2; Eq. 5):
+ *   Q1, R1 <- QR(M1 as [(outer bonds)][(s, shared bond)]), Q2, R2 likewise
+ *     (CholeskyQR2 with FP64-accumulated Grams; a site with no more outer
+ *     entries than d * bond is used as its own R),
+ *   Theta[(r1, i1)][(r2, i2)] = sum G[i1 i2, j1 j2] R1[r1, (j1, b)] R2[r2, (j2, b)],
+ *   its SVD truncated back to the bond's current dimension (one-sided
+ *   Jacobi in FP64), Sigma split evenly between the two factors,
+ *   M1 <- Q1 U sqrt(Sigma), M2 <- Q2 (sqrt(Sigma) V^H)^T,
+ *   each new bond direction's phase fixed on M1: column c of M1 as
+ *   [(outer bonds, s)][c] has a real non-negative inner product with the
+ *   Philox vector of stream (4 << 32) | (a << 16) | b (sites a < b row-major,
+ *   tag 1, key opts->seed); M2 takes the opposite phase.
+ * Bond dimensions are kept (each must not exceed d times the smaller QR
+ * rank); Theta's sides are at most 64.
+ * ------------------------------------------------------------------------ */
+
+/* Plan one TEBD layer of `gate` on `net`.  gate is a HOST array of
+ * (d^2) x (d^2) values, row-major [out pair][in pair] with the first site's
+ * index most significant: doubles for real networks, interleaved (re, im)
+ * doubles for complex ones; it is copied.  opts: seed (gauge vectors);
+ * prec must be PEPS_PREC_PLAIN and flags 0; m, p, q are not used. */
+peps_status peps_tebd_plan(peps_plan **out, const peps_network *net, const double *gate,
+                           const peps_rsvd_opts *opts, size_t *workspace_bytes);
+
+/* Enqueue the layer: the network's site tensors are overwritten with the
+ * updated ones (same shapes).  Same descriptor-upload rule as the other
+ * execute calls. */
+peps_status peps_tebd_execute(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Expectation values <psi|H|psi> / <psi|psi> with cached environments
  * (Eq. 6; Sec. IV-B).  Two boundary sweeps (top-down, and bottom-up on the
  * row-reversed lattice) keep the boundary MPS above and below every row;

@@ -120,7 +120,7 @@ peps_status read_net(const peps_network *n, Net &out, const char *which) {
 // ---- plans ------------------------------------------------------------------
 
 struct peps_plan {
-  enum Kind { EINSUMSVD, CONTRACT, EXPECT, EGRAD, GRAD } kind;
+  enum Kind { EINSUMSVD, CONTRACT, EXPECT, EGRAD, GRAD, TEBD } kind;
   int dt = 0;
   RsvdOpts opts{};
   // einsumsvd
@@ -155,6 +155,8 @@ struct peps_plan {
   int64_t lognorm_strip = 0;                // row 0 norm strip of the original lattice
   size_t lognorm_logs_off = 0;              // logs of the sweep below row 0
   int64_t lognorm_nlogs = 0;
+  // TEBD layer: the two-site gate in the working type (raw bytes)
+  std::vector<uint8_t> gate;
   // energy gradient: caller's gradient tensors, phase split, strip cotangents
   std::vector<void *> grad_site;
   size_t split = 0;                         // ops[0, split): forward; ops[split, end): reverse sweep
@@ -1364,6 +1366,42 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
         C.need(op.aux_ptr, 8.0 * op.fill_n, tag, "src");
         C.need(op.fill_ptr, 4.0 * op.fill_n, tag, "dst");
         break;
+      case Op::BLOBCOPY:
+        C.need(op.fill_ptr, (double)op.fill_n, tag, "dst");
+        if (op.aux_off[0] + (size_t)op.fill_n > P->blob.size()) C.err = std::string(tag) + ": source beyond the blob";
+        break;
+      case Op::THETA:
+        for (int i = 0; i < op.nd; ++i) {
+          const ThetaDesc &t = ((const ThetaDesc *)d)[i];
+          const double n = (double)t.d * t.Db;
+          C.need(t.R1, es * t.r1 * n, tag, "R1");
+          C.need(t.R2, es * t.r2 * n, tag, "R2");
+          C.need(t.G, es * (double)t.d * t.d * t.d * t.d, tag, "G");
+          C.need(t.Theta, es * (double)t.r1 * t.d * t.r2 * t.d, tag, "Theta");
+        }
+        break;
+      case Op::SVDSMALL:
+        for (int i = 0; i < op.nd; ++i) {
+          const SvdSmallDesc &v = ((const SvdSmallDesc *)d)[i];
+          if (v.rows > kSvdSmallMax || v.cols > kSvdSmallMax || v.k > v.rows || v.k > v.cols || v.k < 1)
+            C.err = std::string(tag) + ": Theta size out of range";
+          if (op.smem < svd_small_smem_bytes(dt, v.rows, v.cols)) C.err = std::string(tag) + ": shared memory too small";
+          C.need(v.Theta, es * (double)v.rows * v.cols, tag, "Theta");
+          C.need(v.R1t, es * (double)v.rows * v.k, tag, "R1t");
+          C.need(v.R2t, es * (double)v.cols * v.k, tag, "R2t");
+          if (v.sigma) C.need(v.sigma, 8.0 * v.k, tag, "sigma");
+          if (v.status) C.need(v.status, 4, tag, "status");
+        }
+        break;
+      case Op::SITEGAUGE:
+        for (int i = 0; i < op.nd; ++i) {
+          const SiteGaugeDesc &g = ((const SiteGaugeDesc *)d)[i];
+          if (g.k > kSvdSmallMax) C.err = std::string(tag) + ": bond above the phase buffer";
+          C.need(g.N1, es * (double)g.rows1 * g.k, tag, "N1");
+          C.need(g.N2, es * (double)g.rows2 * g.k, tag, "N2");
+          C.need(g.g, es * (double)g.rows1, tag, "g");
+        }
+        break;
       case Op::ABSORB:
         C.need(op.absorb.U, es * (double)op.absorb.M * op.absorb.k, tag, "U");
         C.need(op.absorb.W, es * (double)op.absorb.k * op.absorb.N, tag, "W");
@@ -1497,6 +1535,59 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
   return "";
 }
 
+// One TEBD layer (Algorithm 1 on every bond): two horizontal passes (bonds
+// starting at even, then odd columns) and two vertical ones, the bonds of a
+// pass disjoint; each pass's launches are grouped over its bonds.  The sites
+// are updated in place; the gate is copied from the descriptor blob into
+// the workspace by the first launch.
+std::string build_tebd(peps_plan *P, uintptr_t base, Builder &B) {
+  B.base = base;
+  B.dt = P->dt;
+  const Net &H = P->ket;
+  const int nrow = H.nrow, ncol = H.ncol;
+  void *gate = B.buf(P->gate.size());
+  {
+    Op op;
+    op.kind = Op::BLOBCOPY; op.fill_ptr = gate; op.aux_off[0] = B.put_bytes(P->gate.data(), P->gate.size());
+    op.fill_n = (int64_t)P->gate.size(); op.tag = "tebd_gate";
+    B.ops.push_back(op);
+  }
+  auto site = [&](int i, int *dims) {
+    const SiteDims &s = H.dims[i];
+    dims[0] = s.d; dims[1] = s.Dl; dims[2] = s.Du; dims[3] = s.Dx; dims[4] = s.De;
+    return const_cast<void *>(H.site[i]);
+  };
+  for (int vertical = 0; vertical < 2; ++vertical)
+    for (int start = 0; start < 2; ++start) {
+      std::vector<TebdBond> bonds;
+      if (!vertical) {
+        for (int p = 0; p < nrow; ++p)
+          for (int q = start; q < ncol - 1; q += 2) {
+            TebdBond t;
+            t.a = p * ncol + q; t.b = t.a + 1;
+            bonds.push_back(t);
+          }
+      } else {
+        for (int p = start; p < nrow - 1; p += 2)
+          for (int q = 0; q < ncol; ++q) {
+            TebdBond t;
+            t.a = p * ncol + q; t.b = t.a + ncol; t.vertical = true;
+            bonds.push_back(t);
+          }
+      }
+      if (bonds.empty()) continue;
+      for (TebdBond &t : bonds) {
+        t.M1 = site(t.a, t.s1);
+        t.M2 = site(t.b, t.s2);
+        std::string e = tebd_bond_shape(t);
+        if (!e.empty()) return e;
+        tebd_alloc(B, t, P->dt);
+      }
+      emit_tebd_pass(B, bonds, gate, P->opts.seed);
+    }
+  return "";
+}
+
 peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool encode = false) {
   Builder B;
   B.encode = encode;
@@ -1516,6 +1607,7 @@ peps_status rebuild(peps_plan *P, void *ws, const peps_einsumsvd_io *io, bool en
   std::string e = P->kind == peps_plan::EINSUMSVD ? build_einsumsvd(P, (uintptr_t)ws, io, B)
                   : P->kind == peps_plan::CONTRACT ? build_contract(P, (uintptr_t)ws, B)
                   : P->kind == peps_plan::EGRAD    ? build_egrad(P, (uintptr_t)ws, io, B)
+                  : P->kind == peps_plan::TEBD     ? build_tebd(P, (uintptr_t)ws, B)
                                                    : build_expect(P, (uintptr_t)ws, B);
   if (!e.empty()) return fail(PEPS_ERR_SHAPE, "%s", e.c_str());
   tc_finish(B);
@@ -1628,6 +1720,12 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s0, bo
       case Op::MEMSET: CUDA_TRY(cudaMemsetAsync(op.fill_ptr, 0, (size_t)op.fill_n, s)); break;
       case Op::AXPY: launch_axpy(dt, op.aux_ptr, op.fill_ptr, op.fill_n, s); break;
       case Op::ABSORB: launch_absorb(dt, op.absorb, s); break;
+      case Op::THETA: launch_tebd(dt, 0, d, op.nd, 0, s); break;
+      case Op::SVDSMALL: launch_tebd(dt, 1, d, op.nd, op.smem, s); break;
+      case Op::SITEGAUGE: launch_tebd(dt, 2, d, op.nd, 0, s); break;
+      case Op::BLOBCOPY:
+        CUDA_TRY(cudaMemcpyAsync(op.fill_ptr, blob + op.aux_off[0], (size_t)op.fill_n, cudaMemcpyDeviceToDevice, s));
+        break;
       case Op::SITEBWD: launch_site_bwd(dt, *(const SiteBwdDesc *)(P->blob.data() + op.desc_off), s); break;
       case Op::STRIPBWD:
         launch_strip_bwd(dt, (const StripDesc *)d, (const StripCol *)(blob + op.aux_off[0]),
@@ -1856,6 +1954,57 @@ peps_status peps_contract_execute(peps_plan *plan, void *workspace, size_t works
   g_last_error.clear();
   if (!plan) return fail(PEPS_ERR_ARG, "plan is NULL");
   if (plan->kind != peps_plan::CONTRACT) return fail(PEPS_ERR_ARG, "not a contraction plan");
+  const bool same = plan->built && plan->built_base == (uintptr_t)workspace;
+  if (!same) {
+    if (peps_status s = rebuild(plan, workspace, nullptr, true)) return s;
+    plan->built_base = (uintptr_t)workspace;
+    plan->built = true;
+  }
+  return enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, !same);
+}
+
+peps_status peps_tebd_plan(peps_plan **out, const peps_network *net, const double *gate,
+                           const peps_rsvd_opts *opts, size_t *workspace_bytes) {
+  g_last_error.clear();
+  if (!out || !workspace_bytes || !gate) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (peps_status s = check_opts(opts)) return s;
+  if (opts->prec != PEPS_PREC_PLAIN) return fail(PEPS_ERR_UNSUPPORTED, "the TEBD layer runs the plain arithmetic");
+  if (opts->flags) return fail(PEPS_ERR_UNSUPPORTED, "no flags apply to the TEBD layer");
+  std::unique_ptr<peps_plan> P(new (std::nothrow) peps_plan());
+  if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
+  P->kind = peps_plan::TEBD;
+  P->opts = to_opts(opts);
+  if (peps_status s = read_net(net, P->ket, "network")) return s;
+  P->dt = P->ket.dt;
+  if (P->ket.nrow > 0xFFFF || P->ket.ncol > 0xFFFF || (int64_t)P->ket.nrow * P->ket.ncol > 0xFFFF)
+    return fail(PEPS_ERR_UNSUPPORTED, "lattice too large");
+  const int d = P->ket.d;
+  const int64_t n = (int64_t)d * d * d * d;
+  const bool cplx = dtype_complex(P->dt), dbl = dtype_double(P->dt);
+  const int es = dtype_size(P->dt);
+  P->gate.resize((size_t)n * es);
+  for (int64_t i = 0; i < n; ++i) {
+    const double re_ = gate[cplx ? 2 * i : i], im_ = cplx ? gate[2 * i + 1] : 0.0;
+    uint8_t *dst = P->gate.data() + i * es;
+    if (dbl) {
+      memcpy(dst, &re_, 8);
+      if (cplx) memcpy(dst + 8, &im_, 8);
+    } else {
+      const float fr = (float)re_, fi = (float)im_;
+      memcpy(dst, &fr, 4);
+      if (cplx) memcpy(dst + 4, &fi, 4);
+    }
+  }
+  if (peps_status s = rebuild(P.get(), nullptr, nullptr)) return s;
+  *workspace_bytes = P->ws_bytes;
+  *out = P.release();
+  return PEPS_OK;
+}
+
+peps_status peps_tebd_execute(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream) {
+  g_last_error.clear();
+  if (!plan) return fail(PEPS_ERR_ARG, "plan is NULL");
+  if (plan->kind != peps_plan::TEBD) return fail(PEPS_ERR_ARG, "not a TEBD plan");
   const bool same = plan->built && plan->built_base == (uintptr_t)workspace;
   if (!same) {
     if (peps_status s = rebuild(plan, workspace, nullptr, true)) return s;
@@ -2258,7 +2407,7 @@ peps_status peps_plan_kernel_launches(const peps_plan *plan, int64_t *count) {
       case Op::CHOL: n += 1 + (op.smem2 > 0); break;                         // one CTA, cluster
       case Op::FINALIZE: n += 1 + (op.blocks > 0); break;                    // gauge projections, finalize
       case Op::TC: n += (op.tc.tiles_m * op.tc.tiles_n > 0) + (op.tc.bpre != 0); break;   // B expansion, GEMM
-      case Op::COPY: case Op::MEMSET: break;                                  // copies, not kernels
+      case Op::COPY: case Op::MEMSET: case Op::BLOBCOPY: break;             // copies, not kernels
       case Op::SKETCH: case Op::GEMM: case Op::GEMM_ATOMIC: case Op::SANDWICH: case Op::ZERO: case Op::SITE:
       case Op::PERMUTE: case Op::PAD: n += op.blocks > 0; break;
       default: n += 1; break;
@@ -2288,6 +2437,10 @@ peps_status peps_plan_launch_kernel(const peps_plan *plan, int64_t i, const char
     case Op::PAD: *kernel = "pad"; break;
     case Op::NARROW: *kernel = "narrow"; break;
     case Op::ABSORB: *kernel = "absorb"; break;
+    case Op::THETA: *kernel = "theta"; break;
+    case Op::SVDSMALL: *kernel = "svd_small"; break;
+    case Op::SITEGAUGE: *kernel = "site_gauge"; break;
+    case Op::BLOBCOPY: *kernel = "copy"; break;
     case Op::STRIP: *kernel = "strip"; break;
     case Op::COPY: *kernel = "copy"; break;
     case Op::SVDBWD: *kernel = "svd_bwd"; break;

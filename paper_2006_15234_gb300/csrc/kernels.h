@@ -170,6 +170,36 @@ struct AbsorbDesc {
 };
 void launch_absorb(int dt, const AbsorbDesc &d, cudaStream_t s);
 
+// ---- operator application by QR-SVD (Algorithm 1), one TEBD pass ----
+constexpr int kSvdSmallMax = 64;   // largest side of Theta (d * QR rank)
+// Theta[(r1, i1)][(r2, i2)] = sum_{j1, j2, b} G[i1 i2, j1 j2] R1[r1][(j1, b)] R2[r2][(j2, b)]
+struct ThetaDesc {
+  const void *R1, *R2;   // [r1][d * Db], [r2][d * Db] (working type, row-major)
+  const void *G;         // d^2 x d^2 (working type), [out pair][in pair]
+  void *Theta;           // [(r1 d)][(r2 d)]
+  int32_t r1, r2, d, Db;
+};
+// Truncated SVD of Theta (rows x cols): R1t = U sqrt(S) [rows][k],
+// R2t = (sqrt(S) V^H)^T [cols][k]; sigma (k values, may be NULL)
+struct SvdSmallDesc {
+  const void *Theta;
+  void *R1t, *R2t;
+  double *sigma;
+  int32_t rows, cols, k;
+  uint32_t *status;   // STATUS_NONFINITE when Theta holds a non-finite value (may be NULL)
+};
+// Phases of the new bond fixed on N1 [rows1][k] against g (rows1 entries);
+// N2 [rows2][k] takes the opposite phase
+struct SiteGaugeDesc {
+  void *N1, *N2;
+  const void *g;
+  int64_t rows1, rows2;
+  int32_t k;
+};
+// kind 0 theta, 1 svd_small, 2 site_gauge (descriptor arrays on the device)
+void launch_tebd(int dt, int kind, const void *d, int nd, int smem, cudaStream_t s);
+int svd_small_smem_bytes(int dt, int rows, int cols);
+
 // Contract a boundary MPS with trivial vertical bonds to a scalar:
 // v = S_0[0,0,:] S_1[:,0,:] ... ; result log|v| + sum(logs), arg v.
 struct ScalarDesc {

@@ -15,7 +15,8 @@ namespace peps {
 
 struct Op {
   enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL, TC,
-              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD, MEMSET, STRIPBWD, SITEBWD, AXPY, PAD, NARROW, ABSORB } kind;
+              PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD, MEMSET, STRIPBWD, SITEBWD, AXPY, PAD, NARROW, ABSORB, THETA, SVDSMALL, SITEGAUGE,
+              BLOBCOPY } kind;
   size_t desc_off = 0;    // byte offset of the descriptor array in the blob
   size_t prefix_off = 0;  // byte offset of the int64 block prefix array in the blob
   int nd = 0;
@@ -31,7 +32,7 @@ struct Op {
   StripBwdScratch sbs{};          // STRIPBWD scratch
   AbsorbDesc absorb{};            // ABSORB
   const double *sbar = nullptr;   // STRIPBWD strip cotangents
-  int64_t fill_n = 0;             // FILL: elements; COPY: bytes; LTU: n; NARROW: real values
+  int64_t fill_n = 0;             // FILL: elements; COPY, BLOBCOPY: bytes; LTU: n; NARROW: real values
   double fill_value = 0.0;
   std::string tag;        // stage name (profiling ledger)
   double flops = 0.0;     // algorithmic flops of the launch
@@ -171,6 +172,31 @@ void emit_einsumsvd_save(Builder &B, Inst &q, const RsvdOpts &o, GradBufs &G);
 // those of V, S, K and Kb (same layouts as the operands).
 void emit_einsumsvd_bwd(Builder &B, Inst &q, const RsvdOpts &o, GradBufs &G, const void *Ubar, const void *Wbar,
                         const double *lbar, void *dV, void *dS, void *dK, void *dKb);
+
+// One bond of a TEBD pass (Algorithm 1): the two sites (updated in place),
+// the geometry and the scratch of its QR factorisations and truncated SVD.
+struct TebdBond {
+  int a = 0, b = 0;                 // row-major site indices (the bond's Philox stream)
+  bool vertical = false;
+  int d = 0, Db = 0;                // physical dimension, shared bond (kept)
+  int s1[5] = {}, s2[5] = {};       // site dims [d][l][u][x][e]
+  void *M1 = nullptr, *M2 = nullptr;
+  int64_t O1 = 0, O2 = 0;           // outer entries of each site matrix
+  bool f1 = false, f2 = false;      // side factorised (more outer entries than d * Db)
+  int r1 = 0, r2 = 0, k = 0;        // QR ranks, new bond (= Db)
+  // scratch
+  void *A1 = nullptr, *A2 = nullptr, *Qa1 = nullptr, *Qa2 = nullptr, *Q1 = nullptr, *Q2 = nullptr;
+  void *G1 = nullptr, *G2 = nullptr;                       // FP64 Grams
+  void *Ra1 = nullptr, *Ra2 = nullptr, *Rb1 = nullptr, *Rb2 = nullptr, *R1 = nullptr, *R2 = nullptr;
+  void *T1 = nullptr, *T2 = nullptr;
+  void *Theta = nullptr, *R1t = nullptr, *R2t = nullptr, *N1 = nullptr, *N2 = nullptr, *g = nullptr;
+  double *sigma = nullptr;
+};
+// Shapes of a bond from its two sites; "" or the reason it is not supported.
+std::string tebd_bond_shape(TebdBond &t);
+void tebd_alloc(Builder &B, TebdBond &t, int dt);
+// One pass of disjoint bonds: every launch grouped over the pass's bonds.
+void emit_tebd_pass(Builder &B, std::vector<TebdBond> &bonds, const void *gate, uint64_t seed);
 
 // Emit every stage of one einsumsvd over a group of instances.
 void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);

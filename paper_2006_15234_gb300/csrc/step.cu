@@ -1229,4 +1229,213 @@ void emit_einsumsvd_simt(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o) 
   emit_epilogue(B, I);
 }
 
+
+// ===========================================================================
+// Operator application by QR-SVD (Algorithm 1) on one TEBD pass.
+// Site matrices (Algorithm 1's "QR(M)"): horizontal bond, M1 as
+// [(l,u,x)][(s,e)] and M2 as [(u,x,e)][(s,l)]; vertical bond, M1 as
+// [(l,u,e)][(s,x)] and M2 as [(l,x,e)][(s,u)].  A side with more outer entries
+// than n = d Db is factorised by CholeskyQR2 (Grams in FP64 accumulators), a
+// side with fewer is its own R (Q = identity).
+// ===========================================================================
+
+std::string tebd_bond_shape(TebdBond &t) {
+  const int *a = t.s1, *b = t.s2;
+  t.d = a[0];
+  if (b[0] != t.d) return "sites of a bond have different physical dimensions";
+  t.Db = t.vertical ? a[3] : a[4];
+  if ((t.vertical ? b[2] : b[1]) != t.Db) return "bond dimensions of neighbouring sites differ";
+  t.O1 = t.vertical ? (int64_t)a[1] * a[2] * a[4] : (int64_t)a[1] * a[2] * a[3];
+  t.O2 = t.vertical ? (int64_t)b[1] * b[3] * b[4] : (int64_t)b[2] * b[3] * b[4];
+  const int n = t.d * t.Db;
+  t.f1 = t.O1 > n;
+  t.f2 = t.O2 > n;
+  t.r1 = t.f1 ? n : (int)t.O1;
+  t.r2 = t.f2 ? n : (int)t.O2;
+  t.k = t.Db;
+  if (t.r1 * t.d > kSvdSmallMax || t.r2 * t.d > kSvdSmallMax)
+    return "QR rank times physical dimension above 64 is not supported";
+  if (t.k > t.r1 * t.d || t.k > t.r2 * t.d) return "bond above the rank of the two-site operator";
+  return "";
+}
+
+void tebd_alloc(Builder &B, TebdBond &t, int dt) {
+  const size_t es = dtype_size(dt), as = acc_size(dt);
+  const size_t n = (size_t)t.d * t.Db, rows = (size_t)t.r1 * t.d, cols = (size_t)t.r2 * t.d;
+  t.A1 = B.buf(t.O1 * n * es);
+  t.A2 = B.buf(t.O2 * n * es);
+  auto side = [&](bool f, int64_t O, void *&Qa, void *&Q, void *&G, void *&Ra, void *&Rb, void *&R, void *&T) {
+    if (!f) return;
+    Qa = B.buf(O * n * es);
+    Q = B.buf(O * n * es);
+    G = B.buf(n * n * as);
+    Ra = B.buf(n * n * as);
+    Rb = B.buf(n * n * as);
+    R = B.buf(n * n * as);
+    T = B.buf(n * n * as);
+  };
+  side(t.f1, t.O1, t.Qa1, t.Q1, t.G1, t.Ra1, t.Rb1, t.R1, t.T1);
+  side(t.f2, t.O2, t.Qa2, t.Q2, t.G2, t.Ra2, t.Rb2, t.R2, t.T2);
+  t.Theta = B.buf(rows * cols * es);
+  t.R1t = B.buf(rows * t.k * es);
+  t.R2t = B.buf(cols * t.k * es);
+  t.N1 = t.f1 ? B.buf(t.O1 * t.d * t.k * es) : t.R1t;
+  t.N2 = t.f2 ? B.buf(t.O2 * t.d * t.k * es) : t.R2t;
+  t.g = B.buf(t.O1 * t.d * es);
+  t.sigma = (double *)B.buf(t.k * 8);
+}
+
+namespace {
+
+// in_stride of a [d][l][u][x][e] site for each of its five axes
+void site_strides(const int *sd, int64_t st[5]) {
+  st[4] = 1;
+  for (int i = 3; i >= 0; --i) st[i] = st[i + 1] * sd[i + 1];
+}
+
+// CholeskyQR2 of the factorised sides: Q = A R^-1 with R = R_b R_a
+void emit_tebd_qr(Builder &B, std::vector<TebdBond> &bonds) {
+  const int as = acc_size(B.dt);
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<std::pair<void *, int64_t>> z;
+    std::vector<GemmDesc> gram, app;
+    std::vector<CholDesc> ch;
+    auto add = [&](TebdBond &t, bool f, int64_t O, void *A, void *Qa, void *Q, void *G, void *Ra, void *Rb, void *R,
+                   void *T) {
+      if (!f) return;
+      const int n = t.d * t.Db;
+      const void *src = pass == 0 ? A : Qa;
+      z.push_back({G, (int64_t)n * n * as / 8});
+      // G[i][j] = sum_o conj(src[o][i]) src[o][j]
+      gram.push_back(mk_gemm(n, n, (int)O, 1, src, 1, n, 0, true, src, n, 1, 0, false, G, n, 1, 0));
+      CholDesc c{};
+      c.G = G; c.T = T; c.n = n; c.tol = chol_tol(B.dt, n); c.status = B.status;
+      if (pass == 0) {
+        c.R = Ra;
+        c.shift = chol_shift(B.dt, n, true);
+      } else {
+        c.R = Rb; c.Rprev = Ra; c.Rout = R;
+      }
+      ch.push_back(c);
+      app.push_back(mk_gemm((int)O, n, n, 1, src, n, 1, 0, false, T, n, 1, 0, false, pass == 0 ? Qa : Q, n, 1, 0));
+    };
+    for (TebdBond &t : bonds) {
+      add(t, t.f1, t.O1, t.A1, t.Qa1, t.Q1, t.G1, t.Ra1, t.Rb1, t.R1, t.T1);
+      add(t, t.f2, t.O2, t.A2, t.Qa2, t.Q2, t.G2, t.Ra2, t.Rb2, t.R2, t.T2);
+    }
+    if (ch.empty()) return;
+    for (auto &g : gram) set_ksplit(g, (int)gram.size());
+    push_zero(B, z, "tebd_qr");
+    push_gemm(B, gram, true, "tebd_qr");
+    Op op;
+    op.kind = Op::CHOL; op.desc_off = B.put(ch); op.nd = (int)ch.size(); op.tag = "tebd_qr";
+    for (auto &c : ch) {
+      op.smem = std::max(op.smem, small_smem_bytes(B.dt, c.n));
+      op.smem2 = std::max(op.smem2, chol_cluster_smem_bytes(B.dt, c.n, true));
+    }
+    B.ops.push_back(op);
+    push_gemm(B, app, false, "tebd_qr");
+  }
+}
+
+template <class D> void push_small(Builder &B, Op::Kind kind, const std::vector<D> &d, const char *tag, int smem = 0) {
+  if (d.empty()) return;
+  Op op;
+  op.kind = kind; op.desc_off = B.put(d); op.nd = (int)d.size(); op.tag = tag; op.smem = smem;
+  B.ops.push_back(op);
+}
+
+}  // namespace
+
+void emit_tebd_pass(Builder &B, std::vector<TebdBond> &bonds, const void *gate, uint64_t seed) {
+  const int es = dtype_size(B.dt);
+  // 1. site matrices (Algorithm 1's QR input), outer bonds first
+  std::vector<PadDesc> in;
+  for (TebdBond &t : bonds) {
+    int64_t a[5], b[5];
+    site_strides(t.s1, a);
+    site_strides(t.s2, b);
+    const int *x = t.s1, *y = t.s2;
+    if (t.vertical) {
+      in.push_back(mk_pad(t.M1, t.A1, {x[1], x[2], x[4], x[0], x[3]}, {x[1], x[2], x[4], x[0], x[3]},
+                          {a[1], a[2], a[4], a[0], a[3]}));
+      in.push_back(mk_pad(t.M2, t.A2, {y[1], y[3], y[4], y[0], y[2]}, {y[1], y[3], y[4], y[0], y[2]},
+                          {b[1], b[3], b[4], b[0], b[2]}));
+    } else {
+      in.push_back(mk_pad(t.M1, t.A1, {x[1], x[2], x[3], x[0], x[4]}, {x[1], x[2], x[3], x[0], x[4]},
+                          {a[1], a[2], a[3], a[0], a[4]}));
+      in.push_back(mk_pad(t.M2, t.A2, {y[2], y[3], y[4], y[0], y[1]}, {y[2], y[3], y[4], y[0], y[1]},
+                          {b[2], b[3], b[4], b[0], b[1]}));
+    }
+  }
+  push_pad(B, in, "tebd_site");
+  // 2. QR factorisations
+  emit_tebd_qr(B, bonds);
+  // 3. Theta, 4. its truncated SVD
+  std::vector<ThetaDesc> th;
+  std::vector<SvdSmallDesc> sv;
+  int smem = 0;
+  for (TebdBond &t : bonds) {
+    ThetaDesc x{};
+    x.R1 = t.f1 ? t.R1 : t.A1; x.R2 = t.f2 ? t.R2 : t.A2; x.G = gate; x.Theta = t.Theta;
+    x.r1 = t.r1; x.r2 = t.r2; x.d = t.d; x.Db = t.Db;
+    th.push_back(x);
+    SvdSmallDesc y{};
+    y.Theta = t.Theta; y.R1t = t.R1t; y.R2t = t.R2t; y.sigma = t.sigma;
+    y.rows = t.r1 * t.d; y.cols = t.r2 * t.d; y.k = t.k; y.status = B.status;
+    sv.push_back(y);
+    smem = std::max(smem, svd_small_smem_bytes(B.dt, y.rows, y.cols));
+  }
+  push_small(B, Op::THETA, th, "tebd_theta");
+  push_small(B, Op::SVDSMALL, sv, "tebd_svd", smem);
+  // 5. N = Q R~ on the factorised sides
+  std::vector<GemmDesc> nq;
+  for (TebdBond &t : bonds) {
+    const int n = t.d * t.Db, dk = t.d * t.k;
+    if (t.f1) nq.push_back(mk_gemm((int)t.O1, dk, n, 1, t.Q1, n, 1, 0, false, t.R1t, dk, 1, 0, false, t.N1, dk, 1, 0));
+    if (t.f2) nq.push_back(mk_gemm((int)t.O2, dk, n, 1, t.Q2, n, 1, 0, false, t.R2t, dk, 1, 0, false, t.N2, dk, 1, 0));
+  }
+  if (!nq.empty()) push_gemm(B, nq, false, "tebd_apply");
+  // 6. gauge vectors (one Philox stream per bond, tag 1) and phases
+  std::vector<SketchDesc> sk;
+  std::vector<int64_t> bl;
+  std::vector<SiteGaugeDesc> ga;
+  const int per = dtype_complex(B.dt) ? 2 : 4;
+  for (TebdBond &t : bonds) {
+    SketchDesc s{};
+    s.X = t.g; s.N = t.O1 * t.d; s.ld = s.N; s.ell = 1; s.tag = 1; s.kind = 0;
+    s.seed = seed; s.instance = (4ull << 32) | ((uint64_t)t.a << 16) | (uint64_t)t.b;
+    s.nblocks = ceil_div(ceil_div(s.N, per), 256);
+    sketch_set_div(s);
+    sk.push_back(s);
+    bl.push_back(s.nblocks);
+    SiteGaugeDesc g{};
+    g.N1 = t.N1; g.N2 = t.N2; g.g = t.g; g.rows1 = t.O1 * t.d; g.rows2 = t.O2 * t.d; g.k = t.k;
+    ga.push_back(g);
+  }
+  push_grouped(B, Op::SKETCH, sk.data(), sizeof(SketchDesc), (int)sk.size(), bl, "tebd_gauge");
+  push_small(B, Op::SITEGAUGE, ga, "tebd_gauge");
+  // 7. back into the site layouts, in place
+  std::vector<PadDesc> out;
+  for (TebdBond &t : bonds) {
+    const int *x = t.s1, *y = t.s2;
+    const int64_t k = t.k, dk = (int64_t)t.d * k;
+    if (t.vertical) {
+      // N1 [l][u][e][s][k] -> [s][l][u][k][e];  N2 [l][x][e][s][k] -> [s][l][k][x][e]
+      out.push_back(mk_pad(t.N1, t.M1, {x[0], x[1], x[2], t.k, x[4]}, {x[0], x[1], x[2], t.k, x[4]},
+                           {k, x[2] * x[4] * dk, x[4] * dk, 1, dk}));
+      out.push_back(mk_pad(t.N2, t.M2, {y[0], y[1], t.k, y[3], y[4]}, {y[0], y[1], t.k, y[3], y[4]},
+                           {k, y[3] * y[4] * dk, 1, y[4] * dk, dk}));
+    } else {
+      // N1 [l][u][x][s][k] -> [s][l][u][x][k];  N2 [u][x][e][s][k] -> [s][k][u][x][e]
+      out.push_back(mk_pad(t.N1, t.M1, {x[0], x[1], x[2], x[3], t.k}, {x[0], x[1], x[2], x[3], t.k},
+                           {k, x[2] * x[3] * dk, x[3] * dk, dk, 1}));
+      out.push_back(mk_pad(t.N2, t.M2, {y[0], t.k, y[2], y[3], y[4]}, {y[0], t.k, y[2], y[3], y[4]},
+                           {k, 1, y[3] * y[4] * dk, y[4] * dk, dk}));
+    }
+  }
+  push_pad(B, out, "tebd_site");
+  (void)es;
+}
+
 }  // namespace peps

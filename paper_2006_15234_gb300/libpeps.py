@@ -38,6 +38,7 @@ EXPORTED_SYMBOLS = [
     "peps_einsumsvd_grad_execute", "peps_grad_plan", "peps_grad_execute", "peps_grad",
     "peps_poll", "peps_plan_set_wait_limit", "peps_debug_sketch",
     "peps_plan_autotune", "peps_plan_tune_table", "peps_plan_set_tune_table", "peps_einsumsvd_set_branches",
+    "peps_tebd_plan", "peps_tebd_execute",
 ]
 
 # Bits of a plan's device status word (peps_poll).
@@ -193,6 +194,11 @@ def load():
     lib.peps_debug_sketch.restype = st
     lib.peps_debug_sketch.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                       C.c_int32, vp, vp, vp]
+    lib.peps_tebd_plan.restype = st
+    lib.peps_tebd_plan.argtypes = [C.POINTER(vp), C.POINTER(Network), C.POINTER(C.c_double), C.POINTER(RsvdOpts),
+                                   C.POINTER(C.c_size_t)]
+    lib.peps_tebd_execute.restype = st
+    lib.peps_tebd_execute.argtypes = [vp, vp, C.c_size_t, vp]
     lib.peps_einsumsvd_set_branches.restype = st
     lib.peps_einsumsvd_set_branches.argtypes = [vp, C.c_int32, C.POINTER(C.c_size_t)]
     lib.peps_plan_autotune.restype = st
@@ -442,6 +448,51 @@ class EinsumsvdPlan(_Ledger):
                 self._plan = None
         except Exception:
             pass
+
+
+class TebdPlan(_Ledger):
+    """One TEBD layer (Algorithm 1 on every bond) applied in place to the
+    PEPS `sites` (CUDA tensors): gate is a (d^2, d^2) host array."""
+
+    def __init__(self, sites, gate, seed):
+        import numpy as np
+        self._lib = load()
+        self._net = _network(sites)
+        cplx = sites[0][0].is_complex()
+        g = np.ascontiguousarray(np.asarray(gate, dtype=np.complex128 if cplx else np.float64))
+        if cplx:
+            g = np.ascontiguousarray(g.view(np.float64))
+        self._gate = g
+        plan = C.c_void_p()
+        ws = C.c_size_t()
+        _check(self._lib.peps_tebd_plan(C.byref(plan), C.byref(self._net.net),
+                                        g.ctypes.data_as(C.POINTER(C.c_double)),
+                                        C.byref(make_opts(1, 0, 0, seed)), C.byref(ws)))
+        self._plan = plan
+        self.workspace_bytes = ws.value
+        self._buf, self._ws = _workspace(ws.value, sites[0][0].device)
+
+    def execute(self, stream=None):
+        _check(self._lib.peps_tebd_execute(self._plan, C.c_void_p(self._ws), C.c_size_t(self.workspace_bytes),
+                                           _stream_handle(stream)))
+
+    def __del__(self):
+        try:
+            if getattr(self, "_plan", None):
+                self._lib.peps_plan_destroy(self._plan)
+                self._plan = None
+        except Exception:
+            pass
+
+
+def tebd_layer(sites, gate, seed, stream=None):
+    """Apply the two-site `gate` to every bond of the PEPS in place."""
+    plan = TebdPlan(sites, gate, seed)
+    plan.execute(stream)
+    return plan
+
+
+__all__ += ["TebdPlan", "tebd_layer"]
 
 
 def boundary_contract(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN,

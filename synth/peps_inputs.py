@@ -70,6 +70,11 @@ CONFIGS = {
     "f2": WorkloadConfig("f2_12x12_tfi_expectation_c64_D4_m16", 12, 12, 2, 4, "c64", True,
                          16, 8, 2, "cgauss_scaled", _BASE_SEED + 5, _BASE_SEED + 6,
                          {"J": 1.0, "h": 3.0}),
+    # One TEBD layer (QR-SVD on every bond) of an imaginary-time TFI gate on a
+    # 16x16, D=8 complex64 PEPS (the lattice of the 16x16 norm workload).
+    "f1": WorkloadConfig("f1_16x16_tebd_layer_c64_D8", 16, 16, 2, 8, "c64", True,
+                         8, 0, 0, "cgauss_fro", _BASE_SEED + 7, _BASE_SEED + 8,
+                         {"J": 1.0, "h": 3.0, "tau": 0.01}),
     # 16x16 norm, complex64, d=2, bond 8, per-tensor Frobenius-normalised.
     "c5": WorkloadConfig("c5_16x16_norm_c64_D8_m256", 16, 16, 2, 8, "c64", True,
                          256, 16, 2, "cgauss_fro", _BASE_SEED + 4, _BASE_SEED + 5),
@@ -208,3 +213,18 @@ def tfi_terms(nrow: int, ncol: int, J: float, h: float) -> list:
         for q in range(ncol):
             terms.append((((p, q),), X, -h))
     return terms
+
+
+def tfi_bond_gate(J: float, h: float, tau: float) -> np.ndarray:
+    """exp(-tau h_ij) of one bond's share of the transverse-field Ising
+    Hamiltonian, h_ij = -J Z_i Z_j - (h / 4) (X_i + X_j) (each site's field
+    split over its four bonds): the two-site operator of one imaginary-time
+    TEBD step, a 4 x 4 matrix [out pair][in pair] (an input, computed with
+    scipy's matrix exponential)."""
+    from scipy.linalg import expm
+    Z, X, I = PAULI["Z"], PAULI["X"], PAULI["I"]
+    hij = -J * np.kron(Z, Z) - (h / 4.0) * (np.kron(X, I) + np.kron(I, X))
+    return expm(-tau * hij)
+
+
+__all__.append("tfi_bond_gate")

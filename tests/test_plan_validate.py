@@ -354,3 +354,35 @@ def test_product_flops_follow_table_2(lib, shape, m, q, prec):
     else:
         assert adj == pytest.approx((q + 1) * prod(ell), rel=1e-12)
         assert agg["epilogue_w"] == pytest.approx(8.0 * k * ell * N, rel=1e-12)
+
+
+@pytest.mark.parametrize("shape,D,dt", [((3, 3), 2, 3), ((4, 4), 3, 1), ((5, 3), 4, 0), ((16, 16), 8, 1),
+                                        ((2, 5), 2, 2), ((1, 4), 2, 1)])
+def test_tebd_layer_plans(lib, shape, D, dt):
+    """The TEBD layer's launches (site matrices, CholeskyQR2, Theta, its SVD,
+    N = Q R~, gauge phases, sites written back in place) stay inside the
+    workspace and the site tensors; one byte less of workspace is refused."""
+    nr, nc = shape
+    shp = [[synth.site_shape(nr, nc, p, q, 2, D) for q in range(nc)] for p in range(nr)]
+    heap = FakeHeap()
+    net, keep = _net(heap, shp, dt)
+    gate = (C.c_double * 32)(*([0.5] * 32))
+    plan, ws = C.c_void_p(), C.c_size_t()
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, C.byref(L.make_opts(1, 0, 0, 3)),
+                              C.byref(ws)) == 0, lib.peps_last_error()
+    wsp = heap(ws.value)
+    assert lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None) == 0, lib.peps_last_error().decode()
+    assert lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value - 1, None) != 0
+    lib.peps_plan_destroy(plan)
+
+
+def test_tebd_refuses_unsupported(lib):
+    heap = FakeHeap()
+    shp = [[synth.site_shape(3, 3, p, q, 2, 2) for q in range(3)] for p in range(3)]
+    net, keep = _net(heap, shp, 1)
+    gate = (C.c_double * 32)(*([0.5] * 32))
+    plan, ws = C.c_void_p(), C.c_size_t()
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, C.byref(L.make_opts(1, 0, 0, 3, prec=1)),
+                              C.byref(ws)) == 3
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), None, C.byref(L.make_opts(1, 0, 0, 3)),
+                              C.byref(ws)) == 1
