@@ -21,7 +21,9 @@ Modules and the passages they follow (arXiv:2006.15234):
   grad        -- central finite differences of the expectation energy.
   qrsvd       -- operator application by QR-SVD (Algorithm 1) with the
                  einsumsvd of G, R1, R2 (Eq. 5), and one TEBD layer over all
-                 nearest-neighbour bonds.
+                 nearest-neighbour bonds (one-site operators by Eq. 4).
+  ite         -- imaginary-time evolution (Sec. II-D): TEBD steps with the
+                 Rayleigh quotient after each.
 
 Parity status: the final scalars of the larger lattices (8x8 and 16x16
 norms) have no closed form; they are pinned only through the checks of each

@@ -39,7 +39,16 @@ Readings of points the paper leaves open (all shared with the GPU path):
     (4 << 32) | (a << 16) | b;
   * a TEBD layer applies G to every horizontal bond (columns 0-1, 2-3, ...,
     then 1-2, 3-4, ...), then to every vertical bond (rows 0-1, 2-3, ...,
-    then 1-2, ...): the bonds of one pass share no site.
+    then 1-2, ...): the bonds of one pass share no site;
+  * a layer may carry one operator per bond, listed in bond order (every
+    horizontal bond by its left site in row-major order, then every
+    vertical bond by its upper site in row-major order), and one-site
+    operators (Eq. 4), applied to every site before the bonds;
+  * for imaginary-time evolution the new bond may be normalised: Sigma is
+    divided by sigma_1 before the split (R1~ = U sqrt(Sigma / sigma_1),
+    R2~ = sqrt(Sigma / sigma_1) V^H), so each bond update applies G up to
+    one positive factor and the state's scale stays bounded over many
+    layers.
 """
 from __future__ import annotations
 
@@ -68,14 +77,15 @@ def _qr(Mmat: np.ndarray):
     return Q, R
 
 
-def _svd_truncate(Theta: np.ndarray, kmax: int):
+def _svd_truncate(Theta: np.ndarray, kmax: int, unit: bool = False):
     U, s, Vh = np.linalg.svd(Theta, full_matrices=False)
     k = min(kmax, len(s))
     U, s, Vh = U[:, :k], s[:k], Vh[:k]
     tol = 16.0 * max(Theta.shape) * np.finfo(np.float64).eps * (s[0] if s.size else 0.0)
     zero = s <= tol
     s = np.where(zero, 0.0, s)
-    r = np.sqrt(s)
+    w = s / s[0] if unit and s.size and s[0] > 0 else s
+    r = np.sqrt(w)
     return U * r[None, :], r[:, None] * Vh, s
 
 
@@ -87,7 +97,12 @@ def _factor(Amat: np.ndarray):
     return _qr(Amat)
 
 
-def apply_two_site(M1, M2, G, D_max, vertical, seed, stream):
+def apply_one_site(M, g):
+    """Eq. 4: M~[i, ...] = sum_j g[i, j] M[j, ...]."""
+    return np.einsum("ij,j...->i...", np.asarray(g), M)
+
+
+def apply_two_site(M1, M2, G, D_max, vertical, seed, stream, unit=False):
     """Algorithm 1 on one bond; returns (M1~, M2~, singular values kept)."""
     d = M1.shape[0]
     if vertical:
@@ -107,7 +122,7 @@ def apply_two_site(M1, M2, G, D_max, vertical, seed, stream):
     T = np.einsum("abjk,rjx,tkx->ratb", G4, R1.reshape(r1, d, Db), R2.reshape(r2, d, Db))
     Theta = T.reshape(r1 * d, r2 * d)
     k = min(D_max, r1 * d, r2 * d)
-    R1t, R2t, s = _svd_truncate(Theta, k)
+    R1t, R2t, s = _svd_truncate(Theta, k, unit)
     N1 = (Q1 @ R1t.reshape(r1, d * k)).reshape(-1, k)          # [(o1, s)][k]
     N2 = (Q2 @ R2t.T.reshape(r2, d * k)).reshape(-1, k)        # [(o2, s)][k]
     g = philox.gauge_vector(N1.shape[0], seed, stream, np.iscomplexobj(N1))
@@ -144,12 +159,29 @@ def tebd_bonds(nrow: int, ncol: int):
     return out
 
 
-def tebd_layer(sites, G, D_max, seed):
-    """G on every nearest-neighbour bond (Algorithm 1 each), in tebd_bonds order."""
+def bond_index(nrow: int, ncol: int, a: int, b: int) -> int:
+    """Position of the bond between sites a < b in bond order."""
+    p, q = divmod(a, ncol)
+    if b == a + 1:
+        return p * (ncol - 1) + q
+    return nrow * (ncol - 1) + p * ncol + q
+
+
+def tebd_layer(sites, G, D_max, seed, unit=False, site_gates=None):
+    """One-site operators on every site (if given), then G on every
+    nearest-neighbour bond (Algorithm 1 each), in tebd_bonds order.
+
+    G: one (d^2 x d^2) operator for every bond, or a list in bond order;
+    site_gates: None, one (d x d) operator, or a row-major list per site."""
     nrow, ncol = len(sites), len(sites[0])
     flat = [np.asarray(T) for row in sites for T in row]
+    if site_gates is not None:
+        per_site = isinstance(site_gates, (list, tuple))
+        flat = [apply_one_site(T, site_gates[i] if per_site else site_gates) for i, T in enumerate(flat)]
+    per_bond = isinstance(G, (list, tuple))
     sig = []
     for a, b, vertical in tebd_bonds(nrow, ncol):
-        flat[a], flat[b], s = apply_two_site(flat[a], flat[b], G, D_max, vertical, seed, bond_stream(a, b))
+        g = G[bond_index(nrow, ncol, a, b)] if per_bond else G
+        flat[a], flat[b], s = apply_two_site(flat[a], flat[b], g, D_max, vertical, seed, bond_stream(a, b), unit)
         sig.append(s)
     return [flat[p * ncol:(p + 1) * ncol] for p in range(nrow)], sig

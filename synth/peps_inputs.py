@@ -228,3 +228,16 @@ def tfi_bond_gate(J: float, h: float, tau: float) -> np.ndarray:
 
 
 __all__.append("tfi_bond_gate")
+
+
+def tfi_ite_gates(J: float, h: float, tau: float):
+    """exp(-tau H_j) for the two kinds of local term of the transverse-field
+    Ising Hamiltonian H = -J sum_<ij> Z_i Z_j - h sum_i X_i: the bond
+    operator exp(tau J Z Z) (4 x 4, [out pair][in pair]) and the site
+    operator exp(tau h X) (2 x 2), by scipy's matrix exponential (inputs)."""
+    from scipy.linalg import expm
+    Z, X = PAULI["Z"], PAULI["X"]
+    return expm(tau * J * np.kron(Z, Z)), expm(tau * h * X)
+
+
+__all__.append("tfi_ite_gates")

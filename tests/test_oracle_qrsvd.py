@@ -119,3 +119,49 @@ def test_identity_gates_keep_the_state():
     a = bruteforce.statevector(ket).reshape(-1)
     b = bruteforce.statevector(new).reshape(-1)
     assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(a)
+
+
+def _apply_site_dense(psi, g, a, n):
+    d = 2
+    T = np.moveaxis(psi.reshape([d] * n), a, 0)
+    T = np.tensordot(g, T, axes=([1], [0]))
+    return np.moveaxis(T, 0, a).reshape(-1)
+
+
+def test_per_bond_and_site_operators_equal_dense_application():
+    """Distinct operators per bond (looked up by the pair of sites they join)
+    and per site: without truncation the layer equals the site operators
+    then the bond operators applied to the state vector in layer order."""
+    nr, nc = 2, 3
+    rng = np.random.default_rng(41)
+    ket = synth.random_peps(nr, nc, 2, 2, "c64", "cgauss_scaled", 43)
+    by_pair = {(a, b): _gate(rng) for a, b, _ in qrsvd.tebd_bonds(nr, nc)}
+    # bond order: horizontal bonds by left site, then vertical bonds by upper site
+    order = [(p * nc + q, p * nc + q + 1) for p in range(nr) for q in range(nc - 1)]
+    order += [(p * nc + q, (p + 1) * nc + q) for p in range(nr - 1) for q in range(nc)]
+    gates = [by_pair[ab] for ab in order]
+    site_ops = [_rand(rng, (2, 2)) for _ in range(nr * nc)]
+    new, _ = qrsvd.tebd_layer(ket, gates, 64, 3, site_gates=site_ops)
+    psi = bruteforce.statevector(ket).reshape(-1)
+    for i, g in enumerate(site_ops):
+        psi = _apply_site_dense(psi, g, i, nr * nc)
+    for a, b, _ in qrsvd.tebd_bonds(nr, nc):
+        psi = _apply_gate_dense(psi, by_pair[(a, b)], a, b, nr * nc)
+    got = bruteforce.statevector(new).reshape(-1)
+    assert np.linalg.norm(got - psi) <= 1e-11 * np.linalg.norm(psi)
+
+
+def test_unit_bonds_change_only_the_scale():
+    """Normalised bonds: the same state up to one positive factor, and each
+    bond's singular values the same up to one positive factor."""
+    ket = synth.random_peps(3, 2, 2, 2, "c64", "cgauss_scaled", 47)
+    G = _gate(np.random.default_rng(49))
+    a, sa = qrsvd.tebd_layer(ket, G, 2, 5)
+    b, sb = qrsvd.tebd_layer(ket, G, 2, 5, unit=True)
+    pa = bruteforce.statevector(a).reshape(-1)
+    pb = bruteforce.statevector(b).reshape(-1)
+    c = np.vdot(pb, pa) / np.vdot(pb, pb)
+    assert abs(c.imag) <= 1e-10 * abs(c) and c.real > 0
+    assert np.linalg.norm(pa - c * pb) <= 1e-10 * np.linalg.norm(pa)
+    for x, y in zip(sa, sb):
+        assert np.allclose(x / x[0], y / y[0], rtol=1e-10)
