@@ -217,6 +217,33 @@ def load_tune(workload):
     return {"source": os.path.relpath(path, ROOT), "table": open(path).read()}
 
 
+# DRAM traffic of the tensor-core GEMM family on the 16 x 16 mixed contraction:
+# ncu dram__bytes_read.sum + dram__bytes_write.sum summed over every tc_gemm
+# launch of one contraction (a one-pass capture of the full workload, tile
+# table applied), divided by the launch count.  It stands only while the
+# kernel's sources hash to the value it was taken with.
+TC_GEMM_TRAFFIC = {"workload": "c5_16x16_norm_c64_D8_m256", "launches": 8526, "read_gb": 21795.914,
+                   "write_gb": 9270.977, "bytes_per_launch": 3.6438e9, "sources_sha": "258729a8e9e5e73f"}
+
+
+def tc_gemm_sources_sha():
+    import hashlib
+    parts = []
+    for f in ("tcgemm.cu", "tcgemm.h", "tc_host.cu"):
+        with open(os.path.join(ROOT, "paper_2006_15234_gb300", "csrc", f), "rb") as fh:
+            parts.append(hashlib.sha256(fh.read()).hexdigest())
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+
+
+def tc_gemm_traffic(workload, kname):
+    """Per-launch DRAM bytes of tc_gemm for this workload, or None when it was
+    not captured for it or the kernel changed since."""
+    t = TC_GEMM_TRAFFIC
+    if kname != "tc_gemm" or workload != t["workload"] or tc_gemm_sources_sha() != t["sources_sha"]:
+        return None
+    return t["bytes_per_launch"]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -424,7 +451,8 @@ def run_ours(args, cfg):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16},
         "roofline": {"bound": bound, "kernel": kname, "achieved": round(achieved, 3),
                      "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
-                     "traffic": None, "launches_per_step": dn,
+                     "traffic": tc_gemm_traffic(cfg.name, kname) if prec == libpeps.PREC_MIXED else None,
+                     "algorithmic_bytes_per_launch": round(dby / dn, 1), "launches_per_step": dn,
                      "avg_launch_ms": round(dt_ms / dn, 5), "peak_source": peak_note,
                      "algorithmic_per_launch": round((dfl if unit == "TFLOP/s" else dby) / dn, 1),
                      "share_of_step": round(dt_ms / max(sum(v[0] for v in by_kern.values()), 1e-9), 4)},
@@ -780,6 +808,62 @@ def run_expect_cache(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def run_ite(args, cfg):
+    """Imaginary-time evolution of the transverse-field Ising model on the
+    8 x 8, D = 4 PEPS (Sec. II-D): each step is one TEBD layer of
+    exp(-tau H_j) (one-site operators, then Algorithm 1 on every bond,
+    normalised bonds) followed by the Rayleigh quotient by Eq. 6 with cached
+    environments.  Device seconds per step; energies before and after the
+    timed steps."""
+    import torch
+    from paper_2006_15234_gb300 import libpeps
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prec = {"plain": libpeps.PREC_PLAIN, "mixed": libpeps.PREC_MIXED, "fast": libpeps.PREC_FAST}[args.prec]
+    ket = synth.peps_for(cfg)
+    kt = [[torch.tensor(T, dtype=torch.complex64, device=dev) for T in row] for row in ket]
+    terms = synth.tfi_terms(cfg.nrow, cfg.ncol, cfg.extra["J"], cfg.extra["h"])
+    Gb, Gs = synth.tfi_ite_gates(cfg.extra["J"], cfg.extra["h"], cfg.extra["tau"])
+    drv = libpeps.IteDriver(kt, Gb, Gs, terms, libpeps.make_opts(cfg.m, cfg.p, cfg.q, cfg.omega_seed, prec=prec),
+                            cfg.seed)
+    flops = sum(f for _, f, _ in drv.tebd.launches()) + sum(f for _, f, _ in drv.expect.launches())
+    stream = torch.cuda.current_stream()
+    e_warm = drv.run(max(3, args.warmup))
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            drv.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    e_end = drv.expect.result()[0]
+    t = float(np.mean(ms))
+    prof_t = drv.tebd.profile()
+    prof_e = drv.expect.profile()
+    line = {
+        "metric": METRIC, "value": round(flops / (t * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(t, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": cfg.dtype,
+        "data": "synthetic (seeded Gaussian PEPS start, exp(-tau H_j) of the TFI model)",
+        "config": {"workload": cfg.name, "nrow": cfg.nrow, "ncol": cfg.ncol, "bond": cfg.D, "m": cfg.m,
+                   "p": cfg.p, "q": cfg.q, "tau": cfg.extra["tau"], "precision_energy": args.prec,
+                   "ite_steps_per_s": round(1e3 / t, 3), "layer_ms": round(float(np.sum(prof_t)), 4),
+                   "energy_ms": round(float(np.sum(prof_e)), 4),
+                   "energy_per_site_after_warmup": round(e_warm[-1] / (cfg.nrow * cfg.ncol), 6),
+                   "energy_per_site_after_timed_steps": round(e_end / (cfg.nrow * cfg.ncol), 6),
+                   "l2": "not flushed: each step reads what the previous one wrote"},
+        "gpu_launches": (drv.tebd.kernel_launches() + drv.expect.kernel_launches()) * args.steps,
+    }
+    clk = clk.summary()
+    if clk:
+        line["clocks"] = clk
+    print(json.dumps(line), flush=True)
+
+
 def run_tebd(args, cfg):
     """One TEBD layer (Algorithm 1 on every nearest-neighbour bond, four
     passes of disjoint bonds) of the imaginary-time TFI gate on the 16 x 16,
@@ -814,6 +898,12 @@ def run_tebd(args, cfg):
             ms.append(e0.elapsed_time(e1))
     t = float(np.mean(ms))
     finite = all(bool(torch.isfinite(T).all()) for row in kt for T in row)
+    # per-launch device times of one more layer (CUDA events on the stream)
+    prof = plan.profile()
+    by_tag, by_kern = {}, {}
+    for (tag, fl, _), kname, dt in zip(plan.launches(), plan.kernels(), prof):
+        by_tag[tag] = by_tag.get(tag, 0.0) + dt
+        by_kern[kname] = by_kern.get(kname, 0.0) + dt
     line = {
         "metric": METRIC, "value": round(flops / (t * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t, 4),
@@ -821,9 +911,12 @@ def run_tebd(args, cfg):
         "data": "synthetic (seeded Gaussian PEPS, imaginary-time TFI gate)",
         "config": {"workload": cfg.name, "nrow": cfg.nrow, "ncol": cfg.ncol, "bond": cfg.D, "bonds": nbonds,
                    "tau": cfg.extra["tau"], "layer_s": round(t / 1e3, 6), "us_per_bond": round(1e3 * t / nbonds, 3),
-                   "kernel_launches": plan.launch_count(), "launch_flops_gflop": round(flops / 1e9, 3),
+                   "ledger_entries": plan.launch_count(), "launch_flops_gflop": round(flops / 1e9, 3),
                    "sites_finite": finite,
                    "l2": "flushed between steps (2x L2 write outside the timed events)"},
+        "gpu_launches": plan.kernel_launches() * args.steps,
+        "kernel_ms": {k: round(v, 4) for k, v in sorted(by_kern.items(), key=lambda kv: -kv[1])},
+        "stage_ms": {k: round(v, 4) for k, v in sorted(by_tag.items(), key=lambda kv: -kv[1])},
     }
     clk = clk.summary()
     if clk:
@@ -973,7 +1066,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3", "f1", "f2"])
+    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3", "f1", "f2", "f3"])
     ap.add_argument("--prec", default="mixed", choices=["plain", "mixed", "fast"])
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip the plain FP32 contraction timed beside the mixed one")
@@ -1002,6 +1095,8 @@ def main():
         run_expect_cache(args, cfg)
     elif args.config == "f1":
         run_tebd(args, cfg)
+    elif args.config == "f3":
+        run_ite(args, cfg)
     else:
         run_ours(args, cfg)
 

@@ -94,7 +94,12 @@ typedef enum { PEPS_SKETCH_GAUSS = 0, PEPS_SKETCH_UNIFORM = 1 } peps_sketch;
  *        elsewhere): alternating canonicalisation of the zip-up (Sec. III-A):
  *        on the even rows 2, 4, ... of a sweep every einsumsvd puts its
  *        singular values into the finished boundary site (U = U~ Sigma /
- *        sigma_1, carry W = V^H) instead of the carry */
+ *        sigma_1, carry W = V^H) instead of the carry
+ *        PEPS_FLAG_UNIT_BOND: TEBD plans only: every updated bond's singular
+ *        values are divided by the largest before the split (M1 <- Q1 U
+ *        sqrt(Sigma / sigma_1), ...), so each bond update applies its
+ *        operator up to one positive factor and the state's scale stays
+ *        bounded over many steps of imaginary-time evolution */
 typedef struct {
   int32_t m, p, q;
   uint64_t seed;
@@ -105,6 +110,7 @@ typedef struct {
 #define PEPS_FLAG_ORTH_Q 1u
 #define PEPS_FLAG_FP64_SMALL 2u
 #define PEPS_FLAG_ALTERNATE 4u
+#define PEPS_FLAG_UNIT_BOND 8u
 
 /* ------------------------------------------------------------------------
  * Batched einsumsvd (Algorithm 3's einsumsvd line, Algorithm 4 inside).
@@ -267,7 +273,8 @@ peps_status peps_boundary_workspace(const peps_network *ket, const peps_network 
 /* ------------------------------------------------------------------------
  * Operator application by QR-SVD (Algorithm 1) and one TEBD layer.
  *
- * A two-site operator G (gate) acts on every nearest-neighbour bond of the
+ * One-site operators (Eq. 4; optional) act on every site first.  Then a
+ * two-site operator G (gate) acts on every nearest-neighbour bond of the
  * network, in place: two passes over the horizontal bonds (those starting at
  * even, then at odd columns), then two over the vertical ones (starting at
  * even, then odd rows); the bonds of one pass share no site and run as
@@ -287,13 +294,27 @@ peps_status peps_boundary_workspace(const peps_network *ket, const peps_network 
  * rank); Theta's sides are at most 64.
  * ------------------------------------------------------------------------ */
 
-/* Plan one TEBD layer of `gate` on `net`.  gate is a HOST array of
- * (d^2) x (d^2) values, row-major [out pair][in pair] with the first site's
- * index most significant: doubles for real networks, interleaved (re, im)
- * doubles for complex ones; it is copied.  opts: seed (gauge vectors);
- * prec must be PEPS_PREC_PLAIN and flags 0; m, p, q are not used. */
-peps_status peps_tebd_plan(peps_plan **out, const peps_network *net, const double *gate,
-                           const peps_rsvd_opts *opts, size_t *workspace_bytes);
+/* Plan one TEBD layer on `net` (one step of imaginary-time evolution,
+ * Sec. II-D, when the operators are exp(-tau H_j)).
+ *   gates: HOST array of ngates operators of (d^2) x (d^2) values, each
+ *     row-major [out pair][in pair] with the first site's index most
+ *     significant: doubles for real networks, interleaved (re, im) doubles
+ *     for complex ones.  ngates = 1: that operator on every bond; otherwise
+ *     ngates must equal the number of bonds, listed in bond order: every
+ *     horizontal bond by its left site in row-major order, then every
+ *     vertical bond by its upper site in row-major order.
+ *   site_gates: HOST array of nsite_gates one-site operators of d x d
+ *     values (row-major [out][in], same element rule), applied before the
+ *     bonds; nsite_gates = 0 (site_gates may be NULL), 1 (every site) or
+ *     nrow * ncol (row-major per site).
+ * Both arrays are copied.  opts: seed (gauge vectors); prec must be
+ * PEPS_PREC_PLAIN; flags 0 or PEPS_FLAG_UNIT_BOND; m, p, q are not used.
+ * Errors: PEPS_ERR_ARG (NULL pointers, bad counts), PEPS_ERR_SHAPE (bond
+ * dimensions the update cannot keep), PEPS_ERR_UNSUPPORTED (precision,
+ * flags, Theta sides above 64, lattices above 65535 sites). */
+peps_status peps_tebd_plan(peps_plan **out, const peps_network *net, const double *gates, int64_t ngates,
+                           const double *site_gates, int64_t nsite_gates, const peps_rsvd_opts *opts,
+                           size_t *workspace_bytes);
 
 /* Enqueue the layer: the network's site tensors are overwritten with the
  * updated ones (same shapes).  Same descriptor-upload rule as the other

@@ -55,7 +55,7 @@ peps_status check_opts(const peps_rsvd_opts *o) {
     return fail(PEPS_ERR_ARG, "unknown sketch kind %d", o->sketch);
   if (o->prec != PEPS_PREC_PLAIN && o->prec != PEPS_PREC_MIXED && o->prec != PEPS_PREC_FAST)
     return fail(PEPS_ERR_ARG, "unknown precision %d", o->prec);
-  if (o->flags & ~(PEPS_FLAG_ORTH_Q | PEPS_FLAG_FP64_SMALL | PEPS_FLAG_ALTERNATE))
+  if (o->flags & ~(PEPS_FLAG_ORTH_Q | PEPS_FLAG_FP64_SMALL | PEPS_FLAG_ALTERNATE | PEPS_FLAG_UNIT_BOND))
     return fail(PEPS_ERR_ARG, "unknown flag bits %#x", o->flags);
   return PEPS_OK;
 }
@@ -66,6 +66,7 @@ RsvdOpts to_opts(const peps_rsvd_opts *o) {
   r.orth_q = (o->flags & PEPS_FLAG_ORTH_Q) != 0;
   r.fp64_small = (o->flags & PEPS_FLAG_FP64_SMALL) != 0;
   r.alternate = (o->flags & PEPS_FLAG_ALTERNATE) != 0;
+  r.unit_bond = (o->flags & PEPS_FLAG_UNIT_BOND) != 0;
   return r;
 }
 
@@ -155,8 +156,10 @@ struct peps_plan {
   int64_t lognorm_strip = 0;                // row 0 norm strip of the original lattice
   size_t lognorm_logs_off = 0;              // logs of the sweep below row 0
   int64_t lognorm_nlogs = 0;
-  // TEBD layer: the two-site gate in the working type (raw bytes)
+  // TEBD layer: the two-site operators, then the one-site operators, in the
+  // working type (raw bytes)
   std::vector<uint8_t> gate;
+  int64_t ngates = 0, nsite_gates = 0;
   // energy gradient: caller's gradient tensors, phase split, strip cotangents
   std::vector<void *> grad_site;
   size_t split = 0;                         // ops[0, split): forward; ops[split, end): reverse sweep
@@ -1393,6 +1396,15 @@ std::string validate_ops(const peps_plan *P, uintptr_t ws, size_t ws_bytes, Chec
           if (v.status) C.need(v.status, 4, tag, "status");
         }
         break;
+      case Op::SITEOP:
+        if (op.blocks < 1 || op.blocks > 65535 || op.nd > 65535) C.err = std::string(tag) + ": grid out of range";
+        for (int i = 0; i < op.nd; ++i) {
+          const SiteOpDesc &x = ((const SiteOpDesc *)d)[i];
+          if (x.d < 1 || x.d > kSiteOpMaxPhys) C.err = std::string(tag) + ": physical dimension out of range";
+          C.need(x.M, es * (double)x.d * x.rest, tag, "M");
+          C.need(x.g, es * (double)x.d * x.d, tag, "g");
+        }
+        break;
       case Op::SITEGAUGE:
         for (int i = 0; i < op.nd; ++i) {
           const SiteGaugeDesc &g = ((const SiteGaugeDesc *)d)[i];
@@ -1552,10 +1564,34 @@ std::string build_tebd(peps_plan *P, uintptr_t base, Builder &B) {
     op.fill_n = (int64_t)P->gate.size(); op.tag = "tebd_gate";
     B.ops.push_back(op);
   }
+  const int d = H.d, es = dtype_size(P->dt);
+  const size_t g2 = (size_t)d * d * d * d * es, g1 = (size_t)d * d * es;
   auto site = [&](int i, int *dims) {
     const SiteDims &s = H.dims[i];
     dims[0] = s.d; dims[1] = s.Dl; dims[2] = s.Du; dims[3] = s.Dx; dims[4] = s.De;
     return const_cast<void *>(H.site[i]);
+  };
+  // one-site operators (Eq. 4) before the bonds
+  if (P->nsite_gates) {
+    std::vector<SiteOpDesc> so;
+    const uint8_t *g0 = (const uint8_t *)gate + P->ngates * g2;
+    for (int i = 0; i < nrow * ncol; ++i) {
+      int dims[5];
+      SiteOpDesc x{};
+      x.M = site(i, dims);
+      x.g = g0 + (P->nsite_gates == 1 ? 0 : (size_t)i * g1);
+      x.d = dims[0];
+      x.rest = (int64_t)dims[1] * dims[2] * dims[3] * dims[4];
+      so.push_back(x);
+    }
+    emit_site_ops(B, so);
+  }
+  // position of the bond a-b in bond order (horizontal by left site, then vertical by upper site)
+  auto bond_gate = [&](int a, int b) {
+    if (P->ngates == 1) return (const void *)gate;
+    const int p = a / ncol, q = a % ncol;
+    const int64_t idx = b == a + 1 ? (int64_t)p * (ncol - 1) + q : (int64_t)nrow * (ncol - 1) + (int64_t)p * ncol + q;
+    return (const void *)((const uint8_t *)gate + idx * g2);
   };
   for (int vertical = 0; vertical < 2; ++vertical)
     for (int start = 0; start < 2; ++start) {
@@ -1582,8 +1618,9 @@ std::string build_tebd(peps_plan *P, uintptr_t base, Builder &B) {
         std::string e = tebd_bond_shape(t);
         if (!e.empty()) return e;
         tebd_alloc(B, t, P->dt);
+        t.gate = bond_gate(t.a, t.b);
       }
-      emit_tebd_pass(B, bonds, gate, P->opts.seed);
+      emit_tebd_pass(B, bonds, P->opts.seed, P->opts.unit_bond);
     }
   return "";
 }
@@ -1723,6 +1760,7 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s0, bo
       case Op::THETA: launch_tebd(dt, 0, d, op.nd, 0, s); break;
       case Op::SVDSMALL: launch_tebd(dt, 1, d, op.nd, op.smem, s); break;
       case Op::SITEGAUGE: launch_tebd(dt, 2, d, op.nd, 0, s); break;
+      case Op::SITEOP: launch_tebd(dt, 3, d, op.nd, (int)op.blocks, s); break;
       case Op::BLOBCOPY:
         CUDA_TRY(cudaMemcpyAsync(op.fill_ptr, blob + op.aux_off[0], (size_t)op.fill_n, cudaMemcpyDeviceToDevice, s));
         break;
@@ -1774,6 +1812,8 @@ peps_status peps_einsumsvd_plan(peps_plan **out, peps_dtype dtype, int32_t batch
   if (!valid_dtype(dtype)) return fail(PEPS_ERR_ARG, "bad dtype %d", (int)dtype);
   if (batch < 1) return fail(PEPS_ERR_ARG, "batch must be >= 1");
   if (peps_status s = check_opts(opts)) return s;
+  if (opts->flags & PEPS_FLAG_UNIT_BOND)
+    return fail(PEPS_ERR_UNSUPPORTED, "PEPS_FLAG_UNIT_BOND applies to TEBD plans only");
   std::unique_ptr<peps_plan> P(new (std::nothrow) peps_plan());
   if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
   P->kind = peps_plan::EINSUMSVD;
@@ -1853,6 +1893,8 @@ peps_status peps_einsumsvd_grad_plan(peps_plan **out, peps_dtype dtype, const pe
   if (!out || !shape || !workspace_bytes) return fail(PEPS_ERR_ARG, "NULL argument");
   if (dtype != PEPS_R32 && dtype != PEPS_R64) return fail(PEPS_ERR_UNSUPPORTED, "the adjoint takes real data");
   if (peps_status s = check_opts(opts)) return s;
+  if (opts->flags & PEPS_FLAG_UNIT_BOND)
+    return fail(PEPS_ERR_UNSUPPORTED, "PEPS_FLAG_UNIT_BOND applies to TEBD plans only");
   if (opts->prec != PEPS_PREC_PLAIN) return fail(PEPS_ERR_UNSUPPORTED, "the adjoint runs the plain arithmetic");
   std::unique_ptr<peps_plan> P(new (std::nothrow) peps_plan());
   if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
@@ -1925,6 +1967,8 @@ peps_status peps_contract_plan(peps_plan **out, const peps_network *ket, const p
   g_last_error.clear();
   if (!out || !workspace_bytes) return fail(PEPS_ERR_ARG, "NULL argument");
   if (peps_status s = check_opts(opts)) return s;
+  if (opts->flags & PEPS_FLAG_UNIT_BOND)
+    return fail(PEPS_ERR_UNSUPPORTED, "PEPS_FLAG_UNIT_BOND applies to TEBD plans only");
   if (direction < 0 || direction > 0xFFFF) return fail(PEPS_ERR_ARG, "direction out of range");
   std::unique_ptr<peps_plan> P(new (std::nothrow) peps_plan());
   if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
@@ -1963,13 +2007,16 @@ peps_status peps_contract_execute(peps_plan *plan, void *workspace, size_t works
   return enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, !same);
 }
 
-peps_status peps_tebd_plan(peps_plan **out, const peps_network *net, const double *gate,
-                           const peps_rsvd_opts *opts, size_t *workspace_bytes) {
+peps_status peps_tebd_plan(peps_plan **out, const peps_network *net, const double *gates, int64_t ngates,
+                           const double *site_gates, int64_t nsite_gates, const peps_rsvd_opts *opts,
+                           size_t *workspace_bytes) {
   g_last_error.clear();
-  if (!out || !workspace_bytes || !gate) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (!out || !workspace_bytes || !gates) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (nsite_gates < 0 || (nsite_gates > 0 && !site_gates)) return fail(PEPS_ERR_ARG, "bad one-site operators");
   if (peps_status s = check_opts(opts)) return s;
   if (opts->prec != PEPS_PREC_PLAIN) return fail(PEPS_ERR_UNSUPPORTED, "the TEBD layer runs the plain arithmetic");
-  if (opts->flags) return fail(PEPS_ERR_UNSUPPORTED, "no flags apply to the TEBD layer");
+  if (opts->flags & ~PEPS_FLAG_UNIT_BOND)
+    return fail(PEPS_ERR_UNSUPPORTED, "only PEPS_FLAG_UNIT_BOND applies to the TEBD layer");
   std::unique_ptr<peps_plan> P(new (std::nothrow) peps_plan());
   if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
   P->kind = peps_plan::TEBD;
@@ -1979,22 +2026,37 @@ peps_status peps_tebd_plan(peps_plan **out, const peps_network *net, const doubl
   if (P->ket.nrow > 0xFFFF || P->ket.ncol > 0xFFFF || (int64_t)P->ket.nrow * P->ket.ncol > 0xFFFF)
     return fail(PEPS_ERR_UNSUPPORTED, "lattice too large");
   const int d = P->ket.d;
-  const int64_t n = (int64_t)d * d * d * d;
+  const int64_t nr = P->ket.nrow, nc = P->ket.ncol;
+  const int64_t nbonds = nr * (nc - 1) + (nr - 1) * nc, nsites = nr * nc;
+  if (ngates != 1 && ngates != nbonds)
+    return fail(PEPS_ERR_ARG, "ngates = %lld: 1 or the number of bonds (%lld)", (long long)ngates,
+                (long long)nbonds);
+  if (nsite_gates != 0 && nsite_gates != 1 && nsite_gates != nsites)
+    return fail(PEPS_ERR_ARG, "nsite_gates = %lld: 0, 1 or the number of sites (%lld)", (long long)nsite_gates,
+                (long long)nsites);
+  if (nsite_gates && d > kSiteOpMaxPhys)
+    return fail(PEPS_ERR_UNSUPPORTED, "one-site operators need d <= %d", kSiteOpMaxPhys);
+  const int64_t n2 = (int64_t)d * d * d * d, n1 = (int64_t)d * d;
   const bool cplx = dtype_complex(P->dt), dbl = dtype_double(P->dt);
   const int es = dtype_size(P->dt);
-  P->gate.resize((size_t)n * es);
-  for (int64_t i = 0; i < n; ++i) {
-    const double re_ = gate[cplx ? 2 * i : i], im_ = cplx ? gate[2 * i + 1] : 0.0;
-    uint8_t *dst = P->gate.data() + i * es;
-    if (dbl) {
-      memcpy(dst, &re_, 8);
-      if (cplx) memcpy(dst + 8, &im_, 8);
-    } else {
-      const float fr = (float)re_, fi = (float)im_;
-      memcpy(dst, &fr, 4);
-      if (cplx) memcpy(dst + 4, &fi, 4);
+  P->ngates = ngates;
+  P->nsite_gates = nsite_gates;
+  P->gate.resize((size_t)(ngates * n2 + nsite_gates * n1) * es);
+  auto put = [&](const double *src, int64_t count, uint8_t *dst) {
+    for (int64_t i = 0; i < count; ++i, dst += es) {
+      const double re_ = src[cplx ? 2 * i : i], im_ = cplx ? src[2 * i + 1] : 0.0;
+      if (dbl) {
+        memcpy(dst, &re_, 8);
+        if (cplx) memcpy(dst + 8, &im_, 8);
+      } else {
+        const float fr = (float)re_, fi = (float)im_;
+        memcpy(dst, &fr, 4);
+        if (cplx) memcpy(dst + 4, &fi, 4);
+      }
     }
-  }
+  };
+  put(gates, ngates * n2, P->gate.data());
+  if (nsite_gates) put(site_gates, nsite_gates * n1, P->gate.data() + ngates * n2 * es);
   if (peps_status s = rebuild(P.get(), nullptr, nullptr)) return s;
   *workspace_bytes = P->ws_bytes;
   *out = P.release();
@@ -2178,6 +2240,8 @@ peps_status peps_expectation_plan(peps_plan **out, const peps_network *ket, cons
   if (!out || !workspace_bytes) return fail(PEPS_ERR_ARG, "NULL argument");
   if (nterms < 0 || (nterms > 0 && !terms)) return fail(PEPS_ERR_ARG, "terms missing");
   if (peps_status s = check_opts(opts)) return s;
+  if (opts->flags & PEPS_FLAG_UNIT_BOND)
+    return fail(PEPS_ERR_UNSUPPORTED, "PEPS_FLAG_UNIT_BOND applies to TEBD plans only");
   std::unique_ptr<peps_plan> P(new (std::nothrow) peps_plan());
   if (!P) return fail(PEPS_ERR_ARG, "out of host memory");
   P->kind = peps_plan::EXPECT;
@@ -2438,6 +2502,7 @@ peps_status peps_plan_launch_kernel(const peps_plan *plan, int64_t i, const char
     case Op::NARROW: *kernel = "narrow"; break;
     case Op::ABSORB: *kernel = "absorb"; break;
     case Op::THETA: *kernel = "theta"; break;
+    case Op::SITEOP: *kernel = "site_op"; break;
     case Op::SVDSMALL: *kernel = "svd_small"; break;
     case Op::SITEGAUGE: *kernel = "site_gauge"; break;
     case Op::BLOBCOPY: *kernel = "copy"; break;

@@ -187,6 +187,16 @@ struct SvdSmallDesc {
   double *sigma;
   int32_t rows, cols, k;
   uint32_t *status;   // STATUS_NONFINITE when Theta holds a non-finite value (may be NULL)
+  int32_t unit;       // 1: split Sigma / sigma_1 instead of Sigma (sigma keeps the true values)
+};
+// One-site operator on a site tensor, in place (Eq. 4):
+// M[i][r] <- sum_j g[i][j] M[j][r], r < rest, d <= kSiteOpMaxPhys
+constexpr int kSiteOpMaxPhys = 16;
+struct SiteOpDesc {
+  void *M;
+  const void *g;      // d x d (working type), [out][in]
+  int64_t rest;       // product of the site's bond dimensions
+  int32_t d;
 };
 // Phases of the new bond fixed on N1 [rows1][k] against g (rows1 entries);
 // N2 [rows2][k] takes the opposite phase
@@ -197,7 +207,9 @@ struct SiteGaugeDesc {
   int32_t k;
 };
 // kind 0 theta, 1 svd_small, 2 site_gauge (descriptor arrays on the device)
-void launch_tebd(int dt, int kind, const void *d, int nd, int smem, cudaStream_t s);
+// kind 0 theta, 1 svd_small (aux = dynamic shared memory bytes), 2 site_gauge,
+// 3 site_op (aux = column blocks per site)
+void launch_tebd(int dt, int kind, const void *d, int nd, int aux, cudaStream_t s);
 int svd_small_smem_bytes(int dt, int rows, int cols);
 
 // Contract a boundary MPS with trivial vertical bonds to a scalar:

@@ -16,7 +16,7 @@ namespace peps {
 struct Op {
   enum Kind { SKETCH, GEMM, GEMM_ATOMIC, SANDWICH, CHOL, JACOBI, FINALIZE, ZERO, SITE, SCALAR, FILL, TC,
               PERMUTE, STRIP, COPY, SVDBWD, LTU, TGRAD, MEMSET, STRIPBWD, SITEBWD, AXPY, PAD, NARROW, ABSORB, THETA, SVDSMALL, SITEGAUGE,
-              BLOBCOPY } kind;
+              BLOBCOPY, SITEOP } kind;
   size_t desc_off = 0;    // byte offset of the descriptor array in the blob
   size_t prefix_off = 0;  // byte offset of the int64 block prefix array in the blob
   int nd = 0;
@@ -128,6 +128,7 @@ struct RsvdOpts {
   bool orth_q;
   bool fp64_small;     // single-precision data: CholeskyQR2's factorisations and the Jacobi SVD in FP64
   bool alternate;      // contraction sweeps: Sigma into the finished site on even rows
+  bool unit_bond;      // TEBD: each new bond's Sigma divided by sigma_1 before the split
 };
 
 // Shape bookkeeping shared by every planner.
@@ -191,12 +192,15 @@ struct TebdBond {
   void *T1 = nullptr, *T2 = nullptr;
   void *Theta = nullptr, *R1t = nullptr, *R2t = nullptr, *N1 = nullptr, *N2 = nullptr, *g = nullptr;
   double *sigma = nullptr;
+  const void *gate = nullptr;       // this bond's d^2 x d^2 operator (device)
 };
 // Shapes of a bond from its two sites; "" or the reason it is not supported.
 std::string tebd_bond_shape(TebdBond &t);
 void tebd_alloc(Builder &B, TebdBond &t, int dt);
 // One pass of disjoint bonds: every launch grouped over the pass's bonds.
-void emit_tebd_pass(Builder &B, std::vector<TebdBond> &bonds, const void *gate, uint64_t seed);
+void emit_tebd_pass(Builder &B, std::vector<TebdBond> &bonds, uint64_t seed, bool unit_bond);
+// One-site operators (Eq. 4) on every listed site, in place: one launch.
+void emit_site_ops(Builder &B, const std::vector<SiteOpDesc> &d);
 
 // Emit every stage of one einsumsvd over a group of instances.
 void emit_einsumsvd(Builder &B, std::vector<Inst *> &I, const RsvdOpts &o);

@@ -1347,7 +1347,23 @@ template <class D> void push_small(Builder &B, Op::Kind kind, const std::vector<
 
 }  // namespace
 
-void emit_tebd_pass(Builder &B, std::vector<TebdBond> &bonds, const void *gate, uint64_t seed) {
+void emit_site_ops(Builder &B, const std::vector<SiteOpDesc> &d) {
+  if (d.empty()) return;
+  int64_t rest = 1;
+  for (const SiteOpDesc &x : d) rest = std::max(rest, x.rest);
+  Op op;
+  op.kind = Op::SITEOP; op.desc_off = B.put(d); op.nd = (int)d.size(); op.tag = "tebd_site_op";
+  op.blocks = std::min<int64_t>(ceil_div(rest, 256), 1024);     // column blocks per site
+  const int es = dtype_size(B.dt);
+  const double mult = dtype_complex(B.dt) ? 8.0 : 2.0;
+  for (const SiteOpDesc &x : d) {
+    op.flops += mult * (double)x.d * x.d * x.rest;
+    op.bytes += 2.0 * es * (double)x.d * x.rest;
+  }
+  B.ops.push_back(op);
+}
+
+void emit_tebd_pass(Builder &B, std::vector<TebdBond> &bonds, uint64_t seed, bool unit_bond) {
   const int es = dtype_size(B.dt);
   // 1. site matrices (Algorithm 1's QR input), outer bonds first
   std::vector<PadDesc> in;
@@ -1377,12 +1393,12 @@ void emit_tebd_pass(Builder &B, std::vector<TebdBond> &bonds, const void *gate, 
   int smem = 0;
   for (TebdBond &t : bonds) {
     ThetaDesc x{};
-    x.R1 = t.f1 ? t.R1 : t.A1; x.R2 = t.f2 ? t.R2 : t.A2; x.G = gate; x.Theta = t.Theta;
+    x.R1 = t.f1 ? t.R1 : t.A1; x.R2 = t.f2 ? t.R2 : t.A2; x.G = t.gate; x.Theta = t.Theta;
     x.r1 = t.r1; x.r2 = t.r2; x.d = t.d; x.Db = t.Db;
     th.push_back(x);
     SvdSmallDesc y{};
     y.Theta = t.Theta; y.R1t = t.R1t; y.R2t = t.R2t; y.sigma = t.sigma;
-    y.rows = t.r1 * t.d; y.cols = t.r2 * t.d; y.k = t.k; y.status = B.status;
+    y.rows = t.r1 * t.d; y.cols = t.r2 * t.d; y.k = t.k; y.status = B.status; y.unit = unit_bond ? 1 : 0;
     sv.push_back(y);
     smem = std::max(smem, svd_small_smem_bytes(B.dt, y.rows, y.cols));
   }

@@ -9,7 +9,8 @@
 //    per bond, Theta in shared memory, one warp per column pair of a
 //    round-robin round); singular values sorted descending, the first k kept,
 //    Sigma split evenly: R1t = U sqrt(Sigma) [(r1, i1)][k] and
-//    R2t = (sqrt(Sigma) V^H)^T as [(r2, i2)][k]; directions at or below
+//    R2t = (sqrt(Sigma) V^H)^T as [(r2, i2)][k] (Sigma / sigma_1 for
+//    normalised bonds); directions at or below
 //    16 max(rows, cols) eps64 sigma_1 are zero.  Theta is scaled to unit
 //    Frobenius norm first, and a column whose norm falls to eps64 or below
 //    is set to zero and leaves the rotations: a Theta with more columns than
@@ -17,6 +18,8 @@
 //    vanishing, and without this they shrink every sweep until their norms
 //    underflow.  Zeroing them changes Theta by at most
 //    sqrt(cols) eps64 ||Theta||_F, below the zero rule above.
+//  * site_op: a one-site operator on the physical index of a site (Eq. 4),
+//    in place, each thread holding one column of the site's d values.
 //  * site_gauge: the phase of every new bond direction c fixed on the
 //    updated first site N1 [(outer, s)][k]: rho_c = <g, N1[:, c]> / |.|,
 //    N1[:, c] *= conj(rho_c), N2[:, c] *= rho_c (real data: a sign).
@@ -58,36 +61,125 @@ __global__ void theta_kernel(const ThetaDesc *__restrict__ descs) {
   }
 }
 
-// complex helpers on double2 / double for the FP64 Jacobi
-template <class A> struct CJ;
-template <> struct CJ<double> {
-  __device__ static double conj(double a) { return a; }
-  __device__ static double abs2(double a) { return a * a; }
-};
-template <> struct CJ<double2> {
-  __device__ static double2 conj(double2 a) { return make_double2(a.x, -a.y); }
-  __device__ static double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
-};
+template <class R> __device__ __forceinline__ R wsum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
+// the single-precision type of an FP64 scalar type
+template <class A> struct Lo;
+template <> struct Lo<double> { using type = float; };
+template <> struct Lo<double2> { using type = float2; };
+
+// One-sided (Hestenes) Jacobi on A (mr x mc, column-major, column j at
+// j * mr) with the rotations accumulated into V (mc x mc, column-major):
+// round-robin pairs, one warp per pair, one barrier per round.  A pair is
+// rotated when |<a_p, a_q>| > tol |a_p| |a_q|; a column of squared norm <=
+// dead2 is set to zero and leaves the rotations (A is scaled to unit
+// Frobenius norm by the caller).  Stops after the first sweep whose largest
+// rotated off-diagonal is <= stop, or after max_sweeps.
+template <class S>
+__device__ void jacobi_sweeps(S *A, S *V, int mr, int mc, int max_sweeps, double tol, double stop, double dead2,
+                              float *off_max) {
+  using R = typename Traits<S>::Real;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int n2 = mc + (mc & 1);
+  const R rtol = (R)tol, rdead = (R)dead2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *off_max = 0.f;
+    __syncthreads();
+    float mine = 0.f;
+    for (int rr = 0; rr < n2 - 1; ++rr) {
+      for (int i = warp; i < n2 / 2; i += nwarps) {
+        int p, q;
+        if (i == 0) { p = rr; q = n2 - 1; }
+        else { p = (rr + i) % (n2 - 1); q = (rr - i + (n2 - 1)) % (n2 - 1); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= mc) continue;
+        S *ap = A + (int64_t)p * mr, *aq = A + (int64_t)q * mr;
+        R al = 0, be = 0;
+        S ga = zero<S>();
+        for (int r = lane; r < mr; r += 32) {
+          al += abs2(ap[r]);
+          be += abs2(aq[r]);
+          ga = fma_(conj_(ap[r]), aq[r], ga);
+        }
+        al = wsum_r(al);
+        be = wsum_r(be);
+        ga = from_parts<S>(wsum_r(re(ga)), wsum_r(im(ga)));
+        if (al <= rdead || be <= rdead) {
+          for (int r = lane; r < mr; r += 32) {
+            if (al <= rdead) ap[r] = zero<S>();
+            if (be <= rdead) aq[r] = zero<S>();
+          }
+          continue;
+        }
+        const R gm = sqrt(abs2(ga)), nrm = sqrt(al * be);
+        if (!(gm > rtol * nrm)) continue;
+        mine = fmaxf(mine, (float)(gm / nrm));
+        // b_q = e^{-i phi} a_q makes <a_p, b_q> = |gamma| real; then the real rotation
+        const S ph = scale(conj_(ga), (R)1 / gm);
+        const R zeta = (be - al) / ((R)2 * gm), az = fabs(zeta);
+        const R t = az > (R)1e15 ? (R)0.5 / zeta : (zeta >= 0 ? (R)1 : (R)-1) / (az + sqrt((R)1 + zeta * zeta));
+        const R c = (R)1 / sqrt((R)1 + t * t), sn = c * t;
+        for (int r = lane; r < mr; r += 32) {
+          const S x = ap[r], y = mul(ph, aq[r]);
+          ap[r] = sub(scale(x, c), scale(y, sn));
+          aq[r] = add(scale(x, sn), scale(y, c));
+        }
+        S *vp = V + (int64_t)p * mc, *vq = V + (int64_t)q * mc;
+        for (int r = lane; r < mc; r += 32) {
+          const S x = vp[r], y = mul(ph, vq[r]);
+          vp[r] = sub(scale(x, c), scale(y, sn));
+          vq[r] = add(scale(x, sn), scale(y, c));
+        }
+      }
+      __syncthreads();
+    }
+    if (lane == 0) atomicMax((int *)off_max, __float_as_int(mine));
+    __syncthreads();
+    const bool done = *off_max <= (float)stop;
+    __syncthreads();
+    if (done) break;
+  }
+}
+
+// Truncated SVD of one Theta.  GB300 runs FP64 at 1/64 of the FP32 rate, so
+// the Jacobi runs in two phases: FP32 sweeps until the columns are
+// orthogonal to ~1e-6, then V is made unitary in FP64 (two Newton-Schulz
+// steps V <- V (3 I - V^H V) / 2), A = Theta V is formed in FP64 and FP64
+// sweeps finish it (two or three, the convergence being quadratic).  The
+// result is the FP64 SVD of the stored Theta.  A Theta with fewer rows than
+// columns is factorised as Theta^H (mr >= mc always).
 template <class T>
 __global__ void svd_small_kernel(const SvdSmallDesc *__restrict__ descs) {
   using Acc = typename Traits<T>::Acc;      // double or double2
+  using S32 = typename Lo<Acc>::type;       // float or float2
   const SvdSmallDesc &g = descs[blockIdx.x];
   const int rows = g.rows, cols = g.cols, k = g.k;
-  const int n2 = cols + (cols & 1);
+  const bool tr = rows < cols;
+  const int mr = tr ? cols : rows, mc = tr ? rows : cols;
   extern __shared__ __align__(16) unsigned char dyn[];
-  Acc *A = (Acc *)dyn;                      // column-major rows x cols (column j at j * rows)
-  Acc *Vm = A + (int64_t)rows * cols;       // column-major cols x cols
+  Acc *A = (Acc *)dyn;                      // mr x mc, column-major
+  Acc *Vm = A + (int64_t)mr * mc;           // mc x mc, column-major
+  S32 *A32 = (S32 *)(Vm + (int64_t)mc * mc);
+  S32 *V32 = A32 + (int64_t)mr * mc;
+  Acc *W = (Acc *)A32;                      // mc x mc FP64 temporary over the FP32 copies (mr >= mc)
   __shared__ double sig[kSvdSmallMax];
   __shared__ int order[kSvdSmallMax];
   __shared__ float off_max;
   __shared__ double part[32];
-  const T *Th = (const T *)g.Theta;
+  const T *Th = (const T *)g.Theta;         // row-major rows x cols
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // working matrix X = Theta, or Theta^H when Theta is wide
+  auto X = [&](int i, int j) -> Acc {
+    return tr ? conj_(widen(Th[(int64_t)j * cols + i])) : widen(Th[(int64_t)i * cols + j]);
+  };
   // ||Theta||_F
   double f2 = 0.0;
-  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) f2 += CJ<Acc>::abs2(widen(Th[e]));
-  f2 = wsum(f2);
+  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) f2 += abs2(widen(Th[e]));
+  f2 = wsum_r(f2);
   if (lane == 0) part[warp] = f2;
   __syncthreads();
   f2 = 0.0;
@@ -106,102 +198,95 @@ __global__ void svd_small_kernel(const SvdSmallDesc *__restrict__ descs) {
     return;
   }
   const double inv = 1.0 / fro;
-  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-    const int r = e / cols, c = e % cols;
-    A[(int64_t)c * rows + r] = scale(widen(Th[e]), inv);
+  // phase 1: FP32 sweeps on X / ||X||_F
+  for (int e = threadIdx.x; e < mr * mc; e += blockDim.x) {
+    const int j = e / mr, i = e % mr;
+    A32[e] = narrow<S32>(scale(X(i, j), inv));
   }
-  for (int e = threadIdx.x; e < cols * cols; e += blockDim.x)
-    Vm[e] = (e / cols == e % cols) ? widen(from_parts<T>(1.0, 0.0)) : zero<Acc>();
+  for (int e = threadIdx.x; e < mc * mc; e += blockDim.x)
+    V32[e] = (e / mc == e % mc) ? from_parts<S32>(1.0, 0.0) : zero<S32>();
   __syncthreads();
-  const double tol = 4.0 * 1.1102230246251565e-16;
-  const double dead2 = 2.220446049250313e-16 * 2.220446049250313e-16;   // (eps64 ||Theta||_F)^2, scaled
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    if (threadIdx.x == 0) off_max = 0.f;
-    __syncthreads();
-    float mine = 0.f;
-    for (int rr = 0; rr < n2 - 1; ++rr) {
-      for (int i = warp; i < n2 / 2; i += nwarps) {
-        int p, q;
-        if (i == 0) { p = rr; q = n2 - 1; }
-        else { p = (rr + i) % (n2 - 1); q = (rr - i + (n2 - 1)) % (n2 - 1); }
-        if (p > q) { const int t = p; p = q; q = t; }
-        if (q >= cols) continue;
-        Acc *ap = A + (int64_t)p * rows, *aq = A + (int64_t)q * rows;
-        double al = 0.0, be = 0.0;
-        Acc ga = zero<Acc>();
-        for (int r = lane; r < rows; r += 32) {
-          al += CJ<Acc>::abs2(ap[r]);
-          be += CJ<Acc>::abs2(aq[r]);
-          ga = fma_(CJ<Acc>::conj(ap[r]), aq[r], ga);
-        }
-        al = wsum(al);
-        be = wsum(be);
-        ga = from_parts<Acc>(wsum(re(ga)), wsum(im(ga)));
-        if (al <= dead2 || be <= dead2) {
-          for (int r = lane; r < rows; r += 32) {
-            if (al <= dead2) ap[r] = zero<Acc>();
-            if (be <= dead2) aq[r] = zero<Acc>();
-          }
-          continue;
-        }
-        const double gm = sqrt(CJ<Acc>::abs2(ga));
-        if (!(gm > tol * sqrt(al * be)) || gm == 0.0) continue;
-        mine = fmaxf(mine, (float)(gm / sqrt(al * be)));
-        // b_q = e^{-i phi} a_q makes <a_p, b_q> = |gamma|; then the real rotation
-        const Acc ph = scale(CJ<Acc>::conj(ga), 1.0 / gm);         // e^{-i phi}
-        const double zeta = (be - al) / (2.0 * gm);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        for (int r = lane; r < rows; r += 32) {
-          const Acc x = ap[r], y = mul(ph, aq[r]);
-          ap[r] = sub(scale(x, c), scale(y, s));
-          aq[r] = add(scale(x, s), scale(y, c));
-        }
-        Acc *vp = Vm + (int64_t)p * cols, *vq = Vm + (int64_t)q * cols;
-        for (int r = lane; r < cols; r += 32) {
-          const Acc x = vp[r], y = mul(ph, vq[r]);
-          vp[r] = sub(scale(x, c), scale(y, s));
-          vq[r] = add(scale(x, s), scale(y, c));
-        }
-      }
-      __syncthreads();
+  const double eps32 = 5.9604644775390625e-08, eps64 = 1.1102230246251565e-16;
+  jacobi_sweeps<S32>(A32, V32, mr, mc, 30, 16.0 * eps32, 64.0 * eps32, 4.0 * eps32 * eps32, &off_max);
+  // phase 2: V unitary in FP64
+  for (int e = threadIdx.x; e < mc * mc; e += blockDim.x) Vm[e] = widen(V32[e]);
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    // Gm = V^H V into A's space (mc x mc, column-major)
+    for (int e = threadIdx.x; e < mc * mc; e += blockDim.x) {
+      const int a = e % mc, b = e / mc;
+      Acc s = zero<Acc>();
+      for (int r = 0; r < mc; ++r) s = fma_(conj_(Vm[(int64_t)a * mc + r]), Vm[(int64_t)b * mc + r], s);
+      A[e] = s;
     }
-    if (lane == 0) atomicMax((int *)&off_max, __float_as_int(mine));
     __syncthreads();
-    const bool done = off_max <= (float)(8.0 * tol);
+    // W = V (3 I - Gm) / 2
+    for (int e = threadIdx.x; e < mc * mc; e += blockDim.x) {
+      const int i = e % mc, b = e / mc;
+      Acc s = zero<Acc>();
+      for (int a = 0; a < mc; ++a) s = fma_(Vm[(int64_t)a * mc + i], A[(int64_t)b * mc + a], s);
+      W[e] = sub(scale(Vm[e], 1.5), scale(s, 0.5));
+    }
     __syncthreads();
-    if (done) break;
+    for (int e = threadIdx.x; e < mc * mc; e += blockDim.x) Vm[e] = W[e];
+    __syncthreads();
   }
+  // phase 3: A = X V / ||X||_F in FP64, then FP64 sweeps
+  for (int e = threadIdx.x; e < mr * mc; e += blockDim.x) {
+    const int j = e / mr, i = e % mr;
+    Acc s = zero<Acc>();
+    for (int c = 0; c < mc; ++c) s = fma_(X(i, c), Vm[(int64_t)j * mc + c], s);
+    A[e] = scale(s, inv);
+  }
+  __syncthreads();
+  jacobi_sweeps<Acc>(A, Vm, mr, mc, 60, 4.0 * eps64, 32.0 * eps64, 4.0 * eps64 * eps64, &off_max);
   // singular values and their descending order (ties by index)
-  for (int j = warp; j < cols; j += nwarps) {
+  for (int j = warp; j < mc; j += nwarps) {
     double s2 = 0.0;
-    for (int r = lane; r < rows; r += 32) s2 += CJ<Acc>::abs2(A[(int64_t)j * rows + r]);
-    s2 = wsum(s2);
+    for (int r = lane; r < mr; r += 32) s2 += abs2(A[(int64_t)j * mr + r]);
+    s2 = wsum_r(s2);
     if (lane == 0) sig[j] = sqrt(s2) * fro;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+  for (int j = threadIdx.x; j < mc; j += blockDim.x) {
     int rank = 0;
-    for (int i = 0; i < cols; ++i) rank += (sig[i] > sig[j]) || (sig[i] == sig[j] && i < j);
+    for (int i = 0; i < mc; ++i) rank += (sig[i] > sig[j]) || (sig[i] == sig[j] && i < j);
     order[rank] = j;
   }
   __syncthreads();
   const double s1 = sig[order[0]];
   const double zt = 16.0 * (double)max(rows, cols) * 2.220446049250313e-16 * s1;
+  // the split weight w_j: sigma_j, or sigma_j / sigma_1 for normalised bonds;
+  // left factor column j: A_j fro / sigma_j (X's U) or V_j (when X = Theta^H)
+  const double wdiv = g.unit ? s1 : 1.0;
   for (int e = threadIdx.x; e < rows * k; e += blockDim.x) {
-    const int r = e / k, c = e % k, j = order[c];
-    const double sv = sig[j];
-    // U sqrt(S) = A_j / sigma_j * sqrt(sigma_j) = A_j / sqrt(sigma_j), A_j = fro x the scaled column
-    R1t[e] = sv > zt ? narrow<T>(scale(A[(int64_t)j * rows + r], fro / sqrt(sv))) : zero<T>();
+    const int r = e / k, c = e % k;
+    T v = zero<T>();
+    if (c < mc) {
+      const int j = order[c];
+      const double sv = sig[j];
+      if (sv > zt)
+        v = tr ? narrow<T>(scale(Vm[(int64_t)j * mc + r], sqrt(sv / wdiv)))
+               : narrow<T>(scale(A[(int64_t)j * mr + r], fro / sv * sqrt(sv / wdiv)));
+    }
+    R1t[e] = v;
   }
+  // right factor (sqrt(w) V^H)^T: conj(V_j) sqrt(w_j), V = X's V or X's U when X = Theta^H
   for (int e = threadIdx.x; e < cols * k; e += blockDim.x) {
-    const int r = e / k, c = e % k, j = order[c];
-    const double sv = sig[j];
-    // (sqrt(S) V^H)[c][r] = sqrt(sigma_j) conj(V[r][j])
-    R2t[e] = sv > zt ? narrow<T>(scale(CJ<Acc>::conj(Vm[(int64_t)j * cols + r]), sqrt(sv))) : zero<T>();
+    const int r = e / k, c = e % k;
+    T v = zero<T>();
+    if (c < mc) {
+      const int j = order[c];
+      const double sv = sig[j];
+      if (sv > zt)
+        v = tr ? narrow<T>(scale(conj_(A[(int64_t)j * mr + r]), fro / sv * sqrt(sv / wdiv)))
+               : narrow<T>(scale(conj_(Vm[(int64_t)j * mc + r]), sqrt(sv / wdiv)));
+    }
+    R2t[e] = v;
   }
   if (g.sigma)
-    for (int c = threadIdx.x; c < k; c += blockDim.x) g.sigma[c] = sig[order[c]] > zt ? sig[order[c]] : 0.0;
+    for (int c = threadIdx.x; c < k; c += blockDim.x)
+      g.sigma[c] = (c < mc && sig[order[c]] > zt) ? sig[order[c]] : 0.0;
 }
 
 template <class T>
@@ -239,7 +324,26 @@ __global__ void site_gauge_kernel(const SiteGaugeDesc *__restrict__ descs) {
   }
 }
 
-template <class T> void tebd_launch(int kind, const void *d, int nd, int smem, cudaStream_t s) {
+// one-site operator, in place: thread r owns column r of M as [d][rest]
+template <class T>
+__global__ void site_op_kernel(const SiteOpDesc *__restrict__ descs) {
+  using Acc = typename Traits<T>::Acc;
+  const SiteOpDesc &g = descs[blockIdx.y];
+  const int d = g.d;
+  T *M = (T *)g.M;
+  const T *G = (const T *)g.g;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < g.rest; r += (int64_t)gridDim.x * blockDim.x) {
+    Acc x[kSiteOpMaxPhys];
+    for (int j = 0; j < d; ++j) x[j] = widen(M[(int64_t)j * g.rest + r]);
+    for (int i = 0; i < d; ++i) {
+      Acc acc = zero<Acc>();
+      for (int j = 0; j < d; ++j) acc = fma_(widen(G[i * d + j]), x[j], acc);
+      M[(int64_t)i * g.rest + r] = narrow<T>(acc);
+    }
+  }
+}
+
+template <class T> void tebd_launch(int kind, const void *d, int nd, int aux, cudaStream_t s) {
   if (nd <= 0) return;
   if (kind == 0) {
     theta_kernel<T><<<nd, 256, 0, s>>>((const ThetaDesc *)d);
@@ -249,25 +353,29 @@ template <class T> void tebd_launch(int kind, const void *d, int nd, int smem, c
       cudaFuncSetAttribute(svd_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       set = true;
     }
-    svd_small_kernel<T><<<nd, 256, smem, s>>>((const SvdSmallDesc *)d);
-  } else {
+    svd_small_kernel<T><<<nd, 256, aux, s>>>((const SvdSmallDesc *)d);
+  } else if (kind == 2) {
     site_gauge_kernel<T><<<nd, 256, 0, s>>>((const SiteGaugeDesc *)d);
+  } else {
+    // grid.y: one row per site; grid.x: aux column blocks (strided loop)
+    site_op_kernel<T><<<dim3((unsigned)aux, (unsigned)nd), 256, 0, s>>>((const SiteOpDesc *)d);
   }
 }
 
 }  // namespace
 
 int svd_small_smem_bytes(int dt, int rows, int cols) {
-  const int as = acc_size(dt);
-  return as * (rows * cols + cols * cols);
+  // FP64 A (mr x mc) and V (mc x mc), and their FP32 copies; mr >= mc
+  const int as = acc_size(dt), mc = rows < cols ? rows : cols;
+  return as * (rows * cols + mc * mc) * 3 / 2;
 }
 
-void launch_tebd(int dt, int kind, const void *d, int nd, int smem, cudaStream_t s) {
+void launch_tebd(int dt, int kind, const void *d, int nd, int aux, cudaStream_t s) {
   switch (dt) {
-    case DT_R32: tebd_launch<float>(kind, d, nd, smem, s); break;
-    case DT_C64: tebd_launch<float2>(kind, d, nd, smem, s); break;
-    case DT_R64: tebd_launch<double>(kind, d, nd, smem, s); break;
-    case DT_C128: tebd_launch<double2>(kind, d, nd, smem, s); break;
+    case DT_R32: tebd_launch<float>(kind, d, nd, aux, s); break;
+    case DT_C64: tebd_launch<float2>(kind, d, nd, aux, s); break;
+    case DT_R64: tebd_launch<double>(kind, d, nd, aux, s); break;
+    case DT_C128: tebd_launch<double2>(kind, d, nd, aux, s); break;
   }
 }
 

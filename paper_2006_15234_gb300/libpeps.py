@@ -19,7 +19,7 @@ __all__ = [
     "debug_tc_gemm", "FLAG_ORTH_Q", "boundary_contract_static", "STATIC_SCRATCH_BYTES",
     "Term", "ExpectationPlan", "expectation", "Cotangent", "Grads", "einsumsvd_grad", "GradPlan",
     "energy_grad", "peps_energy", "STATUS_NONFINITE", "STATUS_JACOBI_NOCONV", "STATUS_TIMEOUT",
-    "ERR_NUMERIC", "ERR_TIMEOUT", "FLAG_FP64_SMALL", "FLAG_ALTERNATE",
+    "ERR_NUMERIC", "ERR_TIMEOUT", "FLAG_FP64_SMALL", "FLAG_ALTERNATE", "FLAG_UNIT_BOND",
 ]
 
 PREC_PLAIN, PREC_MIXED, PREC_FAST = 0, 1, 2
@@ -195,8 +195,8 @@ def load():
     lib.peps_debug_sketch.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                       C.c_int32, vp, vp, vp]
     lib.peps_tebd_plan.restype = st
-    lib.peps_tebd_plan.argtypes = [C.POINTER(vp), C.POINTER(Network), C.POINTER(C.c_double), C.POINTER(RsvdOpts),
-                                   C.POINTER(C.c_size_t)]
+    lib.peps_tebd_plan.argtypes = [C.POINTER(vp), C.POINTER(Network), C.POINTER(C.c_double), C.c_int64,
+                                   C.POINTER(C.c_double), C.c_int64, C.POINTER(RsvdOpts), C.POINTER(C.c_size_t)]
     lib.peps_tebd_execute.restype = st
     lib.peps_tebd_execute.argtypes = [vp, vp, C.c_size_t, vp]
     lib.peps_einsumsvd_set_branches.restype = st
@@ -230,6 +230,7 @@ def dtype_code(dtype) -> int:
 FLAG_ORTH_Q = 1
 FLAG_FP64_SMALL = 2
 FLAG_ALTERNATE = 4
+FLAG_UNIT_BOND = 8
 
 
 def make_opts(m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN, flags=0) -> RsvdOpts:
@@ -451,23 +452,38 @@ class EinsumsvdPlan(_Ledger):
 
 
 class TebdPlan(_Ledger):
-    """One TEBD layer (Algorithm 1 on every bond) applied in place to the
-    PEPS `sites` (CUDA tensors): gate is a (d^2, d^2) host array."""
+    """One TEBD layer (one-site operators by Eq. 4, then Algorithm 1 on every
+    bond) applied in place to the PEPS `sites` (CUDA tensors).
 
-    def __init__(self, sites, gate, seed):
+    gates: one (d^2, d^2) host array for every bond, or a list in bond order
+    (horizontal bonds by left site, then vertical bonds by upper site, both
+    row-major); site_gates: None, one (d, d) array, or a row-major list per
+    site; unit: normalise every new bond by its largest singular value."""
+
+    def __init__(self, sites, gates, seed, unit=False, site_gates=None):
         import numpy as np
         self._lib = load()
         self._net = _network(sites)
         cplx = sites[0][0].is_complex()
-        g = np.ascontiguousarray(np.asarray(gate, dtype=np.complex128 if cplx else np.float64))
-        if cplx:
-            g = np.ascontiguousarray(g.view(np.float64))
-        self._gate = g
+        dt = np.complex128 if cplx else np.float64
+
+        def pack(ops):
+            a = np.ascontiguousarray(np.stack([np.asarray(o, dtype=dt) for o in ops]))
+            return np.ascontiguousarray(a.view(np.float64)) if cplx else a
+        glist = list(gates) if isinstance(gates, (list, tuple)) else [gates]
+        self._gate = pack(glist)
+        slist = [] if site_gates is None else (list(site_gates) if isinstance(site_gates, (list, tuple))
+                                               else [site_gates])
+        self._site_gate = pack(slist) if slist else None
+        sp = (self._site_gate.ctypes.data_as(C.POINTER(C.c_double)) if slist
+              else C.cast(None, C.POINTER(C.c_double)))
         plan = C.c_void_p()
         ws = C.c_size_t()
         _check(self._lib.peps_tebd_plan(C.byref(plan), C.byref(self._net.net),
-                                        g.ctypes.data_as(C.POINTER(C.c_double)),
-                                        C.byref(make_opts(1, 0, 0, seed)), C.byref(ws)))
+                                        self._gate.ctypes.data_as(C.POINTER(C.c_double)), len(glist),
+                                        sp, len(slist),
+                                        C.byref(make_opts(1, 0, 0, seed, flags=FLAG_UNIT_BOND if unit else 0)),
+                                        C.byref(ws)))
         self._plan = plan
         self.workspace_bytes = ws.value
         self._buf, self._ws = _workspace(ws.value, sites[0][0].device)
@@ -485,14 +501,41 @@ class TebdPlan(_Ledger):
             pass
 
 
-def tebd_layer(sites, gate, seed, stream=None):
-    """Apply the two-site `gate` to every bond of the PEPS in place."""
-    plan = TebdPlan(sites, gate, seed)
+def tebd_layer(sites, gates, seed, stream=None, unit=False, site_gates=None):
+    """Apply the one-site operators, then the two-site operators to every
+    bond of the PEPS, in place."""
+    plan = TebdPlan(sites, gates, seed, unit, site_gates)
     plan.execute(stream)
     return plan
 
 
-__all__ += ["TebdPlan", "tebd_layer"]
+class IteDriver:
+    """Imaginary-time evolution (Sec. II-D) of the PEPS `sites` in place:
+    every step is one TEBD layer of exp(-tau H_j) (bond_gates, site_gates;
+    bonds normalised by their largest singular value) followed by the
+    Rayleigh quotient of `terms` (Eq. 6, cached environments) with the
+    contraction options `opts`.  Both plans are built once: the layer keeps
+    every bond dimension, so the expectation plan reads the updated sites."""
+
+    def __init__(self, sites, bond_gates, site_gates, terms, opts: RsvdOpts, seed):
+        self.tebd = TebdPlan(sites, bond_gates, seed, unit=True, site_gates=site_gates)
+        self.expect = ExpectationPlan(sites, terms, opts)
+
+    def step(self, stream=None):
+        """Enqueue one ITE step (no synchronisation)."""
+        self.tebd.execute(stream)
+        self.expect.execute(stream)
+
+    def run(self, steps, stream=None):
+        """Energy after each of `steps` steps (synchronises once per step)."""
+        out = []
+        for _ in range(steps):
+            self.step(stream)
+            out.append(self.expect.result(stream)[0])
+        return out
+
+
+__all__ += ["TebdPlan", "tebd_layer", "IteDriver"]
 
 
 def boundary_contract(ket, bra, m, p, q, seed, sketch=SKETCH_GAUSS, prec=PREC_PLAIN,

@@ -75,6 +75,12 @@ CONFIGS = {
     "f1": WorkloadConfig("f1_16x16_tebd_layer_c64_D8", 16, 16, 2, 8, "c64", True,
                          8, 0, 0, "cgauss_fro", _BASE_SEED + 7, _BASE_SEED + 8,
                          {"J": 1.0, "h": 3.0, "tau": 0.01}),
+    # Imaginary-time evolution of the transverse-field Ising model on an
+    # 8x8, D=4 complex64 PEPS: one TEBD layer of exp(-tau H_j) then the
+    # energy (m = 16 = D^2) per step.
+    "f3": WorkloadConfig("f3_8x8_tfi_ite_c64_D4_m16", 8, 8, 2, 4, "c64", True,
+                         16, 8, 2, "cgauss_scaled", _BASE_SEED + 9, _BASE_SEED + 10,
+                         {"J": 1.0, "h": 3.0, "tau": 0.05}),
     # 16x16 norm, complex64, d=2, bond 8, per-tensor Frobenius-normalised.
     "c5": WorkloadConfig("c5_16x16_norm_c64_D8_m256", 16, 16, 2, 8, "c64", True,
                          256, 16, 2, "cgauss_fro", _BASE_SEED + 4, _BASE_SEED + 5),

@@ -356,20 +356,26 @@ def test_product_flops_follow_table_2(lib, shape, m, q, prec):
         assert agg["epilogue_w"] == pytest.approx(8.0 * k * ell * N, rel=1e-12)
 
 
-@pytest.mark.parametrize("shape,D,dt", [((3, 3), 2, 3), ((4, 4), 3, 1), ((5, 3), 4, 0), ((16, 16), 8, 1),
-                                        ((2, 5), 2, 2), ((1, 4), 2, 1)])
-def test_tebd_layer_plans(lib, shape, D, dt):
-    """The TEBD layer's launches (site matrices, CholeskyQR2, Theta, its SVD,
-    N = Q R~, gauge phases, sites written back in place) stay inside the
-    workspace and the site tensors; one byte less of workspace is refused."""
+@pytest.mark.parametrize("shape,D,dt,per_bond,nsite,flags",
+                         [((3, 3), 2, 3, False, 0, 0), ((4, 4), 3, 1, True, 1, 8), ((5, 3), 4, 0, False, 15, 8),
+                          ((16, 16), 8, 1, False, 1, 8), ((2, 5), 2, 2, True, 10, 0), ((1, 4), 2, 1, False, 0, 0)])
+def test_tebd_layer_plans(lib, shape, D, dt, per_bond, nsite, flags):
+    """The TEBD layer's launches (one-site operators, site matrices,
+    CholeskyQR2, Theta, its SVD, N = Q R~, gauge phases, sites written back
+    in place) stay inside the workspace and the site tensors, with one or
+    per-bond operators and none, one or per-site one-site operators; one
+    byte less of workspace is refused."""
     nr, nc = shape
     shp = [[synth.site_shape(nr, nc, p, q, 2, D) for q in range(nc)] for p in range(nr)]
     heap = FakeHeap()
     net, keep = _net(heap, shp, dt)
-    gate = (C.c_double * 32)(*([0.5] * 32))
+    nb = nr * (nc - 1) + (nr - 1) * nc
+    ng = nb if per_bond else 1
+    gate = (C.c_double * (32 * ng))(*([0.5] * (32 * ng)))
+    sg = (C.c_double * max(1, 8 * nsite))(*([0.25] * max(1, 8 * nsite)))
     plan, ws = C.c_void_p(), C.c_size_t()
-    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, C.byref(L.make_opts(1, 0, 0, 3)),
-                              C.byref(ws)) == 0, lib.peps_last_error()
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, ng, sg if nsite else None, nsite,
+                              C.byref(L.make_opts(1, 0, 0, 3, flags=flags)), C.byref(ws)) == 0, lib.peps_last_error()
     wsp = heap(ws.value)
     assert lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None) == 0, lib.peps_last_error().decode()
     assert lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value - 1, None) != 0
@@ -382,7 +388,19 @@ def test_tebd_refuses_unsupported(lib):
     net, keep = _net(heap, shp, 1)
     gate = (C.c_double * 32)(*([0.5] * 32))
     plan, ws = C.c_void_p(), C.c_size_t()
-    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, C.byref(L.make_opts(1, 0, 0, 3, prec=1)),
-                              C.byref(ws)) == 3
-    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), None, C.byref(L.make_opts(1, 0, 0, 3)),
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, 1, None, 0,
+                              C.byref(L.make_opts(1, 0, 0, 3, prec=1)), C.byref(ws)) == 3
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), None, 1, None, 0, C.byref(L.make_opts(1, 0, 0, 3)),
                               C.byref(ws)) == 1
+    # operator counts: 1 or the number of bonds (12 on 3 x 3); 0, 1 or 9 one-site operators
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, 2, None, 0, C.byref(L.make_opts(1, 0, 0, 3)),
+                              C.byref(ws)) == 1
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, 1, gate, 4, C.byref(L.make_opts(1, 0, 0, 3)),
+                              C.byref(ws)) == 1
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, 1, None, 1, C.byref(L.make_opts(1, 0, 0, 3)),
+                              C.byref(ws)) == 1
+    # flags other than PEPS_FLAG_UNIT_BOND are refused, and UNIT_BOND elsewhere
+    assert lib.peps_tebd_plan(C.byref(plan), C.byref(net), gate, 1, None, 0,
+                              C.byref(L.make_opts(1, 0, 0, 3, flags=L.FLAG_ALTERNATE)), C.byref(ws)) == 3
+    assert lib.peps_contract_plan(C.byref(plan), C.byref(net), None,
+                                  C.byref(L.make_opts(4, 2, 1, 3, flags=L.FLAG_UNIT_BOND)), 0, C.byref(ws)) == 3
