@@ -774,13 +774,20 @@ def run_expect_cache(args, cfg):
             for _ in range(max(1, args.warmup)):
                 plan.execute()
             torch.cuda.synchronize()
+            run = plan.execute
+            graph = None
+            if not args.no_graph:
+                graph = libpeps.cuda_graph(plan.execute)
+                run = graph.replay
+                run()
+                torch.cuda.synchronize()
             ms = []
             for _ in range(args.steps):
                 flush.add_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                plan.execute()
+                run()
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms.append(e0.elapsed_time(e1))
@@ -788,8 +795,8 @@ def run_expect_cache(args, cfg):
             fl = sum(f for _, f, _ in plan.launches())
             out[name] = {"seconds": round(float(np.mean(ms)) / 1e3, 5), "energy": e, "log_norm": lnorm,
                          "launch_flops_tflop": round(fl / 1e12, 4), "kernel_launches": plan.kernel_launches(),
-                         "workspace_gb": round(plan.workspace_bytes / 1e9, 3)}
-            del plan
+                         "workspace_gb": round(plan.workspace_bytes / 1e9, 3), "cuda_graph": graph is not None}
+            del graph, plan
     t_c = out["cached"]["seconds"]
     line = {
         "metric": METRIC, "value": round(out["cached"]["launch_flops_tflop"] / t_c, 4), "unit": "TFLOP/s",
@@ -830,6 +837,9 @@ def run_ite(args, cfg):
     stream = torch.cuda.current_stream()
     e_warm = drv.run(max(3, args.warmup))
     torch.cuda.synchronize()
+    if not args.no_graph:
+        drv.capture()              # one more step, then every step replays the graph
+        e_warm.append(drv.expect.result()[0])
     ms = []
     with ClockSampler(0) as clk:
         for _ in range(args.steps):
@@ -855,6 +865,7 @@ def run_ite(args, cfg):
                    "energy_ms": round(float(np.sum(prof_e)), 4),
                    "energy_per_site_after_warmup": round(e_warm[-1] / (cfg.nrow * cfg.ncol), 6),
                    "energy_per_site_after_timed_steps": round(e_end / (cfg.nrow * cfg.ncol), 6),
+                   "cuda_graph": drv.graph is not None,
                    "l2": "not flushed: each step reads what the previous one wrote"},
         "gpu_launches": (drv.tebd.kernel_launches() + drv.expect.kernel_launches()) * args.steps,
     }

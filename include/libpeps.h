@@ -363,6 +363,23 @@ peps_status peps_expectation_plan(peps_plan **out, const peps_network *ket, cons
 peps_status peps_expectation_execute(peps_plan *plan, void *workspace, size_t workspace_bytes,
                                      void *stream);
 
+/* Two-GPU split of the cached expectation (Sec. IV-B runs one top-down and
+ * one bottom-up boundary sweep per lattice; the two directions are
+ * independent).  part 0 = the top-down sweeps (of the lattice and of its
+ * transpose when vertical terms exist), part 1 = the bottom-up sweeps, part
+ * 2 = the strips, which read both parts' environments.  Protocol for two
+ * ranks holding identical plans (same network shapes, terms and options):
+ * rank r enqueues part r, the ranks exchange their region (an all-gather of
+ * the bytes at [offset, offset + bytes) of each rank's workspace into the
+ * same offsets of the other's), then both enqueue part 2 and read the
+ * result.  One rank may also run parts 0, 1, 2 in turn (the same values as
+ * peps_expectation_execute).  Cached schedule of an expectation plan only
+ * (PEPS_ERR_UNSUPPORTED otherwise); the region of a part is fixed by the
+ * plan.  The part calls follow peps_expectation_execute's upload rule. */
+peps_status peps_expectation_env_region(const peps_plan *plan, int32_t part, size_t *offset, size_t *bytes);
+peps_status peps_expectation_execute_part(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream,
+                                          int32_t part);
+
 /* Synchronise `stream` and read the results: energy = sum of the terms'
  * contributions, log_norm = log <psi|psi> (row 0's strip and the scales of
  * the boundary below it), term_values[t] (nterms doubles, optional) =

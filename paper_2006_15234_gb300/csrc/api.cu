@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -150,6 +151,12 @@ struct peps_plan {
   struct Term { int nsite; int site[2]; std::vector<double> op; double coeff; };
   std::vector<Term> terms;
   bool use_cache = true;
+  // two-rank split of the cached expectation: op ranges of part 0 (top-down
+  // sweeps), 1 (bottom-up sweeps), 2 (strips), and the workspace region
+  // [lo, hi) holding each sweep part's environments, logs and sigmas
+  std::vector<std::pair<size_t, size_t>> part_ops[3];
+  size_t env_lo[2] = {0, 0}, env_hi[2] = {0, 0};
+  bool splittable = false;
   int64_t nstrips = 0;
   size_t strip_off = 0;                     // strip values (accumulation type)
   std::vector<std::vector<std::pair<int64_t, int64_t>>> term_strips;   // per term: (component strip, norm strip)
@@ -928,11 +935,26 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
       all.push_back(&E->bot);
     }
   }
-  Inst owner{};
-  if (!grad) sweep_owner_scratch(B, all, dt, owner);
-  size_t max_carry = 1;
-  for (Sweep *S : all) max_carry = std::max(max_carry, S->max_carry);
-  void *Vbuf[2] = {B.buf(max_carry * es), B.buf(max_carry * es)};
+  // the cached schedule's sweeps (top-down and bottom-up, of the lattice and
+  // of its transpose) are independent: each runs on a graph branch of its
+  // own with its own scratch, and the strips follow the join
+  const bool par = !grad && P->use_cache && all.size() > 1;
+  std::map<const Sweep *, int> branch_of;
+  // (branches 1..n: the caller's stream keeps the prelude and the strips)
+  std::vector<Inst> owners(par ? all.size() + 1 : 1);
+  std::vector<std::array<void *, 2>> vbufs(owners.size());
+  for (size_t i = 0; i < all.size(); ++i) branch_of[all[i]] = par ? (int)i + 1 : 0;
+  if (par) {
+    for (size_t i = 0; i < all.size(); ++i) {
+      sweep_owner_scratch(B, {all[i]}, dt, owners[i + 1]);
+      vbufs[i + 1] = {B.buf(all[i]->max_carry * es), B.buf(all[i]->max_carry * es)};
+    }
+  } else {
+    if (!grad) sweep_owner_scratch(B, all, dt, owners[0]);
+    size_t max_carry = 1;
+    for (Sweep *S : all) max_carry = std::max(max_carry, S->max_carry);
+    vbufs[0] = {B.buf(max_carry * es), B.buf(max_carry * es)};
+  }
   void *ones = B.buf(es);
   auto rows_for = [&](const Sweep &S) {
     std::vector<std::vector<void *>> rows(S.last + 1);
@@ -940,18 +962,26 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
       for (auto &x : S.bound[r]) rows[r].push_back(B.buf((size_t)x.left * x.vert * x.right * es));
     return rows;
   };
-  for (auto &E : envs) {
+  // the top-down environments of every set, then the bottom-up ones: each
+  // sweep direction's results form one contiguous workspace region (the
+  // unit a two-rank split exchanges)
+  B.alloc(0);
+  P->env_lo[0] = (B.top + 255) & ~(size_t)255;
+  for (auto &E : envs)
     if (E->has_top) {
       E->top_rows = rows_for(E->top);
       E->top_logs = (double *)B.buf(std::max<int64_t>(E->top.nsteps, 1) * 8);
       E->top_sigma = (double *)B.buf(std::max<int64_t>(E->top.nsigma, 1) * 8);
     }
+  P->env_hi[0] = B.top;
+  P->env_lo[1] = (B.top + 255) & ~(size_t)255;
+  for (auto &E : envs)
     if (E->has_bot) {
       E->bot_rows = rows_for(E->bot);
       E->bot_logs = (double *)B.buf(std::max<int64_t>(E->bot.nsteps, 1) * 8);
       E->bot_sigma = (double *)B.buf(std::max<int64_t>(E->bot.nsigma, 1) * 8);
     }
-  }
+  P->env_hi[1] = B.top;
   // energy gradient: site cotangents of the four lattices (0 H, 1 Vt, 2 Hf, 3 Vf) and the sweeps' buffers
   std::vector<std::vector<void *>> gl[4];
   const Net *glat[4] = {&H, need_v ? &Vt.net : nullptr, &Hf.net, need_v ? &Vf.net : nullptr};
@@ -1085,15 +1115,34 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
     push_permute(B, Vt.perm, "lattice_copy");
     push_permute(B, Vf.perm, "lattice_copy");
   }
+  // op ranges of the split: the prelude (status word, lattice copies) runs in
+  // both sweep parts
+  for (auto &r : P->part_ops) r.clear();
+  const size_t prelude_end = B.ops.size();
+  P->part_ops[0].push_back({0, prelude_end});
+  P->part_ops[1].push_back({0, prelude_end});
   for (auto &E : envs) {
     if (grad) {
       if (E->has_top) emit_sweep_save(B, E->top, P->opts, E->top_rows, *E->tg, E->top_logs, E->top_sigma);
       if (E->has_bot) emit_sweep_save(B, E->bot, P->opts, E->bot_rows, *E->bg, E->bot_logs, E->bot_sigma);
       continue;
     }
-    if (E->has_top) emit_sweep(B, E->top, P->opts, ones, E->top_rows, Vbuf, E->top_logs, E->top_sigma, owner);
-    if (E->has_bot) emit_sweep(B, E->bot, P->opts, ones, E->bot_rows, Vbuf, E->bot_logs, E->bot_sigma, owner);
+    if (E->has_top) {
+      const size_t a = B.ops.size();
+      const int b = branch_of[&E->top];
+      emit_sweep(B, E->top, P->opts, ones, E->top_rows, vbufs[b].data(), E->top_logs, E->top_sigma, owners[b]);
+      for (size_t k = a; k < B.ops.size(); ++k) B.ops[k].branch = b;
+      P->part_ops[0].push_back({a, B.ops.size()});
+    }
+    if (E->has_bot) {
+      const size_t a = B.ops.size();
+      const int b = branch_of[&E->bot];
+      emit_sweep(B, E->bot, P->opts, ones, E->bot_rows, vbufs[b].data(), E->bot_logs, E->bot_sigma, owners[b]);
+      for (size_t k = a; k < B.ops.size(); ++k) B.ops[k].branch = b;
+      P->part_ops[1].push_back({a, B.ops.size()});
+    }
   }
+  P->splittable = !grad && P->use_cache;
   // operator table in the accumulation type
   std::vector<double> opflat;
   for (auto &m : optab) opflat.insert(opflat.end(), m.begin(), m.end());
@@ -1105,6 +1154,7 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
   st.aux_off[1] = B.put(opflat);
   st.nd = (int)P->nstrips;
   st.tag = "strips";
+  P->part_ops[2].assign(1, {B.ops.size(), B.ops.size() + 1});
   B.ops.push_back(st);
   if (!grad) return "";
 
@@ -1692,11 +1742,14 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s0, bo
   if (events) CUDA_TRY(cudaEventRecord(events[0], s));
   last = std::min(last, P->ops.size());
   // branches > 0 run on the plan's side streams, forked from the caller's
-  // stream here and joined back after the last launch (the profiling replay
+  // stream just before the first op of a branch > 0 (so they see every
+  // earlier op of the range, e.g. the status word's clear and the lattice
+  // copies) and joined back after the last launch (the profiling replay
   // keeps every launch on the caller's stream, one after the other)
   int nbr = 1;
   for (size_t oi = first; oi < last; ++oi) nbr = std::max(nbr, P->ops[oi].branch + 1);
   const bool fork = nbr > 1 && !events;
+  size_t fork_at = last;
   if (fork) {
     while ((int)P->side.size() < nbr - 1) {
       cudaStream_t st = nullptr;
@@ -1708,10 +1761,14 @@ peps_status enqueue(peps_plan *P, void *ws, size_t ws_bytes, cudaStream_t s0, bo
       CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
       P->side_ev.push_back(ev);
     }
-    CUDA_TRY(cudaEventRecord(P->side_ev[0], s0));
-    for (int b = 1; b < nbr; ++b) CUDA_TRY(cudaStreamWaitEvent(P->side[b - 1], P->side_ev[0], 0));
+    for (size_t oi = first; oi < last; ++oi)
+      if (P->ops[oi].branch > 0) { fork_at = oi; break; }
   }
   for (size_t oi = first; oi < last; ++oi) {
+    if (fork && oi == fork_at) {
+      CUDA_TRY(cudaEventRecord(P->side_ev[0], s0));
+      for (int b = 1; b < nbr; ++b) CUDA_TRY(cudaStreamWaitEvent(P->side[b - 1], P->side_ev[0], 0));
+    }
     const Op &op = P->ops[oi];
     s = fork && op.branch > 0 ? P->side[op.branch - 1] : s0;
     const void *d = blob + op.desc_off;
@@ -2291,7 +2348,46 @@ peps_status peps_expectation_execute(peps_plan *plan, void *workspace, size_t wo
     plan->built_base = (uintptr_t)workspace;
     plan->built = true;
   }
-  return enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, !same);
+  if (!plan->splittable) return enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, !same);
+  // the sweeps (on their branches, joined at the end of the first call), then the strips
+  const size_t strips = plan->part_ops[2][0].first;
+  if (peps_status s = enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, !same, nullptr, 0, strips))
+    return s;
+  return enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, false, nullptr, strips);
+}
+
+peps_status peps_expectation_env_region(const peps_plan *plan, int32_t part, size_t *offset, size_t *bytes) {
+  g_last_error.clear();
+  if (!plan || !offset || !bytes) return fail(PEPS_ERR_ARG, "NULL argument");
+  if (plan->kind != peps_plan::EXPECT) return fail(PEPS_ERR_ARG, "not an expectation plan");
+  if (!plan->splittable) return fail(PEPS_ERR_UNSUPPORTED, "the split applies to the cached schedule only");
+  if (part != 0 && part != 1) return fail(PEPS_ERR_ARG, "part %d: 0 (top-down) or 1 (bottom-up)", (int)part);
+  *offset = plan->env_lo[part];
+  *bytes = plan->env_hi[part] - plan->env_lo[part];
+  return PEPS_OK;
+}
+
+peps_status peps_expectation_execute_part(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream,
+                                          int32_t part) {
+  g_last_error.clear();
+  if (!plan) return fail(PEPS_ERR_ARG, "plan is NULL");
+  if (plan->kind != peps_plan::EXPECT) return fail(PEPS_ERR_ARG, "not an expectation plan");
+  if (!plan->splittable) return fail(PEPS_ERR_UNSUPPORTED, "the split applies to the cached schedule only");
+  if (part < 0 || part > 2) return fail(PEPS_ERR_ARG, "part %d: 0, 1 or 2", (int)part);
+  const bool same = plan->built && plan->built_base == (uintptr_t)workspace;
+  if (!same) {
+    if (peps_status s = rebuild(plan, workspace, nullptr, true)) return s;
+    plan->built_base = (uintptr_t)workspace;
+    plan->built = true;
+  }
+  bool upload = !same;
+  for (const auto &r : plan->part_ops[part]) {
+    if (peps_status s = enqueue(plan, workspace, workspace_bytes, (cudaStream_t)stream, upload, nullptr, r.first,
+                                r.second))
+      return s;
+    upload = false;
+  }
+  return PEPS_OK;
 }
 
 peps_status peps_expectation_result(peps_plan *plan, void *workspace, void *stream, double *energy,

@@ -38,7 +38,7 @@ EXPORTED_SYMBOLS = [
     "peps_einsumsvd_grad_execute", "peps_grad_plan", "peps_grad_execute", "peps_grad",
     "peps_poll", "peps_plan_set_wait_limit", "peps_debug_sketch",
     "peps_plan_autotune", "peps_plan_tune_table", "peps_plan_set_tune_table", "peps_einsumsvd_set_branches",
-    "peps_tebd_plan", "peps_tebd_execute",
+    "peps_tebd_plan", "peps_tebd_execute", "peps_expectation_env_region", "peps_expectation_execute_part",
 ]
 
 # Bits of a plan's device status word (peps_poll).
@@ -194,6 +194,10 @@ def load():
     lib.peps_debug_sketch.restype = st
     lib.peps_debug_sketch.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                       C.c_int32, vp, vp, vp]
+    lib.peps_expectation_env_region.restype = st
+    lib.peps_expectation_env_region.argtypes = [vp, C.c_int32, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+    lib.peps_expectation_execute_part.restype = st
+    lib.peps_expectation_execute_part.argtypes = [vp, vp, C.c_size_t, vp, C.c_int32]
     lib.peps_tebd_plan.restype = st
     lib.peps_tebd_plan.argtypes = [C.POINTER(vp), C.POINTER(Network), C.POINTER(C.c_double), C.c_int64,
                                    C.POINTER(C.c_double), C.c_int64, C.POINTER(RsvdOpts), C.POINTER(C.c_size_t)]
@@ -509,6 +513,54 @@ def tebd_layer(sites, gates, seed, stream=None, unit=False, site_gates=None):
     return plan
 
 
+def cuda_graph(fn):
+    """Capture fn() -- enqueue-only calls of plans that have executed once
+    already (so their descriptors are resident) -- into a CUDA graph on a side
+    stream; graph.replay() re-enqueues the whole recorded work with one launch
+    on the current stream."""
+    import torch
+    g = torch.cuda.CUDAGraph()
+    cur = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(cur)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            fn()
+    cur.wait_stream(side)
+    return g
+
+
+__all__.append("cuda_graph")
+
+
+def exchange_env_regions(plan_views, group=None):
+    """The collective of the two-GPU expectation split: rank r (0 or 1) has
+    filled its own part's region (plan_views[r], a uint8 tensor); after the
+    call both regions hold the owners' bytes on every rank.  One broadcast
+    per part from its owner; nothing else crosses ranks."""
+    import torch.distributed as dist
+    for part, view in enumerate(plan_views):
+        dist.broadcast(view, src=part, group=group)
+
+
+__all__.append("exchange_env_regions")
+
+
+def expectation_split(plan, rank, group=None, stream=None):
+    """Cached expectation on two ranks (one GPU each, identical plans): rank
+    r runs the sweeps of part r, the regions are exchanged, both run the
+    strips; returns the result on every rank."""
+    plan.execute_part(rank, stream)
+    import torch
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    exchange_env_regions([plan.env_view(0), plan.env_view(1)], group)
+    plan.execute_part(2, stream)
+    return plan.result(stream)
+
+
+__all__.append("expectation_split")
+
+
 class IteDriver:
     """Imaginary-time evolution (Sec. II-D) of the PEPS `sites` in place:
     every step is one TEBD layer of exp(-tau H_j) (bond_gates, site_gates;
@@ -521,10 +573,25 @@ class IteDriver:
         self.tebd = TebdPlan(sites, bond_gates, seed, unit=True, site_gates=site_gates)
         self.expect = ExpectationPlan(sites, terms, opts)
 
+        self.graph = None
+
     def step(self, stream=None):
-        """Enqueue one ITE step (no synchronisation)."""
+        """Enqueue one ITE step (no synchronisation); after capture(), one
+        replay of the captured step."""
+        if self.graph is not None:
+            self.graph.replay()
+            return
         self.tebd.execute(stream)
         self.expect.execute(stream)
+
+    def capture(self):
+        """Record one step as a CUDA graph (runs one plain step first so the
+        descriptors are resident); later steps replay it."""
+        import torch
+        self.step()
+        torch.cuda.synchronize()
+        self.graph = cuda_graph(lambda: (self.tebd.execute(), self.expect.execute()))
+        return self.graph
 
     def run(self, steps, stream=None):
         """Energy after each of `steps` steps (synchronises once per step)."""
@@ -586,6 +653,25 @@ class ExpectationPlan(_Ledger):
     def execute(self, stream=None):
         _check(self._lib.peps_expectation_execute(self._plan, C.c_void_p(self._ws),
                                                   C.c_size_t(self.workspace_bytes), _stream_handle(stream)))
+
+    def execute_part(self, part, stream=None):
+        """Enqueue one part of the two-GPU split: 0 top-down sweeps, 1
+        bottom-up sweeps, 2 strips (needs both parts' environments)."""
+        _check(self._lib.peps_expectation_execute_part(self._plan, C.c_void_p(self._ws),
+                                                       C.c_size_t(self.workspace_bytes), _stream_handle(stream),
+                                                       int(part)))
+
+    def env_region(self, part):
+        """(byte offset, bytes) of a sweep part's environments in the workspace."""
+        off, n = C.c_size_t(), C.c_size_t()
+        _check(self._lib.peps_expectation_env_region(self._plan, int(part), C.byref(off), C.byref(n)))
+        return off.value, n.value
+
+    def env_view(self, part):
+        """uint8 CUDA tensor over a sweep part's region of the workspace (for
+        the exchange between ranks)."""
+        off, n = self.env_region(part)
+        return self._buf.narrow(0, (self._ws - self._buf.data_ptr()) + off, n)
 
     def result(self, stream=None):
         """(energy, log <psi|psi>, per-term coeff_t <O_t>)."""

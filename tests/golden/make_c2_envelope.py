@@ -21,6 +21,7 @@ step is the largest normwise deviation max_i |sigma_i - sigma_i^ref| /
 sigma_1^ref over the realizations; the log-norm deviations are stored too.
 Only the oracle's functions compute; the wrappers only round and perturb.
 """
+import contextlib
 import json
 import os
 import sys
@@ -41,7 +42,10 @@ def _c64(a):
     return np.asarray(a).astype(np.complex64).astype(np.complex128)
 
 
-def replay(cfg, ket, seed, alternate=False):
+@contextlib.contextmanager
+def single_precision(seed):
+    """The oracle's functions with the arithmetic of a single-precision
+    implementation emulated around them (see the module docstring)."""
     rng = np.random.default_rng(seed)
     Op = implicit.ImplicitOp
     mv, rmv, common = Op.matvec, Op.rmatvec, implicit._common
@@ -83,12 +87,17 @@ def replay(cfg, ket, seed, alternate=False):
     philox.sketch, bmps.einsumsvd = sketch32, es32
     torch.linalg.qr, torch.linalg.svd = qr32, svd32
     try:
-        rec = []
-        la, _ = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec, alternate=alternate)
+        yield
     finally:
         Op.matvec, Op.rmatvec = mv, rmv
         philox.sketch, bmps.einsumsvd = sketch, es
         torch.linalg.qr, torch.linalg.svd = qr, svd
+
+
+def replay(cfg, ket, seed, alternate=False):
+    with single_precision(seed):
+        rec = []
+        la, _ = bmps.contract(ket, ket, cfg.m, cfg.p, cfg.q, cfg.omega_seed, record=rec, alternate=alternate)
     return la, rec
 
 

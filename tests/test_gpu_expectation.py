@@ -70,3 +70,38 @@ def test_complex_lattice_matches_oracle():
     # library reports Re(strip(O) / strip(1)) per term
     ref_t = np.real(np.asarray(ref_t))
     assert np.max(np.abs(tv - ref_t)) <= 1e-5 * max(1.0, np.max(np.abs(ref_t)))
+
+
+@pytest.mark.parametrize("dtype,prec", [("f64", libpeps.PREC_PLAIN), ("c64", libpeps.PREC_MIXED)])
+def test_two_part_split_gives_the_single_plan_values(dtype, prec):
+    """The two-GPU split of the cached expectation emulated with two plans on
+    one GPU: plan A runs the top-down sweeps (part 0), plan B the bottom-up
+    ones (part 1), each copies the other's region (what the all-gather does
+    between ranks), both run the strips (part 2).  Every value equals the
+    single plan's; so does one plan running the three parts in turn."""
+    import torch
+    cplx = dtype.startswith("c")
+    ket = synth.random_peps(4, 3, 2, 2, "c64" if cplx else "f64", "cgauss_scaled" if cplx else "normal", 43)
+    terms = synth.tfi_terms(4, 3, 0.7, 1.3)
+    k = to_dev(ket, dtype)
+    opts = libpeps.make_opts(4, 4, 2, 3, prec=prec)
+    ref = libpeps.ExpectationPlan(k, terms, opts)
+    ref.execute()
+    r = ref.result()
+    a = libpeps.ExpectationPlan(k, terms, opts)
+    b = libpeps.ExpectationPlan(k, terms, opts)
+    assert a.env_region(0) == b.env_region(0) and a.env_region(1) == b.env_region(1)
+    a.execute_part(0)
+    b.execute_part(1)
+    torch.cuda.synchronize()
+    a.env_view(1).copy_(b.env_view(1))
+    b.env_view(0).copy_(a.env_view(0))
+    a.execute_part(2)
+    b.execute_part(2)
+    one = libpeps.ExpectationPlan(k, terms, opts)
+    for part in (0, 1, 2):
+        one.execute_part(part)
+    for got in (a.result(), b.result(), one.result()):
+        assert got[0] == pytest.approx(r[0], rel=1e-12, abs=1e-12)
+        assert got[1] == pytest.approx(r[1], rel=1e-12, abs=1e-12)
+        assert np.allclose(got[2], r[2], rtol=1e-12, atol=1e-12)

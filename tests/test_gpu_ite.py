@@ -80,3 +80,22 @@ def test_ite_energies_match_oracle(dtype, etol, stol):
     worst = _worst(k, ref_sites)
     print(f"ITE {dtype}: worst final site error {worst:.2e}")
     assert worst <= stol
+
+
+def test_captured_ite_step_replays_the_eager_steps():
+    """One ITE step captured as a CUDA graph (both plans, the expectation's
+    sweeps on parallel branches) and replayed gives the eager steps' energies
+    and sites."""
+    nr, nc, D = 3, 4, 2
+    ket = synth.random_peps(nr, nc, 2, D, "c64", "cgauss_scaled", 73)
+    terms = synth.tfi_terms(nr, nc, 1.0, 3.0)
+    Gb, Gs = synth.tfi_ite_gates(1.0, 3.0, 0.1)
+    opts = libpeps.make_opts(16, 8, 2, 9)
+    k1, k2 = to_dev(ket, "c128"), to_dev(ket, "c128")
+    eager = libpeps.IteDriver(k1, Gb, Gs, terms, opts, 5).run(4)
+    drv = libpeps.IteDriver(k2, Gb, Gs, terms, opts, 5)
+    first = drv.run(1)
+    drv.capture()                     # the second step
+    got = first + [drv.expect.result()[0]] + drv.run(2)
+    assert np.allclose(got, eager, rtol=1e-12, atol=0)
+    assert _worst(k2, [[T.cpu().numpy() for T in row] for row in k1]) <= 1e-12

@@ -90,3 +90,73 @@ def test_lpt_shard_properties():
         loads = [sum(costs[i] for i in p) for p in parts]
         lower = max(sum(costs) / world, max(costs))
         assert max(loads) <= 4.0 / 3.0 * lower + 1e-9
+
+
+def _split_rank_main(rank, world, port, out_dir):
+    """The two-GPU expectation split (Sec. IV-B's two sweep directions on two
+    ranks) with the oracle standing in for the device work: rank r runs only
+    the sweeps of its direction (top-down: 0 and 2, bottom-up: 1 and 3),
+    the regions are exchanged by libpeps.exchange_env_regions (one broadcast
+    per part), then every rank evaluates the strips from both parts."""
+    sys.path.insert(0, ROOT)
+    import pickle
+
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from oracle import bmps, expectation
+    from paper_2006_15234_gb300 import libpeps
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ket = synth.random_peps(4, 3, 2, 2, "f64", "normal", 83)
+        terms = synth.tfi_terms(4, 3, 1.0, 3.0)
+        real_sweep = bmps.sweep
+        # the sweeps of Sec. IV-B: directions 0 / 1 top-down / bottom-up on the
+        # lattice, 2 / 3 on its transpose (vertical terms); this rank's part only
+        lattices = {0: ket, 2: bmps.transpose_lattice(ket)}
+        mine, ran = {}, []
+        for direction in (rank, rank + 2):
+            lat = lattices[direction - direction % 2]
+            if direction % 2:
+                lat = bmps.flip_vertical(lat)
+            ran.append(direction)
+            mine[direction] = real_sweep(lat, lat, 4, 4, 1, 5, direction, len(lat) - 2)
+        blob = pickle.dumps(mine)
+        sizes = [None] * world
+        dist.all_gather_object(sizes, len(blob))
+        views = [torch.zeros(n, dtype=torch.uint8) for n in sizes]
+        views[rank][:] = torch.frombuffer(bytearray(blob), dtype=torch.uint8)
+        libpeps.exchange_env_regions(views)
+        both = {}
+        for v in views:
+            both.update(pickle.loads(v.numpy().tobytes()))
+        bmps.sweep = lambda ket_, bra_, m, p, q, seed, direction, last, *a: both[direction]
+        e = expectation.energy(ket, terms, 4, 4, 1, 5)
+        bmps.sweep = real_sweep
+        ref = expectation.energy(ket, terms, 4, 4, 1, 5)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, {"e": e, "ref": ref, "ran": sorted(ran)})
+        if rank == 0:
+            import json
+            with open(os.path.join(out_dir, "split.json"), "w") as f:
+                json.dump(gathered, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_the_expectation_sweeps(tmp_path):
+    """Each rank computes only its sweep direction; after the exchange both
+    ranks hold the single-rank energy exactly."""
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    world = 2
+    mp.spawn(_split_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    import json
+    res = json.load(open(tmp_path / "split.json"))
+    assert res[0]["ran"] == [0, 2] and res[1]["ran"] == [1, 3]
+    for r in res:
+        assert r["e"] == r["ref"]
+    assert res[0]["e"] == res[1]["e"]
+    del torch

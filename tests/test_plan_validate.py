@@ -178,6 +178,16 @@ def test_expectation_plans(lib, key, dt, shape, prec, use_cache):
     wsp = heap(ws.value)
     r = lib.peps_plan_validate(plan, C.c_void_p(wsp), ws.value, None)
     assert r == 0, lib.peps_last_error().decode()
+    # the two-GPU split: each sweep part's environments in one region of the
+    # workspace, the two regions disjoint (cached schedule only)
+    off, n = [C.c_size_t(), C.c_size_t()], [C.c_size_t(), C.c_size_t()]
+    rs = [lib.peps_expectation_env_region(plan, part, C.byref(off[part]), C.byref(n[part])) for part in (0, 1)]
+    if use_cache:
+        assert rs == [0, 0], lib.peps_last_error()
+        assert 0 < n[0].value and 0 < n[1].value
+        assert off[0].value + n[0].value <= off[1].value and off[1].value + n[1].value <= ws.value
+    else:
+        assert rs == [3, 3]
     lib.peps_plan_destroy(plan)
 
 
