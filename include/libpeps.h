@@ -36,7 +36,7 @@ typedef int32_t peps_status;
 #define PEPS_OK               0
 #define PEPS_ERR_ARG          1  /* NULL pointer, bad option value            */
 #define PEPS_ERR_SHAPE        2  /* inconsistent tensor shapes                */
-#define PEPS_ERR_UNSUPPORTED  3  /* valid request this build does not handle  */
+#define PEPS_ERR_UNSUPPORTED  3  /* valid request the library does not handle */
 #define PEPS_ERR_CUDA         4  /* a CUDA runtime call failed                */
 #define PEPS_ERR_WORKSPACE    5  /* workspace missing, misaligned or too small */
 #define PEPS_ERR_NUMERIC      6  /* non-finite value met on the device        */
