@@ -793,9 +793,14 @@ def run_expect_cache(args, cfg):
                 ms.append(e0.elapsed_time(e1))
             e, lnorm, _ = plan.result()
             fl = sum(f for _, f, _ in plan.launches())
+            # per-launch device times of one more execute, by kernel family
+            kms = {}
+            for kname, dt in zip(plan.kernels(), plan.profile()):
+                kms[kname] = kms.get(kname, 0.0) + dt
             out[name] = {"seconds": round(float(np.mean(ms)) / 1e3, 5), "energy": e, "log_norm": lnorm,
                          "launch_flops_tflop": round(fl / 1e12, 4), "kernel_launches": plan.kernel_launches(),
-                         "workspace_gb": round(plan.workspace_bytes / 1e9, 3), "cuda_graph": graph is not None}
+                         "workspace_gb": round(plan.workspace_bytes / 1e9, 3), "cuda_graph": graph is not None,
+                         "kernel_ms": {k: round(v, 3) for k, v in sorted(kms.items(), key=lambda kv: -kv[1])}}
             del graph, plan
     t_c = out["cached"]["seconds"]
     line = {

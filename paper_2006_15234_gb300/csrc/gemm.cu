@@ -41,14 +41,16 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc *__restrict__ d
   const int64_t blk = blockIdx.x;
   const int di = find_desc(prefix, nd, blk);
   const GemmDesc &g = descs[di];
-  int64_t local = blk - prefix[di];
-  const int64_t per_batch = (int64_t)g.ksplit * g.tiles_m * g.tiles_n;
+  // 32-bit block arithmetic (block indices and tile counts fit; 64-bit
+  // division runs through FP64 operations)
+  uint32_t local = (uint32_t)(blk - prefix[di]);
+  const uint32_t mn = (uint32_t)g.tiles_m * (uint32_t)g.tiles_n, per_batch = (uint32_t)g.ksplit * mn;
   const int bi = (int)(local / per_batch);
-  local -= (int64_t)bi * per_batch;
-  const int kc = (int)(local / ((int64_t)g.tiles_m * g.tiles_n));
-  local -= (int64_t)kc * g.tiles_m * g.tiles_n;
-  const int tm = (int)(local / g.tiles_n);
-  const int tn = (int)(local % g.tiles_n);
+  local -= (uint32_t)bi * per_batch;
+  const int kc = (int)(local / mn);
+  local -= (uint32_t)kc * mn;
+  const int tm = (int)(local / (uint32_t)g.tiles_n);
+  const int tn = (int)(local % (uint32_t)g.tiles_n);
   const int m0 = tm * BM, n0 = tn * BN;
   const int kbeg = kc * g.kchunk;
   const int kend = min(g.K, kbeg + g.kchunk);

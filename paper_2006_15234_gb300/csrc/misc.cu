@@ -146,9 +146,11 @@ __global__ void permute_kernel(const PermuteDesc *__restrict__ descs, const int6
   __shared__ T tile[32][33];
   const int di = find_desc(prefix, nd, blockIdx.x);
   const PermuteDesc &g = descs[di];
-  const int64_t tr = (g.R + 31) / 32, tc = (g.Cc + 31) / 32;
-  int64_t blk = blockIdx.x - prefix[di];
-  const int64_t q = blk % g.Q; blk /= g.Q;
+  // block coordinates in 32-bit arithmetic (a block index and the tile counts
+  // fit; 64-bit division runs through FP64 operations, 1/64 rate here)
+  const uint32_t tr = (uint32_t)((g.R + 31) / 32), tc = (uint32_t)((g.Cc + 31) / 32), Q = (uint32_t)g.Q;
+  uint32_t blk = (uint32_t)(blockIdx.x - prefix[di]);
+  const int64_t q = blk % Q; blk /= Q;
   const int64_t cb = blk % tc; blk /= tc;
   const int64_t rb = blk % tr; blk /= tr;
   const int64_t b = blk;

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
   }
   md = block_max(md, red);
   const double shift = g.shift * md;
-  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+  for (int t = threadIdx.x; t < n * n; t += NT) {
     const int i = (int)(t / n), k = (int)(t % n);
     T v = zero<T>();
     if (k >= i) {
@@ -158,24 +158,32 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
   __syncthreads();
   const double thr = g.tol * md;
 
+  // the pivot's FP64 scalars are formed once by thread 0 and read by all
+  // (FP64 square roots and divisions in every thread would cost 16 warps of
+  // 1/64-rate FP64 work per pivot)
+  __shared__ double piv[2];
   for (int j = 0; j < n; ++j) {
-    const double dj = (double)re(W[(int64_t)j * n + j]);
-    const bool isdead = !(dj > thr) || !(md > 0.0);
-    __syncthreads();   // everyone has read W[j][j] before row j is rewritten
-    if (threadIdx.x == 0) dead[j] = isdead;
-    if (isdead) {
+    if (threadIdx.x == 0) {
+      const double dj = (double)re(W[(int64_t)j * n + j]);
+      const bool isdead = !(dj > thr) || !(md > 0.0);
+      dead[j] = isdead;
+      piv[0] = isdead ? 0.0 : sqrt(dj);
+      piv[1] = isdead ? 0.0 : 1.0 / piv[0];
+    }
+    __syncthreads();   // the pivot's scalars are published before row j is rewritten
+    if (dead[j]) {
       for (int k = j + threadIdx.x; k < n; k += NT) W[(int64_t)j * n + k] = zero<T>();
       __syncthreads();
       continue;
     }
-    const double r = sqrt(dj);
-    const typename Traits<T>::Real rinv = (typename Traits<T>::Real)(1.0 / r);
+    const double r = piv[0];
+    const typename Traits<T>::Real rinv = (typename Traits<T>::Real)piv[1];
     for (int k = j + threadIdx.x; k < n; k += NT)
       W[(int64_t)j * n + k] = k == j ? real_scalar<T>(r) : scale(W[(int64_t)j * n + k], rinv);
     __syncthreads();
     // trailing update of the upper triangle: W[i][k] -= conj(R[j][i]) R[j][k], j < i <= k
     const int m = n - j - 1;
-    for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += NT) {
+    for (int t = threadIdx.x; t < m * m; t += NT) {
       const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
       if (i > k) continue;
       W[(int64_t)i * n + k] = sub(W[(int64_t)i * n + k], mul(conj_(W[(int64_t)j * n + i]), W[(int64_t)j * n + k]));
@@ -184,18 +192,18 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
   }
   // R (upper triangle of W, zero below) to global
   if (in_smem)
-    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+    for (int t = threadIdx.x; t < n * n; t += NT) {
       const int i = (int)(t / n), k = (int)(t % n);
       R[t] = k >= i ? W[t] : zero<T>();
     }
   else
-    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT)
+    for (int t = threadIdx.x; t < n * n; t += NT)
       if ((int)(t % n) < (int)(t / n)) R[t] = zero<T>();
   __syncthreads();
 
   if constexpr (sizeof(typename Traits<T>::Real) == 8) {
     if (g.Rlow) {
-      for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+      for (int t = threadIdx.x; t < n * n; t += NT) {
         if constexpr (sizeof(T) == 16) ((float2 *)g.Rlow)[t] = narrow<float2>(widen(R[t]));
         else ((float *)g.Rlow)[t] = narrow<float>(widen(R[t]));
       }
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
   }
   if constexpr (sizeof(typename Traits<T>::Real) == 8) {
     if (g.Tlow) {
-      for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+      for (int t = threadIdx.x; t < n * n; t += NT) {
         if constexpr (sizeof(T) == 16) ((float2 *)g.Tlow)[t] = narrow<float2>(widen(Tm[t]));
         else ((float *)g.Tlow)[t] = narrow<float>(widen(Tm[t]));
       }
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(NT) chol_kernel(const CholDesc *__restrict__ d
   if (g.Rprev) {
     const T *P = (const T *)g.Rprev;
     T *O = (T *)g.Rout;
-    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) {
+    for (int t = threadIdx.x; t < n * n; t += NT) {
       const int i = (int)(t / n), k = (int)(t % n);
       T s = zero<T>();
       for (int l = i; l <= k; ++l) s = fma_(R[(int64_t)i * n + l], P[(int64_t)l * n + k], s);
@@ -270,6 +278,7 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
   const int nb = chol_cluster_nb(n, (int)sizeof(T), needT);
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ double red[32];
+  __shared__ double piv[2];
   const int cap = (n + kCholCTAs - 1) / kCholCTAs;
   const int nloc = rank < n ? (n - rank + kCholCTAs - 1) / kCholCTAs : 0;   // rows rank + kCholCTAs * li
   T *Wl = (T *)dyn;
@@ -289,7 +298,7 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
   }
   md = block_max(md, red);
   const double shift = g.shift * md, thr = g.tol * md;
-  for (int64_t t = threadIdx.x; t < (int64_t)nloc * n; t += NT) {
+  for (int t = threadIdx.x; t < nloc * n; t += NT) {
     const int li = (int)(t / n), k = (int)(t % n), i = rank + kCholCTAs * li;
     T v = zero<T>();
     if (k >= i) {
@@ -316,7 +325,7 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
     if (j0 > 0) keep_panel(Wl, j0 - nb, nb, j0 - nb);
     __syncthreads();                   // the panel buffer is read out
     const int w = n - j0;
-    for (int64_t t = threadIdx.x; t < (int64_t)jb * w; t += NT) {
+    for (int t = threadIdx.x; t < jb * w; t += NT) {
       const int p = (int)(t / w), k = j0 + (int)(t % w), j = j0 + p;
       P[(int64_t)p * n + k] = cluster.map_shared_rank(Wl, j % kCholCTAs)[(int64_t)(j / kCholCTAs) * n + k];
     }
@@ -324,20 +333,26 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
     for (int p = 0; p < jb; ++p) {
       const int j = j0 + p;
       T *row = P + (int64_t)p * n;
-      const double dj = re(row[j]);
-      const bool dead = !(dj > thr) || !(md > 0.0);
-      __syncthreads();                 // every thread has read the pivot before the row changes
+      // the pivot's FP64 scalars, formed once by thread 0 and read by all
+      if (threadIdx.x == 0) {
+        const double dj = re(row[j]);
+        const bool dead = !(dj > thr) || !(md > 0.0);
+        piv[0] = dead ? -1.0 : sqrt(dj);
+        piv[1] = dead ? 0.0 : 1.0 / piv[0];
+      }
+      __syncthreads();                 // the scalars are published before the row changes
+      const bool dead = piv[0] < 0.0;
       if (dead) {
         for (int k = j + threadIdx.x; k < n; k += NT) row[k] = zero<T>();
       } else {
-        const double r = sqrt(dj);
-        const Real rinv = (Real)(1.0 / r);
+        const double r = piv[0];
+        const Real rinv = (Real)piv[1];
         for (int k = j + threadIdx.x; k < n; k += NT) row[k] = k == j ? real_scalar<T>(r) : scale(row[k], rinv);
       }
       __syncthreads();
       // later rows of the panel: W[i][k] -= conj(R[j][i]) R[j][k], k >= i
       const int rem = jb - p - 1;
-      for (int64_t t = threadIdx.x; t < (int64_t)rem * w; t += NT) {
+      for (int t = threadIdx.x; t < rem * w; t += NT) {
         const int pp = p + 1 + (int)(t / w), k = j0 + (int)(t % w), i = j0 + pp;
         if (k < i) continue;
         T *x = P + (int64_t)pp * n + k;
@@ -347,7 +362,7 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
     }
     // this CTA's rows below the panel
     const int li0 = first_li(j0 + jb);
-    for (int64_t t = threadIdx.x; t < (int64_t)(nloc - li0) * n; t += NT) {
+    for (int t = threadIdx.x; t < (nloc - li0) * n; t += NT) {
       const int li = li0 + (int)(t / n), k = (int)(t % n), i = rank + kCholCTAs * li;
       if (k < i) continue;
       T x = Wl[(int64_t)li * n + k];
@@ -374,7 +389,7 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
         __syncthreads();               // the panel buffer is read out
       }
       const int w = n - k0;
-      for (int64_t t = threadIdx.x; t < (int64_t)kb * w; t += NT) {
+      for (int t = threadIdx.x; t < kb * w; t += NT) {
         const int p = (int)(t / w), c = k0 + (int)(t % w), k = k0 + p;
         const int64_t o = (int64_t)(k / kCholCTAs) * n;
         P[(int64_t)p * n + c] = cluster.map_shared_rank(Tl, k % kCholCTAs)[o + c];
@@ -394,7 +409,7 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
         __syncthreads();
         // earlier rows of the panel: T[i][c] += R[i][k] T[k][c], c >= k
         const int m = n - k;
-        for (int64_t t = threadIdx.x; t < (int64_t)p * m; t += NT) {
+        for (int t = threadIdx.x; t < p * m; t += NT) {
           const int pi = (int)(t / m), c = k + (int)(t % m);
           T *x = P + (int64_t)pi * n + c;
           *x = fma_(B[pi * nb + p], trow[c], *x);
@@ -403,7 +418,7 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
       }
       // this CTA's rows above the panel
       const int li1 = first_li(k0);    // rows i < k0: local indices below li1
-      for (int64_t t = threadIdx.x; t < (int64_t)li1 * w; t += NT) {
+      for (int t = threadIdx.x; t < li1 * w; t += NT) {
         const int li = (int)(t / w), c = k0 + (int)(t % w);
         T x = Tl[(int64_t)li * n + c];
         for (int p = kb - 1; p >= 0; --p) {
@@ -423,7 +438,7 @@ __global__ void __cluster_dims__(kCholCTAs, 1, 1) __launch_bounds__(NT)
   // outputs: R (upper, zero below), T, R * Rprev, R in single precision
   T *R = (T *)g.R;
   T *Tg = (T *)g.T;
-  for (int64_t t = threadIdx.x; t < (int64_t)nloc * n; t += NT) {
+  for (int t = threadIdx.x; t < nloc * n; t += NT) {
     const int li = (int)(t / n), k = (int)(t % n), i = rank + kCholCTAs * li;
     const int64_t o = (int64_t)i * n + k;
     R[o] = Wl[t];
@@ -546,7 +561,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict
   T *Mg = (T *)g.Mw;
   T *M = in_smem ? (T *)dyn : Mg;
   // column c of Rb^H = conj(row c of Rb)
-  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) M[t] = conj_(Rb[t]);
+  for (int t = threadIdx.x; t < n * n; t += NT) M[t] = conj_(Rb[t]);
   __syncthreads();
   const int n2 = n + (n & 1);
   const int warps = NT / 32, w = threadIdx.x >> 5;
@@ -584,7 +599,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const JacobiDesc *__restrict
     if ((threadIdx.x & 31) == 0) g.sig[c] = sqrt(s2);
   }
   if (in_smem)
-    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += NT) Mg[t] = M[t];
+    for (int t = threadIdx.x; t < n * n; t += NT) Mg[t] = M[t];
 }
 
 
@@ -624,7 +639,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NTJ)
   T *local = (T *)dyn;
   const int cpc = (n + kClusterCTAs - 1) / kClusterCTAs;     // columns per CTA
   const T *Rb = (const T *)g.Rb;
-  for (int64_t t = threadIdx.x; t < (int64_t)cpc * n; t += NTJ) {
+  for (int t = threadIdx.x; t < cpc * n; t += NTJ) {
     const int lc = (int)(t / n), r = (int)(t % n), c = rank * cpc + lc;
     local[t] = c < n ? conj_(Rb[(int64_t)c * n + r]) : zero<T>();
   }
@@ -716,7 +731,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NTJ)
   const T *Rb = (const T *)g.Rb;
   T *cs = set0;
   for (int sl = 0; sl < 2; ++sl)
-    for (int64_t t = threadIdx.x; t < bsz; t += NTJ) {
+    for (int t = threadIdx.x; t < (int)bsz; t += NTJ) {
       const int j = (int)(t / n), r = (int)(t % n), c = (sl ? pos1 : pos0) * bs + j;
       cs[sl * bsz + t] = c < n ? conj_(Rb[(int64_t)c * n + r]) : zero<T>();
     }
@@ -771,7 +786,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(NTJ)
                                   : cluster.map_shared_rank(cs, rank - 1);
       const T *src1 = rank <= kClusterCTAs - 2 ? cluster.map_shared_rank(cs, rank + 1) + bsz
                                                : cluster.map_shared_rank(cs, kClusterCTAs - 1);
-      for (int64_t t = threadIdx.x; t < bsz; t += NTJ) {
+      for (int t = threadIdx.x; t < (int)bsz; t += NTJ) {
         nx[t] = src0[t];
         nx[bsz + t] = src1[t];
       }
@@ -926,7 +941,7 @@ __global__ void __launch_bounds__(NT) finalize_kernel(const FinalizeDesc *__rest
   }
   __syncthreads();
   T *Ut = (T *)g.Ut;
-  for (int64_t t = threadIdx.x; t < (int64_t)n * k; t += NT) {
+  for (int t = threadIdx.x; t < n * k; t += NT) {
     const int j = (int)(t / k), i = (int)(t % k);
     Ut[t] = mul(M[(int64_t)order[i] * n + j], rho[i]);
   }
