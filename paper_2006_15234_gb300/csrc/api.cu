@@ -1088,6 +1088,8 @@ std::string build_expect(peps_plan *P, uintptr_t base, Builder &B) {
     }
   P->nstrips = (int64_t)sd.size();
   P->lognorm_strip = norm_strip[{0, 0}];
+  if (std::max(std::max(l_cap, a1_cap), std::max(a2_cap, a3_cap)) >= ((int64_t)1 << 31))
+    return "strip blocks of 2^31 elements or more are not supported";
   const int64_t per = l_cap + a1_cap + a2_cap + a3_cap;
   void *scr = B.buf((size_t)P->nstrips * per * as);
   P->strip_off = B.alloc((size_t)P->nstrips * as);

@@ -225,13 +225,25 @@ __global__ void pad_kernel(const PadDesc *__restrict__ descs, const int64_t *__r
   const PadDesc &g = descs[di];
   const int64_t o = (int64_t)(blockIdx.x - prefix[di]) * kPadPerBlock + threadIdx.x;
   if (o >= g.total) return;
-  int64_t r = o, off = 0;
+  int64_t off = 0;
   bool in_range = true;
-  for (int d = g.nd - 1; d >= 0; --d) {
-    const int64_t dig = r % g.dims[d];
-    r /= g.dims[d];
-    in_range = in_range && dig < g.lim[d];
-    off += dig * g.in_stride[d];
+  if (g.total < ((int64_t)1 << 31)) {
+    // 32-bit digits (a 64-bit division runs through FP64 operations)
+    uint32_t r = (uint32_t)o;
+    for (int d = g.nd - 1; d >= 0; --d) {
+      const uint32_t dim = (uint32_t)g.dims[d], dig = r % dim;
+      r /= dim;
+      in_range = in_range && (int)dig < g.lim[d];
+      off += (int64_t)dig * g.in_stride[d];
+    }
+  } else {
+    int64_t r = o;
+    for (int d = g.nd - 1; d >= 0; --d) {
+      const int64_t dig = r % g.dims[d];
+      r /= g.dims[d];
+      in_range = in_range && dig < g.lim[d];
+      off += dig * g.in_stride[d];
+    }
   }
   ((T *)g.out)[o] = in_range ? ((const T *)g.in)[off] : zero<T>();
 }

@@ -12,7 +12,10 @@
 //   L'[b][e][E][f]            = sum_{c,x,X} A3 Bl[c][(x,X)][f]
 // with K' = op K on the physical index.  One CTA per strip; the blocks live
 // in a per-strip slice of global scratch (they are small: m^2 D^4 values at
-// most); every sum is accumulated in FP64.
+// most); every sum is accumulated in FP64.  Element indices are decomposed in
+// 32-bit arithmetic (the planner keeps every block below 2^31 elements; a
+// 64-bit division runs through FP64 operations, which this GPU issues at
+// 1/64 of the FP32 rate).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -45,8 +48,8 @@ __global__ void __launch_bounds__(kStripThreads) strip_kernel(const StripDesc *_
     // A1[l][L][c][u][U][b]
     {
       const int64_t n = (int64_t)Dl * Dl * cc * vu * b;
-      for (int64_t t = threadIdx.x; t < n; t += kStripThreads) {
-        int64_t r = t;
+      for (uint32_t t = threadIdx.x; t < (uint32_t)n; t += kStripThreads) {
+        uint32_t r = t;
         const int bb = (int)(r % b); r /= b;
         const int uU = (int)(r % vu); r /= vu;
         const int c_ = (int)(r % cc); r /= cc;
@@ -61,8 +64,8 @@ __global__ void __launch_bounds__(kStripThreads) strip_kernel(const StripDesc *_
     // A2[L][c][U][b][s][x][e]
     {
       const int64_t n = (int64_t)Dl * cc * Du * b * d * Dx * De;
-      for (int64_t t = threadIdx.x; t < n; t += kStripThreads) {
-        int64_t r = t;
+      for (uint32_t t = threadIdx.x; t < (uint32_t)n; t += kStripThreads) {
+        uint32_t r = t;
         const int e = (int)(r % De); r /= De;
         const int x = (int)(r % Dx); r /= Dx;
         const int s_ = (int)(r % d); r /= d;
@@ -91,8 +94,8 @@ __global__ void __launch_bounds__(kStripThreads) strip_kernel(const StripDesc *_
     // A3[c][b][e][x][X][E]
     {
       const int64_t n = (int64_t)cc * b * De * Dx * Dx * De;
-      for (int64_t t = threadIdx.x; t < n; t += kStripThreads) {
-        int64_t r = t;
+      for (uint32_t t = threadIdx.x; t < (uint32_t)n; t += kStripThreads) {
+        uint32_t r = t;
         const int E = (int)(r % De); r /= De;
         const int X = (int)(r % Dx); r /= Dx;
         const int x = (int)(r % Dx); r /= Dx;
@@ -114,8 +117,8 @@ __global__ void __launch_bounds__(kStripThreads) strip_kernel(const StripDesc *_
     // L'[b][e][E][f]
     {
       const int64_t n = (int64_t)b * De * De * f;
-      for (int64_t t = threadIdx.x; t < n; t += kStripThreads) {
-        int64_t r = t;
+      for (uint32_t t = threadIdx.x; t < (uint32_t)n; t += kStripThreads) {
+        uint32_t r = t;
         const int ff = (int)(r % f); r /= f;
         const int E = (int)(r % De); r /= De;
         const int e = (int)(r % De); r /= De;

@@ -314,11 +314,12 @@ __global__ void site_gauge_kernel(const SiteGaugeDesc *__restrict__ descs) {
     }
   }
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < g.rows1 * k; e += blockDim.x) {
+  // (32-bit element indices: a site matrix holds far fewer than 2^31 values)
+  for (int e = threadIdx.x; e < (int)(g.rows1 * k); e += blockDim.x) {
     const double2 p = rho[e % k];
     N1[e] = mul(N1[e], from_parts<T>(p.x, -p.y));
   }
-  for (int64_t e = threadIdx.x; e < g.rows2 * k; e += blockDim.x) {
+  for (int e = threadIdx.x; e < (int)(g.rows2 * k); e += blockDim.x) {
     const double2 p = rho[e % k];
     N2[e] = mul(N2[e], from_parts<T>(p.x, p.y));
   }
