@@ -186,7 +186,8 @@ struct SvdSmallDesc {
   void *R1t, *R2t;
   double *sigma;
   int32_t rows, cols, k;
-  uint32_t *status;   // STATUS_NONFINITE when Theta holds a non-finite value (may be NULL)
+  uint32_t *status;   // STATUS_NONFINITE for a non-finite Theta, STATUS_JACOBI_NOCONV at the
+                      // FP64 sweep limit (may be NULL)
   int32_t unit;       // 1: split Sigma / sigma_1 instead of Sigma (sigma keeps the true values)
 };
 // One-site operator on a site tensor, in place (Eq. 4):

@@ -80,7 +80,7 @@ template <> struct Lo<double2> { using type = float2; };
 // Frobenius norm by the caller).  Stops after the first sweep whose largest
 // rotated off-diagonal is <= stop, or after max_sweeps.
 template <class S>
-__device__ void jacobi_sweeps(S *A, S *V, int mr, int mc, int max_sweeps, double tol, double stop, double dead2,
+__device__ bool jacobi_sweeps(S *A, S *V, int mr, int mc, int max_sweeps, double tol, double stop, double dead2,
                               float *off_max) {
   using R = typename Traits<S>::Real;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -141,8 +141,9 @@ __device__ void jacobi_sweeps(S *A, S *V, int mr, int mc, int max_sweeps, double
     __syncthreads();
     const bool done = *off_max <= (float)stop;
     __syncthreads();
-    if (done) break;
+    if (done) return true;
   }
+  return false;
 }
 
 // Truncated SVD of one Theta.  GB300 runs FP64 at 1/64 of the FP32 rate, so
@@ -239,7 +240,9 @@ __global__ void svd_small_kernel(const SvdSmallDesc *__restrict__ descs) {
     A[e] = scale(s, inv);
   }
   __syncthreads();
-  jacobi_sweeps<Acc>(A, Vm, mr, mc, 60, 4.0 * eps64, 32.0 * eps64, 4.0 * eps64 * eps64, &off_max);
+  if (!jacobi_sweeps<Acc>(A, Vm, mr, mc, 60, 4.0 * eps64, 32.0 * eps64, 4.0 * eps64 * eps64, &off_max) &&
+      threadIdx.x == 0 && g.status)
+    atomicOr(g.status, STATUS_JACOBI_NOCONV);
   // singular values and their descending order (ties by index)
   for (int j = warp; j < mc; j += nwarps) {
     double s2 = 0.0;

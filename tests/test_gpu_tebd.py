@@ -62,3 +62,19 @@ def test_identity_gate_keeps_amplitudes():
     a = bruteforce.statevector(ket).reshape(-1)
     b = bruteforce.statevector(new).reshape(-1)
     assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a)
+
+
+def test_status_word_of_the_layer():
+    """A clean layer leaves the plan's status word at zero; a NaN in one site
+    tensor sets STATUS_NONFINITE (the layer has no result call: peps_poll is
+    its report)."""
+    ket = synth.random_peps(3, 3, 2, 2, "c64", "cgauss_scaled", 5)
+    k = to_dev(ket, "c64")
+    plan = libpeps.TebdPlan(k, np.eye(4), 1)
+    plan.execute()
+    r, word = plan.poll()
+    assert r == 0 and word == 0
+    k[1][1][0, 0, 0, 0, 0] = float("nan")
+    plan.execute()
+    r, word = plan.poll()
+    assert word & libpeps.STATUS_NONFINITE
