@@ -593,10 +593,15 @@ class IteDriver:
         self.graph = cuda_graph(lambda: (self.tebd.execute(), self.expect.execute()))
         return self.graph
 
-    def run(self, steps, stream=None):
-        """Energy after each of `steps` steps (synchronises once per step)."""
+    def run(self, steps, stream=None, every=1):
+        """Energy after every `every`-th of `steps` steps and after the last
+        (Sec. II-D evaluates it for the final state only: every = steps);
+        synchronises once per evaluation."""
         out = []
-        for _ in range(steps):
+        for i in range(steps):
+            if self.graph is None and (i + 1) % every != 0 and i + 1 != steps:
+                self.tebd.execute(stream)       # evolution only
+                continue
             self.step(stream)
             out.append(self.expect.result(stream)[0])
         return out
