@@ -820,6 +820,58 @@ def run_expect_cache(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def run_onelayer(args, cfg):
+    """One-layer boundary contraction (Algorithm 2 with the one-layer zip-up)
+    of an 8 x 8 PEPS without physical index, the contraction bond equal to
+    the initial bond, D = m = 2, 4, 8 (the supported range of the one-layer
+    site stages), and D = 8 with m = 64: device seconds per contraction as a
+    replayed CUDA graph, and the contracted log|v|."""
+    import torch
+    from paper_2006_15234_gb300 import libpeps
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prec = {"plain": libpeps.PREC_PLAIN, "mixed": libpeps.PREC_MIXED, "fast": libpeps.PREC_FAST}[args.prec]
+    stream = torch.cuda.current_stream()
+    points = []
+    with ClockSampler(0) as clk:
+        for D, m in ((2, 2), (4, 4), (8, 8), (8, 64)):
+            ket = synth.random_peps(cfg.nrow, cfg.ncol, 1, D, "f32", cfg.dist, cfg.seed + D)
+            kt = [[torch.tensor(T, dtype=torch.float32, device=dev) for T in row] for row in ket]
+            plan = libpeps.ContractPlan(kt, None, libpeps.make_opts(m, cfg.p, cfg.q, cfg.omega_seed, prec=prec))
+            plan.execute()
+            torch.cuda.synchronize()
+            run = plan.execute if args.no_graph else libpeps.cuda_graph(plan.execute).replay
+            for _ in range(max(1, args.warmup)):
+                run()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            la, _ = plan.result()
+            points.append({"D": D, "m": m, "contraction_ms": round(float(np.mean(ms)), 4), "log_abs": la,
+                           "kernel_launches": plan.kernel_launches()})
+            del plan
+    t = points[2]["contraction_ms"]
+    line = {
+        "metric": METRIC, "value": round(t / 1e3, 6), "unit": "s per contraction (D = m = 8)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded N(0,1)/2 PEPS without physical index)",
+        "config": {"workload": cfg.name, "nrow": cfg.nrow, "ncol": cfg.ncol, "precision": args.prec,
+                   "p": cfg.p, "q": cfg.q, "points": points, "cuda_graph": not args.no_graph},
+    }
+    clk = clk.summary()
+    if clk:
+        line["clocks"] = clk
+    print(json.dumps(line), flush=True)
+
+
 def run_ite(args, cfg):
     """Imaginary-time evolution of the transverse-field Ising model on the
     8 x 8, D = 4 PEPS (Sec. II-D): an ITE step is one TEBD layer of
@@ -1088,7 +1140,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3", "f1", "f2", "f3"])
+    ap.add_argument("--config", default="c5", choices=["c2", "c5", "c4", "c3", "f1", "f2", "f3", "f4"])
     ap.add_argument("--prec", default="mixed", choices=["plain", "mixed", "fast"])
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip the plain FP32 contraction timed beside the mixed one")
@@ -1119,6 +1171,8 @@ def main():
         run_tebd(args, cfg)
     elif args.config == "f3":
         run_ite(args, cfg)
+    elif args.config == "f4":
+        run_onelayer(args, cfg)
     else:
         run_ours(args, cfg)
 

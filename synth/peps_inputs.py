@@ -81,6 +81,10 @@ CONFIGS = {
     "f3": WorkloadConfig("f3_8x8_tfi_ite_c64_D4_m16", 8, 8, 2, 4, "c64", True,
                          16, 8, 2, "cgauss_scaled", _BASE_SEED + 9, _BASE_SEED + 10,
                          {"J": 1.0, "h": 3.0, "tau": 0.05}),
+    # One-layer contraction of an 8x8 PEPS without physical index (d = 1), the
+    # contraction bond equal to the initial bond (D = m; run for D = 2, 4, 8).
+    "f4": WorkloadConfig("f4_8x8_onelayer_f32_D_eq_m", 8, 8, 1, 8, "f32", False,
+                         8, 4, 2, "normal_half", _BASE_SEED + 11, _BASE_SEED + 12),
     # 16x16 norm, complex64, d=2, bond 8, per-tensor Frobenius-normalised.
     "c5": WorkloadConfig("c5_16x16_norm_c64_D8_m256", 16, 16, 2, 8, "c64", True,
                          256, 16, 2, "cgauss_fro", _BASE_SEED + 4, _BASE_SEED + 5),

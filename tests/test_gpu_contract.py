@@ -95,6 +95,21 @@ def test_c1_one_layer_fp64_matches_oracle_and_bruteforce():
     assert sigma_errors(sig, rec).max() < 1e-10
 
 
+def test_one_layer_8x8_truncated_matches_oracle():
+    """One-layer zip-up with truncation (the contraction bond equal to the
+    initial bond, D = m = 4, 8 x 8 without physical index) against the oracle:
+    every step's singular values and log|v| in FP64; the single-precision
+    mixed path of the same network within 1e-5 relative on log|v|."""
+    ket = synth.random_peps(8, 8, 1, 4, "f64", "normal_half", 91)
+    rec = []
+    la, ph, sig = _run(ket, None, "f64", 4, 4, 2, 13)
+    ra, rp = bmps.contract(ket, None, 4, 4, 2, 13, record=rec)
+    assert la == pytest.approx(ra, abs=1e-9 * max(1.0, abs(ra)))
+    assert sigma_errors(sig, rec).max() < 1e-10
+    lm, _, _ = _run(ket, None, "f32", 4, 4, 2, 13, prec=libpeps.PREC_MIXED)
+    assert abs(lm - ra) <= 1e-5 * abs(ra)
+
+
 @pytest.mark.parametrize("shape,D,m,dtype", [((3, 3), 2, 16, "c128"), ((3, 5), 2, 64, "c128"),
                                              ((2, 4), 2, 16, "f64")])
 def test_two_layer_exact_regime_fp64(shape, D, m, dtype):
