@@ -178,3 +178,16 @@ def test_blocked_cluster_cholesky_panels(n, nb):
     assert np.abs(R.conj().T @ R - G).max() <= 1e-12 * np.abs(G).max()
     assert np.abs(T @ R - np.eye(n)).max() <= 1e-10
     assert np.array_equal(np.tril(T, -1), np.zeros_like(T))
+
+
+def test_tc_gemm_traffic_is_reported_only_for_its_capture():
+    """The roofline's DRAM traffic is the ncu capture of the 16x16 workload's
+    tc_gemm launches: reported for that workload and kernel while the
+    kernel's sources hash to the value recorded with it, null otherwise."""
+    import bench
+    t = bench.TC_GEMM_TRAFFIC
+    assert t["bytes_per_launch"] == pytest.approx((t["read_gb"] + t["write_gb"]) * 1e9 / t["launches"], rel=1e-3)
+    assert bench.tc_gemm_traffic("c2_8x8_norm_c64_D4_m32", "tc_gemm") is None
+    assert bench.tc_gemm_traffic(t["workload"], "chol") is None
+    got = bench.tc_gemm_traffic(t["workload"], "tc_gemm")
+    assert got is None if bench.tc_gemm_sources_sha() != t["sources_sha"] else got == t["bytes_per_launch"]
