@@ -118,11 +118,15 @@ __device__ bool jacobi_sweeps(S *A, S *V, int mr, int mc, int max_sweeps, double
         const R gm = sqrt(abs2(ga)), nrm = sqrt(al * be);
         if (!(gm > rtol * nrm)) continue;
         mine = fmaxf(mine, (float)(gm / nrm));
+        // one reciprocal of |gamma| serves the phase and zeta, and the cosine
+        // comes from rsqrt: FP64 divisions and square roots are the expensive
+        // part of a rotation on this GPU
+        const R ig = (R)1 / gm;
         // b_q = e^{-i phi} a_q makes <a_p, b_q> = |gamma| real; then the real rotation
-        const S ph = scale(conj_(ga), (R)1 / gm);
-        const R zeta = (be - al) / ((R)2 * gm), az = fabs(zeta);
+        const S ph = scale(conj_(ga), ig);
+        const R zeta = (be - al) * ((R)0.5 * ig), az = fabs(zeta);
         const R t = az > (R)1e15 ? (R)0.5 / zeta : (zeta >= 0 ? (R)1 : (R)-1) / (az + sqrt((R)1 + zeta * zeta));
-        const R c = (R)1 / sqrt((R)1 + t * t), sn = c * t;
+        const R c = rsqrt((R)1 + t * t), sn = c * t;
         for (int r = lane; r < mr; r += 32) {
           const S x = ap[r], y = mul(ph, aq[r]);
           ap[r] = sub(scale(x, c), scale(y, sn));
