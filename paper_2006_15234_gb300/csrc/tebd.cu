@@ -115,8 +115,10 @@ __device__ bool jacobi_sweeps(S *A, S *V, int mr, int mc, int max_sweeps, double
           }
           continue;
         }
-        const R gm = sqrt(abs2(ga)), nrm = sqrt(al * be);
-        if (!(gm > rtol * nrm)) continue;
+        // the rotation test on squares: a converged pair costs no square root
+        const R gm2 = abs2(ga), n2 = al * be;
+        if (!(gm2 > rtol * rtol * n2)) continue;
+        const R gm = sqrt(gm2), nrm = sqrt(n2);
         mine = fmaxf(mine, (float)(gm / nrm));
         // one reciprocal of |gamma| serves the phase and zeta, and the cosine
         // comes from rsqrt: FP64 divisions and square roots are the expensive
