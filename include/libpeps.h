@@ -318,7 +318,9 @@ peps_status peps_tebd_plan(peps_plan **out, const peps_network *net, const doubl
 
 /* Enqueue the layer: the network's site tensors are overwritten with the
  * updated ones (same shapes).  Same descriptor-upload rule as the other
- * execute calls. */
+ * execute calls.  The layer has no result call: peps_poll reads its status
+ * word (PEPS_STATUS_NONFINITE for a non-finite Theta or Gram,
+ * PEPS_STATUS_JACOBI_NOCONV when a bond's SVD reached its sweep limit). */
 peps_status peps_tebd_execute(peps_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
